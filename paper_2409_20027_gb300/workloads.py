@@ -1,0 +1,174 @@
+"""Seeded synthetic workloads shaped like the paper's examples (Sec. IV) and the
+benchmark configurations built on them.
+
+This module only builds problem data (model constants, weights, bounds, initial
+states, horizons) from numpy ``default_rng`` seeds.  It contains none of the
+method's arithmetic, so both the CUDA path and the CPU oracle consume identical
+inputs from it.
+
+Models (``Problem.model``): 0 pendulum (Sec. IV-A), 1 cart-pole (Sec. IV-B),
+2 quadrotor (12 states, 4 rotor thrusts), 3 synthetic ``x+ = A x + B u + c tanh(W x)``.
+Cost: ``sum_t (x-xref)^T Q (x-xref) + (u-uref)^T R (u-uref) + (x_T-xref)^T Qf (x_T-xref)``
+(no 1/2 factor).  Constraints: box bounds on states and controls (``inf`` = none).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+PENDULUM, CARTPOLE, QUADROTOR, SYNTH = 0, 1, 2, 3
+EULER, RK4 = 0, 1
+INF = np.inf
+
+
+@dataclass
+class Problem:
+    model: int
+    nx: int
+    nu: int
+    dt: float
+    integrator: int
+    prm: np.ndarray                  # model constants (<= 8)
+    Q: np.ndarray
+    R: np.ndarray
+    Qf: np.ndarray
+    xref: np.ndarray
+    uref: np.ndarray
+    xlo: np.ndarray
+    xhi: np.ndarray
+    ulo: np.ndarray
+    uhi: np.ndarray
+    A: np.ndarray | None = None      # synthetic model only
+    B: np.ndarray | None = None
+    W: np.ndarray | None = None
+    name: str = ""
+
+    def replace(self, **kw) -> "Problem":
+        d = dict(self.__dict__)
+        d.update(kw)
+        return Problem(**d)
+
+
+def _f(a):
+    return np.asarray(a, dtype=np.float64)
+
+
+# ---------------------------------------------------------------- pendulum
+def pendulum(dt: float = 0.05, b: float = 0.1) -> Problem:
+    """Torque-limited pendulum swing-up: g=9.81, l=1, m=1, damping b, Euler step dt,
+    Q=diag(1,0.1), R=0.01, Qf=diag(10,1), target (pi, 0), |u| <= 5."""
+    return Problem(model=PENDULUM, nx=2, nu=1, dt=dt, integrator=EULER,
+                   prm=_f([9.81, 1.0, 1.0, b]),
+                   Q=np.diag([1.0, 0.1]), R=np.array([[0.01]]), Qf=np.diag([10.0, 1.0]),
+                   xref=_f([np.pi, 0.0]), uref=_f([0.0]),
+                   xlo=_f([-INF, -INF]), xhi=_f([INF, INF]), ulo=_f([-5.0]), uhi=_f([5.0]),
+                   name="pendulum")
+
+
+def pendulum_x0(seed: int) -> np.ndarray:
+    """x0 = (0, 0) + N(0, 0.05^2) per component."""
+    return np.random.default_rng(seed).normal(0.0, 0.05, size=2)
+
+
+# ---------------------------------------------------------------- cart-pole
+def cartpole(T: int | None = None, dt: float = 0.01, horizon: float | None = None) -> Problem:
+    """Force-limited cart-pole: m_c=1, m_p=0.1, l=0.5, g=9.81, RK4 step.  State
+    (p, theta, p', theta'), theta = pi upright.  Q=diag(1,10,0.1,0.1), R=0.01, Qf=100 Q,
+    target (0, pi, 0, 0), |u| <= 10, |p| <= 2.  With ``horizon`` the step is horizon/T
+    (fixed physical time, varying sampling rate, as in Sec. IV)."""
+    if horizon is not None:
+        dt = horizon / T
+    Q = np.diag([1.0, 10.0, 0.1, 0.1])
+    return Problem(model=CARTPOLE, nx=4, nu=1, dt=dt, integrator=RK4,
+                   prm=_f([1.0, 0.1, 0.5, 9.81]),
+                   Q=Q, R=np.array([[0.01]]), Qf=100.0 * Q,
+                   xref=_f([0.0, np.pi, 0.0, 0.0]), uref=_f([0.0]),
+                   xlo=_f([-2.0, -INF, -INF, -INF]), xhi=_f([2.0, INF, INF, INF]),
+                   ulo=_f([-10.0]), uhi=_f([10.0]), name="cartpole")
+
+
+def cartpole_x0(seed: int) -> np.ndarray:
+    """p ~ U[-0.5, 0.5], theta ~ U[pi-0.3, pi+0.3], velocities 0."""
+    r = np.random.default_rng(seed)
+    p = r.uniform(-0.5, 0.5)
+    th = r.uniform(np.pi - 0.3, np.pi + 0.3)
+    return _f([p, th, 0.0, 0.0])
+
+
+def batch_horizons(B: int, seed: int = 0, lo: int = 64, hi: int = 4096) -> np.ndarray:
+    """T_b = round(exp(U[ln lo, ln hi])): log-uniform horizons."""
+    r = np.random.default_rng(seed)
+    return np.rint(np.exp(r.uniform(np.log(lo), np.log(hi), size=B))).astype(np.int32)
+
+
+def uniform_horizons(B: int, seed: int = 0, lo: int = 1024, hi: int = 8192) -> np.ndarray:
+    """T_b ~ U{lo, ..., hi}."""
+    return np.random.default_rng(seed).integers(lo, hi + 1, size=B).astype(np.int32)
+
+
+def cartpole_batch_x0(B: int, seed: int = 0) -> np.ndarray:
+    """B initial states, instance b drawn from seed (seed, b)."""
+    return np.stack([cartpole_x0(np.random.SeedSequence([seed, b]).generate_state(1)[0])
+                     for b in range(B)])
+
+
+# ---------------------------------------------------------------- quadrotor
+QUAD_MASS = 0.5
+QUAD_G = 9.81
+
+
+def quadrotor(waypoint=None, dt: float = 0.01) -> Problem:
+    """12-state quadrotor (position, ZYX Euler angles, world velocity, body rates),
+    4 rotor thrusts, mass 0.5, inertia diag(2.3e-3, 2.3e-3, 4e-3), arm 0.17,
+    yaw-moment coefficient 0.01, Euler step.  Hover-to-waypoint tracking,
+    Q=diag(1,1,1,.1,.1,.1,.1,.1,.1,.01,.01,.01), R=0.1 I around hover thrust,
+    Qf=10 Q, thrust box [0, 4] per rotor."""
+    wp = np.zeros(3) if waypoint is None else _f(waypoint)
+    q = np.array([1.0] * 3 + [0.1] * 3 + [0.1] * 3 + [0.01] * 3)
+    xref = np.zeros(12)
+    xref[:3] = wp
+    hover = QUAD_MASS * QUAD_G / 4.0
+    return Problem(model=QUADROTOR, nx=12, nu=4, dt=dt, integrator=EULER,
+                   prm=_f([QUAD_MASS, 2.3e-3, 2.3e-3, 4e-3, 0.17, 0.01, QUAD_G]),
+                   Q=np.diag(q), R=0.1 * np.eye(4), Qf=10.0 * np.diag(q),
+                   xref=xref, uref=np.full(4, hover),
+                   xlo=np.full(12, -INF), xhi=np.full(12, INF),
+                   ulo=np.zeros(4), uhi=np.full(4, 4.0), name="quadrotor")
+
+
+def quadrotor_hover_u() -> float:
+    """Hover thrust per rotor, m g / 4 (a strictly feasible start inside [0, 4])."""
+    return QUAD_MASS * QUAD_G / 4.0
+
+
+def quadrotor_waypoints(B: int, seed: int = 0) -> np.ndarray:
+    """Waypoints uniform in the 2 m cube [-1, 1]^3 around the hover point (origin)."""
+    return np.random.default_rng(seed).uniform(-1.0, 1.0, size=(B, 3))
+
+
+# ---------------------------------------------------------------- synthetic
+def _haar(r: np.random.Generator, n: int) -> np.ndarray:
+    q, rr = np.linalg.qr(r.normal(size=(n, n)))
+    return q * np.sign(np.diag(rr))
+
+
+def synth(seed: int = 0, nx: int = 32, nu: int = 8) -> Problem:
+    """x+ = A x + B u + 0.1 tanh(W x): A = 0.98 * Haar orthogonal, B ~ N(0, 1/nu),
+    W ~ N(0, 1/nx), Q = U diag(U[0.1, 10]) U^T, R = 0.1 I, Qf = Q, |u| <= 1, target 0."""
+    r = np.random.default_rng(seed)
+    A = 0.98 * _haar(r, nx)
+    B = r.normal(0.0, np.sqrt(1.0 / nu), size=(nx, nu))
+    W = r.normal(0.0, np.sqrt(1.0 / nx), size=(nx, nx))
+    U = _haar(r, nx)
+    Q = U @ np.diag(r.uniform(0.1, 10.0, size=nx)) @ U.T
+    Q = 0.5 * (Q + Q.T)
+    return Problem(model=SYNTH, nx=nx, nu=nu, dt=1.0, integrator=EULER, prm=_f([0.1]),
+                   Q=Q, R=0.1 * np.eye(nu), Qf=Q.copy(), xref=np.zeros(nx), uref=np.zeros(nu),
+                   xlo=np.full(nx, -INF), xhi=np.full(nx, INF),
+                   ulo=-np.ones(nu), uhi=np.ones(nu), A=A, B=B, W=W, name="synth")
+
+
+def synth_x0(seed: int, nx: int = 32) -> np.ndarray:
+    """x0 ~ N(0, I)."""
+    return np.random.default_rng(seed + 1000).normal(size=nx)
