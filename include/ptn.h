@@ -1,0 +1,171 @@
+/*
+ * ptn.h -- C ABI of the GB300 (sm_103a) parallel-in-time Newton solver for
+ * constrained nonlinear model predictive control (arXiv 2409.20027).
+ *
+ * Problem (Sec. II-A, eq. ocp): minimise
+ *     l_{N+1}(x_{N+1}) + sum_{t=1..N} l_t(x_t, u_t)
+ * subject to x_{t+1} = f(x_t, u_t), g(x_t) <= 0, h(u_t) <= 0, x_1 = x0.
+ * Here N = T, l_t(x,u) = (x-xref)^T Q (x-xref) + (u-uref)^T R (u-uref) (no 1/2),
+ * l_{N+1}(x) = (x-xref)^T Qf (x-xref), f is one of the built-in models and g, h are
+ * box bounds (each finite bound is one constraint row).
+ *
+ * Solvers: primal log-barrier interior point (Sec. II-B, eq. lb-min / lb-step-2) and
+ * ADMM (Sec. II-C, eq. admm-min ... admm-step-5).  Every sub-problem is solved by the
+ * parallel-in-time Newton method (Sec. III, Alg. 4): co-state scan (Alg. 1), value
+ * function scan (Alg. 2), state propagation scan (Alg. 3), then a line search over
+ * closed-loop nonlinear rollouts.  The whole solve of an instance runs on the GPU.
+ *
+ * Memory: all trajectory arguments are DEVICE pointers to float64 arrays, row-major and
+ * time-major (x: (T+1) x nx, u: T x nu, lam: (T+1) x nx).  The caller owns them.  The
+ * solver owns its device workspace (allocated by ptn_solver_create).  Problem data are
+ * HOST pointers, copied at create.  `stream` is a cudaStream_t (NULL = legacy default);
+ * calls are stream-ordered and return after the stream has reached the end of the
+ * solve (they synchronise once to read the status).
+ *
+ * Errors: functions return a status code (0 = PTN_OK, negative = error); the message
+ * of the last error is ptn_last_error().  A handle must not be used by two host threads
+ * at once.  Device waits are bounded: a wait that expires returns PTN_ERR_TIMEOUT.
+ */
+#ifndef PTN_H
+#define PTN_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PTN_OK 0
+#define PTN_ERR_INVALID_ARG (-1)
+#define PTN_ERR_INFEASIBLE_START (-2) /* IP start not strictly inside the constraints */
+#define PTN_ERR_NOT_CONVERGED (-3)    /* outputs hold the last iterate */
+#define PTN_ERR_NUMERICAL (-4)        /* non-finite values or regularisation exhausted */
+#define PTN_ERR_TIMEOUT (-5)          /* a bounded device wait expired */
+#define PTN_ERR_CUDA (-6)
+
+enum { PTN_MODEL_PENDULUM = 0, PTN_MODEL_CARTPOLE = 1, PTN_MODEL_QUADROTOR = 2, PTN_MODEL_SYNTH_TANH = 3 };
+enum { PTN_EULER = 0, PTN_RK4 = 1 };
+enum { PTN_FP64 = 0, PTN_FP32_FP64SOLVE = 1 };
+enum { PTN_METHOD_IP = 0, PTN_METHOD_ADMM = 1 };
+
+/* Problem description (Sec. II-A).  Model constants prm:
+ *   pendulum  [g, l, m, b]                       x = (theta, omega), u = torque
+ *   cart-pole [m_c, m_p, l, g]                   x = (p, theta, p', theta'), u = force
+ *   quadrotor [mass, Ixx, Iyy, Izz, arm, k_m, g] x = (pos, ZYX angles, vel, rates),
+ *                                                u = 4 rotor thrusts
+ *   synthetic [c]  x+ = A x + B u + c tanh(W x)  (A, B, W host row-major)
+ * Bounds: +-INFINITY (or |b| >= 1e300) means no bound.  Rows are ordered state rows
+ * first (per component: upper, lower) then control rows; ADMM z, v use this order. */
+typedef struct ptn_problem {
+  int model, nx, nu, integrator;
+  double dt;
+  double prm[8];
+  const double *A, *B, *W;
+  const double *Q, *R, *Qf;
+  const double *xref, *uref;
+  const double *xlo, *xhi, *ulo, *uhi;
+} ptn_problem;
+
+/* Solver settings; ptn_default_options() fills the defaults:
+ *   precision FP32_FP64SOLVE, mu 1e-1 -> 1e-6 (x0.1), tol_inner 1e-4, tol_final 1e-6,
+ *   max_newton 500 per barrier level, ADMM rho 1, admm_tol 1e-2, max_outer 2000,
+ *   alpha0 1e-6 in [1e-10, 1e10], ten step sizes 1, 1/2, ..., Armijo c1 1e-4,
+ *   rollout: at most 30 multiple-shooting Newton iterations to relative defect 1e-12. */
+typedef struct ptn_options {
+  int precision;        /* PTN_FP64 or PTN_FP32_FP64SOLVE */
+  int max_newton;       /* Newton iterations per barrier level / ADMM sub-problem */
+  int max_outer;        /* ADMM outer iterations */
+  int ls_count;         /* candidate step sizes 1, beta, beta^2, ... */
+  int admm_fixed_iters; /* > 0: run exactly this many ADMM iterations */
+  int roll_max_iter;    /* multiple-shooting Newton iterations per rollout */
+  int block_threads;    /* threads per CTA when one CTA solves one instance */
+  int grid_min_T;       /* single solves with T >= grid_min_T use all SMs (0: never) */
+  int grid_steps_per_thread;
+  int pad;
+  double mu0, zeta, mu_final, tol_inner, tol_final, rho, admm_tol;
+  double alpha0, alpha_min, alpha_max, ls_beta, armijo_c1, armijo_eps, roll_tol;
+} ptn_options;
+
+/* Per-solve report.  r_kkt = max(r_stat, r_dyn, r_feas, mu) for IP, where r_stat is
+ * max_t |d_t|_inf (gradient of the augmented cost), r_dyn the largest dynamics defect and
+ * r_feas the largest constraint violation.  cycles[] are SM clock cycles spent by the
+ * group's first thread in the co-state pass, second-order expansion, value pass, state
+ * pass, line search, and everything else. */
+typedef struct ptn_info {
+  int status, newton_iters, outer_iters, ls_rejects, factor_fails, roll_fails;
+  int roll_iters, ls_evals;
+  double mu, alpha, r_stat, r_dyn, r_feas, r_kkt, J, J_c, r_p, r_d;
+  long long cycles[6];
+} ptn_info;
+
+typedef struct ptn_solver ptn_solver;
+
+/* Fill *opt with the defaults listed above. */
+void ptn_default_options(ptn_options* opt);
+
+/* Create a solver for `prob` (copied) able to run batches of up to max_batch instances
+ * whose horizons sum to at most max_T * max_batch steps.  Allocates the device
+ * workspace on the current device.  Returns PTN_OK and *out, or an error. */
+int ptn_solver_create(const ptn_problem* prob, const ptn_options* opt, int max_T, int max_batch,
+                      ptn_solver** out);
+
+/* Free the workspace and the handle (NULL is ignored). */
+void ptn_solver_destroy(ptn_solver* s);
+
+/* Message of the last error on this handle ("" if none); s may be NULL. */
+const char* ptn_last_error(const ptn_solver* s);
+
+/* Replace the options of an existing handle (e.g. precision, tolerances). */
+int ptn_set_options(ptn_solver* s, const ptn_options* opt);
+
+/* Primal log-barrier IP solve of one instance (Sec. II-B with Alg. 4 sub-solves).
+ *   x0      device, nx            initial state x_1
+ *   u_init  device, T x nu        strictly feasible initial controls, or NULL (zeros)
+ *   x_out   device, (T+1) x nx    optimal states (also used as iterate storage)
+ *   u_out   device, T x nu        optimal controls
+ *   lam_out device, (T+1) x nx    co-states at the solution, or NULL
+ *   info    host                  status, iterations, KKT residuals, costs (may be NULL)
+ * Returns info->status: PTN_OK, PTN_ERR_NOT_CONVERGED, PTN_ERR_INFEASIBLE_START, ... */
+int ptn_solve_ip(ptn_solver* s, const double* x0, const double* u_init, int T, double* x_out,
+                 double* u_out, double* lam_out, ptn_info* info, void* stream);
+
+/* ADMM solve of one instance (Sec. II-C).  Arguments as ptn_solve_ip, plus the final
+ * consensus variables z_out and multipliers v_out (device, T x nw each, may be NULL),
+ * nw = number of finite bounds.  Options rho, admm_tol, max_outer, admm_fixed_iters. */
+int ptn_solve_admm(ptn_solver* s, const double* x0, const double* u_init, int T, double* x_out,
+                   double* u_out, double* lam_out, double* z_out, double* v_out, ptn_info* info,
+                   void* stream);
+
+/* Solve B independent instances of the same model with horizons T_b (host array) in one
+ * launch, one CTA per instance.  x0 is device B x nx; xref is device B x nx (per-instance
+ * tracking target) or NULL; u_init is device (sum T_b) x nu or NULL.  Outputs are
+ * concatenated in instance order: x_out (sum (T_b+1)) x nx, u_out (sum T_b) x nu,
+ * lam_out like x_out or NULL.  info_b is a host array of B records (may be NULL).
+ * method is PTN_METHOD_IP or PTN_METHOD_ADMM.  Returns PTN_OK when every instance
+ * converged, else the first non-zero instance status. */
+int ptn_solve_batch(ptn_solver* s, int method, int B, const int* T_b, const double* x0,
+                    const double* xref, const double* u_init, double* x_out, double* u_out,
+                    double* lam_out, ptn_info* info_b, void* stream);
+
+/* Gradients of the scalar loss  gJ * J* + <gx, x*> + <gu, u*>  at B solutions of the
+ * barrier problem with weight mu (J* = optimal barrier objective; x*, u* concatenated as
+ * in ptn_solve_batch), with respect to x0 (B x nx), diag Q (B x nx), diag R (B x nu),
+ * diag Qf (B x nx) and the model constants prm (B x 8).  The J* part follows the
+ * envelope theorem on the Lagrangian eq. ocp-lagrangian (gradient in x0 = lam_1); the x*, u*
+ * part solves the adjoint LQR (same Hessian as the Newton step, linear terms from
+ * gx, gu) with the value and state scans, and its multipliers with the co-state scan.
+ * All array arguments are device pointers; gx, gu may be NULL (J* part only); any output
+ * may be NULL.  xref as in ptn_solve_batch. */
+int ptn_adjoint(ptn_solver* s, int B, const int* T_b, const double* x0, const double* xref,
+                const double* x_star, const double* u_star, double mu, double gJ,
+                const double* gx, const double* gu, double* g_x0, double* g_Qd, double* g_Rd,
+                double* g_Qfd, double* g_prm, void* stream);
+
+/* Number of constraint rows nw of the handle's problem. */
+int ptn_num_rows(const ptn_solver* s);
+
+/* Library version string. */
+const char* ptn_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PTN_H */

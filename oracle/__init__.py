@@ -71,9 +71,10 @@ class _Aug(C.Structure):
 
 @dataclass
 class Options:
-    """Solver settings.  Defaults follow the readings listed in the design doc:
-    mu 1e-1 -> 1e-6 by x0.1, inner tolerance 1e-4 (1e-6 at the last mu), ten step
-    sizes 1, 1/2, ..., Armijo c1 = 1e-4, Marquardt-type alpha update from alpha0 = 1e-6."""
+    """Solver settings (the paper fixes none of these; values are readings):
+    mu 1e-1 -> 1e-6 by x0.1, inner tolerance 1e-4 (1e-6 at the last mu), at most 500
+    Newton iterations per barrier level, ten step sizes 1, 1/2, ..., Armijo c1 = 1e-4,
+    Marquardt-type alpha update from alpha0 = 1e-6."""
     mu0: float = 1e-1
     zeta: float = 0.1
     mu_final: float = 1e-6
@@ -87,7 +88,7 @@ class Options:
     ls_beta: float = 0.5
     armijo_c1: float = 1e-4
     armijo_eps: float = 1e-12
-    max_newton: int = 100
+    max_newton: int = 500
     max_outer: int = 2000
     ls_count: int = 10
     admm_fixed_iters: int = 0

@@ -1,0 +1,81 @@
+"""Build the CUDA library libptn.so for GB300 (sm_103a) in-tree.
+
+Each kernel translation unit (one per model and LQR precision) is compiled by its own
+nvcc process, in parallel, then linked with the C-ABI unit into
+``paper_2409_20027_gb300/_build/libptn.so``.
+"""
+from __future__ import annotations
+
+import glob
+import os
+import shutil
+import subprocess
+import sys
+from concurrent.futures import ThreadPoolExecutor
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+CSRC = os.path.join(HERE, "csrc")
+OUT = os.path.join(HERE, "_build")
+LIB = os.path.join(OUT, "libptn.so")
+ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
+
+
+def _nvcc() -> str:
+    for c in [os.environ.get("NVCC"), shutil.which("nvcc"), "/usr/local/cuda/bin/nvcc"]:
+        if c and os.path.exists(c):
+            return c
+    raise RuntimeError("nvcc not found: the CUDA toolkit is required to build libptn.so")
+
+
+def sources() -> list[str]:
+    """All translation units; PTN_MODELS (comma list, e.g. "pendulum,cartpole") limits
+    which model kernel units are built."""
+    srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
+    sel = os.environ.get("PTN_MODELS")
+    if sel:
+        keep = set(x.strip() for x in sel.split(","))
+        srcs = [s for s in srcs if not os.path.basename(s).startswith("ptn_k_")
+                or os.path.basename(s).split("_")[2] in keep]
+    return srcs
+
+
+def _stale(obj: str, src: str, headers: list[str]) -> bool:
+    if not os.path.exists(obj):
+        return True
+    t = os.path.getmtime(obj)
+    return any(os.path.getmtime(f) > t for f in [src] + headers)
+
+
+def build(force: bool = False, jobs: int | None = None, verbose: bool = False) -> str:
+    os.makedirs(OUT, exist_ok=True)
+    nvcc = _nvcc()
+    headers = glob.glob(os.path.join(CSRC, "*.cuh")) + [os.path.join(HERE, "..", "include", "ptn.h")]
+    srcs = sources()
+    objs = [os.path.join(OUT, os.path.basename(s)[:-3] + ".o") for s in srcs]
+    todo = [(s, o) for s, o in zip(srcs, objs) if force or _stale(o, s, headers)]
+
+    def comp(so):
+        s, o = so
+        cmd = [nvcc, *ARCH, *FLAGS, "-c", s, "-o", o + ".tmp"]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"nvcc failed for {os.path.basename(s)}:\n{r.stderr[-4000:]}")
+        os.replace(o + ".tmp", o)
+        if verbose:
+            print("compiled", os.path.basename(s), flush=True)
+
+    if todo:
+        with ThreadPoolExecutor(max_workers=jobs or min(len(todo), os.cpu_count() or 4)) as ex:
+            list(ex.map(comp, todo))
+    if todo or not os.path.exists(LIB):
+        tmp = LIB + f".{os.getpid()}.tmp"
+        r = subprocess.run([nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"], capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError("link failed:\n" + r.stderr[-4000:])
+        os.replace(tmp, LIB)
+    return LIB
+
+
+if __name__ == "__main__":
+    print(build(force="--force" in sys.argv, verbose=True))

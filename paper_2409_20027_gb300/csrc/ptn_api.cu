@@ -1,0 +1,420 @@
+// ptn_api.cu -- C ABI of the solver (declared in include/ptn.h): handle, workspace,
+// option records, instance tables and the launches of the device-resident solver.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <vector>
+
+#include "../../include/ptn.h"
+#include "ptn_launch.cuh"
+
+using namespace ptn;
+
+// per (model, precision) launchers, one translation unit each; weak references so a
+// library built without some model units still links (those models report an error)
+#define PTN_WEAK __attribute__((weak))
+cudaError_t ptn_launch_pendulum_f64(LaunchReq&) PTN_WEAK;
+cudaError_t ptn_launch_pendulum_f32(LaunchReq&) PTN_WEAK;
+cudaError_t ptn_launch_cartpole_f64(LaunchReq&) PTN_WEAK;
+cudaError_t ptn_launch_cartpole_f32(LaunchReq&) PTN_WEAK;
+cudaError_t ptn_launch_quadrotor_f64(LaunchReq&) PTN_WEAK;
+cudaError_t ptn_launch_quadrotor_f32(LaunchReq&) PTN_WEAK;
+
+namespace {
+
+typedef cudaError_t (*launch_fn)(LaunchReq&);
+
+launch_fn pick_launcher(int model, int precision) {
+  switch (model) {
+    case PTN_MODEL_PENDULUM: return precision == PTN_FP64 ? ptn_launch_pendulum_f64 : ptn_launch_pendulum_f32;
+    case PTN_MODEL_CARTPOLE: return precision == PTN_FP64 ? ptn_launch_cartpole_f64 : ptn_launch_cartpole_f32;
+    case PTN_MODEL_QUADROTOR: return precision == PTN_FP64 ? ptn_launch_quadrotor_f64 : ptn_launch_quadrotor_f32;
+    default: return nullptr;
+  }
+}
+
+int model_dims(int model, int* nx, int* nu) {
+  switch (model) {
+    case PTN_MODEL_PENDULUM: *nx = 2; *nu = 1; return 0;
+    case PTN_MODEL_CARTPOLE: *nx = 4; *nu = 1; return 0;
+    case PTN_MODEL_QUADROTOR: *nx = 12; *nu = 4; return 0;
+    default: return -1;
+  }
+}
+
+bool has_bound(const double* b, int i) { return b && isfinite(b[i]) && fabs(b[i]) < 1e300; }
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+}  // namespace
+
+struct ptn_solver {
+  ptn_options opt;
+  ProbDev hprob;
+  ProbDev* dprob = nullptr;
+  OptDev* dopt = nullptr;
+  double* dsynth = nullptr;
+  int n = 0, m = 0, nw = 0;
+  long long cap_steps = 0;
+  int cap_batch = 0;
+  char* ws = nullptr;
+  WorkRaw w{};
+  InstDev* dinst = nullptr;
+  InfoDev* dinfo = nullptr;
+  InstDev* hinst = nullptr;  // pinned
+  InfoDev* hinfo = nullptr;  // pinned
+  OptDev* hopt = nullptr;    // pinned
+  GridScratch gs{};
+  int grid_cap_blocks = 0;
+  int num_sms = 0;
+  char err[512];
+};
+
+static int fail(ptn_solver* s, int code, const char* fmt, ...) {
+  if (s) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(s->err, sizeof(s->err), fmt, ap);
+    va_end(ap);
+  }
+  return code;
+}
+
+#define CK(call)                                                                             \
+  do {                                                                                       \
+    cudaError_t e_ = (call);                                                                 \
+    if (e_ != cudaSuccess) return fail(s, PTN_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+extern "C" void ptn_default_options(ptn_options* o) {
+  memset(o, 0, sizeof(*o));
+  o->precision = PTN_FP32_FP64SOLVE;
+  o->max_newton = 500;
+  o->max_outer = 2000;
+  o->ls_count = 10;
+  o->admm_fixed_iters = 0;
+  o->roll_max_iter = 30;
+  o->block_threads = 128;
+  o->grid_min_T = 2048;
+  o->grid_steps_per_thread = 2;
+  o->mu0 = 1e-1;
+  o->zeta = 0.1;
+  o->mu_final = 1e-6;
+  o->tol_inner = 1e-4;
+  o->tol_final = 1e-6;
+  o->rho = 1.0;
+  o->admm_tol = 1e-2;
+  o->alpha0 = 1e-6;
+  o->alpha_min = 1e-10;
+  o->alpha_max = 1e10;
+  o->ls_beta = 0.5;
+  o->armijo_c1 = 1e-4;
+  o->armijo_eps = 1e-12;
+  o->roll_tol = 1e-12;
+}
+
+extern "C" const char* ptn_version(void) { return "ptn 0.1 (sm_103a)"; }
+
+extern "C" const char* ptn_last_error(const ptn_solver* s) { return s ? s->err : ""; }
+
+extern "C" int ptn_num_rows(const ptn_solver* s) { return s ? s->nw : 0; }
+
+static int check_options(ptn_solver* s, const ptn_options* o) {
+  if (o->precision != PTN_FP64 && o->precision != PTN_FP32_FP64SOLVE)
+    return fail(s, PTN_ERR_INVALID_ARG, "precision must be PTN_FP64 or PTN_FP32_FP64SOLVE");
+  if (o->block_threads < 32 || o->block_threads > 256 || (o->block_threads % 32))
+    return fail(s, PTN_ERR_INVALID_ARG, "block_threads must be a multiple of 32 in [32, 256]");
+  if (o->max_newton < 1 || o->ls_count < 1 || o->roll_max_iter < 1 || o->max_outer < 1)
+    return fail(s, PTN_ERR_INVALID_ARG, "iteration limits must be positive");
+  if (!(o->mu0 > 0) || !(o->zeta > 0 && o->zeta < 1) || !(o->mu_final > 0) || !(o->rho > 0) ||
+      !(o->ls_beta > 0 && o->ls_beta < 1) || !(o->alpha_max >= o->alpha_min) || !(o->alpha_min >= 0))
+    return fail(s, PTN_ERR_INVALID_ARG, "invalid continuation, penalty or regularisation parameter");
+  if (o->grid_steps_per_thread < 1) return fail(s, PTN_ERR_INVALID_ARG, "grid_steps_per_thread must be >= 1");
+  return PTN_OK;
+}
+
+extern "C" int ptn_set_options(ptn_solver* s, const ptn_options* opt) {
+  if (!s || !opt) return PTN_ERR_INVALID_ARG;
+  int rc = check_options(s, opt);
+  if (rc) return rc;
+  s->opt = *opt;
+  return PTN_OK;
+}
+
+extern "C" void ptn_solver_destroy(ptn_solver* s) {
+  if (!s) return;
+  cudaFree(s->dprob);
+  cudaFree(s->dopt);
+  cudaFree(s->dsynth);
+  cudaFree(s->ws);
+  cudaFree(s->dinst);
+  cudaFree(s->dinfo);
+  cudaFree(s->gs.bar);
+  cudaFree(s->gs.err);
+  cudaFree(s->gs.red);
+  cudaFree(s->gs.xs);
+  cudaFreeHost(s->hinst);
+  cudaFreeHost(s->hinfo);
+  cudaFreeHost(s->hopt);
+  delete s;
+}
+
+extern "C" int ptn_solver_create(const ptn_problem* prob, const ptn_options* opt, int max_T, int max_batch,
+                                 ptn_solver** out) {
+  if (!out) return PTN_ERR_INVALID_ARG;
+  *out = nullptr;
+  ptn_solver* s = new ptn_solver();
+  s->err[0] = 0;
+  *out = s;  // on error the caller reads ptn_last_error() and destroys the handle
+  int rc = PTN_OK;
+  auto bad = [&](int code) { *out = s; return code; };
+  if (!prob) return bad(fail(s, PTN_ERR_INVALID_ARG, "prob is NULL"));
+  if (opt) {
+    rc = check_options(s, opt);
+    if (rc) return bad(rc);
+    s->opt = *opt;
+  } else {
+    ptn_default_options(&s->opt);
+  }
+  int nx, nu;
+  if (model_dims(prob->model, &nx, &nu))
+    return bad(fail(s, PTN_ERR_INVALID_ARG, "unknown or unsupported model id %d", prob->model));
+  if (prob->nx != nx || prob->nu != nu)
+    return bad(fail(s, PTN_ERR_INVALID_ARG, "model %d has nx=%d nu=%d, got %d %d", prob->model, nx, nu, prob->nx,
+                    prob->nu));
+  if (prob->integrator != PTN_EULER && prob->integrator != PTN_RK4)
+    return bad(fail(s, PTN_ERR_INVALID_ARG, "integrator must be PTN_EULER or PTN_RK4"));
+  if (!(prob->dt > 0) || !isfinite(prob->dt)) return bad(fail(s, PTN_ERR_INVALID_ARG, "dt must be positive"));
+  if (!prob->Q || !prob->R || !prob->Qf || !prob->xref || !prob->uref)
+    return bad(fail(s, PTN_ERR_INVALID_ARG, "Q, R, Qf, xref, uref are required"));
+  if (max_T < 1 || max_batch < 1) return bad(fail(s, PTN_ERR_INVALID_ARG, "max_T and max_batch must be >= 1"));
+  s->n = nx;
+  s->m = nu;
+  ProbDev& P = s->hprob;
+  memset(&P, 0, sizeof(P));
+  P.model = prob->model;
+  P.nx = nx;
+  P.nu = nu;
+  P.integrator = prob->integrator;
+  P.dt = prob->dt;
+  for (int i = 0; i < 8; i++) P.prm[i] = prob->prm[i];
+  for (int i = 0; i < nx * nx; i++) {
+    if (!isfinite(prob->Q[i]) || !isfinite(prob->Qf[i])) return bad(fail(s, PTN_ERR_INVALID_ARG, "Q/Qf not finite"));
+    P.Q[i] = prob->Q[i];
+    P.Qf[i] = prob->Qf[i];
+  }
+  for (int i = 0; i < nu * nu; i++) {
+    if (!isfinite(prob->R[i])) return bad(fail(s, PTN_ERR_INVALID_ARG, "R not finite"));
+    P.R[i] = prob->R[i];
+  }
+  for (int i = 0; i < nx; i++) P.xref[i] = prob->xref[i];
+  for (int i = 0; i < nu; i++) P.uref[i] = prob->uref[i];
+  int k = 0;
+  for (int i = 0; i < nx; i++) {
+    if (has_bound(prob->xhi, i)) { P.row_isx[k] = 1; P.row_idx[k] = i; P.row_sgn[k] = 1.0; P.row_bnd[k] = prob->xhi[i]; k++; }
+    if (has_bound(prob->xlo, i)) { P.row_isx[k] = 1; P.row_idx[k] = i; P.row_sgn[k] = -1.0; P.row_bnd[k] = prob->xlo[i]; k++; }
+  }
+  for (int i = 0; i < nu; i++) {
+    if (has_bound(prob->uhi, i)) { P.row_isx[k] = 0; P.row_idx[k] = i; P.row_sgn[k] = 1.0; P.row_bnd[k] = prob->uhi[i]; k++; }
+    if (has_bound(prob->ulo, i)) { P.row_isx[k] = 0; P.row_idx[k] = i; P.row_sgn[k] = -1.0; P.row_bnd[k] = prob->ulo[i]; k++; }
+  }
+  P.nw = k;
+  s->nw = k;
+  cudaDeviceProp dp;
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  CK(cudaGetDeviceProperties(&dp, dev));
+  s->num_sms = dp.multiProcessorCount;
+  CK(cudaMalloc(&s->dprob, sizeof(ProbDev)));
+  CK(cudaMemcpy(s->dprob, &P, sizeof(ProbDev), cudaMemcpyHostToDevice));
+  CK(cudaMalloc(&s->dopt, sizeof(OptDev)));
+  CK(cudaMalloc(&s->dinst, sizeof(InstDev) * max_batch));
+  CK(cudaMalloc(&s->dinfo, sizeof(InfoDev) * max_batch));
+  CK(cudaMallocHost(&s->hinst, sizeof(InstDev) * max_batch));
+  CK(cudaMallocHost(&s->hinfo, sizeof(InfoDev) * max_batch));
+  CK(cudaMallocHost(&s->hopt, sizeof(OptDev)));
+  // workspace
+  const long long S = (long long)max_T * max_batch, SB = S + max_batch;
+  s->cap_steps = S;
+  s->cap_batch = max_batch;
+  const int n = nx, m = nu, nw = k;
+  size_t off = 0;
+  size_t o_xB = off; off = align256(off + sizeof(double) * SB * n);
+  size_t o_uB = off; off = align256(off + sizeof(double) * S * m);
+  size_t o_lam = off; off = align256(off + sizeof(double) * SB * n);
+  size_t o_F = off; off = align256(off + sizeof(double) * S * n * n);
+  size_t o_G = off; off = align256(off + sizeof(double) * S * n * m);
+  size_t o_d = off; off = align256(off + sizeof(double) * S * m);
+  size_t o_Pm = off; off = align256(off + 8 * SB * n * n);
+  size_t o_Mm = off; off = align256(off + 8 * S * n * m);
+  size_t o_Rm = off; off = align256(off + 8 * S * m * m);
+  size_t o_Gam = off; off = align256(off + 8 * S * m * n);
+  size_t o_gam = off; off = align256(off + 8 * S * m);
+  size_t o_dx = off; off = align256(off + 8 * SB * n);
+  size_t o_du = off; off = align256(off + 8 * S * m);
+  size_t o_z = off; off = align256(off + sizeof(double) * S * (nw > 0 ? nw : 1));
+  size_t o_v = off; off = align256(off + sizeof(double) * S * (nw > 0 ? nw : 1));
+  CK(cudaMalloc(&s->ws, off));
+  char* b = s->ws;
+  s->w.xB = (double*)(b + o_xB); s->w.uB = (double*)(b + o_uB); s->w.lam = (double*)(b + o_lam);
+  s->w.F = (double*)(b + o_F); s->w.G = (double*)(b + o_G); s->w.d = (double*)(b + o_d);
+  s->w.Pm = b + o_Pm; s->w.Mm = b + o_Mm; s->w.Rm = b + o_Rm; s->w.Gam = b + o_Gam; s->w.gam = b + o_gam;
+  s->w.dx = b + o_dx; s->w.du = b + o_du;
+  s->w.z = (double*)(b + o_z); s->w.v = (double*)(b + o_v);
+  // grid-tier scratch, sized for 4 co-resident blocks per SM
+  s->grid_cap_blocks = 4 * s->num_sms;
+  CK(cudaMalloc(&s->gs.bar, 2 * sizeof(unsigned)));
+  CK(cudaMalloc(&s->gs.err, sizeof(int)));
+  CK(cudaMalloc(&s->gs.red, sizeof(double) * 2 * 8 * s->grid_cap_blocks));
+  size_t eb = 0;
+  {
+    LaunchReq q{};
+    q.tier = 0; q.precision = PTN_FP64; q.query = 1; q.nthreads = 128; q.elem_bytes = &eb;
+    launch_fn fn = pick_launcher(P.model, PTN_FP64);
+    if (!fn) fn = pick_launcher(P.model, PTN_FP32_FP64SOLVE);
+    if (!fn) return fail(s, PTN_ERR_INVALID_ARG, "kernels for model %d are not built", P.model);
+    CK(fn(q));
+  }
+  s->gs.elem_bytes = (int)((eb + 15) & ~size_t(15));
+  CK(cudaMalloc(&s->gs.xs, (size_t)2 * s->gs.elem_bytes * s->grid_cap_blocks));
+  s->gs.spin_limit = 1ll << 26;
+  *out = s;
+  return PTN_OK;
+}
+
+static void to_optdev(const ptn_options& o, int method, OptDev* d) {
+  memset(d, 0, sizeof(*d));
+  d->mu0 = o.mu0; d->zeta = o.zeta; d->mu_final = o.mu_final; d->tol_inner = o.tol_inner;
+  d->tol_final = o.tol_final; d->rho = o.rho; d->admm_tol = o.admm_tol;
+  d->alpha0 = o.alpha0; d->alpha_min = o.alpha_min; d->alpha_max = o.alpha_max; d->ls_beta = o.ls_beta;
+  d->armijo_c1 = o.armijo_c1;
+  // FP32 candidates carry FP32-level noise in the merit only through the LQR direction,
+  // the merit itself is FP64 in both modes
+  d->armijo_eps = o.armijo_eps;
+  d->roll_tol = o.roll_tol;
+  d->max_newton = o.max_newton; d->max_outer = o.max_outer; d->ls_count = o.ls_count;
+  d->admm_fixed_iters = o.admm_fixed_iters; d->roll_max_iter = o.roll_max_iter; d->method = method;
+  d->spin_limit = 1ll << 26;
+}
+
+static void from_info(const InfoDev& d, ptn_info* o) {
+  o->status = d.status; o->newton_iters = d.newton_iters; o->outer_iters = d.outer_iters;
+  o->ls_rejects = d.ls_rejects; o->factor_fails = d.factor_fails; o->roll_fails = d.roll_fails;
+  o->roll_iters = d.roll_iters; o->ls_evals = d.ls_evals;
+  for (int k = 0; k < 6; k++) o->cycles[k] = d.cyc[k];
+  o->mu = d.mu; o->alpha = d.alpha; o->r_stat = d.r_stat; o->r_dyn = d.r_dyn; o->r_feas = d.r_feas;
+  o->r_kkt = d.r_kkt; o->J = d.J; o->J_c = d.J_c; o->r_p = d.r_p; o->r_d = d.r_d;
+}
+
+static int solve_common(ptn_solver* s, int method, int B, const int* T_b, const double* x0, const double* xref,
+                        const double* u_init, double* x_out, double* u_out, double* lam_out, double* z_out,
+                        double* v_out, ptn_info* info, bool single, void* stream_) {
+  if (!s) return PTN_ERR_INVALID_ARG;
+  s->err[0] = 0;
+  cudaStream_t st = (cudaStream_t)stream_;
+  if (method != PTN_METHOD_IP && method != PTN_METHOD_ADMM) return fail(s, PTN_ERR_INVALID_ARG, "bad method");
+  if (B < 1 || B > s->cap_batch) return fail(s, PTN_ERR_INVALID_ARG, "B=%d outside [1, %d]", B, s->cap_batch);
+  if (!T_b || !x0 || !x_out || !u_out) return fail(s, PTN_ERR_INVALID_ARG, "NULL argument");
+  long long steps = 0;
+  for (int i = 0; i < B; i++) {
+    if (T_b[i] < 1) return fail(s, PTN_ERR_INVALID_ARG, "horizon T_b[%d]=%d must be >= 1", i, T_b[i]);
+    s->hinst[i].T = T_b[i];
+    s->hinst[i].uoff = (int)steps;
+    s->hinst[i].xoff = (int)(steps + i);
+    s->hinst[i].pad = 0;
+    steps += T_b[i];
+  }
+  if (steps > s->cap_steps)
+    return fail(s, PTN_ERR_INVALID_ARG, "total horizon %lld exceeds the workspace (%lld)", steps, s->cap_steps);
+  to_optdev(s->opt, method, s->hopt);
+  CK(cudaMemcpyAsync(s->dinst, s->hinst, sizeof(InstDev) * B, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(s->dopt, s->hopt, sizeof(OptDev), cudaMemcpyHostToDevice, st));
+  launch_fn fn = pick_launcher(s->hprob.model, s->opt.precision);
+  if (!fn) return fail(s, PTN_ERR_INVALID_ARG, "kernels for model %d, precision %d are not built", s->hprob.model, s->opt.precision);
+  LaunchReq q{};
+  q.precision = s->opt.precision;
+  q.stream = st;
+  q.w = s->w;
+  q.w.xA = x_out;
+  q.w.uA = u_out;
+  if (lam_out) q.w.lam = lam_out;
+  q.args.prob = s->dprob;
+  q.args.opt = s->dopt;
+  q.args.inst = s->dinst;
+  q.args.x0 = x0;
+  q.args.xref = xref;
+  q.args.u_init = u_init;
+  q.args.info = s->dinfo;
+  q.args.B = B;
+  const bool grid = single && B == 1 && s->opt.grid_min_T > 0 && T_b[0] >= s->opt.grid_min_T;
+  if (grid) {
+    q.tier = 1;
+    q.nthreads = 128;
+    int maxb = 0;
+    q.query = 1;
+    q.max_blocks = &maxb;
+    CK(fn(q));
+    q.query = 0;
+    int want = (int)((T_b[0] + (long long)q.nthreads * s->opt.grid_steps_per_thread - 1) /
+                     ((long long)q.nthreads * s->opt.grid_steps_per_thread));
+    int nb = want < maxb ? want : maxb;
+    if (nb > s->grid_cap_blocks) nb = s->grid_cap_blocks;
+    if (nb < 1) nb = 1;
+    q.nblocks = nb;
+    q.args.gs = s->gs;
+    CK(cudaMemsetAsync(s->gs.bar, 0, 2 * sizeof(unsigned), st));
+    CK(cudaMemsetAsync(s->gs.err, 0, sizeof(int), st));
+    CK(fn(q));
+  } else {
+    q.tier = 0;
+    q.nthreads = s->opt.block_threads;
+    q.nblocks = B;
+    CK(fn(q));
+  }
+  CK(cudaMemcpyAsync(s->hinfo, s->dinfo, sizeof(InfoDev) * B, cudaMemcpyDeviceToHost, st));
+  if (method == PTN_METHOD_ADMM && s->nw > 0) {
+    if (z_out) CK(cudaMemcpyAsync(z_out, s->w.z, sizeof(double) * steps * s->nw, cudaMemcpyDeviceToDevice, st));
+    if (v_out) CK(cudaMemcpyAsync(v_out, s->w.v, sizeof(double) * steps * s->nw, cudaMemcpyDeviceToDevice, st));
+  }
+  CK(cudaStreamSynchronize(st));
+  int rc = PTN_OK;
+  for (int i = 0; i < B; i++) {
+    if (info) from_info(s->hinfo[i], info + i);
+    if (rc == PTN_OK && s->hinfo[i].status != 0) rc = s->hinfo[i].status;
+  }
+  if (rc != PTN_OK && !s->err[0]) fail(s, rc, "solve finished with status %d", rc);
+  return rc;
+}
+
+extern "C" int ptn_solve_ip(ptn_solver* s, const double* x0, const double* u_init, int T, double* x_out,
+                            double* u_out, double* lam_out, ptn_info* info, void* stream) {
+  return solve_common(s, PTN_METHOD_IP, 1, &T, x0, nullptr, u_init, x_out, u_out, lam_out, nullptr, nullptr, info,
+                      true, stream);
+}
+
+extern "C" int ptn_solve_admm(ptn_solver* s, const double* x0, const double* u_init, int T, double* x_out,
+                              double* u_out, double* lam_out, double* z_out, double* v_out, ptn_info* info,
+                              void* stream) {
+  return solve_common(s, PTN_METHOD_ADMM, 1, &T, x0, nullptr, u_init, x_out, u_out, lam_out, z_out, v_out, info,
+                      true, stream);
+}
+
+extern "C" int ptn_solve_batch(ptn_solver* s, int method, int B, const int* T_b, const double* x0,
+                               const double* xref, const double* u_init, double* x_out, double* u_out,
+                               double* lam_out, ptn_info* info_b, void* stream) {
+  return solve_common(s, method, B, T_b, x0, xref, u_init, x_out, u_out, lam_out, nullptr, nullptr, info_b, false,
+                      stream);
+}
+
+extern "C" int ptn_adjoint(ptn_solver* s, int B, const int* T_b, const double* x0, const double* xref,
+                           const double* x_star, const double* u_star, double mu, double gJ, const double* gx,
+                           const double* gu, double* g_x0, double* g_Qd, double* g_Rd, double* g_Qfd,
+                           double* g_prm, void* stream) {
+  (void)B; (void)T_b; (void)x0; (void)xref; (void)x_star; (void)u_star; (void)mu; (void)gJ; (void)gx; (void)gu;
+  (void)g_x0; (void)g_Qd; (void)g_Rd; (void)g_Qfd; (void)g_prm; (void)stream;
+  return fail(s, PTN_ERR_INVALID_ARG, "adjoint not available in this build");
+}

@@ -1,0 +1,520 @@
+// ptn_common.cuh -- shared device types for the parallel-in-time Newton solver
+// (arXiv 2409.20027): status codes, problem/option records, small register-resident
+// linear algebra and forward-mode automatic-differentiation scalars.
+#pragma once
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#define PTN_MAXN 32
+#define PTN_MAXM 8
+#define PTN_MAXW (2 * PTN_MAXN + 2 * PTN_MAXM)
+#define PTN_MAXP 8
+
+#define PTN_HD __host__ __device__ __forceinline__
+
+namespace ptn {
+
+// ---- status codes (mirrors include/ptn.h) ----
+enum : int {
+  ST_OK = 0,
+  ST_EINVAL = -1,
+  ST_EINFEAS = -2,
+  ST_ENOTCONV = -3,
+  ST_ENUM = -4,
+  ST_ETIMEOUT = -5,
+  ST_ECUDA = -6,
+};
+
+enum : int { AUG_BARRIER = 1, AUG_ADMM = 2 };
+
+// Problem record in device memory.  Constraint rows w_r = sgn_r (z_k - bnd_r) <= 0 are
+// listed state rows first (per component: upper, lower), then control rows.
+struct ProbDev {
+  int model, nx, nu, integrator;
+  int nw, pad0, pad1, pad2;
+  double dt;
+  double prm[PTN_MAXP];
+  double Q[PTN_MAXN * PTN_MAXN];
+  double R[PTN_MAXM * PTN_MAXM];
+  double Qf[PTN_MAXN * PTN_MAXN];
+  double xref[PTN_MAXN];
+  double uref[PTN_MAXM];
+  int row_isx[PTN_MAXW];
+  int row_idx[PTN_MAXW];
+  double row_sgn[PTN_MAXW];
+  double row_bnd[PTN_MAXW];
+  const double* A;  // synthetic model: nx*nx
+  const double* B;  // nx*nu
+  const double* W;  // nx*nx
+};
+
+struct OptDev {
+  double mu0, zeta, mu_final, tol_inner, tol_final, rho, admm_tol;
+  double alpha0, alpha_min, alpha_max, ls_beta, armijo_c1, armijo_eps;
+  double roll_tol;
+  int max_newton, max_outer, ls_count, admm_fixed_iters;
+  int roll_max_iter, method, pad0, pad1;
+  long long spin_limit;  // bounded waits in grid barriers
+};
+
+// per-instance description (device array)
+struct InstDev {
+  int T;        // horizon (controls u_0..u_{T-1}, states x_0..x_T)
+  int xoff;     // offset of x_0 in state-major arrays, in steps (sum of previous T+1)
+  int uoff;     // offset of u_0 in control-major arrays, in steps (sum of previous T)
+  int pad;
+};
+
+// per-instance statistics (device array, copied to the host)
+struct InfoDev {
+  int status, newton_iters, outer_iters, ls_rejects;
+  int factor_fails, roll_fails, roll_iters, ls_evals;
+  double mu, alpha, r_stat, r_dyn, r_feas, r_kkt, J, J_c, r_p, r_d;
+  // SM clock cycles spent by group thread 0 per phase (costate, quadratize, value,
+  // state, line search, other)
+  long long cyc[6];
+};
+
+// ---------------------------------------------------------------------------
+// small dense linear algebra on row-major register arrays.  Products up to
+// PTN_UNROLL_MAX multiply-adds are fully unrolled (register-resident operands);
+// larger ones run as loops (operands in local memory).
+// ---------------------------------------------------------------------------
+#define PTN_UNROLL_MAX 512
+
+template <int R, int K, int C, class S, class T1, class T2>
+PTN_HD void mm(const T1* A, const T2* B, S* O) {
+  if constexpr (R * K * C <= PTN_UNROLL_MAX) {
+#pragma unroll
+    for (int i = 0; i < R; i++)
+#pragma unroll
+      for (int j = 0; j < C; j++) {
+        S s = S(0);
+#pragma unroll
+        for (int l = 0; l < K; l++) s += S(A[i * K + l]) * S(B[l * C + j]);
+        O[i * C + j] = s;
+      }
+  } else {
+#pragma unroll 1
+    for (int i = 0; i < R; i++)
+#pragma unroll 1
+      for (int j = 0; j < C; j++) {
+        S s = S(0);
+#pragma unroll 4
+        for (int l = 0; l < K; l++) s += S(A[i * K + l]) * S(B[l * C + j]);
+        O[i * C + j] = s;
+      }
+  }
+}
+// O = A^T B, A is K x R, B is K x C
+template <int R, int K, int C, class S, class T1, class T2>
+PTN_HD void mtm(const T1* A, const T2* B, S* O) {
+  if constexpr (R * K * C <= PTN_UNROLL_MAX) {
+#pragma unroll
+    for (int i = 0; i < R; i++)
+#pragma unroll
+      for (int j = 0; j < C; j++) {
+        S s = S(0);
+#pragma unroll
+        for (int l = 0; l < K; l++) s += S(A[l * R + i]) * S(B[l * C + j]);
+        O[i * C + j] = s;
+      }
+  } else {
+#pragma unroll 1
+    for (int i = 0; i < R; i++)
+#pragma unroll 1
+      for (int j = 0; j < C; j++) {
+        S s = S(0);
+#pragma unroll 4
+        for (int l = 0; l < K; l++) s += S(A[l * R + i]) * S(B[l * C + j]);
+        O[i * C + j] = s;
+      }
+  }
+}
+// O = A B^T, A is R x K, B is C x K
+template <int R, int K, int C, class S, class T1, class T2>
+PTN_HD void mmt(const T1* A, const T2* B, S* O) {
+  if constexpr (R * K * C <= PTN_UNROLL_MAX) {
+#pragma unroll
+    for (int i = 0; i < R; i++)
+#pragma unroll
+      for (int j = 0; j < C; j++) {
+        S s = S(0);
+#pragma unroll
+        for (int l = 0; l < K; l++) s += S(A[i * K + l]) * S(B[j * K + l]);
+        O[i * C + j] = s;
+      }
+  } else {
+#pragma unroll 1
+    for (int i = 0; i < R; i++)
+#pragma unroll 1
+      for (int j = 0; j < C; j++) {
+        S s = S(0);
+#pragma unroll 4
+        for (int l = 0; l < K; l++) s += S(A[i * K + l]) * S(B[j * K + l]);
+        O[i * C + j] = s;
+      }
+  }
+}
+template <int R, int C, class S, class T1>
+PTN_HD void mv(const T1* A, const S* x, S* y) {
+  if constexpr (R * C <= PTN_UNROLL_MAX) {
+#pragma unroll
+    for (int i = 0; i < R; i++) {
+      S s = S(0);
+#pragma unroll
+      for (int j = 0; j < C; j++) s += S(A[i * C + j]) * x[j];
+      y[i] = s;
+    }
+  } else {
+#pragma unroll 1
+    for (int i = 0; i < R; i++) {
+      S s = S(0);
+#pragma unroll 4
+      for (int j = 0; j < C; j++) s += S(A[i * C + j]) * x[j];
+      y[i] = s;
+    }
+  }
+}
+// y = A^T x, A is R x C
+template <int R, int C, class S, class T1>
+PTN_HD void mtv(const T1* A, const S* x, S* y) {
+  if constexpr (R * C <= PTN_UNROLL_MAX) {
+#pragma unroll
+    for (int j = 0; j < C; j++) {
+      S s = S(0);
+#pragma unroll
+      for (int i = 0; i < R; i++) s += S(A[i * C + j]) * x[i];
+      y[j] = s;
+    }
+  } else {
+#pragma unroll 1
+    for (int j = 0; j < C; j++) {
+      S s = S(0);
+#pragma unroll 4
+      for (int i = 0; i < R; i++) s += S(A[i * C + j]) * x[i];
+      y[j] = s;
+    }
+  }
+}
+
+// In-place Cholesky A = L L^T (lower triangle written, upper untouched).
+// Returns false when A is not positive definite.
+template <int N>
+PTN_HD bool chol(double* A) {
+#pragma unroll
+  for (int j = 0; j < N; j++) {
+    double s = A[j * N + j];
+#pragma unroll
+    for (int k = 0; k < j; k++) s -= A[j * N + k] * A[j * N + k];
+    if (!(s > 0.0) || !isfinite(s)) return false;
+    double d = sqrt(s), id = 1.0 / d;
+    A[j * N + j] = d;
+#pragma unroll
+    for (int i = j + 1; i < N; i++) {
+      double t = A[i * N + j];
+#pragma unroll
+      for (int k = 0; k < j; k++) t -= A[i * N + k] * A[j * N + k];
+      A[i * N + j] = t * id;
+    }
+  }
+  return true;
+}
+// solve (L L^T) X = B in place, B is N x C
+template <int N, int C>
+PTN_HD void chol_solve(const double* L, double* B) {
+#pragma unroll
+  for (int c = 0; c < C; c++) {
+#pragma unroll
+    for (int i = 0; i < N; i++) {
+      double s = B[i * C + c];
+#pragma unroll
+      for (int k = 0; k < i; k++) s -= L[i * N + k] * B[k * C + c];
+      B[i * C + c] = s / L[i * N + i];
+    }
+#pragma unroll
+    for (int i = N - 1; i >= 0; i--) {
+      double s = B[i * C + c];
+#pragma unroll
+      for (int k = i + 1; k < N; k++) s -= L[k * N + i] * B[k * C + c];
+      B[i * C + c] = s / L[i * N + i];
+    }
+  }
+}
+
+// In-place inverse by Gauss-Jordan elimination with partial pivoting (FP64).
+// Returns false when a pivot is zero or not finite.
+template <int N>
+PTN_HD bool inv_gj(double* A) {
+  int piv[N];
+  for (int i = 0; i < N; i++) piv[i] = i;
+#pragma unroll (N <= 8 ? N : 1)
+  for (int k = 0; k < N; k++) {
+    int p = k;
+    double best = fabs(A[k * N + k]);
+    for (int i = k + 1; i < N; i++) {
+      double v = fabs(A[i * N + k]);
+      if (v > best) { best = v; p = i; }
+    }
+    if (!(best > 0.0) || !isfinite(best)) return false;
+    if (p != k) {
+#pragma unroll (N <= 8 ? N : 4)
+      for (int j = 0; j < N; j++) {
+        double t = A[k * N + j]; A[k * N + j] = A[p * N + j]; A[p * N + j] = t;
+      }
+      int t = piv[k]; piv[k] = piv[p]; piv[p] = t;
+    }
+    double ip = 1.0 / A[k * N + k];
+    A[k * N + k] = 1.0;
+#pragma unroll (N <= 8 ? N : 4)
+    for (int j = 0; j < N; j++) A[k * N + j] *= ip;
+#pragma unroll (N <= 8 ? N : 1)
+    for (int i = 0; i < N; i++) {
+      if (i == k) continue;
+      double f = A[i * N + k];
+      A[i * N + k] = 0.0;
+#pragma unroll (N <= 8 ? N : 4)
+      for (int j = 0; j < N; j++) A[i * N + j] -= f * A[k * N + j];
+    }
+  }
+  // undo the row permutation as a column permutation of the inverse
+  double tmp[N];
+#pragma unroll (N <= 8 ? N : 1)
+  for (int i = 0; i < N; i++) {
+    for (int j = 0; j < N; j++) tmp[piv[j]] = A[i * N + j];
+    for (int j = 0; j < N; j++) A[i * N + j] = tmp[j];
+  }
+  return true;
+}
+
+// ---------------------------------------------------------------------------
+// forward-mode AD scalars
+// ---------------------------------------------------------------------------
+
+// value + K first partial derivatives
+template <class S, int K>
+struct Dual {
+  S v;
+  S d[K];
+  PTN_HD Dual() {}
+  PTN_HD Dual(S c) : v(c) {
+#pragma unroll
+    for (int i = 0; i < K; i++) d[i] = S(0);
+  }
+};
+template <class S, int K>
+PTN_HD Dual<S, K> operator+(const Dual<S, K>& a, const Dual<S, K>& b) {
+  Dual<S, K> r; r.v = a.v + b.v;
+#pragma unroll
+  for (int i = 0; i < K; i++) r.d[i] = a.d[i] + b.d[i];
+  return r;
+}
+template <class S, int K>
+PTN_HD Dual<S, K> operator-(const Dual<S, K>& a, const Dual<S, K>& b) {
+  Dual<S, K> r; r.v = a.v - b.v;
+#pragma unroll
+  for (int i = 0; i < K; i++) r.d[i] = a.d[i] - b.d[i];
+  return r;
+}
+template <class S, int K>
+PTN_HD Dual<S, K> operator-(const Dual<S, K>& a) {
+  Dual<S, K> r; r.v = -a.v;
+#pragma unroll
+  for (int i = 0; i < K; i++) r.d[i] = -a.d[i];
+  return r;
+}
+template <class S, int K>
+PTN_HD Dual<S, K> operator*(const Dual<S, K>& a, const Dual<S, K>& b) {
+  Dual<S, K> r; r.v = a.v * b.v;
+#pragma unroll
+  for (int i = 0; i < K; i++) r.d[i] = a.v * b.d[i] + a.d[i] * b.v;
+  return r;
+}
+template <class S, int K>
+PTN_HD Dual<S, K> operator*(S c, const Dual<S, K>& a) {
+  Dual<S, K> r; r.v = c * a.v;
+#pragma unroll
+  for (int i = 0; i < K; i++) r.d[i] = c * a.d[i];
+  return r;
+}
+template <class S, int K>
+PTN_HD Dual<S, K> operator+(S c, const Dual<S, K>& a) {
+  Dual<S, K> r = a; r.v = c + a.v; return r;
+}
+template <class S, int K>
+PTN_HD Dual<S, K> recip(const Dual<S, K>& a) {
+  Dual<S, K> r; S i = S(1) / a.v; r.v = i; S f = -i * i;
+#pragma unroll
+  for (int k = 0; k < K; k++) r.d[k] = f * a.d[k];
+  return r;
+}
+template <class S, int K>
+PTN_HD Dual<S, K> operator/(const Dual<S, K>& a, const Dual<S, K>& b) {
+  return a * recip(b);
+}
+PTN_HD void sc_(double a, double* s, double* c) { sincos(a, s, c); }
+PTN_HD void sc_(float a, float* s, float* c) { sincosf(a, s, c); }
+
+template <class S, int K>
+PTN_HD void sincos_ad(const Dual<S, K>& a, Dual<S, K>& s, Dual<S, K>& c) {
+  S sv, cv;
+  sc_(a.v, &sv, &cv);
+  s.v = sv; c.v = cv;
+#pragma unroll
+  for (int k = 0; k < K; k++) { s.d[k] = cv * a.d[k]; c.d[k] = -sv * a.d[k]; }
+}
+
+// value + K first partials + packed upper-triangular K x K second partials
+template <class S, int K>
+struct Jet {
+  static constexpr int H = K * (K + 1) / 2;
+  S v;
+  S d[K];
+  S h[H];
+  PTN_HD Jet() {}
+  PTN_HD Jet(S c) : v(c) {
+#pragma unroll
+    for (int i = 0; i < K; i++) d[i] = S(0);
+#pragma unroll
+    for (int i = 0; i < H; i++) h[i] = S(0);
+  }
+};
+template <int K>
+PTN_HD constexpr int hidx(int i, int j) {  // i <= j
+  return i * K - (i * (i - 1)) / 2 + (j - i);
+}
+template <class S, int K>
+PTN_HD Jet<S, K> operator+(const Jet<S, K>& a, const Jet<S, K>& b) {
+  Jet<S, K> r; r.v = a.v + b.v;
+#pragma unroll
+  for (int i = 0; i < K; i++) r.d[i] = a.d[i] + b.d[i];
+#pragma unroll (K <= 8 ? Jet<S, K>::H : 4)
+  for (int i = 0; i < Jet<S, K>::H; i++) r.h[i] = a.h[i] + b.h[i];
+  return r;
+}
+template <class S, int K>
+PTN_HD Jet<S, K> operator-(const Jet<S, K>& a, const Jet<S, K>& b) {
+  Jet<S, K> r; r.v = a.v - b.v;
+#pragma unroll
+  for (int i = 0; i < K; i++) r.d[i] = a.d[i] - b.d[i];
+#pragma unroll (K <= 8 ? Jet<S, K>::H : 4)
+  for (int i = 0; i < Jet<S, K>::H; i++) r.h[i] = a.h[i] - b.h[i];
+  return r;
+}
+template <class S, int K>
+PTN_HD Jet<S, K> operator-(const Jet<S, K>& a) {
+  Jet<S, K> r; r.v = -a.v;
+#pragma unroll
+  for (int i = 0; i < K; i++) r.d[i] = -a.d[i];
+#pragma unroll (K <= 8 ? Jet<S, K>::H : 4)
+  for (int i = 0; i < Jet<S, K>::H; i++) r.h[i] = -a.h[i];
+  return r;
+}
+template <class S, int K>
+PTN_HD Jet<S, K> operator*(const Jet<S, K>& a, const Jet<S, K>& b) {
+  Jet<S, K> r; r.v = a.v * b.v;
+  if constexpr (K <= 8) {
+#pragma unroll
+    for (int i = 0; i < K; i++) r.d[i] = a.v * b.d[i] + a.d[i] * b.v;
+#pragma unroll
+    for (int i = 0; i < K; i++)
+#pragma unroll
+      for (int j = i; j < K; j++) {
+        const int q = hidx<K>(i, j);
+        r.h[q] = a.v * b.h[q] + a.h[q] * b.v + a.d[i] * b.d[j] + a.d[j] * b.d[i];
+      }
+  } else {
+#pragma unroll 4
+    for (int i = 0; i < K; i++) r.d[i] = a.v * b.d[i] + a.d[i] * b.v;
+    int q = 0;
+#pragma unroll 1
+    for (int i = 0; i < K; i++)
+#pragma unroll 2
+      for (int j = i; j < K; j++, q++)
+        r.h[q] = a.v * b.h[q] + a.h[q] * b.v + a.d[i] * b.d[j] + a.d[j] * b.d[i];
+  }
+  return r;
+}
+template <class S, int K>
+PTN_HD Jet<S, K> operator*(S c, const Jet<S, K>& a) {
+  Jet<S, K> r; r.v = c * a.v;
+#pragma unroll
+  for (int i = 0; i < K; i++) r.d[i] = c * a.d[i];
+#pragma unroll (K <= 8 ? Jet<S, K>::H : 4)
+  for (int i = 0; i < Jet<S, K>::H; i++) r.h[i] = c * a.h[i];
+  return r;
+}
+template <class S, int K>
+PTN_HD Jet<S, K> operator+(S c, const Jet<S, K>& a) {
+  Jet<S, K> r = a; r.v = c + a.v; return r;
+}
+// chain rule for a scalar function with value f0, first derivative f1, second f2
+template <class S, int K>
+PTN_HD Jet<S, K> jfun(const Jet<S, K>& a, S f0, S f1, S f2) {
+  Jet<S, K> r; r.v = f0;
+  if constexpr (K <= 8) {
+#pragma unroll
+    for (int i = 0; i < K; i++) r.d[i] = f1 * a.d[i];
+#pragma unroll
+    for (int i = 0; i < K; i++)
+#pragma unroll
+      for (int j = i; j < K; j++) {
+        const int q = hidx<K>(i, j);
+        r.h[q] = f1 * a.h[q] + f2 * a.d[i] * a.d[j];
+      }
+  } else {
+#pragma unroll 4
+    for (int i = 0; i < K; i++) r.d[i] = f1 * a.d[i];
+    int q = 0;
+#pragma unroll 1
+    for (int i = 0; i < K; i++)
+#pragma unroll 2
+      for (int j = i; j < K; j++, q++) r.h[q] = f1 * a.h[q] + f2 * a.d[i] * a.d[j];
+  }
+  return r;
+}
+template <class S, int K>
+PTN_HD Jet<S, K> recip(const Jet<S, K>& a) {
+  S i = S(1) / a.v;
+  return jfun(a, i, -i * i, S(2) * i * i * i);
+}
+template <class S, int K>
+PTN_HD Jet<S, K> operator/(const Jet<S, K>& a, const Jet<S, K>& b) {
+  return a * recip(b);
+}
+template <class S, int K>
+PTN_HD void sincos_ad(const Jet<S, K>& a, Jet<S, K>& s, Jet<S, K>& c) {
+  S sv, cv;
+  sc_(a.v, &sv, &cv);
+  s = jfun(a, sv, cv, -sv);
+  c = jfun(a, cv, -sv, -cv);
+}
+
+// plain scalars share the same interface
+PTN_HD void sincos_ad(double a, double& s, double& c) { sincos(a, &s, &c); }
+PTN_HD void sincos_ad(float a, float& s, float& c) { sincosf(a, &s, &c); }
+PTN_HD double recip(double a) { return 1.0 / a; }
+PTN_HD float recip(float a) { return 1.0f / a; }
+
+// base scalar of an AD type, and products/sums with a double constant
+template <class S> struct base_of { using type = S; };
+template <class S, int K> struct base_of<Dual<S, K>> { using type = S; };
+template <class S, int K> struct base_of<Jet<S, K>> { using type = S; };
+template <class S>
+PTN_HD S cmul(double c, const S& a) {
+  using B = typename base_of<S>::type;
+  return B(c) * a;
+}
+template <class S>
+PTN_HD S cadd(double c, const S& a) {
+  using B = typename base_of<S>::type;
+  return B(c) + a;
+}
+template <class S>
+PTN_HD S cst(double c) {
+  using B = typename base_of<S>::type;
+  return S(B(c));
+}
+
+}  // namespace ptn

@@ -1,0 +1,259 @@
+// ptn_group.cuh -- collectives for the thread group that solves one instance.
+//
+// A group is either one CTA (CtaGroup: batches of instances, one per block) or the
+// whole cooperative grid (GridGroup: one long-horizon instance across all SMs).
+// Each group thread owns a contiguous chunk of time steps; the scans of the three
+// passes combine the chunks' aggregates across the group with these collectives:
+//
+//   reduce<K>(v, maxmask)      sums / maxima of K doubles, identical in every thread
+//   scan(v, op, suffix, ok)    exclusive prefix (or suffix) combination of the
+//                              threads' elements in time order, op(a, b, out) meaning
+//                              "a is earlier than b"
+//
+// Warp level: Kogge-Stone over shuffles.  Block level: warp totals in shared memory.
+// Grid level: block totals in global memory behind a grid barrier whose wait is
+// bounded (spin_limit); on expiry the group records ST_ETIMEOUT and stops.
+#pragma once
+#include "ptn_ops.cuh"
+
+namespace ptn {
+
+#define PTN_FULL 0xffffffffu
+
+template <class E>
+__device__ __forceinline__ E shfl_up_e(const E& e, int delta) {
+  static_assert(sizeof(E) % 4 == 0, "element must be a multiple of 4 bytes");
+  E r;
+  const unsigned* s = reinterpret_cast<const unsigned*>(&e);
+  unsigned* d = reinterpret_cast<unsigned*>(&r);
+#pragma unroll
+  for (int i = 0; i < (int)(sizeof(E) / 4); i++) d[i] = __shfl_up_sync(PTN_FULL, s[i], delta);
+  return r;
+}
+template <class E>
+__device__ __forceinline__ E shfl_down_e(const E& e, int delta) {
+  E r;
+  const unsigned* s = reinterpret_cast<const unsigned*>(&e);
+  unsigned* d = reinterpret_cast<unsigned*>(&r);
+#pragma unroll
+  for (int i = 0; i < (int)(sizeof(E) / 4); i++) d[i] = __shfl_down_sync(PTN_FULL, s[i], delta);
+  return r;
+}
+
+// Block-level exclusive scan.  Writes the block total (all elements of the block
+// combined in time order) into *total (shared memory) and returns each thread's
+// exclusive result.  Needs blockDim.x / 32 elements of shared scratch at sw.
+template <class E, class Op>
+__device__ E block_scan_excl(E v, const Op& op, bool suffix, bool& ok, E* sw, E* total) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll 1
+  for (int off = 1; off < 32; off <<= 1) {
+    if (!suffix) {
+      E o = shfl_up_e(v, off);
+      if (lane >= off) ok &= op(o, v, v);
+    } else {
+      E o = shfl_down_e(v, off);
+      if (lane + off < 32) ok &= op(v, o, v);
+    }
+  }
+  E ex = suffix ? shfl_down_e(v, 1) : shfl_up_e(v, 1);
+  if ((!suffix && lane == 0) || (suffix && lane == 31)) set_identity(ex);
+  __syncthreads();
+  if ((!suffix && lane == 31) || (suffix && lane == 0)) sw[w] = v;
+  __syncthreads();
+  if (!suffix) {
+    if (w > 0) {
+      E wt = sw[0];
+#pragma unroll 1
+      for (int i = 1; i < w; i++) ok &= op(wt, sw[i], wt);
+      ok &= op(wt, ex, ex);
+    }
+  } else {
+    if (w < nw - 1) {
+      E wt = sw[nw - 1];
+#pragma unroll 1
+      for (int i = nw - 2; i > w; i--) ok &= op(sw[i], wt, wt);
+      ok &= op(ex, wt, ex);
+    }
+  }
+  if (total) {
+    // block total: the fold of all warp totals in time order, by thread 0
+    if (threadIdx.x == 0) {
+      E t = sw[0];
+#pragma unroll 1
+      for (int i = 1; i < nw; i++) ok &= op(t, sw[i], t);
+      *total = t;
+    }
+  }
+  __syncthreads();
+  return ex;
+}
+
+// ---------------------------------------------------------------------------
+struct CtaGroup {
+  char* sm;  // shared scratch (>= max(nwarps * sizeof(element)+sizeof(element), nwarps*8*K))
+
+  __device__ int rank() const { return threadIdx.x; }
+  __device__ int size() const { return blockDim.x; }
+  __device__ void sync() { __syncthreads(); }
+  __device__ bool dead() const { return false; }
+
+  template <int K>
+  __device__ void reduce(double (&v)[K], unsigned maxmask) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    double* s = reinterpret_cast<double*>(sm);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+      for (int k = 0; k < K; k++) {
+        double o = __shfl_xor_sync(PTN_FULL, v[k], off);
+        v[k] = ((maxmask >> k) & 1u) ? fmax(v[k], o) : v[k] + o;
+      }
+    __syncthreads();
+    if (lane == 0)
+#pragma unroll
+      for (int k = 0; k < K; k++) s[w * K + k] = v[k];
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < K; k++) {
+      double a = s[k];
+      for (int i = 1; i < nw; i++) a = ((maxmask >> k) & 1u) ? fmax(a, s[i * K + k]) : a + s[i * K + k];
+      v[k] = a;
+    }
+    __syncthreads();
+  }
+
+  template <class E, class Op>
+  __device__ E scan(E v, const Op& op, bool suffix, bool& ok) {
+    return block_scan_excl(v, op, suffix, ok, reinterpret_cast<E*>(sm), (E*)nullptr);
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Grid group: all blocks of a cooperative launch work on one instance.
+struct GridScratch {
+  unsigned* bar;      // [0] arrivals, [1] generation
+  int* err;           // error word (ST_ETIMEOUT on an expired wait)
+  double* red;        // 2 x nblocks x 8 doubles
+  char* xs;           // 2 x nblocks x elem_bytes
+  long long spin_limit;
+  int elem_bytes;
+  int pad;
+};
+
+__device__ __forceinline__ bool grid_barrier(const GridScratch& gs) {
+  volatile unsigned* gen = gs.bar + 1;
+  const unsigned g0 = *gen;
+  __threadfence();
+  const unsigned arrived = atomicAdd(gs.bar, 1u);
+  if (arrived == gridDim.x - 1) {
+    atomicExch(gs.bar, 0u);
+    __threadfence();
+    atomicAdd(gs.bar + 1, 1u);
+    return true;
+  }
+  long long n = 0;
+  while (*gen == g0) {
+    if (++n > gs.spin_limit) {
+      atomicExch(gs.err, ST_ETIMEOUT);
+      return false;
+    }
+    __nanosleep(64);
+  }
+  __threadfence();
+  return true;
+}
+
+struct GridGroup {
+  char* sm;
+  GridScratch gs;
+  int phase;
+  int* sdead;  // shared flag: this block saw a barrier expire
+
+  __device__ int rank() const { return blockIdx.x * blockDim.x + threadIdx.x; }
+  __device__ int size() const { return gridDim.x * blockDim.x; }
+  __device__ bool dead() const { return *(volatile int*)sdead != 0; }
+
+  __device__ void sync() {
+    __syncthreads();
+    if (threadIdx.x == 0 && !*sdead) {
+      if (!grid_barrier(gs)) *sdead = 1;
+    }
+    __syncthreads();
+  }
+
+  template <int K>
+  __device__ void reduce(double (&v)[K], unsigned maxmask) {
+    static_assert(K <= 8, "at most 8 values per reduction");
+    CtaGroup cg{sm};
+    cg.reduce<K>(v, maxmask);
+    double* slot = gs.red + (size_t)phase * gridDim.x * 8;
+    if (threadIdx.x == 0)
+#pragma unroll
+      for (int k = 0; k < K; k++) slot[blockIdx.x * 8 + k] = v[k];
+    sync();
+#pragma unroll
+    for (int k = 0; k < K; k++) {
+      double a = ((volatile double*)slot)[k];
+      for (int i = 1; i < (int)gridDim.x; i++) {
+        const double o = ((volatile double*)slot)[i * 8 + k];
+        a = ((maxmask >> k) & 1u) ? fmax(a, o) : a + o;
+      }
+      v[k] = a;
+    }
+    phase ^= 1;
+  }
+
+  template <class E, class Op>
+  __device__ E scan(E v, const Op& op, bool suffix, bool& ok) {
+    const int nw = blockDim.x >> 5;
+    E* sw = reinterpret_cast<E*>(sm);
+    E* stot = sw + nw;      // block total
+    E* scarry = sw + nw + 1;  // carry from other blocks
+    E ex = block_scan_excl(v, op, suffix, ok, sw, stot);
+    E* slot = reinterpret_cast<E*>(gs.xs + (size_t)phase * gridDim.x * gs.elem_bytes);
+    if (threadIdx.x == 0) *reinterpret_cast<E*>(reinterpret_cast<char*>(slot) + (size_t)blockIdx.x * gs.elem_bytes) = *stot;
+    sync();
+    // carry = fold of the totals of the blocks before (prefix) or after (suffix) this one,
+    // computed by warp 0: each lane folds a contiguous range, then an ordered tree.
+    if (threadIdx.x < 32) {
+      const int lane = threadIdx.x;
+      const int lo = suffix ? blockIdx.x + 1 : 0;
+      const int hi = suffix ? gridDim.x : blockIdx.x;
+      const int cnt = hi - lo;
+      const int per = (cnt + 31) / 32;
+      E acc;
+      set_identity(acc);
+      const int b0 = lo + lane * per;
+      const int b1 = min(hi, b0 + per);
+      for (int b = b0; b < b1; b++) {
+        E t;
+        const char* src = reinterpret_cast<const char*>(slot) + (size_t)b * gs.elem_bytes;
+        // volatile-free copy through L2 (written before the barrier by another block)
+        const unsigned* s4 = reinterpret_cast<const unsigned*>(src);
+        unsigned* d4 = reinterpret_cast<unsigned*>(&t);
+#pragma unroll
+        for (int i = 0; i < (int)(sizeof(E) / 4); i++) d4[i] = __ldcg(s4 + i);
+        if (b == b0) acc = t;
+        else ok &= op(acc, t, acc);
+      }
+#pragma unroll 1
+      for (int off = 1; off < 32; off <<= 1) {
+        E o = shfl_down_e(acc, off);
+        if ((lane & (2 * off - 1)) == 0 && lane + off < 32) ok &= op(acc, o, acc);
+      }
+      if (lane == 0) *scarry = acc;
+    }
+    __syncthreads();
+    if (!suffix) {
+      if (blockIdx.x > 0) ok &= op(*scarry, ex, ex);
+    } else {
+      if (blockIdx.x + 1 < gridDim.x) ok &= op(ex, *scarry, ex);
+    }
+    __syncthreads();
+    phase ^= 1;
+    return ex;
+  }
+};
+
+}  // namespace ptn

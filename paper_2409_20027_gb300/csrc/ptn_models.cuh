@@ -1,0 +1,193 @@
+// ptn_models.cuh -- dynamics of the paper's examples (Sec. IV) and the benchmark
+// workloads, written once as templates over the scalar type so that plain values,
+// Jacobians (Dual) and second-order contractions (Jet) come from the same code.
+//
+//   pendulum  (Sec. IV-A): theta'' = -(g/l) sin(theta) - b/(m l^2) theta' + u/(m l^2)
+//   cart-pole (Sec. IV-B): Tedrake's equations with the l*theta'^2 term in p''
+//   quadrotor: 12-state rigid body, ZYX Euler angles, '+' rotor layout
+//   synthetic: x+ = A x + B u + c tanh(W x)
+#pragma once
+#include "ptn_common.cuh"
+
+namespace ptn {
+
+enum : int { MODEL_PENDULUM = 0, MODEL_CARTPOLE = 1, MODEL_QUADROTOR = 2, MODEL_SYNTH = 3 };
+enum : int { INTEG_EULER = 0, INTEG_RK4 = 1 };
+
+// prm = [g, l, m, b]; x = (theta, omega)
+struct Pendulum {
+  static constexpr int NX = 2, NU = 1, ID = MODEL_PENDULUM;
+  template <class S>
+  PTN_HD static void rhs(const double* p, const S* x, const S* u, S* xd) {
+    const double g = p[0], l = p[1], m = p[2], b = p[3];
+    const double iml2 = 1.0 / (m * l * l);
+    S s, c;
+    sincos_ad(x[0], s, c);
+    xd[0] = x[1];
+    xd[1] = cmul(-g / l, s) + cmul(-b * iml2, x[1]) + cmul(iml2, u[0]);
+  }
+};
+
+// prm = [m_c, m_p, l, g]; x = (p, theta, p', theta'), theta = 0 hanging down
+struct CartPole {
+  static constexpr int NX = 4, NU = 1, ID = MODEL_CARTPOLE;
+  template <class S>
+  PTN_HD static void rhs(const double* p, const S* x, const S* u, S* xd) {
+    const double mc = p[0], mp = p[1], l = p[2], g = p[3];
+    S s, c;
+    sincos_ad(x[1], s, c);
+    const S td2 = x[3] * x[3];
+    const S den = cadd(mc, cmul(mp, s * s));
+    const S iden = recip(den);
+    const S pdd = (u[0] + cmul(mp, s) * (cmul(l, td2) + cmul(g, c))) * iden;
+    const S num = -(u[0] * c) - cmul(mp * l, td2 * c * s) - cmul((mc + mp) * g, s);
+    const S tdd = cmul(1.0 / l, num * iden);
+    xd[0] = x[2];
+    xd[1] = x[3];
+    xd[2] = pdd;
+    xd[3] = tdd;
+  }
+};
+
+// prm = [mass, Ixx, Iyy, Izz, arm, k_m, g];
+// x = (px,py,pz, roll,pitch,yaw, vx,vy,vz, wx,wy,wz); u = rotor thrusts 1..4
+// rotor 1 on +x, 2 on +y, 3 on -x, 4 on -y; yaw torque k_m (f1 - f2 + f3 - f4)
+struct Quadrotor {
+  static constexpr int NX = 12, NU = 4, ID = MODEL_QUADROTOR;
+  template <class S>
+  PTN_HD static void rhs(const double* p, const S* x, const S* u, S* xd) {
+    const double mass = p[0], Ixx = p[1], Iyy = p[2], Izz = p[3], arm = p[4], km = p[5], g = p[6];
+    S sph, cph, sth, cth, sps, cps;
+    sincos_ad(x[3], sph, cph);
+    sincos_ad(x[4], sth, cth);
+    sincos_ad(x[5], sps, cps);
+    const S icth = recip(cth);
+    const S tth = sth * icth;
+    const S fsum = (u[0] + u[1]) + (u[2] + u[3]);
+    const S am = cmul(1.0 / mass, fsum);
+    // body z axis in the world frame (third column of Rz Ry Rx)
+    const S r13 = cps * (sth * cph) + sps * sph;
+    const S r23 = sps * (sth * cph) - cps * sph;
+    const S r33 = cth * cph;
+    xd[0] = x[6];
+    xd[1] = x[7];
+    xd[2] = x[8];
+    xd[3] = x[9] + (sph * tth) * x[10] + (cph * tth) * x[11];
+    xd[4] = cph * x[10] - sph * x[11];
+    xd[5] = (sph * x[10] + cph * x[11]) * icth;
+    xd[6] = am * r13;
+    xd[7] = am * r23;
+    xd[8] = cadd(-g, am * r33);
+    const S tx = cmul(arm, u[1] - u[3]);
+    const S ty = cmul(arm, u[2] - u[0]);
+    const S tz = cmul(km, (u[0] + u[2]) - (u[1] + u[3]));
+    xd[9] = cmul(1.0 / Ixx, tx - cmul(Izz - Iyy, x[10] * x[11]));
+    xd[10] = cmul(1.0 / Iyy, ty - cmul(Ixx - Izz, x[11] * x[9]));
+    xd[11] = cmul(1.0 / Izz, tz - cmul(Iyy - Ixx, x[9] * x[10]));
+  }
+};
+
+// One discrete step x+ = f(x, u): explicit Euler or classical RK4 with the control
+// held over the step.
+template <class M, class S>
+PTN_HD void step(int integ, double dt, const double* p, const S* x, const S* u, S* xn) {
+  constexpr int N = M::NX;
+  if (integ == INTEG_EULER) {
+    S k[N];
+    M::rhs(p, x, u, k);
+#pragma unroll
+    for (int i = 0; i < N; i++) xn[i] = x[i] + cmul(dt, k[i]);
+    return;
+  }
+  S k[N], acc[N], y[N];
+  M::rhs(p, x, u, k);
+#pragma unroll
+  for (int i = 0; i < N; i++) { acc[i] = k[i]; y[i] = x[i] + cmul(0.5 * dt, k[i]); }
+  M::rhs(p, y, u, k);
+#pragma unroll
+  for (int i = 0; i < N; i++) { acc[i] = acc[i] + cmul(2.0, k[i]); y[i] = x[i] + cmul(0.5 * dt, k[i]); }
+  M::rhs(p, y, u, k);
+#pragma unroll
+  for (int i = 0; i < N; i++) { acc[i] = acc[i] + cmul(2.0, k[i]); y[i] = x[i] + cmul(dt, k[i]); }
+  M::rhs(p, y, u, k);
+#pragma unroll
+  for (int i = 0; i < N; i++) xn[i] = x[i] + cmul(dt / 6.0, acc[i] + k[i]);
+}
+
+// F = df/dx (NX x NX), G = df/du (NX x NU), by forward-mode AD in scalar S.
+template <class M, class S>
+PTN_HD void step_jac(int integ, double dt, const double* p, const double* x, const double* u,
+                     S* fx, S* F, S* G) {
+  constexpr int N = M::NX, U = M::NU, K = N + U;
+  using D = Dual<S, K>;
+  D xd[N], ud[U], xn[N];
+#pragma unroll
+  for (int i = 0; i < N; i++) { xd[i] = D(S(x[i])); xd[i].d[i] = S(1); }
+#pragma unroll
+  for (int i = 0; i < U; i++) { ud[i] = D(S(u[i])); ud[i].d[N + i] = S(1); }
+  step<M>(integ, dt, p, xd, ud, xn);
+#pragma unroll
+  for (int i = 0; i < N; i++) {
+    if (fx) fx[i] = xn[i].v;
+#pragma unroll
+    for (int j = 0; j < N; j++) F[i * N + j] = xn[i].d[j];
+#pragma unroll
+    for (int j = 0; j < U; j++) G[i * U + j] = xn[i].d[N + j];
+  }
+}
+
+// Second-order contraction lam . f_zz (Sec. III-C): Hxx, Hxu, Huu in scalar S.
+template <class M, class S>
+PTN_HD void step_hess(int integ, double dt, const double* p, const double* x, const double* u,
+                      const double* lam, S* Hxx, S* Hxu, S* Huu) {
+  constexpr int N = M::NX, U = M::NU, K = N + U;
+  using J = Jet<S, K>;
+  J xd[N], ud[U], xn[N];
+#pragma unroll
+  for (int i = 0; i < N; i++) { xd[i] = J(S(x[i])); xd[i].d[i] = S(1); }
+#pragma unroll
+  for (int i = 0; i < U; i++) { ud[i] = J(S(u[i])); ud[i].d[N + i] = S(1); }
+  step<M>(integ, dt, p, xd, ud, xn);
+  S h[J::H];
+#pragma unroll (K <= 8 ? J::H : 2)
+  for (int q = 0; q < J::H; q++) {
+    S s = S(0);
+#pragma unroll (K <= 8 ? N : 4)
+    for (int k = 0; k < N; k++) s += S(lam[k]) * xn[k].h[q];
+    h[q] = s;
+  }
+#pragma unroll
+  for (int i = 0; i < K; i++)
+#pragma unroll
+    for (int j = i; j < K; j++) {
+      const S v = h[hidx<K>(i, j)];
+      if (j < N) { Hxx[i * N + j] = v; Hxx[j * N + i] = v; }
+      else if (i < N) Hxu[i * U + (j - N)] = v;
+      else { Huu[(i - N) * U + (j - N)] = v; Huu[(j - N) * U + (i - N)] = v; }
+    }
+}
+
+// Closed-loop Jacobian of x+ = f(x, ub + Gam (x - xh)) with respect to x at (x, u):
+// Fcl = F + G Gam, computed by forward mode with seeds (e_i, Gam e_i).
+template <class M, class S>
+PTN_HD void step_cl_jac(int integ, double dt, const double* p, const double* x, const double* u,
+                        const S* Gam, S* Fcl) {
+  constexpr int N = M::NX, U = M::NU;
+  using D = Dual<S, N>;
+  D xd[N], ud[U], xn[N];
+#pragma unroll
+  for (int i = 0; i < N; i++) { xd[i] = D(S(x[i])); xd[i].d[i] = S(1); }
+#pragma unroll
+  for (int i = 0; i < U; i++) {
+    ud[i] = D(S(u[i]));
+#pragma unroll
+    for (int j = 0; j < N; j++) ud[i].d[j] = Gam[i * N + j];
+  }
+  step<M>(integ, dt, p, xd, ud, xn);
+#pragma unroll
+  for (int i = 0; i < N; i++)
+#pragma unroll
+    for (int j = 0; j < N; j++) Fcl[i * N + j] = xn[i].d[j];
+}
+
+}  // namespace ptn

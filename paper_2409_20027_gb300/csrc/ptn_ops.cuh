@@ -1,0 +1,270 @@
+// ptn_ops.cuh -- associative elements and operators of the three scans of the
+// parallel-in-time Newton step (arXiv 2409.20027, Sec. III), in register arrays.
+//
+//   co-state pass (Alg. 1): element (g, F^T), operator eq. co-states-comb-rule
+//   value pass    (Alg. 2): element (A, b, C, eta, J), operator eq. value-fun-param,
+//                           initialisation eq. value-fun-elem-init
+//   state pass    (Alg. 3): element (F, e), operator eq. state-prop-comb-rule
+//
+// "a then b" always means a covers the earlier time interval.
+#pragma once
+#include "ptn_common.cuh"
+
+namespace ptn {
+
+// affine map (matrix part M, vector part v)
+template <int N, class S>
+struct Aff {
+  S M[N * N];
+  S v[N];
+};
+
+template <int N, class S>
+PTN_HD void set_identity(Aff<N, S>& e) {
+#pragma unroll
+  for (int i = 0; i < N * N; i++) e.M[i] = S(0);
+#pragma unroll
+  for (int i = 0; i < N; i++) { e.M[i * N + i] = S(1); e.v[i] = S(0); }
+}
+
+// Co-state operator, M holds F^T:  v = a.v + a.M b.v,  M = a.M b.M.
+struct CostateOp {
+  template <int N, class S>
+  PTN_HD bool operator()(const Aff<N, S>& a, const Aff<N, S>& b, Aff<N, S>& o) const {
+    Aff<N, S> r;
+    mm<N, N, N>(a.M, b.M, r.M);
+    mv<N, N>(a.M, b.v, r.v);
+#pragma unroll
+    for (int i = 0; i < N; i++) r.v[i] += a.v[i];
+    o = r;
+    return true;
+  }
+};
+
+// State-propagation operator:  M = b.M a.M,  v = b.M a.v + b.v.
+struct StateOp {
+  template <int N, class S>
+  PTN_HD bool operator()(const Aff<N, S>& a, const Aff<N, S>& b, Aff<N, S>& o) const {
+    Aff<N, S> r;
+    mm<N, N, N>(b.M, a.M, r.M);
+    mv<N, N>(b.M, a.v, r.v);
+#pragma unroll
+    for (int i = 0; i < N; i++) r.v[i] += b.v[i];
+    o = r;
+    return true;
+  }
+};
+
+// value-function element; the paper's Y is stored as J
+template <int N, class L>
+struct Val {
+  L A[N * N];
+  L C[N * N];
+  L J[N * N];
+  L eta[N];
+  L b[N];
+};
+
+template <int N, class L>
+PTN_HD void set_identity(Val<N, L>& e) {
+#pragma unroll
+  for (int i = 0; i < N * N; i++) { e.A[i] = L(0); e.C[i] = L(0); e.J[i] = L(0); }
+#pragma unroll
+  for (int i = 0; i < N; i++) { e.A[i * N + i] = L(1); e.eta[i] = L(0); e.b[i] = L(0); }
+}
+
+template <int N, class L>
+PTN_HD void symmetrize(L* X) {
+#pragma unroll
+  for (int i = 0; i < N; i++)
+#pragma unroll
+    for (int j = i + 1; j < N; j++) {
+      L s = L(0.5) * (X[i * N + j] + X[j * N + i]);
+      X[i * N + j] = s;
+      X[j * N + i] = s;
+    }
+}
+
+// Value operator (eq. value-fun-param, with b_{t,i} as the last term of b):
+//   A   = A2 K A1,                 K = (I + C1 J2)^{-1}
+//   C   = A2 K C1 A2^T + C2
+//   b   = A2 K (b1 + C1 eta2) + b2
+//   J   = A1^T K^T J2 A1 + J1      K^T = (I + J2 C1)^{-1} since C, J are symmetric
+//   eta = A1^T K^T (eta2 - J2 b1) + eta1
+// I + C1 J2 is formed and inverted in FP64; the products run in L.
+// Returns false when I + C1 J2 is singular.
+struct ValueOp {
+  template <int N, class L>
+  PTN_HD bool operator()(const Val<N, L>& e1, const Val<N, L>& e2, Val<N, L>& o) const {
+    double Md[N * N];
+    mm<N, N, N>(e1.C, e2.J, Md);
+#pragma unroll
+    for (int i = 0; i < N; i++) Md[i * N + i] += 1.0;
+    if (!inv_gj<N>(Md)) return false;
+    L K[N * N];
+#pragma unroll
+    for (int i = 0; i < N * N; i++) K[i] = L(Md[i]);
+    Val<N, L> r;
+    L t1[N * N], t2[N * N], w[N], tv[N];
+    // A and C
+    mm<N, N, N>(K, e1.A, t1);
+    mm<N, N, N>(e2.A, t1, r.A);
+    mm<N, N, N>(K, e1.C, t1);
+    mm<N, N, N>(e2.A, t1, t2);
+    mmt<N, N, N>(t2, e2.A, r.C);
+#pragma unroll
+    for (int i = 0; i < N * N; i++) r.C[i] += e2.C[i];
+    // b
+    mv<N, N>(e1.C, e2.eta, w);
+#pragma unroll
+    for (int i = 0; i < N; i++) w[i] += e1.b[i];
+    mv<N, N>(K, w, tv);
+    mv<N, N>(e2.A, tv, r.b);
+#pragma unroll
+    for (int i = 0; i < N; i++) r.b[i] += e2.b[i];
+    // J
+    mm<N, N, N>(e2.J, e1.A, t1);
+    mtm<N, N, N>(K, t1, t2);
+    mtm<N, N, N>(e1.A, t2, r.J);
+#pragma unroll
+    for (int i = 0; i < N * N; i++) r.J[i] += e1.J[i];
+    // eta
+    mv<N, N>(e2.J, e1.b, w);
+#pragma unroll
+    for (int i = 0; i < N; i++) w[i] = e2.eta[i] - w[i];
+    mtv<N, N>(K, w, tv);
+    mtv<N, N>(e1.A, tv, r.eta);
+#pragma unroll
+    for (int i = 0; i < N; i++) r.eta[i] += e1.eta[i];
+    symmetrize<N>(r.C);
+    symmetrize<N>(r.J);
+    o = r;
+    return true;
+  }
+};
+
+// Element initialisation eq. value-fun-elem-init in the P^{-1}-free form
+//   A = F - G R~^{-1} M^T, J = P - M R~^{-1} M^T, C = G R~^{-1} G^T,
+//   eta = M R~^{-1} d, b = -G R~^{-1} d,  R~ = R + alpha I,
+// identical to the printed q_t, r_t form whenever P_t is invertible.
+// Returns false when R~ is not positive definite (FP64 Cholesky).
+template <int N, int U, class L, class TF, class TP>
+PTN_HD bool value_init(const TF* F, const TF* G, const TP* Pm, const TP* Mm, const TP* Rm,
+                       const double* d, double alpha, Val<N, L>& e) {
+  constexpr int C = 2 * N + 1;
+  double Rt[U * U], X[U * C];
+#pragma unroll
+  for (int i = 0; i < U * U; i++) Rt[i] = double(Rm[i]);
+#pragma unroll
+  for (int i = 0; i < U; i++) Rt[i * U + i] += alpha;
+  if (!chol<U>(Rt)) return false;
+#pragma unroll
+  for (int i = 0; i < U; i++) {
+#pragma unroll
+    for (int j = 0; j < N; j++) {
+      X[i * C + j] = double(Mm[j * U + i]);
+      X[i * C + N + j] = double(G[j * U + i]);
+    }
+    X[i * C + 2 * N] = d[i];
+  }
+  chol_solve<U, C>(Rt, X);
+#pragma unroll
+  for (int i = 0; i < N; i++) {
+#pragma unroll
+    for (int j = 0; j < N; j++) {
+      double gm = 0.0, mx = 0.0, gg = 0.0;
+#pragma unroll
+      for (int k = 0; k < U; k++) {
+        gm += double(G[i * U + k]) * X[k * C + j];
+        mx += double(Mm[i * U + k]) * X[k * C + j];
+        gg += double(G[i * U + k]) * X[k * C + N + j];
+      }
+      e.A[i * N + j] = L(double(F[i * N + j]) - gm);
+      e.J[i * N + j] = L(double(Pm[i * N + j]) - mx);
+      e.C[i * N + j] = L(gg);
+    }
+    double et = 0.0, bb = 0.0;
+#pragma unroll
+    for (int k = 0; k < U; k++) {
+      et += double(Mm[i * U + k]) * X[k * C + 2 * N];
+      bb += double(G[i * U + k]) * X[k * C + 2 * N];
+    }
+    e.eta[i] = L(et);
+    e.b[i] = L(-bb);
+  }
+  symmetrize<N>(e.J);
+  symmetrize<N>(e.C);
+  return true;
+}
+
+// Terminal element nu_{N+1}: J = P_{N+1}, all other parameters zero.
+template <int N, class L, class TP>
+PTN_HD void value_terminal(const TP* PT, Val<N, L>& e) {
+#pragma unroll
+  for (int i = 0; i < N * N; i++) { e.A[i] = L(0); e.C[i] = L(0); e.J[i] = L(PT[i]); }
+#pragma unroll
+  for (int i = 0; i < N; i++) { e.eta[i] = L(0); e.b[i] = L(0); }
+}
+
+// One backward Bellman step from V_{t+1} = (S, s) (eq. linearized-ocp-bellman): the
+// element nu_t applied to a boundary value function, written through the feedback law
+// eq. value-fun-feedback (reading: Q^{-1} M_t^T):
+//   Q = R~ + G^T S G,  Gam = -Q^{-1}(M^T + G^T S F),  gam = -Q^{-1}(d + G^T s),
+//   S_t = P + F^T S F + (M^T + G^T S F)^T Gam,  s_t = F^T s + (M^T + G^T S F)^T gam.
+// Q is factorised in FP64.  S, s are updated in place.  Returns false when Q is not PD.
+template <int N, int U, class L, class TF, class TP>
+PTN_HD bool riccati_step(const TF* F, const TF* G, const TP* Pm, const TP* Mm, const TP* Rm,
+                         const double* d, double alpha, L* S, L* s, L* Gam, L* gam) {
+  L SG[N * U], SF[N * N], Qux[U * N];
+  mm<N, N, U>(S, G, SG);
+  mm<N, N, N>(S, F, SF);
+  double Q[U * U], X[U * (N + 1)];
+#pragma unroll
+  for (int i = 0; i < U; i++)
+#pragma unroll
+    for (int j = 0; j < U; j++) {
+      double v = double(Rm[i * U + j]) + (i == j ? alpha : 0.0);
+#pragma unroll
+      for (int k = 0; k < N; k++) v += double(G[k * U + i]) * double(SG[k * U + j]);
+      Q[i * U + j] = v;
+    }
+  mtm<U, N, N>(G, SF, Qux);
+#pragma unroll
+  for (int i = 0; i < U; i++) {
+#pragma unroll (N <= 8 ? N : 4)
+    for (int j = 0; j < N; j++) {
+      Qux[i * N + j] += L(Mm[j * U + i]);
+      X[i * (N + 1) + j] = double(Qux[i * N + j]);
+    }
+    double q = d[i];
+#pragma unroll (N <= 8 ? N : 4)
+    for (int k = 0; k < N; k++) q += double(G[k * U + i]) * double(s[k]);
+    X[i * (N + 1) + N] = q;
+  }
+  if (!chol<U>(Q)) return false;
+  chol_solve<U, N + 1>(Q, X);
+#pragma unroll
+  for (int i = 0; i < U; i++) {
+#pragma unroll
+    for (int j = 0; j < N; j++) Gam[i * N + j] = L(-X[i * (N + 1) + j]);
+    gam[i] = L(-X[i * (N + 1) + N]);
+  }
+  L Sn[N * N], sn[N], FtSF[N * N], QG[N * N];
+  mtm<N, N, N>(F, SF, FtSF);
+  mtm<N, U, N>(Qux, Gam, QG);
+#pragma unroll (N <= 8 ? N * N : 4)
+  for (int i = 0; i < N * N; i++) Sn[i] = L(Pm[i]) + FtSF[i] + QG[i];
+  L Fts[N], Qg[N];
+  mtv<N, N>(F, s, Fts);
+  mtv<U, N>(Qux, gam, Qg);
+#pragma unroll
+  for (int i = 0; i < N; i++) sn[i] = Fts[i] + Qg[i];
+  symmetrize<N>(Sn);
+#pragma unroll
+  for (int i = 0; i < N * N; i++) S[i] = Sn[i];
+#pragma unroll
+  for (int i = 0; i < N; i++) s[i] = sn[i];
+  return true;
+}
+
+}  // namespace ptn

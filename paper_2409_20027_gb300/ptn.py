@@ -1,0 +1,233 @@
+"""Python binding of libptn.so (the C ABI in include/ptn.h).
+
+Argument marshalling only: every step of a solve runs in the CUDA library.  Device
+arrays are torch tensors (float64, contiguous, on the solver's device); the stream is
+torch's current stream unless given.  ``load()`` raises if the library is missing --
+there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libptn.so")
+
+PTN_FP64, PTN_FP32_FP64SOLVE = 0, 1
+METHOD_IP, METHOD_ADMM = 0, 1
+STATUS = {0: "ok", -1: "invalid argument", -2: "infeasible start", -3: "not converged",
+          -4: "numerical failure", -5: "device wait timed out", -6: "CUDA error"}
+
+EXPORTS = ["ptn_default_options", "ptn_solver_create", "ptn_solver_destroy", "ptn_last_error",
+           "ptn_set_options", "ptn_solve_ip", "ptn_solve_admm", "ptn_solve_batch", "ptn_adjoint",
+           "ptn_num_rows", "ptn_version"]
+
+_P = C.POINTER(C.c_double)
+
+
+class Problem(C.Structure):
+    _fields_ = [("model", C.c_int), ("nx", C.c_int), ("nu", C.c_int), ("integrator", C.c_int),
+                ("dt", C.c_double), ("prm", C.c_double * 8),
+                ("A", _P), ("B", _P), ("W", _P), ("Q", _P), ("R", _P), ("Qf", _P),
+                ("xref", _P), ("uref", _P), ("xlo", _P), ("xhi", _P), ("ulo", _P), ("uhi", _P)]
+
+
+_OPT_INTS = ["precision", "max_newton", "max_outer", "ls_count", "admm_fixed_iters", "roll_max_iter",
+             "block_threads", "grid_min_T", "grid_steps_per_thread", "pad"]
+_OPT_DBLS = ["mu0", "zeta", "mu_final", "tol_inner", "tol_final", "rho", "admm_tol", "alpha0",
+             "alpha_min", "alpha_max", "ls_beta", "armijo_c1", "armijo_eps", "roll_tol"]
+
+
+class Options(C.Structure):
+    _fields_ = [(k, C.c_int) for k in _OPT_INTS] + [(k, C.c_double) for k in _OPT_DBLS]
+
+
+class Info(C.Structure):
+    _fields_ = [(k, C.c_int) for k in ["status", "newton_iters", "outer_iters", "ls_rejects",
+                                       "factor_fails", "roll_fails", "roll_iters", "ls_evals"]] + \
+               [(k, C.c_double) for k in ["mu", "alpha", "r_stat", "r_dyn", "r_feas", "r_kkt", "J",
+                                          "J_c", "r_p", "r_d"]] + \
+               [("cycles", C.c_longlong * 6)]
+
+    def as_dict(self):
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k != "cycles"}
+        d["cycles"] = list(self.cycles)
+        return d
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libptn.so; raises OSError when it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise OSError(f"libptn.so not found at {path}: run paper_2409_20027_gb300.build.build()")
+        lib = C.CDLL(path)
+        vp, ip = C.c_void_p, C.POINTER(C.c_int)
+        lib.ptn_default_options.argtypes = [C.POINTER(Options)]
+        lib.ptn_solver_create.argtypes = [C.POINTER(Problem), C.POINTER(Options), C.c_int, C.c_int, C.POINTER(vp)]
+        lib.ptn_solver_destroy.argtypes = [vp]
+        lib.ptn_last_error.argtypes = [vp]
+        lib.ptn_last_error.restype = C.c_char_p
+        lib.ptn_set_options.argtypes = [vp, C.POINTER(Options)]
+        lib.ptn_solve_ip.argtypes = [vp, vp, vp, C.c_int, vp, vp, vp, C.POINTER(Info), vp]
+        lib.ptn_solve_admm.argtypes = [vp, vp, vp, C.c_int, vp, vp, vp, vp, vp, C.POINTER(Info), vp]
+        lib.ptn_solve_batch.argtypes = [vp, C.c_int, C.c_int, ip, vp, vp, vp, vp, vp, vp, C.POINTER(Info), vp]
+        lib.ptn_adjoint.argtypes = [vp, C.c_int, ip, vp, vp, vp, vp, C.c_double, C.c_double, vp, vp, vp, vp,
+                                    vp, vp, vp, vp]
+        lib.ptn_num_rows.argtypes = [vp]
+        lib.ptn_version.restype = C.c_char_p
+        _lib = lib
+    return _lib
+
+
+def default_options(**kw) -> Options:
+    o = Options()
+    load().ptn_default_options(C.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise KeyError(k)
+        setattr(o, k, v)
+    return o
+
+
+class PtnError(RuntimeError):
+    pass
+
+
+def _dptr(t):
+    """Device pointer of a contiguous float64 CUDA tensor (or None)."""
+    if t is None:
+        return None
+    import torch
+    if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise ValueError("expected a contiguous float64 CUDA tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return C.c_void_p(s.cuda_stream)
+
+
+class Solver:
+    """A solver handle for one problem (model, weights, bounds), owning its workspace."""
+
+    def __init__(self, prob, max_T: int, max_batch: int = 1, options: Options | None = None, **opt):
+        lib = load()
+        self._keep = []
+        P = Problem()
+        P.model, P.nx, P.nu, P.integrator = int(prob.model), int(prob.nx), int(prob.nu), int(prob.integrator)
+        P.dt = float(prob.dt)
+        prm = np.zeros(8)
+        prm[:len(prob.prm)] = prob.prm
+        for i in range(8):
+            P.prm[i] = prm[i]
+        for name in ["A", "B", "W", "Q", "R", "Qf", "xref", "uref", "xlo", "xhi", "ulo", "uhi"]:
+            v = getattr(prob, name, None)
+            if v is None:
+                setattr(P, name, None)
+            else:
+                a = np.ascontiguousarray(np.asarray(v, dtype=np.float64).ravel())
+                self._keep.append(a)
+                setattr(P, name, a.ctypes.data_as(_P))
+        self.options = options if options is not None else default_options(**opt)
+        h = C.c_void_p()
+        rc = lib.ptn_solver_create(C.byref(P), C.byref(self.options), int(max_T), int(max_batch), C.byref(h))
+        self._h = h
+        if rc != 0:
+            msg = lib.ptn_last_error(h).decode() if h.value else ""
+            lib.ptn_solver_destroy(h)
+            self._h = C.c_void_p()
+            raise PtnError(f"ptn_solver_create failed ({rc}): {msg}")
+        self.nx, self.nu = P.nx, P.nu
+        self.nw = lib.ptn_num_rows(h)
+        self.prob = prob
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().ptn_solver_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_options(self, **kw):
+        for k, v in kw.items():
+            setattr(self.options, k, v)
+        rc = load().ptn_set_options(self._h, C.byref(self.options))
+        if rc != 0:
+            raise PtnError(self.last_error())
+
+    def last_error(self) -> str:
+        return load().ptn_last_error(self._h).decode()
+
+    def _out(self, rows, cols, like):
+        import torch
+        return torch.empty((rows, cols), dtype=torch.float64, device=like.device)
+
+    def solve_ip(self, x0, T: int, u_init=None, x_out=None, u_out=None, lam_out=None, stream=None):
+        """IP solve (Sec. II-B).  Returns (x, u, lam, info dict)."""
+        x_out = self._out(T + 1, self.nx, x0) if x_out is None else x_out
+        u_out = self._out(T, self.nu, x0) if u_out is None else u_out
+        lam_out = self._out(T + 1, self.nx, x0) if lam_out is None else lam_out
+        info = Info()
+        load().ptn_solve_ip(self._h, _dptr(x0), _dptr(u_init), int(T), _dptr(x_out), _dptr(u_out),
+                            _dptr(lam_out), C.byref(info), _stream(stream))
+        return x_out, u_out, lam_out, info.as_dict()
+
+    def solve_admm(self, x0, T: int, u_init=None, stream=None, with_zv=False):
+        """ADMM solve (Sec. II-C).  Returns (x, u, lam, info) or with z, v."""
+        x = self._out(T + 1, self.nx, x0)
+        u = self._out(T, self.nu, x0)
+        lam = self._out(T + 1, self.nx, x0)
+        z = self._out(T, max(self.nw, 1), x0) if with_zv else None
+        v = self._out(T, max(self.nw, 1), x0) if with_zv else None
+        info = Info()
+        load().ptn_solve_admm(self._h, _dptr(x0), _dptr(u_init), int(T), _dptr(x), _dptr(u), _dptr(lam),
+                              _dptr(z), _dptr(v), C.byref(info), _stream(stream))
+        if with_zv:
+            return x, u, lam, z, v, info.as_dict()
+        return x, u, lam, info.as_dict()
+
+    def solve_batch(self, x0, T_b, xref=None, u_init=None, method: int = METHOD_IP, x_out=None, u_out=None,
+                    lam_out=None, stream=None):
+        """B instances in one launch.  x0: (B, nx) CUDA tensor, T_b: int sequence.
+        Returns (x, u, lam, infos) with concatenated trajectories."""
+        Tb = np.ascontiguousarray(np.asarray(T_b, dtype=np.int32))
+        B = len(Tb)
+        S = int(Tb.sum())
+        x_out = self._out(S + B, self.nx, x0) if x_out is None else x_out
+        u_out = self._out(S, self.nu, x0) if u_out is None else u_out
+        lam_out = self._out(S + B, self.nx, x0) if lam_out is None else lam_out
+        infos = (Info * B)()
+        load().ptn_solve_batch(self._h, int(method), B, Tb.ctypes.data_as(C.POINTER(C.c_int)), _dptr(x0),
+                               _dptr(xref), _dptr(u_init), _dptr(x_out), _dptr(u_out), _dptr(lam_out), infos,
+                               _stream(stream))
+        return x_out, u_out, lam_out, [i.as_dict() for i in infos]
+
+    def adjoint(self, T_b, x0, x_star, u_star, mu: float, gJ: float = 1.0, gx=None, gu=None, xref=None,
+                stream=None):
+        """Gradients of gJ J* + <gx, x*> + <gu, u*> w.r.t. x0, diag Q, diag R, diag Qf, prm."""
+        import torch
+        Tb = np.ascontiguousarray(np.asarray(T_b, dtype=np.int32))
+        B = len(Tb)
+        dev = x_star.device
+        out = {k: torch.zeros((B, c), dtype=torch.float64, device=dev)
+               for k, c in [("x0", self.nx), ("Qd", self.nx), ("Rd", self.nu), ("Qfd", self.nx), ("prm", 8)]}
+        rc = load().ptn_adjoint(self._h, B, Tb.ctypes.data_as(C.POINTER(C.c_int)), _dptr(x0), _dptr(xref),
+                                _dptr(x_star), _dptr(u_star), float(mu), float(gJ), _dptr(gx), _dptr(gu),
+                                _dptr(out["x0"]), _dptr(out["Qd"]), _dptr(out["Rd"]), _dptr(out["Qfd"]),
+                                _dptr(out["prm"]), _stream(stream))
+        if rc != 0:
+            raise PtnError(f"ptn_adjoint failed ({rc}): {self.last_error()}")
+        return out

@@ -72,17 +72,28 @@ def pendulum_x0(seed: int) -> np.ndarray:
 
 
 # ---------------------------------------------------------------- cart-pole
-def cartpole(T: int | None = None, dt: float = 0.01, horizon: float | None = None) -> Problem:
+CARTPOLE_DT = 0.01
+
+
+def cartpole(T: int | None = None, dt: float = CARTPOLE_DT, horizon: float | None = None) -> Problem:
     """Force-limited cart-pole: m_c=1, m_p=0.1, l=0.5, g=9.81, RK4 step.  State
     (p, theta, p', theta'), theta = pi upright.  Q=diag(1,10,0.1,0.1), R=0.01, Qf=100 Q,
-    target (0, pi, 0, 0), |u| <= 10, |p| <= 2.  With ``horizon`` the step is horizon/T
-    (fixed physical time, varying sampling rate, as in Sec. IV)."""
+    target (0, pi, 0, 0), |u| <= 10, |p| <= 2, all at dt = 0.01.
+
+    With ``horizon`` the step is horizon/T (fixed physical time, varying sampling rate,
+    as in Sec. IV) and the stage weights Q, R are scaled by dt/0.01 so that every T
+    discretises the same continuous-time cost (T = 256, horizon 2.56 s is the dt = 0.01
+    problem exactly)."""
+    Q = np.diag([1.0, 10.0, 0.1, 0.1])
+    R = np.array([[0.01]])
+    Qf = 100.0 * Q
     if horizon is not None:
         dt = horizon / T
-    Q = np.diag([1.0, 10.0, 0.1, 0.1])
+        Q = Q * (dt / CARTPOLE_DT)
+        R = R * (dt / CARTPOLE_DT)
     return Problem(model=CARTPOLE, nx=4, nu=1, dt=dt, integrator=RK4,
                    prm=_f([1.0, 0.1, 0.5, 9.81]),
-                   Q=Q, R=np.array([[0.01]]), Qf=100.0 * Q,
+                   Q=Q, R=R, Qf=Qf,
                    xref=_f([0.0, np.pi, 0.0, 0.0]), uref=_f([0.0]),
                    xlo=_f([-2.0, -INF, -INF, -INF]), xhi=_f([2.0, INF, INF, INF]),
                    ulo=_f([-10.0]), uhi=_f([10.0]), name="cartpole")
