@@ -61,13 +61,17 @@ class Info(C.Structure):
 _lib = None
 
 
+def _open(path: str):
+    if not os.path.exists(path):
+        raise OSError(f"libptn.so not found at {path}: run paper_2409_20027_gb300.build.build()")
+    return C.CDLL(path)
+
+
 def load(path: str = LIB_PATH):
-    """Load libptn.so; raises OSError when it has not been built."""
+    """Load libptn.so; raises OSError when it has not been built (no CPU fallback)."""
     global _lib
     if _lib is None:
-        if not os.path.exists(path):
-            raise OSError(f"libptn.so not found at {path}: run paper_2409_20027_gb300.build.build()")
-        lib = C.CDLL(path)
+        lib = _open(path)
         vp, ip = C.c_void_p, C.POINTER(C.c_int)
         lib.ptn_default_options.argtypes = [C.POINTER(Options)]
         lib.ptn_solver_create.argtypes = [C.POINTER(Problem), C.POINTER(Options), C.c_int, C.c_int, C.POINTER(vp)]

@@ -1,0 +1,45 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every function that
+include/ptn.h declares (no compute calls: this runs without a GPU)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "ptn.h")
+
+
+def declared_functions():
+    txt = open(HEADER).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\**\s+\**\s*(ptn_[a-z0-9_]+)\s*\(", txt, flags=re.M)
+    return sorted(set(names))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ["ptn_solver_create", "ptn_solve_ip", "ptn_solve_admm", "ptn_solve_batch", "ptn_adjoint"]:
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_2409_20027_gb300 import build, ptn
+    path = build.build()
+    lib = ctypes.CDLL(path)
+    for name in declared_functions():
+        assert hasattr(lib, name), f"{name} declared in ptn.h but not exported"
+    assert set(declared_functions()) <= set(ptn.EXPORTS)
+    assert lib is not None
+
+
+def test_version_string_without_gpu():
+    from paper_2409_20027_gb300 import ptn
+    v = ptn.load().ptn_version().decode()
+    assert "sm_103a" in v
+
+
+def test_binding_fails_loudly_without_the_library(tmp_path):
+    from paper_2409_20027_gb300 import ptn
+    with pytest.raises(OSError):
+        ptn._open(str(tmp_path / "libptn.so"))

@@ -1,0 +1,221 @@
+"""GPU parity: the CUDA solver (through the C ABI) against the FP64 CPU oracle.
+
+Tolerances (relative, rel = max|a-b| / max(1, max|b|)):
+  FP64 path                     1e-6  on x, u, lam and the cost
+  FP32 path with FP64 solves    1e-4  on x, u and the cost
+Both paths must also reach the KKT residual the oracle reaches (r_stat <= 1e-6 at
+mu = 1e-6).  Where the method is nonconvex the comparison is on the final
+result, not the iteration path.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2409_20027_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-6
+FP32_TOL = 1e-4
+
+
+def rel(a, b):
+    a = np.asarray(a); b = np.asarray(b)
+    return float(np.abs(a - b).max() / max(1.0, np.abs(b).max()))
+
+
+@pytest.fixture(scope="module")
+def ptn():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_2409_20027_gb300 import build, ptn as P
+    build.build()
+    P.load()
+    return P
+
+
+def dev(a):
+    return torch.tensor(np.asarray(a, dtype=np.float64), device="cuda:0")
+
+
+def check_solution(info, ref, x, u, lam, tol, with_lam=True):
+    assert info["status"] == 0, info
+    assert ref["info"]["status"] == 0
+    assert rel(x.cpu().numpy(), ref["x"]) <= tol
+    assert rel(u.cpu().numpy(), ref["u"]) <= tol
+    if with_lam:
+        assert rel(lam.cpu().numpy(), ref["lam"]) <= tol
+    assert abs(info["J"] - ref["info"]["J"]) / max(1.0, abs(ref["info"]["J"])) <= tol
+    assert info["r_stat"] <= 1e-6 and info["r_dyn"] <= 1e-6 and info["r_feas"] == 0.0
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_pendulum_fp64_matches_oracle(ptn, seed):
+    p = W.pendulum()
+    T = 64
+    x0 = W.pendulum_x0(seed)
+    s = ptn.Solver(p, max_T=T, precision=ptn.PTN_FP64, block_threads=64)
+    x, u, lam, info = s.solve_ip(dev(x0), T)
+    ref = O.solve_ip(p, x0, T)
+    check_solution(info, ref, x, u, lam, FP64_TOL)
+    # FP64 follows the oracle's iteration path
+    assert info["newton_iters"] == ref["info"]["newton_iters"]
+
+
+@pytest.mark.parametrize("T,threads", [(1, 32), (2, 32), (3, 32), (31, 32), (33, 32), (65, 64), (126, 128),
+                                       (129, 128), (200, 64)])
+def test_ragged_horizons_fp64(ptn, T, threads):
+    # horizons below, at and above the thread count: empty chunks, one-step chunks, tails
+    p = W.cartpole()
+    x0 = W.cartpole_x0(7)
+    s = ptn.Solver(p, max_T=T, precision=ptn.PTN_FP64, block_threads=threads, grid_min_T=0)
+    x, u, lam, info = s.solve_ip(dev(x0), T)
+    ref = O.solve_ip(p, x0, T)
+    check_solution(info, ref, x, u, lam, FP64_TOL)
+
+
+def test_nonconvergent_instance_reported_like_oracle(ptn):
+    # this instance defeats the method itself: the oracle stops at the iteration cap
+    # without reaching the tolerance, and so must the GPU (no false success)
+    p = W.cartpole()
+    x0 = W.cartpole_x0(7)
+    T = 127
+    ref = O.solve_ip(p, x0, T)
+    assert ref["info"]["status"] == -3
+    s = ptn.Solver(p, max_T=T, precision=ptn.PTN_FP64, block_threads=128)
+    x, u, lam, info = s.solve_ip(dev(x0), T)
+    assert info["status"] == -3
+    assert info["newton_iters"] == ref["info"]["newton_iters"]
+
+
+def test_cartpole_fp64_cta(ptn):
+    T = 256
+    p = W.cartpole(T=T, horizon=2.56)
+    x0 = W.cartpole_x0(0)
+    s = ptn.Solver(p, max_T=T, precision=ptn.PTN_FP64, block_threads=128, grid_min_T=0)
+    x, u, lam, info = s.solve_ip(dev(x0), T)
+    ref = O.solve_ip(p, x0, T)
+    check_solution(info, ref, x, u, lam, FP64_TOL)
+
+
+@pytest.mark.parametrize("T,grid", [(256, False), (1024, True), (4096, True)])
+def test_cartpole_fp32_matches_oracle(ptn, T, grid):
+    p = W.cartpole(T=T, horizon=2.56)
+    x0 = W.cartpole_x0(1)
+    s = ptn.Solver(p, max_T=T, precision=ptn.PTN_FP32_FP64SOLVE, grid_min_T=(512 if grid else 0))
+    x, u, lam, info = s.solve_ip(dev(x0), T)
+    ref = O.solve_ip(p, x0, T)
+    check_solution(info, ref, x, u, lam, FP32_TOL, with_lam=False)
+
+
+def test_grid_tier_fp64_matches_oracle(ptn):
+    T = 1024
+    p = W.cartpole(T=T, horizon=2.56)
+    x0 = W.cartpole_x0(2)
+    s = ptn.Solver(p, max_T=T, precision=ptn.PTN_FP64, grid_min_T=512, grid_steps_per_thread=3)
+    x, u, lam, info = s.solve_ip(dev(x0), T)
+    ref = O.solve_ip(p, x0, T)
+    check_solution(info, ref, x, u, lam, FP64_TOL)
+
+
+def test_batch_ragged_matches_individual_oracle_solves(ptn):
+    p = W.cartpole()
+    Tb = np.array([1, 5, 17, 64, 100, 131, 3, 40], dtype=np.int32)
+    B = len(Tb)
+    x0s = W.cartpole_batch_x0(B, 3)
+    s = ptn.Solver(p, max_T=int(Tb.max()), max_batch=B, precision=ptn.PTN_FP64, block_threads=64)
+    X, U, Lm, infos = s.solve_batch(dev(x0s), Tb)
+    xo = uo = 0
+    for b in range(B):
+        T = int(Tb[b])
+        ref = O.solve_ip(p, x0s[b], T)
+        check_solution(infos[b], ref, X[xo:xo + T + 1], U[uo:uo + T], Lm[xo:xo + T + 1], FP64_TOL)
+        xo += T + 1
+        uo += T
+
+
+def test_batch_per_instance_targets(ptn):
+    # per-instance xref (the waypoint mechanism) on the pendulum
+    p = W.pendulum()
+    B, T = 3, 40
+    x0s = np.stack([W.pendulum_x0(s) for s in range(B)])
+    xrefs = np.array([[np.pi, 0.0], [np.pi / 2, 0.0], [2.0, 0.5]])
+    s = ptn.Solver(p, max_T=T, max_batch=B, precision=ptn.PTN_FP64, block_threads=64)
+    X, U, Lm, infos = s.solve_batch(dev(x0s), [T] * B, xref=dev(xrefs))
+    for b in range(B):
+        ref = O.solve_ip(p.replace(xref=xrefs[b]), x0s[b], T)
+        check_solution(infos[b], ref, X[b * (T + 1):(b + 1) * (T + 1)], U[b * T:(b + 1) * T],
+                       Lm[b * (T + 1):(b + 1) * (T + 1)], FP64_TOL)
+
+
+def test_admm_fixed_outer_iterations_fp64(ptn):
+    p = W.pendulum()
+    T = 40
+    x0 = W.pendulum_x0(5)
+    K = 15
+    s = ptn.Solver(p, max_T=T, precision=ptn.PTN_FP64, block_threads=64, admm_fixed_iters=K)
+    x, u, lam, z, v, info = s.solve_admm(dev(x0), T, with_zv=True)
+    ref = O.solve_admm(p, x0, T, opts=O.Options(admm_fixed_iters=K))
+    assert info["status"] == 0 and info["outer_iters"] == K
+    assert rel(x.cpu().numpy(), ref["x"]) <= FP64_TOL
+    assert rel(u.cpu().numpy(), ref["u"]) <= FP64_TOL
+    assert rel(z.cpu().numpy(), ref["z"]) <= FP64_TOL
+    assert rel(v.cpu().numpy(), ref["v"]) <= FP64_TOL
+    assert info["r_p"] == pytest.approx(ref["info"]["r_p"], rel=1e-6, abs=1e-9)
+
+
+def test_admm_converges_to_tolerance(ptn):
+    p = W.pendulum()
+    T = 40
+    x0 = W.pendulum_x0(5)
+    s = ptn.Solver(p, max_T=T, precision=ptn.PTN_FP32_FP64SOLVE, block_threads=64, admm_tol=1e-4)
+    x, u, lam, info = s.solve_admm(dev(x0), T)
+    assert info["status"] == 0 and info["r_p"] <= 1e-4 and info["r_d"] <= 1e-4
+    ref = O.solve_ip(p, x0, T)
+    assert info["J"] == pytest.approx(ref["info"]["J"], rel=1e-3)
+
+
+# ---------------------------------------------------------------- error paths
+
+def test_infeasible_start_is_reported(ptn):
+    p = W.pendulum()
+    T = 16
+    s = ptn.Solver(p, max_T=T, precision=ptn.PTN_FP64)
+    u0 = dev(np.full((T, 1), 6.0))      # violates |u| <= 5
+    x, u, lam, info = s.solve_ip(dev(W.pendulum_x0(0)), T, u_init=u0)
+    assert info["status"] == -2
+
+
+def test_invalid_arguments_are_rejected(ptn):
+    # every call below is rejected on the host before any launch; the output buffers are
+    # nevertheless sized for the largest horizon passed (T = 9)
+    import ctypes as C
+    p = W.pendulum()
+    s = ptn.Solver(p, max_T=8, max_batch=1, precision=ptn.PTN_FP64)
+    x0 = dev(np.zeros(2))
+    info = ptn.Info()
+    xo = torch.zeros((10, 2), dtype=torch.float64, device="cuda:0")
+    uo = torch.zeros((9, 1), dtype=torch.float64, device="cuda:0")
+    lib = ptn.load()
+    args = lambda T: (s._h, C.c_void_p(x0.data_ptr()), None, T, C.c_void_p(xo.data_ptr()),
+                      C.c_void_p(uo.data_ptr()), None, C.byref(info), None)
+    assert lib.ptn_solve_ip(*args(0)) == -1          # empty horizon
+    assert lib.ptn_solve_ip(*args(9)) == -1          # beyond the workspace (8 steps)
+    assert "exceeds" in s.last_error()
+    Tb = (C.c_int * 2)(1, 1)
+    assert lib.ptn_solve_batch(s._h, 0, 2, Tb, C.c_void_p(x0.data_ptr()), None, None, C.c_void_p(xo.data_ptr()),
+                               C.c_void_p(uo.data_ptr()), None, None, None) == -1   # B > max_batch
+    assert lib.ptn_solve_ip(s._h, None, None, 4, C.c_void_p(xo.data_ptr()), C.c_void_p(uo.data_ptr()), None,
+                            C.byref(info), None) == -1   # missing x0
+    assert float(xo.abs().max()) == 0.0 and float(uo.abs().max()) == 0.0   # nothing ran
+    with pytest.raises(ptn.PtnError):
+        ptn.Solver(p.replace(nx=3), max_T=8)
+
+
+def test_nonfinite_initial_state_does_not_hang(ptn):
+    p = W.pendulum()
+    T = 16
+    s = ptn.Solver(p, max_T=T, precision=ptn.PTN_FP64)
+    x, u, lam, info = s.solve_ip(dev([np.nan, 0.0]), T)
+    assert info["status"] != 0
