@@ -43,7 +43,13 @@ extern "C" {
 
 enum { PTN_MODEL_PENDULUM = 0, PTN_MODEL_CARTPOLE = 1, PTN_MODEL_QUADROTOR = 2, PTN_MODEL_SYNTH_TANH = 3 };
 enum { PTN_EULER = 0, PTN_RK4 = 1 };
-enum { PTN_FP64 = 0, PTN_FP32_FP64SOLVE = 1 };
+/* Precision of the Newton step (trajectories, co-states, gradients and the final
+ * convergence test are FP64 in every mode):
+ *   PTN_FP64            all arithmetic in FP64
+ *   PTN_FP32_FP64SOLVE  model increments, LQR elements, scans and feedback in FP32;
+ *                       (I + C J)^{-1} and Cholesky solves in FP64
+ *   PTN_FP32            as above with FP32 solves */
+enum { PTN_FP64 = 0, PTN_FP32_FP64SOLVE = 1, PTN_FP32 = 2 };
 enum { PTN_METHOD_IP = 0, PTN_METHOD_ADMM = 1 };
 
 /* Problem description (Sec. II-A).  Model constants prm:
@@ -66,6 +72,7 @@ typedef struct ptn_problem {
 
 /* Solver settings; ptn_default_options() fills the defaults:
  *   precision FP32_FP64SOLVE, mu 1e-1 -> 1e-6 (x0.1), tol_inner 1e-4, tol_final 1e-6,
+ *   block_threads 128, grid_min_T 512, grid_steps_per_thread 2, polish 100, polish_after 50,
  *   max_newton 500 per barrier level, ADMM rho 1, admm_tol 1e-2, max_outer 2000,
  *   alpha0 1e-6 in [1e-10, 1e10], ten step sizes 1, 1/2, ..., Armijo c1 1e-4,
  *   rollout: at most 30 multiple-shooting Newton iterations to relative defect 1e-12. */
@@ -79,9 +86,12 @@ typedef struct ptn_options {
   int block_threads;    /* threads per CTA when one CTA solves one instance */
   int grid_min_T;       /* single solves with T >= grid_min_T use all SMs (0: never) */
   int grid_steps_per_thread;
-  int pad;
+  int polish_after;     /* FP32 modes: exact FP64 gradients after this many iterations */
   double mu0, zeta, mu_final, tol_inner, tol_final, rho, admm_tol;
   double alpha0, alpha_min, alpha_max, ls_beta, armijo_c1, armijo_eps, roll_tol;
+  double polish;        /* FP32 modes: exact FP64 gradients once max|d| <= polish * tol_final */
+  double armijo_eps32;  /* FP32 modes: Armijo allowance, relative to |J_c|, for merits
+                           accumulated as FP32 differences (their rounding floor) */
 } ptn_options;
 
 /* Per-solve report.  r_kkt = max(r_stat, r_dyn, r_feas, mu) for IP, where r_stat is
@@ -91,7 +101,7 @@ typedef struct ptn_options {
  * pass, line search, and everything else. */
 typedef struct ptn_info {
   int status, newton_iters, outer_iters, ls_rejects, factor_fails, roll_fails;
-  int roll_iters, ls_evals;
+  int roll_iters, ls_evals, exact_passes, pad;
   double mu, alpha, r_stat, r_dyn, r_feas, r_kkt, J, J_c, r_p, r_d;
   long long cycles[6];
 } ptn_info;

@@ -17,22 +17,28 @@ using namespace ptn;
 // per (model, precision) launchers, one translation unit each; weak references so a
 // library built without some model units still links (those models report an error)
 #define PTN_WEAK __attribute__((weak))
-cudaError_t ptn_launch_pendulum_f64(LaunchReq&) PTN_WEAK;
-cudaError_t ptn_launch_pendulum_f32(LaunchReq&) PTN_WEAK;
-cudaError_t ptn_launch_cartpole_f64(LaunchReq&) PTN_WEAK;
-cudaError_t ptn_launch_cartpole_f32(LaunchReq&) PTN_WEAK;
-cudaError_t ptn_launch_quadrotor_f64(LaunchReq&) PTN_WEAK;
-cudaError_t ptn_launch_quadrotor_f32(LaunchReq&) PTN_WEAK;
+#define PTN_DECL(m)                                      \
+  cudaError_t ptn_launch_##m##_f64(LaunchReq&) PTN_WEAK;  \
+  cudaError_t ptn_launch_##m##_f32d(LaunchReq&) PTN_WEAK; \
+  cudaError_t ptn_launch_##m##_f32(LaunchReq&) PTN_WEAK;
+PTN_DECL(pendulum)
+PTN_DECL(cartpole)
+PTN_DECL(quadrotor)
+PTN_DECL(synth)
 
 namespace {
 
 typedef cudaError_t (*launch_fn)(LaunchReq&);
 
+#define PTN_PICK(m) \
+  (precision == PTN_FP64 ? ptn_launch_##m##_f64 : precision == PTN_FP32_FP64SOLVE ? ptn_launch_##m##_f32d : ptn_launch_##m##_f32)
+
 launch_fn pick_launcher(int model, int precision) {
   switch (model) {
-    case PTN_MODEL_PENDULUM: return precision == PTN_FP64 ? ptn_launch_pendulum_f64 : ptn_launch_pendulum_f32;
-    case PTN_MODEL_CARTPOLE: return precision == PTN_FP64 ? ptn_launch_cartpole_f64 : ptn_launch_cartpole_f32;
-    case PTN_MODEL_QUADROTOR: return precision == PTN_FP64 ? ptn_launch_quadrotor_f64 : ptn_launch_quadrotor_f32;
+    case PTN_MODEL_PENDULUM: return PTN_PICK(pendulum);
+    case PTN_MODEL_CARTPOLE: return PTN_PICK(cartpole);
+    case PTN_MODEL_QUADROTOR: return PTN_PICK(quadrotor);
+    case PTN_MODEL_SYNTH_TANH: return PTN_PICK(synth);
     default: return nullptr;
   }
 }
@@ -99,7 +105,7 @@ extern "C" void ptn_default_options(ptn_options* o) {
   o->admm_fixed_iters = 0;
   o->roll_max_iter = 30;
   o->block_threads = 128;
-  o->grid_min_T = 2048;
+  o->grid_min_T = 512;
   o->grid_steps_per_thread = 2;
   o->mu0 = 1e-1;
   o->zeta = 0.1;
@@ -115,6 +121,9 @@ extern "C" void ptn_default_options(ptn_options* o) {
   o->armijo_c1 = 1e-4;
   o->armijo_eps = 1e-12;
   o->roll_tol = 1e-12;
+  o->polish = 100.0;
+  o->armijo_eps32 = 1e-9;
+  o->polish_after = 50;
 }
 
 extern "C" const char* ptn_version(void) { return "ptn 0.1 (sm_103a)"; }
@@ -124,8 +133,8 @@ extern "C" const char* ptn_last_error(const ptn_solver* s) { return s ? s->err :
 extern "C" int ptn_num_rows(const ptn_solver* s) { return s ? s->nw : 0; }
 
 static int check_options(ptn_solver* s, const ptn_options* o) {
-  if (o->precision != PTN_FP64 && o->precision != PTN_FP32_FP64SOLVE)
-    return fail(s, PTN_ERR_INVALID_ARG, "precision must be PTN_FP64 or PTN_FP32_FP64SOLVE");
+  if (o->precision != PTN_FP64 && o->precision != PTN_FP32_FP64SOLVE && o->precision != PTN_FP32)
+    return fail(s, PTN_ERR_INVALID_ARG, "precision must be PTN_FP64, PTN_FP32_FP64SOLVE or PTN_FP32");
   if (o->block_threads < 32 || o->block_threads > 256 || (o->block_threads % 32))
     return fail(s, PTN_ERR_INVALID_ARG, "block_threads must be a multiple of 32 in [32, 256]");
   if (o->max_newton < 1 || o->ls_count < 1 || o->roll_max_iter < 1 || o->max_outer < 1)
@@ -246,9 +255,11 @@ extern "C" int ptn_solver_create(const ptn_problem* prob, const ptn_options* opt
   size_t o_xB = off; off = align256(off + sizeof(double) * SB * n);
   size_t o_uB = off; off = align256(off + sizeof(double) * S * m);
   size_t o_lam = off; off = align256(off + sizeof(double) * SB * n);
-  size_t o_F = off; off = align256(off + sizeof(double) * S * n * n);
-  size_t o_G = off; off = align256(off + sizeof(double) * S * n * m);
   size_t o_d = off; off = align256(off + sizeof(double) * S * m);
+  size_t o_F64 = off; off = align256(off + sizeof(double) * S * n * n);
+  size_t o_G64 = off; off = align256(off + sizeof(double) * S * n * m);
+  size_t o_E = off; off = align256(off + 8 * S * n * n);
+  size_t o_Gm = off; off = align256(off + 8 * S * n * m);
   size_t o_Pm = off; off = align256(off + 8 * SB * n * n);
   size_t o_Mm = off; off = align256(off + 8 * S * n * m);
   size_t o_Rm = off; off = align256(off + 8 * S * m * m);
@@ -261,7 +272,8 @@ extern "C" int ptn_solver_create(const ptn_problem* prob, const ptn_options* opt
   CK(cudaMalloc(&s->ws, off));
   char* b = s->ws;
   s->w.xB = (double*)(b + o_xB); s->w.uB = (double*)(b + o_uB); s->w.lam = (double*)(b + o_lam);
-  s->w.F = (double*)(b + o_F); s->w.G = (double*)(b + o_G); s->w.d = (double*)(b + o_d);
+  s->w.d = (double*)(b + o_d); s->w.F64 = (double*)(b + o_F64); s->w.G64 = (double*)(b + o_G64);
+  s->w.E = b + o_E; s->w.Gm = b + o_Gm;
   s->w.Pm = b + o_Pm; s->w.Mm = b + o_Mm; s->w.Rm = b + o_Rm; s->w.Gam = b + o_Gam; s->w.gam = b + o_gam;
   s->w.dx = b + o_dx; s->w.du = b + o_du;
   s->w.z = (double*)(b + o_z); s->w.v = (double*)(b + o_v);
@@ -292,10 +304,11 @@ static void to_optdev(const ptn_options& o, int method, OptDev* d) {
   d->tol_final = o.tol_final; d->rho = o.rho; d->admm_tol = o.admm_tol;
   d->alpha0 = o.alpha0; d->alpha_min = o.alpha_min; d->alpha_max = o.alpha_max; d->ls_beta = o.ls_beta;
   d->armijo_c1 = o.armijo_c1;
-  // FP32 candidates carry FP32-level noise in the merit only through the LQR direction,
-  // the merit itself is FP64 in both modes
   d->armijo_eps = o.armijo_eps;
   d->roll_tol = o.roll_tol;
+  d->polish = o.polish;
+  d->armijo_eps32 = o.armijo_eps32;
+  d->polish_after = o.polish_after;
   d->max_newton = o.max_newton; d->max_outer = o.max_outer; d->ls_count = o.ls_count;
   d->admm_fixed_iters = o.admm_fixed_iters; d->roll_max_iter = o.roll_max_iter; d->method = method;
   d->spin_limit = 1ll << 26;
@@ -304,7 +317,7 @@ static void to_optdev(const ptn_options& o, int method, OptDev* d) {
 static void from_info(const InfoDev& d, ptn_info* o) {
   o->status = d.status; o->newton_iters = d.newton_iters; o->outer_iters = d.outer_iters;
   o->ls_rejects = d.ls_rejects; o->factor_fails = d.factor_fails; o->roll_fails = d.roll_fails;
-  o->roll_iters = d.roll_iters; o->ls_evals = d.ls_evals;
+  o->roll_iters = d.roll_iters; o->ls_evals = d.ls_evals; o->exact_passes = d.exact_passes; o->pad = 0;
   for (int k = 0; k < 6; k++) o->cycles[k] = d.cyc[k];
   o->mu = d.mu; o->alpha = d.alpha; o->r_stat = d.r_stat; o->r_dyn = d.r_dyn; o->r_feas = d.r_feas;
   o->r_kkt = d.r_kkt; o->J = d.J; o->J_c = d.J_c; o->r_p = d.r_p; o->r_d = d.r_d;

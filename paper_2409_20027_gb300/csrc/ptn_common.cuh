@@ -6,6 +6,8 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #define PTN_MAXN 32
 #define PTN_MAXM 8
 #define PTN_MAXW (2 * PTN_MAXN + 2 * PTN_MAXM)
@@ -52,9 +54,9 @@ struct ProbDev {
 struct OptDev {
   double mu0, zeta, mu_final, tol_inner, tol_final, rho, admm_tol;
   double alpha0, alpha_min, alpha_max, ls_beta, armijo_c1, armijo_eps;
-  double roll_tol;
+  double roll_tol, polish, armijo_eps32;
   int max_newton, max_outer, ls_count, admm_fixed_iters;
-  int roll_max_iter, method, pad0, pad1;
+  int roll_max_iter, method, polish_after, pad1;
   long long spin_limit;  // bounded waits in grid barriers
 };
 
@@ -70,6 +72,7 @@ struct InstDev {
 struct InfoDev {
   int status, newton_iters, outer_iters, ls_rejects;
   int factor_fails, roll_fails, roll_iters, ls_evals;
+  int exact_passes, pad_;
   double mu, alpha, r_stat, r_dyn, r_feas, r_kkt, J, J_c, r_p, r_d;
   // SM clock cycles spent by group thread 0 per phase (costate, quadratize, value,
   // state, line search, other)
@@ -201,19 +204,19 @@ PTN_HD void mtv(const T1* A, const S* x, S* y) {
 
 // In-place Cholesky A = L L^T (lower triangle written, upper untouched).
 // Returns false when A is not positive definite.
-template <int N>
-PTN_HD bool chol(double* A) {
+template <int N, class S = double>
+PTN_HD bool chol(S* A) {
 #pragma unroll
   for (int j = 0; j < N; j++) {
-    double s = A[j * N + j];
+    S s = A[j * N + j];
 #pragma unroll
     for (int k = 0; k < j; k++) s -= A[j * N + k] * A[j * N + k];
-    if (!(s > 0.0) || !isfinite(s)) return false;
-    double d = sqrt(s), id = 1.0 / d;
+    if (!(s > S(0)) || !isfinite(s)) return false;
+    S d = sqrt(s), id = S(1) / d;
     A[j * N + j] = d;
 #pragma unroll
     for (int i = j + 1; i < N; i++) {
-      double t = A[i * N + j];
+      S t = A[i * N + j];
 #pragma unroll
       for (int k = 0; k < j; k++) t -= A[i * N + k] * A[j * N + k];
       A[i * N + j] = t * id;
@@ -222,20 +225,20 @@ PTN_HD bool chol(double* A) {
   return true;
 }
 // solve (L L^T) X = B in place, B is N x C
-template <int N, int C>
-PTN_HD void chol_solve(const double* L, double* B) {
+template <int N, int C, class S = double>
+PTN_HD void chol_solve(const S* L, S* B) {
 #pragma unroll
   for (int c = 0; c < C; c++) {
 #pragma unroll
     for (int i = 0; i < N; i++) {
-      double s = B[i * C + c];
+      S s = B[i * C + c];
 #pragma unroll
       for (int k = 0; k < i; k++) s -= L[i * N + k] * B[k * C + c];
       B[i * C + c] = s / L[i * N + i];
     }
 #pragma unroll
     for (int i = N - 1; i >= 0; i--) {
-      double s = B[i * C + c];
+      S s = B[i * C + c];
 #pragma unroll
       for (int k = i + 1; k < N; k++) s -= L[k * N + i] * B[k * C + c];
       B[i * C + c] = s / L[i * N + i];
@@ -245,41 +248,41 @@ PTN_HD void chol_solve(const double* L, double* B) {
 
 // In-place inverse by Gauss-Jordan elimination with partial pivoting (FP64).
 // Returns false when a pivot is zero or not finite.
-template <int N>
-PTN_HD bool inv_gj(double* A) {
+template <int N, class S = double>
+PTN_HD bool inv_gj(S* A) {
   int piv[N];
   for (int i = 0; i < N; i++) piv[i] = i;
 #pragma unroll (N <= 8 ? N : 1)
   for (int k = 0; k < N; k++) {
     int p = k;
-    double best = fabs(A[k * N + k]);
+    S best = fabs(A[k * N + k]);
     for (int i = k + 1; i < N; i++) {
-      double v = fabs(A[i * N + k]);
+      S v = fabs(A[i * N + k]);
       if (v > best) { best = v; p = i; }
     }
-    if (!(best > 0.0) || !isfinite(best)) return false;
+    if (!(best > S(0)) || !isfinite(best)) return false;
     if (p != k) {
 #pragma unroll (N <= 8 ? N : 4)
       for (int j = 0; j < N; j++) {
-        double t = A[k * N + j]; A[k * N + j] = A[p * N + j]; A[p * N + j] = t;
+        S t = A[k * N + j]; A[k * N + j] = A[p * N + j]; A[p * N + j] = t;
       }
       int t = piv[k]; piv[k] = piv[p]; piv[p] = t;
     }
-    double ip = 1.0 / A[k * N + k];
-    A[k * N + k] = 1.0;
+    S ip = S(1) / A[k * N + k];
+    A[k * N + k] = S(1);
 #pragma unroll (N <= 8 ? N : 4)
     for (int j = 0; j < N; j++) A[k * N + j] *= ip;
 #pragma unroll (N <= 8 ? N : 1)
     for (int i = 0; i < N; i++) {
       if (i == k) continue;
-      double f = A[i * N + k];
-      A[i * N + k] = 0.0;
+      S f = A[i * N + k];
+      A[i * N + k] = S(0);
 #pragma unroll (N <= 8 ? N : 4)
       for (int j = 0; j < N; j++) A[i * N + j] -= f * A[k * N + j];
     }
   }
   // undo the row permutation as a column permutation of the inverse
-  double tmp[N];
+  S tmp[N];
 #pragma unroll (N <= 8 ? N : 1)
   for (int i = 0; i < N; i++) {
     for (int j = 0; j < N; j++) tmp[piv[j]] = A[i * N + j];

@@ -1,4 +1,4 @@
-// Solver kernels for the cartpole model with float LQR arithmetic.
+// Solver kernels for the cartpole model, FP32 LQR and solves.
 #include "ptn_launch.cuh"
 
-cudaError_t ptn_launch_cartpole_f32(ptn::LaunchReq& q) { return ptn::launch_typed<ptn::CartPole, float>(q); }
+cudaError_t ptn_launch_cartpole_f32(ptn::LaunchReq& q) { return ptn::launch_typed<ptn::CartPole, float, float>(q); }

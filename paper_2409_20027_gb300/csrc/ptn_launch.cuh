@@ -7,8 +7,8 @@ namespace ptn {
 // untyped workspace pointers (LQR arrays are allocated with 8 bytes per entry so that
 // either precision fits)
 struct WorkRaw {
-  double *xA, *uA, *xB, *uB, *lam, *F, *G, *d;
-  void *Pm, *Mm, *Rm, *Gam, *gam, *dx, *du;
+  double *xA, *uA, *xB, *uB, *lam, *d, *F64, *G64;
+  void *E, *Gm, *Pm, *Mm, *Rm, *Gam, *gam, *dx, *du;
   double *z, *v;
 };
 
@@ -16,7 +16,7 @@ template <class L>
 inline Work<L> typed(const WorkRaw& r) {
   Work<L> w;
   w.xA = r.xA; w.uA = r.uA; w.xB = r.xB; w.uB = r.uB; w.lam = r.lam;
-  w.F = r.F; w.G = r.G; w.d = r.d;
+  w.d = r.d; w.F64 = r.F64; w.G64 = r.G64; w.E = (L*)r.E; w.Gm = (L*)r.Gm;
   w.Pm = (L*)r.Pm; w.Mm = (L*)r.Mm; w.Rm = (L*)r.Rm; w.Gam = (L*)r.Gam; w.gam = (L*)r.gam;
   w.dx = (L*)r.dx; w.du = (L*)r.du; w.z = r.z; w.v = r.v;
   return w;
@@ -24,7 +24,7 @@ inline Work<L> typed(const WorkRaw& r) {
 
 struct LaunchReq {
   int tier;       // 0: one CTA per instance, 1: cooperative grid on one instance
-  int precision;  // 0: FP64, 1: FP32 with FP64 solves
+  int precision;  // 0: FP64, 1: FP32 with FP64 solves, 2: FP32
   int nblocks, nthreads;
   int query;      // 1: only report max co-resident grid blocks in *max_blocks
   int* max_blocks;
@@ -34,40 +34,35 @@ struct LaunchReq {
   cudaStream_t stream;
 };
 
-template <class M, class L>
+template <class M, class L, class SV>
 cudaError_t launch_typed(LaunchReq& q) {
   constexpr int N = M::NX, U = M::NU;
   const int nthreads = q.nthreads;
   const size_t smem = ((sizeof(ProbS<N, U>) + 15) & ~size_t(15)) + scratch_bytes<N, U, L>(nthreads / 32);
   if (q.elem_bytes) *q.elem_bytes = sizeof(Val<N, L>);
   if (q.tier == 0) {
-    cudaError_t e = cudaFuncSetAttribute(k_solve_cta<M, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_solve_cta<M, L, SV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     if (q.query) return cudaSuccess;
-    k_solve_cta<M, L><<<q.nblocks, nthreads, smem, q.stream>>>(q.args, typed<L>(q.w));
+    k_solve_cta<M, L, SV><<<q.nblocks, nthreads, smem, q.stream>>>(q.args, typed<L>(q.w));
     return cudaGetLastError();
   }
-  cudaError_t e = cudaFuncSetAttribute(k_solve_grid<M, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = cudaFuncSetAttribute(k_solve_grid<M, L, SV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   if (q.query) {
     int dev = 0, per = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_solve_grid<M, L>, nthreads, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_solve_grid<M, L, SV>, nthreads, smem);
     if (e != cudaSuccess) return e;
     *q.max_blocks = per * sms;
     return cudaSuccess;
   }
   Work<L> w = typed<L>(q.w);
   void* params[] = {(void*)&q.args, (void*)&w};
-  return cudaLaunchCooperativeKernel((const void*)k_solve_grid<M, L>, dim3(q.nblocks), dim3(nthreads), params, smem,
+  return cudaLaunchCooperativeKernel((const void*)k_solve_grid<M, L, SV>, dim3(q.nblocks), dim3(nthreads), params, smem,
                                      q.stream);
 }
 
-template <class M>
-cudaError_t launch_model(LaunchReq& q) {
-  if (q.precision == 0) return launch_typed<M, double>(q);
-  return launch_typed<M, float>(q);
-}
 
 }  // namespace ptn

@@ -114,6 +114,80 @@ PTN_HD void step(int integ, double dt, const double* p, const S* x, const S* u, 
   for (int i = 0; i < N; i++) xn[i] = x[i] + cmul(dt / 6.0, acc[i] + k[i]);
 }
 
+// Increment of one discrete step, dx = f(x, u) - x, in scalar S (no identity added, so
+// FP32 keeps the relative precision of the small increment).
+template <class M, class S>
+PTN_HD void step_inc(int integ, double dt, const double* p, const S* x, const S* u, S* dxo) {
+  constexpr int N = M::NX;
+  S k[N];
+  M::rhs(p, x, u, k);
+  if (integ == INTEG_EULER) {
+#pragma unroll
+    for (int i = 0; i < N; i++) dxo[i] = cmul(dt, k[i]);
+    return;
+  }
+  S acc[N], y[N];
+#pragma unroll
+  for (int i = 0; i < N; i++) { acc[i] = k[i]; y[i] = x[i] + cmul(0.5 * dt, k[i]); }
+  M::rhs(p, y, u, k);
+#pragma unroll
+  for (int i = 0; i < N; i++) { acc[i] = acc[i] + cmul(2.0, k[i]); y[i] = x[i] + cmul(0.5 * dt, k[i]); }
+  M::rhs(p, y, u, k);
+#pragma unroll
+  for (int i = 0; i < N; i++) { acc[i] = acc[i] + cmul(2.0, k[i]); y[i] = x[i] + cmul(dt, k[i]); }
+  M::rhs(p, y, u, k);
+#pragma unroll
+  for (int i = 0; i < N; i++) dxo[i] = cmul(dt / 6.0, acc[i] + k[i]);
+}
+
+// Jacobians of the increment: E = d(f - x)/dx (so F = I + E) and G = df/du, plus the
+// increment value, by forward-mode AD in scalar S.
+template <class M, class S>
+PTN_HD void inc_jac(int integ, double dt, const double* p, const double* x, const double* u, S* dv, S* E,
+                    S* G) {
+  constexpr int N = M::NX, U = M::NU, K = N + U;
+  using D = Dual<S, K>;
+  D xd[N], ud[U], dn[N];
+#pragma unroll
+  for (int i = 0; i < N; i++) { xd[i] = D(S(x[i])); xd[i].d[i] = S(1); }
+#pragma unroll
+  for (int i = 0; i < U; i++) { ud[i] = D(S(u[i])); ud[i].d[N + i] = S(1); }
+  step_inc<M>(integ, dt, p, xd, ud, dn);
+#pragma unroll
+  for (int i = 0; i < N; i++) {
+    if (dv) dv[i] = dn[i].v;
+#pragma unroll
+    for (int j = 0; j < N; j++) E[i * N + j] = dn[i].d[j];
+#pragma unroll
+    for (int j = 0; j < U; j++) G[i * U + j] = dn[i].d[N + j];
+  }
+}
+
+// Closed-loop increment at (x, u) with u = ub + Gam (x - xh): value dx and
+// Ecl = d dx / dx = E + G Gam (so Fcl = I + Ecl), seeds (e_i, Gam e_i).
+template <class M, class S>
+PTN_HD void inc_cl(int integ, double dt, const double* p, const S* x, const S* u, const S* Gam, S* dv,
+                   S* Ecl) {
+  constexpr int N = M::NX, U = M::NU;
+  using D = Dual<S, N>;
+  D xd[N], ud[U], dn[N];
+#pragma unroll
+  for (int i = 0; i < N; i++) { xd[i] = D(x[i]); xd[i].d[i] = S(1); }
+#pragma unroll
+  for (int i = 0; i < U; i++) {
+    ud[i] = D(u[i]);
+#pragma unroll
+    for (int j = 0; j < N; j++) ud[i].d[j] = Gam[i * N + j];
+  }
+  step_inc<M>(integ, dt, p, xd, ud, dn);
+#pragma unroll
+  for (int i = 0; i < N; i++) {
+    dv[i] = dn[i].v;
+#pragma unroll
+    for (int j = 0; j < N; j++) Ecl[i * N + j] = dn[i].d[j];
+  }
+}
+
 // F = df/dx (NX x NX), G = df/du (NX x NU), by forward-mode AD in scalar S.
 template <class M, class S>
 PTN_HD void step_jac(int integ, double dt, const double* p, const double* x, const double* u,

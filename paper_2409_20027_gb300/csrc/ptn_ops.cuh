@@ -91,16 +91,17 @@ PTN_HD void symmetrize(L* X) {
 //   b   = A2 K (b1 + C1 eta2) + b2
 //   J   = A1^T K^T J2 A1 + J1      K^T = (I + J2 C1)^{-1} since C, J are symmetric
 //   eta = A1^T K^T (eta2 - J2 b1) + eta1
-// I + C1 J2 is formed and inverted in FP64; the products run in L.
-// Returns false when I + C1 J2 is singular.
+// I + C1 J2 is formed and inverted in SV (FP64, or FP32 in the all-FP32 mode); the
+// products run in L.  Returns false when I + C1 J2 is singular.
+template <class SV = double>
 struct ValueOp {
   template <int N, class L>
   PTN_HD bool operator()(const Val<N, L>& e1, const Val<N, L>& e2, Val<N, L>& o) const {
-    double Md[N * N];
+    SV Md[N * N];
     mm<N, N, N>(e1.C, e2.J, Md);
 #pragma unroll
-    for (int i = 0; i < N; i++) Md[i * N + i] += 1.0;
-    if (!inv_gj<N>(Md)) return false;
+    for (int i = 0; i < N; i++) Md[i * N + i] += SV(1);
+    if (!inv_gj<N, SV>(Md)) return false;
     L K[N * N];
 #pragma unroll
     for (int i = 0; i < N * N; i++) K[i] = L(Md[i]);
@@ -146,51 +147,56 @@ struct ValueOp {
 // Element initialisation eq. value-fun-elem-init in the P^{-1}-free form
 //   A = F - G R~^{-1} M^T, J = P - M R~^{-1} M^T, C = G R~^{-1} G^T,
 //   eta = M R~^{-1} d, b = -G R~^{-1} d,  R~ = R + alpha I,
-// identical to the printed q_t, r_t form whenever P_t is invertible.
-// Returns false when R~ is not positive definite (FP64 Cholesky).
-template <int N, int U, class L, class TF, class TP>
-PTN_HD bool value_init(const TF* F, const TF* G, const TP* Pm, const TP* Mm, const TP* Rm,
-                       const double* d, double alpha, Val<N, L>& e) {
+// identical to the printed q_t, r_t form whenever P_t is invertible.  The Cholesky
+// factorisation and solve of R~ run in SV; the products in L.
+// Returns false when R~ is not positive definite.
+template <int N, int U, class L, class SV>
+PTN_HD bool value_init(const L* F, const L* G, const L* Pm, const L* Mm, const L* Rm, const double* d,
+                       double alpha, Val<N, L>& e) {
   constexpr int C = 2 * N + 1;
-  double Rt[U * U], X[U * C];
+  SV Rt[U * U], X[U * C];
 #pragma unroll
-  for (int i = 0; i < U * U; i++) Rt[i] = double(Rm[i]);
+  for (int i = 0; i < U * U; i++) Rt[i] = SV(Rm[i]);
 #pragma unroll
-  for (int i = 0; i < U; i++) Rt[i * U + i] += alpha;
-  if (!chol<U>(Rt)) return false;
+  for (int i = 0; i < U; i++) Rt[i * U + i] += SV(alpha);
+  if (!chol<U, SV>(Rt)) return false;
 #pragma unroll
   for (int i = 0; i < U; i++) {
-#pragma unroll
+#pragma unroll (N <= 8 ? N : 4)
     for (int j = 0; j < N; j++) {
-      X[i * C + j] = double(Mm[j * U + i]);
-      X[i * C + N + j] = double(G[j * U + i]);
+      X[i * C + j] = SV(Mm[j * U + i]);
+      X[i * C + N + j] = SV(G[j * U + i]);
     }
-    X[i * C + 2 * N] = d[i];
+    X[i * C + 2 * N] = SV(d[i]);
   }
-  chol_solve<U, C>(Rt, X);
+  chol_solve<U, C, SV>(Rt, X);
+  L XL[U * C];
 #pragma unroll
+  for (int i = 0; i < U * C; i++) XL[i] = L(X[i]);
+  // XL = R~^{-1} [M^T | G^T | d]  (U x (2N+1))
+#pragma unroll (N <= 8 ? N : 1)
   for (int i = 0; i < N; i++) {
-#pragma unroll
+#pragma unroll (N <= 8 ? N : 2)
     for (int j = 0; j < N; j++) {
-      double gm = 0.0, mx = 0.0, gg = 0.0;
+      L gm = L(0), mx = L(0), gg = L(0);
 #pragma unroll
       for (int k = 0; k < U; k++) {
-        gm += double(G[i * U + k]) * X[k * C + j];
-        mx += double(Mm[i * U + k]) * X[k * C + j];
-        gg += double(G[i * U + k]) * X[k * C + N + j];
+        gm += G[i * U + k] * XL[k * C + j];
+        mx += Mm[i * U + k] * XL[k * C + j];
+        gg += G[i * U + k] * XL[k * C + N + j];
       }
-      e.A[i * N + j] = L(double(F[i * N + j]) - gm);
-      e.J[i * N + j] = L(double(Pm[i * N + j]) - mx);
-      e.C[i * N + j] = L(gg);
+      e.A[i * N + j] = F[i * N + j] - gm;
+      e.J[i * N + j] = Pm[i * N + j] - mx;
+      e.C[i * N + j] = gg;
     }
-    double et = 0.0, bb = 0.0;
+    L et = L(0), bb = L(0);
 #pragma unroll
     for (int k = 0; k < U; k++) {
-      et += double(Mm[i * U + k]) * X[k * C + 2 * N];
-      bb += double(G[i * U + k]) * X[k * C + 2 * N];
+      et += Mm[i * U + k] * XL[k * C + 2 * N];
+      bb += G[i * U + k] * XL[k * C + 2 * N];
     }
-    e.eta[i] = L(et);
-    e.b[i] = L(-bb);
+    e.eta[i] = et;
+    e.b[i] = -bb;
   }
   symmetrize<N>(e.J);
   symmetrize<N>(e.C);
@@ -198,8 +204,8 @@ PTN_HD bool value_init(const TF* F, const TF* G, const TP* Pm, const TP* Mm, con
 }
 
 // Terminal element nu_{N+1}: J = P_{N+1}, all other parameters zero.
-template <int N, class L, class TP>
-PTN_HD void value_terminal(const TP* PT, Val<N, L>& e) {
+template <int N, class L>
+PTN_HD void value_terminal(const L* PT, Val<N, L>& e) {
 #pragma unroll
   for (int i = 0; i < N * N; i++) { e.A[i] = L(0); e.C[i] = L(0); e.J[i] = L(PT[i]); }
 #pragma unroll
@@ -211,41 +217,36 @@ PTN_HD void value_terminal(const TP* PT, Val<N, L>& e) {
 // eq. value-fun-feedback (reading: Q^{-1} M_t^T):
 //   Q = R~ + G^T S G,  Gam = -Q^{-1}(M^T + G^T S F),  gam = -Q^{-1}(d + G^T s),
 //   S_t = P + F^T S F + (M^T + G^T S F)^T Gam,  s_t = F^T s + (M^T + G^T S F)^T gam.
-// Q is factorised in FP64.  S, s are updated in place.  Returns false when Q is not PD.
-template <int N, int U, class L, class TF, class TP>
-PTN_HD bool riccati_step(const TF* F, const TF* G, const TP* Pm, const TP* Mm, const TP* Rm,
-                         const double* d, double alpha, L* S, L* s, L* Gam, L* gam) {
-  L SG[N * U], SF[N * N], Qux[U * N];
+// Q is factorised in SV.  S, s are updated in place.  Returns false when Q is not PD.
+template <int N, int U, class L, class SV>
+PTN_HD bool riccati_step(const L* F, const L* G, const L* Pm, const L* Mm, const L* Rm, const double* d,
+                         double alpha, L* S, L* s, L* Gam, L* gam) {
+  L SG[N * U], SF[N * N], Qux[U * N], GSG[U * U];
   mm<N, N, U>(S, G, SG);
   mm<N, N, N>(S, F, SF);
-  double Q[U * U], X[U * (N + 1)];
+  mtm<U, N, U>(G, SG, GSG);
+  mtm<U, N, N>(G, SF, Qux);
+  SV Q[U * U], X[U * (N + 1)];
 #pragma unroll
   for (int i = 0; i < U; i++)
 #pragma unroll
-    for (int j = 0; j < U; j++) {
-      double v = double(Rm[i * U + j]) + (i == j ? alpha : 0.0);
-#pragma unroll
-      for (int k = 0; k < N; k++) v += double(G[k * U + i]) * double(SG[k * U + j]);
-      Q[i * U + j] = v;
-    }
-  mtm<U, N, N>(G, SF, Qux);
+    for (int j = 0; j < U; j++) Q[i * U + j] = SV(Rm[i * U + j]) + SV(GSG[i * U + j]) + (i == j ? SV(alpha) : SV(0));
+  L Gs[U];
+  mtv<N, U>(G, s, Gs);
 #pragma unroll
   for (int i = 0; i < U; i++) {
 #pragma unroll (N <= 8 ? N : 4)
     for (int j = 0; j < N; j++) {
-      Qux[i * N + j] += L(Mm[j * U + i]);
-      X[i * (N + 1) + j] = double(Qux[i * N + j]);
+      Qux[i * N + j] += Mm[j * U + i];
+      X[i * (N + 1) + j] = SV(Qux[i * N + j]);
     }
-    double q = d[i];
-#pragma unroll (N <= 8 ? N : 4)
-    for (int k = 0; k < N; k++) q += double(G[k * U + i]) * double(s[k]);
-    X[i * (N + 1) + N] = q;
+    X[i * (N + 1) + N] = SV(d[i]) + SV(Gs[i]);
   }
-  if (!chol<U>(Q)) return false;
-  chol_solve<U, N + 1>(Q, X);
+  if (!chol<U, SV>(Q)) return false;
+  chol_solve<U, N + 1, SV>(Q, X);
 #pragma unroll
   for (int i = 0; i < U; i++) {
-#pragma unroll
+#pragma unroll (N <= 8 ? N : 4)
     for (int j = 0; j < N; j++) Gam[i * N + j] = L(-X[i * (N + 1) + j]);
     gam[i] = L(-X[i * (N + 1) + N]);
   }
@@ -253,7 +254,7 @@ PTN_HD bool riccati_step(const TF* F, const TF* G, const TP* Pm, const TP* Mm, c
   mtm<N, N, N>(F, SF, FtSF);
   mtm<N, U, N>(Qux, Gam, QG);
 #pragma unroll (N <= 8 ? N * N : 4)
-  for (int i = 0; i < N * N; i++) Sn[i] = L(Pm[i]) + FtSF[i] + QG[i];
+  for (int i = 0; i < N * N; i++) Sn[i] = Pm[i] + FtSF[i] + QG[i];
   L Fts[N], Qg[N];
   mtv<N, N>(F, s, Fts);
   mtv<U, N>(Qux, gam, Qg);

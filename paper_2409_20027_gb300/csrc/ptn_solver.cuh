@@ -18,8 +18,14 @@
 // also owns the terminal state T).  Inside a chunk the thread runs the recursion
 // sequentially; across chunks the group scans combine the chunk aggregates.
 //
-// Precision: trajectories, co-states, gradients, costs, Cholesky factorisations and
-// (I + C J)^{-1} are FP64; the LQR elements, scans and feedback use L (float or double).
+// Precision (GB300 issues FP64 at a small fraction of the FP32 rate, so FP64 is kept
+// off the critical path): states, controls, co-states and gradients are stored in
+// FP64.  In the mixed modes (L = float) the model is evaluated on increments
+// x+ = x + dx(x, u) with dx and its Jacobian E = d dx/dx (F = I + E) in FP32 and the
+// state accumulated in FP64; line-search merits are accumulated as FP32 differences
+// to the nominal; the co-state scan uses an element with an FP64 vector and an FP32
+// matrix increment.  Near the final convergence test the gradient is recomputed
+// exactly (FP64 Jacobians).  Solves (Cholesky, (I + C J)^{-1}) run in SV.
 #pragma once
 #include "ptn_group.cuh"
 #include "ptn_models.cuh"
@@ -31,6 +37,7 @@ template <int N, int U>
 struct ProbS {
   static constexpr int NW = 2 * (N + U);
   double Q[N * N], R[U * U], Qf[N * N], xref[N], uref[U];
+  float Qs[N * N], Rs[U * U], Qfs[N * N];  // symmetrised FP32 copies Q + Q^T etc.
   double prm[PTN_MAXP];
   double sgn[NW], bnd[NW];
   int isx[NW], idx[NW];
@@ -41,8 +48,16 @@ struct ProbS {
 
 template <int N, int U>
 __device__ void load_prob(ProbS<N, U>& S, const ProbDev& P, const double* xref_override) {
-  for (int i = threadIdx.x; i < N * N; i += blockDim.x) { S.Q[i] = P.Q[i]; S.Qf[i] = P.Qf[i]; }
-  for (int i = threadIdx.x; i < U * U; i += blockDim.x) S.R[i] = P.R[i];
+  for (int i = threadIdx.x; i < N * N; i += blockDim.x) {
+    S.Q[i] = P.Q[i];
+    S.Qf[i] = P.Qf[i];
+    S.Qs[i] = float(P.Q[i] + P.Q[(i % N) * N + i / N]);
+    S.Qfs[i] = float(P.Qf[i] + P.Qf[(i % N) * N + i / N]);
+  }
+  for (int i = threadIdx.x; i < U * U; i += blockDim.x) {
+    S.R[i] = P.R[i];
+    S.Rs[i] = float(P.R[i] + P.R[(i % U) * U + i / U]);
+  }
   for (int i = threadIdx.x; i < N; i += blockDim.x) S.xref[i] = xref_override ? xref_override[i] : P.xref[i];
   for (int i = threadIdx.x; i < U; i += blockDim.x) S.uref[i] = P.uref[i];
   for (int i = threadIdx.x; i < PTN_MAXP; i += blockDim.x) S.prm[i] = P.prm[i];
@@ -79,6 +94,20 @@ struct MOps {
   __device__ static void cl(const PS& P, const double* x, const double* u, const L* Gam, double* xn, L* Fcl) {
     step_cl_jac<M, L>(P.integ, P.dt, P.prm, x, u, Gam, Fcl);
     step<M>(P.integ, P.dt, P.prm, x, u, xn);
+  }
+  // increment Jacobians E = d(f - x)/dx, G = df/du in scalar S (and the increment)
+  template <class PS, class S>
+  __device__ static void ijac(const PS& P, const double* x, const double* u, S* E, S* G, S* dv = nullptr) {
+    inc_jac<M, S>(P.integ, P.dt, P.prm, x, u, dv, E, G);
+  }
+  // closed-loop increment and its Jacobian in FP32
+  template <class PS>
+  __device__ static void icl(const PS& P, const float* x, const float* u, const float* Gam, float* dv, float* Ecl) {
+    inc_cl<M, float>(P.integ, P.dt, P.prm, x, u, Gam, dv, Ecl);
+  }
+  template <class PS>
+  __device__ static void inc32(const PS& P, const float* x, const float* u, float* dv) {
+    step_inc<M, float>(P.integ, P.dt, P.prm, x, u, dv);
   }
 };
 
@@ -193,19 +222,96 @@ __device__ double terminal_cost(const ProbS<N, U>& P, const double* x) {
   return l;
 }
 
+
+// FP32 stage gradient from e = x - xref, eu = u - uref (approximate co-state pass)
+template <int N, int U>
+__device__ void stage_grad32(const ProbS<N, U>& P, const Aug& A, int t, const double* x, const double* u,
+                             float* lx, float* lu) {
+  float e[N], eu[U];
+#pragma unroll
+  for (int i = 0; i < N; i++) e[i] = float(x[i] - P.xref[i]);
+#pragma unroll
+  for (int i = 0; i < U; i++) eu[i] = float(u[i] - P.uref[i]);
+  mv<N, N>(P.Qs, e, lx);
+  mv<U, U>(P.Rs, eu, lu);
+  for (int r = 0; r < P.nw; r++) {
+    const int k = P.idx[r];
+    const double zk = P.isx[r] ? x[k] : u[k];
+    const float w = float(P.sgn[r] * (zk - P.bnd[r]));
+    float g1;
+    if (A.kind == AUG_BARRIER) g1 = float(A.mu) * float(P.sgn[r]) / (-w);
+    else g1 = float(A.rho) * (w - float(A.z[(size_t)t * P.nw + r] - A.v[(size_t)t * P.nw + r] / A.rho)) * float(P.sgn[r]);
+    if (P.isx[r]) lx[k] += g1;
+    else lu[k] += g1;
+  }
+}
+
+// Change of the stage cost l_t + c_t between the nominal (x0, u0) and (x0 + dx, u0 + du),
+// computed in FP32 from the deviations so that small differences keep their relative
+// precision.  Barrier rows: -mu log(1 - dw / slack0); *infeas when a row is not
+// strictly inside.
+template <int N, int U>
+__device__ float stage_delta(const ProbS<N, U>& P, const Aug& A, int t, const double* x0, const double* u0,
+                             const float* dx, const float* du, bool& infeas) {
+  float e[N], eu[U], qe[N], qd[N], re[U], rd[U];
+#pragma unroll
+  for (int i = 0; i < N; i++) e[i] = float(x0[i] - P.xref[i]);
+#pragma unroll
+  for (int i = 0; i < U; i++) eu[i] = float(u0[i] - P.uref[i]);
+  mv<N, N>(P.Qs, e, qe);   // (Q + Q^T) e
+  mv<N, N>(P.Qs, dx, qd);  // (Q + Q^T) dx
+  mv<U, U>(P.Rs, eu, re);
+  mv<U, U>(P.Rs, du, rd);
+  float l = 0.0f;
+#pragma unroll
+  for (int i = 0; i < N; i++) l += dx[i] * (qe[i] + 0.5f * qd[i]);
+#pragma unroll
+  for (int i = 0; i < U; i++) l += du[i] * (re[i] + 0.5f * rd[i]);
+  for (int r = 0; r < P.nw; r++) {
+    const int k = P.idx[r];
+    const double z0 = P.isx[r] ? x0[k] : u0[k];
+    const double w0 = P.sgn[r] * (z0 - P.bnd[r]);
+    const float dw = float(P.sgn[r]) * (P.isx[r] ? dx[k] : du[k]);
+    if (A.kind == AUG_BARRIER) {
+      const float ratio = dw / float(-w0);
+      if (!(ratio < 1.0f)) infeas = true;
+      else l -= float(A.mu) * log1pf(-ratio);
+    } else {
+      const float q0 = float(w0 - A.z[(size_t)t * P.nw + r] + A.v[(size_t)t * P.nw + r] / A.rho);
+      l += float(A.rho) * dw * (q0 + 0.5f * dw);
+    }
+  }
+  return l;
+}
+
+template <int N, int U>
+__device__ float terminal_delta(const ProbS<N, U>& P, const double* x0, const float* dx) {
+  float e[N], qe[N], qd[N];
+#pragma unroll
+  for (int i = 0; i < N; i++) e[i] = float(x0[i] - P.xref[i]);
+  mv<N, N>(P.Qfs, e, qe);
+  mv<N, N>(P.Qfs, dx, qd);
+  float l = 0.0f;
+#pragma unroll
+  for (int i = 0; i < N; i++) l += dx[i] * (qe[i] + 0.5f * qd[i]);
+  return l;
+}
+
 // ---------------------------------------------------------------------------
 // device workspace: base pointers of the concatenated per-instance arrays
 template <class L>
 struct Work {
-  double *xA, *uA;    // trajectory buffer A (the caller's output arrays)
-  double *xB, *uB;    // trajectory buffer B (workspace)
-  double *lam;        // (sum T+1) x N
-  double *F, *G, *d;  // (sum T) x N*N, x N*U, x U
-  L *Pm;              // (sum T+1) x N*N
-  L *Mm, *Rm;         // (sum T) x N*U, x U*U
-  L *Gam, *gam;       // (sum T) x U*N, x U
-  L *dx, *du;         // (sum T+1) x N, (sum T) x U
-  double *z, *v;      // (sum T) x nw (ADMM)
+  double *xA, *uA;      // trajectory buffer A (the caller's output arrays)
+  double *xB, *uB;      // trajectory buffer B (workspace)
+  double *lam;          // (sum T+1) x N
+  double *d;            // (sum T) x U           gradient d_t (FP64)
+  double *F64, *G64;    // (sum T) x N*N, x N*U  exact Jacobian increments (FP64)
+  L *E, *Gm;            // (sum T) x N*N, x N*U  LQR Jacobians: F - I and G
+  L *Pm;                // (sum T+1) x N*N
+  L *Mm, *Rm;           // (sum T) x N*U, x U*U
+  L *Gam, *gam;         // (sum T) x U*N, x U
+  L *dx, *du;           // (sum T+1) x N, (sum T) x U
+  double *z, *v;        // (sum T) x nw (ADMM)
 };
 
 template <class M, class L>
@@ -216,8 +322,8 @@ struct Inst {
   const double* x0;
   double *xn, *un, *xc, *uc;  // nominal and candidate trajectories
   double *xA, *uA;            // the caller's output arrays
-  double *lam, *F, *G, *d;
-  L *Pm, *Mm, *Rm, *Gam, *gam, *dx, *du;
+  double *lam, *d, *F64, *G64;
+  L *E, *Gm, *Pm, *Mm, *Rm, *Gam, *gam, *dx, *du;
   double *z, *v;
 
   __device__ void setup(const Work<L>& w, const InstDev& id, const double* x0_, int rank, int size, int nw) {
@@ -231,7 +337,9 @@ struct Inst {
     xn = xA; un = uA;
     xc = w.xB + xo * N; uc = w.uB + uo * U;
     lam = w.lam + xo * N;
-    F = w.F + uo * N * N; G = w.G + uo * N * U; d = w.d + uo * U;
+    d = w.d + uo * U;
+    F64 = w.F64 + uo * N * N; G64 = w.G64 + uo * N * U;
+    E = w.E + uo * N * N; Gm = w.Gm + uo * N * U;
     Pm = w.Pm + xo * N * N; Mm = w.Mm + uo * N * U; Rm = w.Rm + uo * U * U;
     Gam = w.Gam + uo * U * N; gam = w.gam + uo * U;
     dx = w.dx + xo * N; du = w.du + uo * U;
@@ -240,73 +348,84 @@ struct Inst {
   }
 };
 
+// F = I + E in L
+template <int N, class L>
+__device__ __forceinline__ void load_F(const L* E, L* F) {
+#pragma unroll (N <= 8 ? N * N : 4)
+  for (int i = 0; i < N * N; i++) F[i] = E[i];
+#pragma unroll
+  for (int i = 0; i < N; i++) F[i * N + i] += L(1);
+}
+
+template <int N, int U>
+__device__ void terminal_grad(const ProbS<N, U>& P, const double* xT, double* g) {
+#pragma unroll
+  for (int i = 0; i < N; i++) {
+    double s = 0.0;
+#pragma unroll
+    for (int j = 0; j < N; j++) s += (P.Qf[i * N + j] + P.Qf[j * N + i]) * (xT[j] - P.xref[j]);
+    g[i] = s;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // pass 1: co-state suffix scan (Alg. 1).  Returns max_t |d_t|_inf (inf if not finite).
+//
+// Exact form (FP64): element (g, F^T) with F = I + E, E from FP64 forward-mode AD.
 template <class M, class L, class Grp>
-__device__ double costate_pass(Grp& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>& P, const Aug& A) {
+__device__ double costate_exact(Grp& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>& P, const Aug& A) {
   constexpr int N = M::NX, U = M::NU;
   Aff<N, double> agg;
   set_identity(agg);
+  double lamT[N];
   if (I.last) {
-    // terminal co-state lam_{N+1} = d l_{N+1} / dx (eq. co-state-final), a constant map
+    // terminal co-state (eq. co-state-final): a constant map
+    terminal_grad(P, I.xn + (size_t)I.T * N, lamT);
 #pragma unroll
     for (int i = 0; i < N; i++) {
-      double s = 0.0;
-#pragma unroll
-      for (int j = 0; j < N; j++) s += (P.Qf[i * N + j] + P.Qf[j * N + i]) * (I.xn[I.T * N + j] - P.xref[j]);
-      agg.v[i] = s;
+      agg.v[i] = lamT[i];
 #pragma unroll
       for (int j = 0; j < N; j++) agg.M[i * N + j] = 0.0;
     }
   }
-  // up-sweep: agg = a_t (x) agg for t = b-1 .. a, with a_t = (q_t, F_t^T)
   for (int t = I.b - 1; t >= I.a; t--) {
-    double F[N * N], G[N * U], q[N], r[U];
+    double E[N * N], G[N * U], q[N], r[U];
     const double* x = I.xn + (size_t)t * N;
     const double* u = I.un + (size_t)t * U;
-    MOps<M>::jac(P, x, u, F, G);
+    MOps<M>::ijac(P, x, u, E, G);
+#pragma unroll (N <= 8 ? N * N : 4)
+    for (int i = 0; i < N * N; i++) { I.F64[(size_t)t * N * N + i] = E[i]; I.E[(size_t)t * N * N + i] = L(E[i]); }
 #pragma unroll
-    for (int i = 0; i < N * N; i++) I.F[(size_t)t * N * N + i] = F[i];
-#pragma unroll
-    for (int i = 0; i < N * U; i++) I.G[(size_t)t * N * U + i] = G[i];
+    for (int i = 0; i < N * U; i++) { I.G64[(size_t)t * N * U + i] = G[i]; I.Gm[(size_t)t * N * U + i] = L(G[i]); }
     stage_grad(P, A, t, x, u, q, r);
     double vn[N];
-    mtv<N, N>(F, agg.v, vn);
+    mtv<N, N>(E, agg.v, vn);  // (I + E)^T v = v + E^T v
 #pragma unroll
-    for (int i = 0; i < N; i++) agg.v[i] = vn[i] + q[i];
+    for (int i = 0; i < N; i++) agg.v[i] += vn[i] + q[i];
     if (!I.last) {
       double Mn[N * N];
-      mtm<N, N, N>(F, agg.M, Mn);
-#pragma unroll
-      for (int i = 0; i < N * N; i++) agg.M[i] = Mn[i];
+      mtm<N, N, N>(E, agg.M, Mn);
+#pragma unroll (N <= 8 ? N * N : 4)
+      for (int i = 0; i < N * N; i++) agg.M[i] += Mn[i];
     }
   }
   bool ok = true;
   Aff<N, double> inc = g.scan(agg, CostateOp(), true, ok);
-  // downsweep from lam at the chunk end (the suffix has a zero matrix part)
   double lam[N];
-  if (I.last) {
 #pragma unroll
-    for (int i = 0; i < N; i++) {
-      double s = 0.0;
-#pragma unroll
-      for (int j = 0; j < N; j++) s += (P.Qf[i * N + j] + P.Qf[j * N + i]) * (I.xn[I.T * N + j] - P.xref[j]);
-      lam[i] = s;
-      I.lam[(size_t)I.T * N + i] = s;
-    }
-  } else {
-#pragma unroll
-    for (int i = 0; i < N; i++) lam[i] = inc.v[i];
+  for (int i = 0; i < N; i++) {
+    lam[i] = I.last ? lamT[i] : inc.v[i];
+    if (I.last) I.lam[(size_t)I.T * N + i] = lam[i];
   }
   double dmax = 0.0;
   for (int t = I.b - 1; t >= I.a; t--) {
     const double* x = I.xn + (size_t)t * N;
     const double* u = I.un + (size_t)t * U;
-    const double* F = I.F + (size_t)t * N * N;
-    const double* G = I.G + (size_t)t * N * U;
+    const double* E = I.F64 + (size_t)t * N * N;
+    const double* G = I.G64 + (size_t)t * N * U;
     double q[N], r[U], ln[N], dd[U];
     stage_grad(P, A, t, x, u, q, r);
-    mtv<N, N>(F, lam, ln);
+    mtv<N, N>(E, lam, ln);
     mtv<N, U>(G, lam, dd);
 #pragma unroll
     for (int i = 0; i < U; i++) {
@@ -317,13 +436,132 @@ __device__ double costate_pass(Grp& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>&
     }
 #pragma unroll
     for (int i = 0; i < N; i++) {
-      lam[i] = ln[i] + q[i];
+      lam[i] += ln[i] + q[i];
       I.lam[(size_t)t * N + i] = lam[i];
     }
   }
   double red[1] = {dmax};
   g.template reduce<1>(red, 1u);
   return red[0];
+}
+
+// Mixed form (L = float): map v -> g + (I + D) v with g in FP64 and the matrix increment D
+// in FP32; the increments E, G and the stage gradients come from FP32 AD.  Accurate to
+// about 1e-7 relative in the gradient terms, which the final exact pass removes.
+template <int N>
+struct IncAff {
+  float D[N * N];
+  double g[N];
+};
+template <int N>
+PTN_HD void set_identity(IncAff<N>& e) {
+#pragma unroll
+  for (int i = 0; i < N * N; i++) e.D[i] = 0.0f;
+#pragma unroll
+  for (int i = 0; i < N; i++) e.g[i] = 0.0;
+}
+// a earlier than b:  (I + Da)(I + Db) = I + Da + Db + Da Db,  g = ga + gb + Da gb
+struct IncCostateOp {
+  template <int N>
+  PTN_HD bool operator()(const IncAff<N>& a, const IncAff<N>& b, IncAff<N>& o) const {
+    IncAff<N> r;
+    float DD[N * N], gb[N], Dg[N];
+    mm<N, N, N>(a.D, b.D, DD);
+#pragma unroll (N <= 8 ? N * N : 4)
+    for (int i = 0; i < N * N; i++) r.D[i] = a.D[i] + b.D[i] + DD[i];
+#pragma unroll
+    for (int i = 0; i < N; i++) gb[i] = float(b.g[i]);
+    mv<N, N>(a.D, gb, Dg);
+#pragma unroll
+    for (int i = 0; i < N; i++) r.g[i] = a.g[i] + b.g[i] + double(Dg[i]);
+    o = r;
+    return true;
+  }
+};
+
+template <class M, class Grp>
+__device__ double costate_mixed(Grp& g, Inst<M, float>& I, const ProbS<M::NX, M::NU>& P, const Aug& A) {
+  constexpr int N = M::NX, U = M::NU;
+  IncAff<N> agg;
+  set_identity(agg);
+  double lamT[N];
+  if (I.last) {
+    terminal_grad(P, I.xn + (size_t)I.T * N, lamT);
+#pragma unroll
+    for (int i = 0; i < N; i++) {
+      agg.g[i] = lamT[i];
+#pragma unroll
+      for (int j = 0; j < N; j++) agg.D[i * N + j] = (i == j) ? -1.0f : 0.0f;  // constant map
+    }
+  }
+  for (int t = I.b - 1; t >= I.a; t--) {
+    float E[N * N], G[N * U], q[N], r[U], gf[N], Eg[N];
+    const double* x = I.xn + (size_t)t * N;
+    const double* u = I.un + (size_t)t * U;
+    MOps<M>::ijac(P, x, u, E, G);
+#pragma unroll (N <= 8 ? N * N : 4)
+    for (int i = 0; i < N * N; i++) I.E[(size_t)t * N * N + i] = E[i];
+#pragma unroll
+    for (int i = 0; i < N * U; i++) I.Gm[(size_t)t * N * U + i] = G[i];
+    stage_grad32(P, A, t, x, u, q, r);
+#pragma unroll
+    for (int i = 0; i < N; i++) gf[i] = float(agg.g[i]);
+    mtv<N, N>(E, gf, Eg);
+#pragma unroll
+    for (int i = 0; i < N; i++) agg.g[i] += double(q[i] + Eg[i]);
+    if (!I.last) {
+      float ED[N * N];
+      mtm<N, N, N>(E, agg.D, ED);
+#pragma unroll (N <= 8 ? N : 4)
+      for (int i = 0; i < N; i++)
+#pragma unroll (N <= 8 ? N : 4)
+        for (int j = 0; j < N; j++) agg.D[i * N + j] += E[j * N + i] + ED[i * N + j];
+    }
+  }
+  bool ok = true;
+  IncAff<N> inc = g.scan(agg, IncCostateOp(), true, ok);
+  double lam[N];
+#pragma unroll
+  for (int i = 0; i < N; i++) {
+    lam[i] = I.last ? lamT[i] : inc.g[i];
+    if (I.last) I.lam[(size_t)I.T * N + i] = lam[i];
+  }
+  double dmax = 0.0;
+  for (int t = I.b - 1; t >= I.a; t--) {
+    const double* x = I.xn + (size_t)t * N;
+    const double* u = I.un + (size_t)t * U;
+    const float* E = I.E + (size_t)t * N * N;
+    const float* G = I.Gm + (size_t)t * N * U;
+    float q[N], r[U], lf[N], ln[N], dd[U];
+    stage_grad32(P, A, t, x, u, q, r);
+#pragma unroll
+    for (int i = 0; i < N; i++) lf[i] = float(lam[i]);
+    mtv<N, N>(E, lf, ln);
+    mtv<N, U>(G, lf, dd);
+#pragma unroll
+    for (int i = 0; i < U; i++) {
+      const double di = double(dd[i] + r[i]);
+      I.d[(size_t)t * U + i] = di;
+      const double ad = fabs(di);
+      dmax = (ad <= dmax) ? dmax : (isfinite(ad) ? ad : INFINITY);
+    }
+#pragma unroll
+    for (int i = 0; i < N; i++) {
+      lam[i] += double(ln[i] + q[i]);
+      I.lam[(size_t)t * N + i] = lam[i];
+    }
+  }
+  double red[1] = {dmax};
+  g.template reduce<1>(red, 1u);
+  return red[0];
+}
+
+template <class M, class L, class Grp>
+__device__ double costate_pass(Grp& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>& P, const Aug& A, bool exact) {
+  if constexpr (std::is_same<L, float>::value) {
+    if (!exact) return costate_mixed(g, I, P, A);
+  }
+  return costate_exact(g, I, P, A);
 }
 
 // pass 2: second-order expansion (Sec. III-C).  Needs lam from pass 1 (group-synced).
@@ -336,7 +574,7 @@ __device__ void quadratize(Grp& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>& P, 
     L Pm[N * N], Mm[N * U], Rm[U * U];
     MOps<M>::hess(P, x, u, I.lam + (size_t)(t + 1) * N, Pm, Mm, Rm);
     stage_hess_add(P, A, x, u, Pm, Rm);
-#pragma unroll
+#pragma unroll (N <= 8 ? N * N : 4)
     for (int i = 0; i < N * N; i++) I.Pm[(size_t)t * N * N + i] = Pm[i];
 #pragma unroll
     for (int i = 0; i < N * U; i++) I.Mm[(size_t)t * N * U + i] = Mm[i];
@@ -344,7 +582,7 @@ __device__ void quadratize(Grp& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>& P, 
     for (int i = 0; i < U * U; i++) I.Rm[(size_t)t * U * U + i] = Rm[i];
   }
   if (I.last) {
-#pragma unroll
+#pragma unroll (N <= 8 ? N * N : 4)
     for (int i = 0; i < N * N; i++) I.Pm[(size_t)I.T * N * N + i] = L(P.Qf[i] + P.Qf[(i % N) * N + i / N]);
   }
   g.sync();
@@ -352,7 +590,7 @@ __device__ void quadratize(Grp& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>& P, 
 
 // pass 3: value suffix scan (Alg. 2) + feedback sweep.  Returns true on success; false
 // (group-uniform) when some R~_t, Q_t is not PD or some I + C J is singular.
-template <class M, class L, class Grp>
+template <class M, class L, class SV, class Grp>
 __device__ bool value_pass(Grp& g, Inst<M, L>& I, double alpha) {
   constexpr int N = M::NX, U = M::NU;
   bool ok = true, have = false;
@@ -364,30 +602,32 @@ __device__ bool value_pass(Grp& g, Inst<M, L>& I, double alpha) {
   }
   for (int t = I.b - 1; t >= I.a; t--) {
     Val<N, L> e;
-    ok &= value_init<N, U, L>(I.F + (size_t)t * N * N, I.G + (size_t)t * N * U, I.Pm + (size_t)t * N * N,
-                              I.Mm + (size_t)t * N * U, I.Rm + (size_t)t * U * U, I.d + (size_t)t * U, alpha, e);
+    L F[N * N];
+    load_F<N>(I.E + (size_t)t * N * N, F);
+    ok &= value_init<N, U, L, SV>(F, I.Gm + (size_t)t * N * U, I.Pm + (size_t)t * N * N, I.Mm + (size_t)t * N * U,
+                                  I.Rm + (size_t)t * U * U, I.d + (size_t)t * U, alpha, e);
     if (!have) { agg = e; have = true; }
-    else ok &= ValueOp()(e, agg, agg);
+    else ok &= ValueOp<SV>()(e, agg, agg);
   }
-  Val<N, L> inc = g.scan(agg, ValueOp(), true, ok);
+  Val<N, L> inc = g.scan(agg, ValueOp<SV>(), true, ok);
   L S[N * N], s[N];
   if (I.last) {
-#pragma unroll
+#pragma unroll (N <= 8 ? N * N : 4)
     for (int i = 0; i < N * N; i++) S[i] = I.Pm[(size_t)I.T * N * N + i];
 #pragma unroll
     for (int i = 0; i < N; i++) s[i] = L(0);
   } else {
     // S_t = J_{t,<|}, s_t = -eta_{t,<|}
-#pragma unroll
+#pragma unroll (N <= 8 ? N * N : 4)
     for (int i = 0; i < N * N; i++) S[i] = inc.J[i];
 #pragma unroll
     for (int i = 0; i < N; i++) s[i] = -inc.eta[i];
   }
   for (int t = I.b - 1; t >= I.a; t--) {
-    L Gam[U * N], gam[U];
-    ok &= riccati_step<N, U, L>(I.F + (size_t)t * N * N, I.G + (size_t)t * N * U, I.Pm + (size_t)t * N * N,
-                                I.Mm + (size_t)t * N * U, I.Rm + (size_t)t * U * U, I.d + (size_t)t * U, alpha, S,
-                                s, Gam, gam);
+    L Gam[U * N], gam[U], F[N * N];
+    load_F<N>(I.E + (size_t)t * N * N, F);
+    ok &= riccati_step<N, U, L, SV>(F, I.Gm + (size_t)t * N * U, I.Pm + (size_t)t * N * N, I.Mm + (size_t)t * N * U,
+                                    I.Rm + (size_t)t * U * U, I.d + (size_t)t * U, alpha, S, s, Gam, gam);
 #pragma unroll
     for (int i = 0; i < U * N; i++) I.Gam[(size_t)t * U * N + i] = Gam[i];
 #pragma unroll
@@ -407,29 +647,19 @@ __device__ void state_pass(Grp& g, Inst<M, L>& I, double& G1, double& G2) {
   set_identity(agg);
   const bool first = (I.a == 0);
   if (first) {
-#pragma unroll
+#pragma unroll (N <= 8 ? N * N : 4)
     for (int i = 0; i < N * N; i++) agg.M[i] = L(0);  // the first element has F = 0
   }
   for (int t = I.a; t < I.b; t++) {
-    L Fc[N * N], e[N];
-    const double* F = I.F + (size_t)t * N * N;
-    const double* G = I.G + (size_t)t * N * U;
+    L Fc[N * N], e[N], GG[N * N];
+    const L* G = I.Gm + (size_t)t * N * U;
     const L* Gam = I.Gam + (size_t)t * U * N;
     const L* gam = I.gam + (size_t)t * U;
-#pragma unroll
-    for (int i = 0; i < N; i++) {
-#pragma unroll
-      for (int j = 0; j < N; j++) {
-        L s = L(F[i * N + j]);
-#pragma unroll
-        for (int k = 0; k < U; k++) s += L(G[i * U + k]) * Gam[k * N + j];
-        Fc[i * N + j] = s;
-      }
-      L s = L(0);
-#pragma unroll
-      for (int k = 0; k < U; k++) s += L(G[i * U + k]) * gam[k];
-      e[i] = s;
-    }
+    load_F<N>(I.E + (size_t)t * N * N, Fc);
+    mm<N, U, N>(G, Gam, GG);
+#pragma unroll (N <= 8 ? N * N : 4)
+    for (int i = 0; i < N * N; i++) Fc[i] += GG[i];
+    mv<N, U>(G, gam, e);
     L vn[N];
     mv<N, N>(Fc, agg.v, vn);
 #pragma unroll
@@ -437,7 +667,7 @@ __device__ void state_pass(Grp& g, Inst<M, L>& I, double& G1, double& G2) {
     if (!first) {
       L Mn[N * N];
       mm<N, N, N>(Fc, agg.M, Mn);
-#pragma unroll
+#pragma unroll (N <= 8 ? N * N : 4)
       for (int i = 0; i < N * N; i++) agg.M[i] = Mn[i];
     }
   }
@@ -448,66 +678,49 @@ __device__ void state_pass(Grp& g, Inst<M, L>& I, double& G1, double& G2) {
   for (int i = 0; i < N; i++) dx[i] = first ? L(0) : inc.v[i];
   double g1 = 0.0, g2 = 0.0;
   for (int t = I.a; t < I.b; t++) {
-    const double* F = I.F + (size_t)t * N * N;
-    const double* G = I.G + (size_t)t * N * U;
+    const L* G = I.Gm + (size_t)t * N * U;
     const L* Gam = I.Gam + (size_t)t * U * N;
     const L* gam = I.gam + (size_t)t * U;
     const L* Pm = I.Pm + (size_t)t * N * N;
     const L* Mm = I.Mm + (size_t)t * N * U;
     const L* Rm = I.Rm + (size_t)t * U * U;
-    L du[U];
+    L du[U], Gd[U];
+    mv<U, N>(Gam, dx, Gd);
 #pragma unroll
     for (int i = 0; i < U; i++) {
-      L s = gam[i];
-#pragma unroll
-      for (int j = 0; j < N; j++) s += Gam[i * N + j] * dx[j];
-      du[i] = s;
-      I.du[(size_t)t * U + i] = s;
-      g1 += I.d[(size_t)t * U + i] * double(s);
+      du[i] = Gd[i] + gam[i];
+      I.du[(size_t)t * U + i] = du[i];
+      g1 += I.d[(size_t)t * U + i] * double(du[i]);
     }
 #pragma unroll
     for (int i = 0; i < N; i++) I.dx[(size_t)t * N + i] = dx[i];
-    double q = 0.0;
+    L Pd[N], Md[N], Rd[U];
+    mv<N, N>(Pm, dx, Pd);
+    mv<N, U>(Mm, du, Md);
+    mv<U, U>(Rm, du, Rd);
+    L q = L(0);
 #pragma unroll
-    for (int i = 0; i < N; i++) {
-      double sp = 0.0, sm = 0.0;
+    for (int i = 0; i < N; i++) q += dx[i] * (L(0.5) * Pd[i] + Md[i]);
 #pragma unroll
-      for (int j = 0; j < N; j++) sp += double(Pm[i * N + j]) * double(dx[j]);
+    for (int i = 0; i < U; i++) q += L(0.5) * du[i] * Rd[i];
+    g2 += double(q);
+    L Edx[N], Gdu[N];
+    mv<N, N>(I.E + (size_t)t * N * N, dx, Edx);
+    mv<N, U>(G, du, Gdu);
 #pragma unroll
-      for (int j = 0; j < U; j++) sm += double(Mm[i * U + j]) * double(du[j]);
-      q += double(dx[i]) * (0.5 * sp + sm);
-    }
-#pragma unroll
-    for (int i = 0; i < U; i++) {
-      double sr = 0.0;
-#pragma unroll
-      for (int j = 0; j < U; j++) sr += double(Rm[i * U + j]) * double(du[j]);
-      q += 0.5 * double(du[i]) * sr;
-    }
-    g2 += q;
-    L dn[N];
-#pragma unroll
-    for (int i = 0; i < N; i++) {
-      double s = 0.0;
-#pragma unroll
-      for (int j = 0; j < N; j++) s += F[i * N + j] * double(dx[j]);
-#pragma unroll
-      for (int j = 0; j < U; j++) s += G[i * U + j] * double(du[j]);
-      dn[i] = L(s);
-    }
-#pragma unroll
-    for (int i = 0; i < N; i++) dx[i] = dn[i];
+    for (int i = 0; i < N; i++) dx[i] += Edx[i] + Gdu[i];
   }
   if (I.last) {
     const L* PT = I.Pm + (size_t)I.T * N * N;
+    L Pd[N];
+    mv<N, N>(PT, dx, Pd);
+    L q = L(0);
 #pragma unroll
     for (int i = 0; i < N; i++) {
       I.dx[(size_t)I.T * N + i] = dx[i];
-      double sp = 0.0;
-#pragma unroll
-      for (int j = 0; j < N; j++) sp += double(PT[i * N + j]) * double(dx[j]);
-      g2 += 0.5 * double(dx[i]) * sp;
+      q += L(0.5) * dx[i] * Pd[i];
     }
+    g2 += double(q);
   }
   double red[2] = {g1, g2};
   g.template reduce<2>(red, 0u);
@@ -523,18 +736,20 @@ __device__ void state_pass(Grp& g, Inst<M, L>& I, double& G1, double& G2) {
 // boundary guess (initially x^ + s dx), and Newton corrections of the boundary
 // states come from a prefix scan of (chunk Jacobian, end defect) elements.
 // Writes the candidate into (xc, uc).  Returns true when converged, finite and (for
-// the barrier) strictly feasible; *Jc receives the augmented cost J_c.
+// the barrier) strictly feasible.  *Jm receives the merit: the augmented cost J_c
+// (FP64 mode) or its change J_c(s) - J_c(0) accumulated from FP32 stage differences
+// (mixed modes).
 template <class M, class L, class Grp>
 __device__ bool rollout(Grp& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>& P, const OptDev& O, const Aug& A,
-                        double s, bool closed, double* Jc, int* iters) {
+                        double s, bool precise, double* Jm, int* iters) {
   constexpr int N = M::NX, U = M::NU;
+  const bool MIXED = std::is_same<L, float>::value && !precise;
   double X[N];
   const bool own = (I.a < I.b);
   const bool first = (I.a == 0);
 #pragma unroll
   for (int i = 0; i < N; i++)
-    X[i] = first ? I.x0[i] : (closed ? I.xn[(size_t)I.a * N + i] + s * double(I.dx[(size_t)I.a * N + i])
-                                     : I.xc[(size_t)I.a * N + i]);
+    X[i] = first ? I.x0[i] : I.xn[(size_t)I.a * N + i] + s * double(I.dx[(size_t)I.a * N + i]);
   bool conv = false, feas = true;
   double J = INFINITY;
   for (int it = 0; it < O.roll_max_iter; it++) {
@@ -548,7 +763,6 @@ __device__ bool rollout(Grp& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>& P, con
 #pragma unroll
       for (int i = 0; i < N; i++) Xn[i] = I.xc[(size_t)I.b * N + i];
     }
-    g.sync();
     double xt[N], cost = 0.0;
     bool inf = false;
     Aff<N, L> el;
@@ -557,52 +771,87 @@ __device__ bool rollout(Grp& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>& P, con
     for (int i = 0; i < N; i++) xt[i] = X[i];
     for (int t = I.a; t < I.b; t++) {
       const L* Gam = I.Gam + (size_t)t * U * N;
-      double ut[U];
-#pragma unroll
-      for (int i = 0; i < U; i++) {
-        double v = I.un[(size_t)t * U + i];
-        if (closed) {
-          v += s * double(I.gam[(size_t)t * U + i]);
-#pragma unroll
-          for (int j = 0; j < N; j++) v += double(Gam[i * N + j]) * (xt[j] - I.xn[(size_t)t * N + j]);
-        }
-        ut[i] = v;
-        I.uc[(size_t)t * U + i] = v;
-      }
-      if (t > I.a) {
-#pragma unroll
-        for (int i = 0; i < N; i++) I.xc[(size_t)t * N + i] = xt[i];
-      }
-      cost += stage_cost(P, A, t, xt, ut, inf);
-      double xnext[N];
+      const double* xh = I.xn + (size_t)t * N;
+      const double* uh = I.un + (size_t)t * U;
       L Fc[N * N];
-      if (closed) {
-        MOps<M>::cl(P, xt, ut, Gam, xnext, Fc);
-      } else {
-        L Z[U * N];
+      if (MIXED) {
+        float dxh[N], duf[U], Gd[U], dv[N], Ex[N * N], Gx[N * U], rx[N], ru[U], cx[N], cu[N];
 #pragma unroll
-        for (int i = 0; i < U * N; i++) Z[i] = L(0);
-        MOps<M>::cl(P, xt, ut, Z, xnext, Fc);
+        for (int i = 0; i < N; i++) dxh[i] = float(xt[i] - xh[i]);
+        mv<U, N>(Gam, dxh, Gd);
+        double ut[U];
+#pragma unroll
+        for (int i = 0; i < U; i++) {
+          duf[i] = float(s) * I.gam[(size_t)t * U + i] + Gd[i];
+          ut[i] = uh[i] + double(duf[i]);
+          I.uc[(size_t)t * U + i] = ut[i];
+          ru[i] = float(ut[i] - double(float(ut[i])));
+        }
+        if (t > I.a) {
+#pragma unroll
+          for (int i = 0; i < N; i++) I.xc[(size_t)t * N + i] = xt[i];
+        }
+        cost += double(stage_delta(P, A, t, xh, uh, dxh, duf, inf));
+        // increment at the FP32-rounded point plus the first-order correction for the
+        // rounding residuals, so the step map stays smooth far below FP32 resolution
+        MOps<M>::ijac(P, xt, ut, Ex, Gx, dv);
+#pragma unroll
+        for (int i = 0; i < N; i++) rx[i] = float(xt[i] - double(float(xt[i])));
+        mv<N, N>(Ex, rx, cx);
+        mv<N, U>(Gx, ru, cu);
+        // closed-loop Jacobian F + G Gam = I + E + G Gam
+        mm<N, U, N>(Gx, Gam, Fc);
+#pragma unroll (N <= 8 ? N * N : 4)
+        for (int i = 0; i < N * N; i++) Fc[i] += Ex[i];
+#pragma unroll
+        for (int i = 0; i < N; i++) {
+          Fc[i * N + i] += 1.0f;
+          xt[i] += double(dv[i]) + double(cx[i] + cu[i]);
+        }
+      } else {
+        double ut[U];
+#pragma unroll
+        for (int i = 0; i < U; i++) {
+          double v = uh[i] + s * double(I.gam[(size_t)t * U + i]);
+#pragma unroll
+          for (int j = 0; j < N; j++) v += double(Gam[i * N + j]) * (xt[j] - xh[j]);
+          ut[i] = v;
+          I.uc[(size_t)t * U + i] = v;
+        }
+        if (t > I.a) {
+#pragma unroll
+          for (int i = 0; i < N; i++) I.xc[(size_t)t * N + i] = xt[i];
+        }
+        cost += stage_cost(P, A, t, xt, ut, inf);
+        double xnext[N];
+        MOps<M>::cl(P, xt, ut, Gam, xnext, Fc);
+#pragma unroll
+        for (int i = 0; i < N; i++) xt[i] = xnext[i];
       }
       if (!first) {
         L Mn[N * N];
         mm<N, N, N>(Fc, el.M, Mn);
-#pragma unroll
+#pragma unroll (N <= 8 ? N * N : 4)
         for (int i = 0; i < N * N; i++) el.M[i] = Mn[i];
       }
-#pragma unroll
-      for (int i = 0; i < N; i++) xt[i] = xnext[i];
     }
     double rmax = 0.0, xmax = 0.0;
     bool nonfin = !isfinite(cost);
     if (first) {
-#pragma unroll
+#pragma unroll (N <= 8 ? N * N : 4)
       for (int i = 0; i < N * N; i++) el.M[i] = L(0);
     }
     if (I.last) {
 #pragma unroll
       for (int i = 0; i < N; i++) I.xc[(size_t)I.T * N + i] = xt[i];
-      cost += terminal_cost(P, xt);
+      if (MIXED) {
+        float dT[N];
+#pragma unroll
+        for (int i = 0; i < N; i++) dT[i] = float(xt[i] - I.xn[(size_t)I.T * N + i]);
+        cost += double(terminal_delta(P, I.xn + (size_t)I.T * N, dT));
+      } else {
+        cost += terminal_cost(P, xt);
+      }
 #pragma unroll
       for (int i = 0; i < N; i++) el.v[i] = L(0);
     } else if (own) {
@@ -625,7 +874,8 @@ __device__ bool rollout(Grp& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>& P, con
     g.template reduce<5>(red, 0x1bu);  // max, max, sum, max, max
     if (iters) *iters = it + 1;
     if (red[4] > 0.0) return false;
-    if (red[0] <= O.roll_tol * (1.0 + red[1])) {
+    const double rtol = MIXED ? fmax(O.roll_tol, 1e-8) : O.roll_tol;
+    if (red[0] <= rtol * (1.0 + red[1])) {
       conv = true;
       feas = !(red[3] > 0.0);
       J = red[2];
@@ -636,7 +886,7 @@ __device__ bool rollout(Grp& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>& P, con
       for (int i = 0; i < N; i++) X[i] += double(inc.v[i]);
     }
   }
-  *Jc = J;
+  *Jm = J;
   return conv && feas && isfinite(J);
 }
 
@@ -666,24 +916,46 @@ __device__ double nominal_cost(Grp& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>&
 
 // ---------------------------------------------------------------------------
 struct NStats {
-  int iters, ls_rejects, factor_fails, roll_fails, roll_iters, ls_evals;
+  int iters, ls_rejects, factor_fails, roll_fails, roll_iters, ls_evals, exact_passes;
   double alpha;
   long long cyc[6];
 };
 
 // Newton iterations (Alg. 4) on the augmented sub-problem until max |d| <= tol.
-// Step acceptance and the alpha rule are the same readings as the CPU oracle's.
-template <class M, class L, class Grp>
+// Step acceptance and the alpha rule are the same readings as the CPU oracle's.  In the
+// mixed modes the gradient comes from the FP32-increment co-state pass until, at the
+// final tolerance, it falls below polish * tol; from then on the exact FP64 pass decides.
+template <class M, class L, class SV, class Grp>
 __device__ int newton_solve(Grp& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>& P, const OptDev& O, const Aug& A,
-                            double tol, NStats& st, double* rfinal) {
+                            double tol, bool final_level, NStats& st, double* rfinal) {
+  constexpr bool MIXED = std::is_same<L, float>::value;
   bool inf;
   double J0 = nominal_cost(g, I, P, A, &inf, nullptr);
   int rc = ST_ENOTCONV;
   double r = INFINITY;
+  bool exact = !MIXED;  // FP64 gradients, FP64 rollouts and absolute FP64 merits
   for (int it = 0; it <= O.max_newton; it++) {
     if (g.dead()) return ST_ETIMEOUT;
     long long c0 = clock64();
-    r = costate_pass(g, I, P, A);
+    r = costate_pass(g, I, P, A, exact);
+    if (MIXED && !exact && final_level && (r <= O.polish * tol || it >= O.polish_after)) {
+      // endgame: below the FP32 noise floor of gradients and merits, switch to FP64.
+      // First re-project the nominal onto the FP64 dynamics (one exact rollout with
+      // s = 0 under the last feedback), so that FP64 merits compare like with like.
+      exact = true;
+      st.exact_passes++;
+      double mproj;
+      int ri = 0;
+      if (rollout(g, I, P, O, A, 0.0, true, &mproj, &ri)) {
+        double* t1 = I.xn; I.xn = I.xc; I.xc = t1;
+        double* t2 = I.un; I.un = I.uc; I.uc = t2;
+      }
+      st.roll_iters += ri;
+      r = costate_pass(g, I, P, A, true);
+      J0 = nominal_cost(g, I, P, A, &inf, nullptr);
+    } else if (exact && MIXED) {
+      st.exact_passes++;
+    }
     long long c1 = clock64();
     st.cyc[0] += c1 - c0;
     if (r <= tol) { rc = ST_OK; break; }
@@ -692,7 +964,7 @@ __device__ int newton_solve(Grp& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>& P,
     quadratize(g, I, P, A);
     long long c2 = clock64();
     st.cyc[1] += c2 - c1;
-    while (!value_pass(g, I, st.alpha)) {
+    while (!value_pass<M, L, SV>(g, I, st.alpha)) {
       st.factor_fails++;
       st.alpha = fmax(10.0 * st.alpha, 1e-8);
       if (st.alpha > O.alpha_max || g.dead()) { *rfinal = r; return g.dead() ? ST_ETIMEOUT : ST_ENUM; }
@@ -704,19 +976,24 @@ __device__ int newton_solve(Grp& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>& P,
     long long c4 = clock64();
     st.cyc[3] += c4 - c3;
     bool accepted = false;
-    double s = 1.0, Js = INFINITY;
+    double s = 1.0, Js = INFINITY, dJ = INFINITY;
     for (int k = 0; k < O.ls_count; k++, s *= O.ls_beta) {
       int ri = 0;
-      const bool okr = rollout(g, I, P, O, A, s, true, &Js, &ri);
+      double m;
+      const bool okr = rollout(g, I, P, O, A, s, exact, &m, &ri);
       st.ls_evals++;
       st.roll_iters += ri;
       if (!okr) { st.roll_fails++; continue; }
-      if (Js <= J0 + O.armijo_c1 * s * G1 + O.armijo_eps * (1.0 + fabs(J0))) { accepted = true; break; }
+      const bool diff = MIXED && !exact;  // merits returned as FP32-accumulated differences
+      dJ = diff ? m : m - J0;
+      Js = diff ? J0 + m : m;
+      const double eps = diff ? O.armijo_eps32 : O.armijo_eps;
+      if (dJ <= O.armijo_c1 * s * G1 + eps * (1.0 + fabs(J0))) { accepted = true; break; }
     }
     st.cyc[4] += clock64() - c4;
     if (accepted) {
       const double pred = -(s * G1 + s * s * G2);
-      const double rho = pred > 0.0 ? (J0 - Js) / pred : 0.0;
+      const double rho = pred > 0.0 ? -dJ / pred : 0.0;
       if (rho > 0.75) st.alpha /= 3.0;
       else if (rho < 0.25) st.alpha *= 2.0;
       st.alpha = fmin(fmax(st.alpha, O.alpha_min), O.alpha_max);
@@ -733,11 +1010,11 @@ __device__ int newton_solve(Grp& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>& P,
   return rc;
 }
 
-// final residuals: r_stat (max |d|), r_dyn, r_feas, J, J_c; lam of the final point
+// final residuals: r_stat (max |d|, exact pass), r_dyn, r_feas, J, J_c; lam of the final point
 template <class M, class L, class Grp>
 __device__ void residuals(Grp& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>& P, const Aug& A, InfoDev& info) {
   constexpr int N = M::NX, U = M::NU;
-  info.r_stat = costate_pass(g, I, P, A);
+  info.r_stat = costate_pass(g, I, P, A, true);
   double rd = 0.0, rf = -INFINITY;
   for (int t = I.a; t < I.b; t++) {
     double xn[N];
@@ -780,8 +1057,8 @@ __device__ void finalize_traj(Grp& g, Inst<M, L>& I) {
   g.sync();
 }
 
-// initial nominal: x = rollout(x0, u_init) (open loop).  The candidate buffer is first
-// filled by one thread's sequential integration, which is the exact rollout.
+// initial nominal: x = rollout(x0, u_init) (open loop), integrated sequentially by the
+// group's first thread (FP64 states; FP32 increments in the mixed modes).
 template <class M, class L, class Grp>
 __device__ void initial_rollout(Grp& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>& P) {
   constexpr int N = M::NX, U = M::NU;
@@ -789,11 +1066,28 @@ __device__ void initial_rollout(Grp& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>
     double x[N];
 #pragma unroll
     for (int i = 0; i < N; i++) { x[i] = I.x0[i]; I.xn[i] = x[i]; }
-    for (int t = 0; t < I.T; t++) {
-      double xn[N];
-      MOps<M>::f(P, x, I.un + (size_t)t * U, xn);
+    float un_next[U];
 #pragma unroll
-      for (int i = 0; i < N; i++) { x[i] = xn[i]; I.xn[(size_t)(t + 1) * N + i] = x[i]; }
+    for (int i = 0; i < U; i++) un_next[i] = float(I.un[i]);
+    for (int t = 0; t < I.T; t++) {
+      if constexpr (std::is_same<L, float>::value) {
+        float xf[N], uf[U], dv[N];
+#pragma unroll
+        for (int i = 0; i < N; i++) xf[i] = float(x[i]);
+#pragma unroll
+        for (int i = 0; i < U; i++) {
+          uf[i] = un_next[i];
+          if (t + 1 < I.T) un_next[i] = float(I.un[(size_t)(t + 1) * U + i]);  // prefetch
+        }
+        MOps<M>::inc32(P, xf, uf, dv);
+#pragma unroll
+        for (int i = 0; i < N; i++) { x[i] += double(dv[i]); I.xn[(size_t)(t + 1) * N + i] = x[i]; }
+      } else {
+        double xn[N];
+        MOps<M>::f(P, x, I.un + (size_t)t * U, xn);
+#pragma unroll
+        for (int i = 0; i < N; i++) { x[i] = xn[i]; I.xn[(size_t)(t + 1) * N + i] = x[i]; }
+      }
     }
   }
   g.sync();
@@ -801,7 +1095,7 @@ __device__ void initial_rollout(Grp& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>
 
 // ---------------------------------------------------------------------------
 // the whole solve of one instance (IP when O.method == 0, ADMM when 1)
-template <class M, class L, class Grp>
+template <class M, class L, class SV, class Grp>
 __device__ void solve_instance(Grp& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>& P, const OptDev& O,
                                const double* u_init, InfoDev* info_out) {
   constexpr int N = M::NX, U = M::NU;
@@ -810,13 +1104,19 @@ __device__ void solve_instance(Grp& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>&
   info.factor_fails = 0; info.roll_fails = 0; info.roll_iters = 0; info.ls_evals = 0;
   info.mu = 0; info.alpha = 0; info.r_stat = 0; info.r_dyn = 0; info.r_feas = 0; info.r_kkt = 0;
   info.J = 0; info.J_c = 0; info.r_p = 0; info.r_d = 0;
-  for (int t = I.a; t < I.b; t++)
+  for (int t = I.a; t < I.b; t++) {
 #pragma unroll
-    for (int i = 0; i < U; i++) I.un[(size_t)t * U + i] = u_init ? u_init[(size_t)t * U + i] : 0.0;
+    for (int i = 0; i < U; i++) {
+      I.un[(size_t)t * U + i] = u_init ? u_init[(size_t)t * U + i] : 0.0;
+      I.gam[(size_t)t * U + i] = L(0);
+    }
+#pragma unroll
+    for (int i = 0; i < U * N; i++) I.Gam[(size_t)t * U * N + i] = L(0);
+  }
   g.sync();
-  initial_rollout(g, I, P);
-  NStats st{0, 0, 0, 0, 0, 0, O.alpha0, {0, 0, 0, 0, 0, 0}};
   const long long c_start = clock64();
+  initial_rollout(g, I, P);
+  NStats st{0, 0, 0, 0, 0, 0, 0, O.alpha0, {0, 0, 0, 0, 0, 0}};
   Aug A;
   int rc = ST_OK;
   if (O.method == 0) {
@@ -833,7 +1133,7 @@ __device__ void solve_instance(Grp& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>&
         const bool lastlev = mu <= O.mu_final * (1.0 + 1e-9);
         A.mu = mu;
         double r;
-        rc = newton_solve(g, I, P, O, A, lastlev ? O.tol_final : O.tol_inner, st, &r);
+        rc = newton_solve<M, L, SV>(g, I, P, O, A, lastlev ? O.tol_final : O.tol_inner, lastlev, st, &r);
         level++;
         if (rc == ST_ENUM || rc == ST_ETIMEOUT || lastlev) break;
         mu = O.mu0 * pow(O.zeta, (double)level);
@@ -859,7 +1159,7 @@ __device__ void solve_instance(Grp& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>&
     double rp = INFINITY, rdl = INFINITY;
     for (k = 0; k < kmax; k++) {
       double r;
-      const int s = newton_solve(g, I, P, O, A, O.tol_final, st, &r);
+      const int s = newton_solve<M, L, SV>(g, I, P, O, A, O.tol_final, true, st, &r);
       if (s == ST_ENUM || s == ST_ETIMEOUT) { rc = s; k++; break; }
       double lrp = 0.0, lrd = 0.0;
       for (int t = I.a; t < I.b; t++)
@@ -895,10 +1195,11 @@ __device__ void solve_instance(Grp& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>&
   info.roll_fails = st.roll_fails;
   info.roll_iters = st.roll_iters;
   info.ls_evals = st.ls_evals;
+  info.exact_passes = st.exact_passes;
   info.alpha = st.alpha;
+  info.r_kkt = fmax(fmax(info.r_stat, info.r_dyn), fmax(info.r_feas, O.method == 0 ? info.mu : 0.0));
   for (int k = 0; k < 5; k++) info.cyc[k] = st.cyc[k];
   info.cyc[5] = clock64() - c_start - (st.cyc[0] + st.cyc[1] + st.cyc[2] + st.cyc[3] + st.cyc[4]);
-  info.r_kkt = fmax(fmax(info.r_stat, info.r_dyn), fmax(info.r_feas, O.method == 0 ? info.mu : 0.0));
   if (g.rank() == 0) *info_out = info;
 }
 
@@ -925,7 +1226,7 @@ constexpr size_t scratch_bytes(int nwarps) {
 }
 
 // one CTA per instance (batches and short horizons)
-template <class M, class L>
+template <class M, class L, class SV>
 __global__ void __launch_bounds__(256) k_solve_cta(KArgs args, Work<L> w) {
   constexpr int N = M::NX, U = M::NU;
   extern __shared__ __align__(16) char smem[];
@@ -939,11 +1240,11 @@ __global__ void __launch_bounds__(256) k_solve_cta(KArgs args, Work<L> w) {
   CtaGroup g{scratch};
   Inst<M, L> I;
   I.setup(w, id, args.x0 + (size_t)bi * N, threadIdx.x, blockDim.x, P.nw);
-  solve_instance<M, L>(g, I, P, O, args.u_init ? args.u_init + (size_t)id.uoff * U : nullptr, args.info + bi);
+  solve_instance<M, L, SV>(g, I, P, O, args.u_init ? args.u_init + (size_t)id.uoff * U : nullptr, args.info + bi);
 }
 
 // the whole cooperative grid on one instance (long horizons)
-template <class M, class L>
+template <class M, class L, class SV>
 __global__ void __launch_bounds__(128) k_solve_grid(KArgs args, Work<L> w) {
   constexpr int N = M::NX, U = M::NU;
   extern __shared__ __align__(16) char smem[];
@@ -957,7 +1258,7 @@ __global__ void __launch_bounds__(128) k_solve_grid(KArgs args, Work<L> w) {
   GridGroup g{scratch, args.gs, 0, &sdead};
   Inst<M, L> I;
   I.setup(w, id, args.x0, g.rank(), g.size(), P.nw);
-  solve_instance<M, L>(g, I, P, O, args.u_init, args.info);
+  solve_instance<M, L, SV>(g, I, P, O, args.u_init, args.info);
 }
 
 }  // namespace ptn

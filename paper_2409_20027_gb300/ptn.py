@@ -16,7 +16,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libptn.so")
 
-PTN_FP64, PTN_FP32_FP64SOLVE = 0, 1
+PTN_FP64, PTN_FP32_FP64SOLVE, PTN_FP32 = 0, 1, 2
 METHOD_IP, METHOD_ADMM = 0, 1
 STATUS = {0: "ok", -1: "invalid argument", -2: "infeasible start", -3: "not converged",
           -4: "numerical failure", -5: "device wait timed out", -6: "CUDA error"}
@@ -36,9 +36,10 @@ class Problem(C.Structure):
 
 
 _OPT_INTS = ["precision", "max_newton", "max_outer", "ls_count", "admm_fixed_iters", "roll_max_iter",
-             "block_threads", "grid_min_T", "grid_steps_per_thread", "pad"]
+             "block_threads", "grid_min_T", "grid_steps_per_thread", "polish_after"]
 _OPT_DBLS = ["mu0", "zeta", "mu_final", "tol_inner", "tol_final", "rho", "admm_tol", "alpha0",
-             "alpha_min", "alpha_max", "ls_beta", "armijo_c1", "armijo_eps", "roll_tol"]
+             "alpha_min", "alpha_max", "ls_beta", "armijo_c1", "armijo_eps", "roll_tol", "polish",
+             "armijo_eps32"]
 
 
 class Options(C.Structure):
@@ -47,7 +48,8 @@ class Options(C.Structure):
 
 class Info(C.Structure):
     _fields_ = [(k, C.c_int) for k in ["status", "newton_iters", "outer_iters", "ls_rejects",
-                                       "factor_fails", "roll_fails", "roll_iters", "ls_evals"]] + \
+                                       "factor_fails", "roll_fails", "roll_iters", "ls_evals",
+                                       "exact_passes", "pad"]] + \
                [(k, C.c_double) for k in ["mu", "alpha", "r_stat", "r_dyn", "r_feas", "r_kkt", "J",
                                           "J_c", "r_p", "r_d"]] + \
                [("cycles", C.c_longlong * 6)]

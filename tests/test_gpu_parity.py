@@ -99,14 +99,31 @@ def test_cartpole_fp64_cta(ptn):
     check_solution(info, ref, x, u, lam, FP64_TOL)
 
 
-@pytest.mark.parametrize("T,grid", [(256, False), (1024, True), (4096, True)])
-def test_cartpole_fp32_matches_oracle(ptn, T, grid):
+@pytest.mark.parametrize("T,grid,prec", [(256, False, 1), (1024, True, 1), (4096, True, 1), (4096, True, 2)])
+def test_cartpole_fp32_matches_oracle(ptn, T, grid, prec):
+    # The reduced Hessian of this single-shooting problem is ill-conditioned, so a
+    # 1e-6 stationarity tolerance leaves the controls determined only to ~1e-3: two
+    # different iteration paths (FP32 vs FP64 arithmetic) stop at different points of
+    # that ball.  Both sides therefore solve to 1e-7, where the minimiser is pinned to
+    # well below the 1e-4 parity bar (the oracle's own noise floor is near 1e-8 here).
     p = W.cartpole(T=T, horizon=2.56)
     x0 = W.cartpole_x0(1)
-    s = ptn.Solver(p, max_T=T, precision=ptn.PTN_FP32_FP64SOLVE, grid_min_T=(512 if grid else 0))
+    s = ptn.Solver(p, max_T=T, precision=prec, grid_min_T=(512 if grid else 0), tol_final=1e-7)
+    x, u, lam, info = s.solve_ip(dev(x0), T)
+    ref = O.solve_ip(p, x0, T, opts=O.Options(tol_final=1e-7))
+    check_solution(info, ref, x, u, lam, FP32_TOL, with_lam=False)
+
+
+@pytest.mark.parametrize("T,prec", [(256, 1), (4096, 1), (4096, 2)])
+def test_cartpole_fp32_reaches_kkt(ptn, T, prec):
+    # at the default tolerance the FP32 paths reach KKT <= 1e-6 and the oracle's cost
+    p = W.cartpole(T=T, horizon=2.56)
+    x0 = W.cartpole_x0(1)
+    s = ptn.Solver(p, max_T=T, precision=prec, grid_min_T=512)
     x, u, lam, info = s.solve_ip(dev(x0), T)
     ref = O.solve_ip(p, x0, T)
-    check_solution(info, ref, x, u, lam, FP32_TOL, with_lam=False)
+    assert info["status"] == 0 and info["r_kkt"] <= 1e-6 * (1 + 1e-9)
+    assert abs(info["J"] - ref["info"]["J"]) / abs(ref["info"]["J"]) <= FP32_TOL
 
 
 def test_grid_tier_fp64_matches_oracle(ptn):
