@@ -73,6 +73,7 @@ typedef struct ptn_problem {
 /* Solver settings; ptn_default_options() fills the defaults:
  *   precision FP32_FP64SOLVE, mu 1e-1 -> 1e-6 (x0.1), tol_inner 1e-4, tol_final 1e-6,
  *   block_threads 128, grid_min_T 512, grid_steps_per_thread 2, polish 100, polish_after 50,
+ *   cluster_max_blocks 16,
  *   max_newton 500 per barrier level, ADMM rho 1, admm_tol 1e-2, max_outer 2000,
  *   alpha0 1e-6 in [1e-10, 1e10], ten step sizes 1, 1/2, ..., Armijo c1 1e-4,
  *   rollout: at most 30 multiple-shooting Newton iterations to relative defect 1e-12. */
@@ -87,6 +88,10 @@ typedef struct ptn_options {
   int grid_min_T;       /* single solves with T >= grid_min_T use all SMs (0: never) */
   int grid_steps_per_thread;
   int polish_after;     /* FP32 modes: exact FP64 gradients after this many iterations */
+  int cluster_max_blocks; /* single solves needing 2..cluster_max_blocks CTAs (block_threads
+                             threads, grid_steps_per_thread steps each) run on one thread-block
+                             cluster (at most 16; 0: never) before the cooperative grid is used */
+  int pad_opt;
   double mu0, zeta, mu_final, tol_inner, tol_final, rho, admm_tol;
   double alpha0, alpha_min, alpha_max, ls_beta, armijo_c1, armijo_eps, roll_tol;
   double polish;        /* FP32 modes: exact FP64 gradients once max|d| <= polish * tol_final */
@@ -98,12 +103,12 @@ typedef struct ptn_options {
  * max_t |d_t|_inf (gradient of the augmented cost), r_dyn the largest dynamics defect and
  * r_feas the largest constraint violation.  cycles[] are SM clock cycles spent by the
  * group's first thread in the co-state pass, second-order expansion, value pass, state
- * pass, line search, and everything else. */
+ * pass, line search, initial rollout, and everything else. */
 typedef struct ptn_info {
   int status, newton_iters, outer_iters, ls_rejects, factor_fails, roll_fails;
   int roll_iters, ls_evals, exact_passes, pad;
   double mu, alpha, r_stat, r_dyn, r_feas, r_kkt, J, J_c, r_p, r_d;
-  long long cycles[6];
+  long long cycles[7];
 } ptn_info;
 
 typedef struct ptn_solver ptn_solver;

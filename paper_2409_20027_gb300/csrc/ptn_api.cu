@@ -124,6 +124,7 @@ extern "C" void ptn_default_options(ptn_options* o) {
   o->polish = 100.0;
   o->armijo_eps32 = 1e-9;
   o->polish_after = 50;
+  o->cluster_max_blocks = 16;
 }
 
 extern "C" const char* ptn_version(void) { return "ptn 0.1 (sm_103a)"; }
@@ -143,6 +144,8 @@ static int check_options(ptn_solver* s, const ptn_options* o) {
       !(o->ls_beta > 0 && o->ls_beta < 1) || !(o->alpha_max >= o->alpha_min) || !(o->alpha_min >= 0))
     return fail(s, PTN_ERR_INVALID_ARG, "invalid continuation, penalty or regularisation parameter");
   if (o->grid_steps_per_thread < 1) return fail(s, PTN_ERR_INVALID_ARG, "grid_steps_per_thread must be >= 1");
+  if (o->cluster_max_blocks < 0 || o->cluster_max_blocks > 16)
+    return fail(s, PTN_ERR_INVALID_ARG, "cluster_max_blocks must be in [0, 16]");
   return PTN_OK;
 }
 
@@ -309,6 +312,7 @@ static void to_optdev(const ptn_options& o, int method, OptDev* d) {
   d->polish = o.polish;
   d->armijo_eps32 = o.armijo_eps32;
   d->polish_after = o.polish_after;
+  d->init_max_iter = 64;
   d->max_newton = o.max_newton; d->max_outer = o.max_outer; d->ls_count = o.ls_count;
   d->admm_fixed_iters = o.admm_fixed_iters; d->roll_max_iter = o.roll_max_iter; d->method = method;
   d->spin_limit = 1ll << 26;
@@ -318,7 +322,7 @@ static void from_info(const InfoDev& d, ptn_info* o) {
   o->status = d.status; o->newton_iters = d.newton_iters; o->outer_iters = d.outer_iters;
   o->ls_rejects = d.ls_rejects; o->factor_fails = d.factor_fails; o->roll_fails = d.roll_fails;
   o->roll_iters = d.roll_iters; o->ls_evals = d.ls_evals; o->exact_passes = d.exact_passes; o->pad = 0;
-  for (int k = 0; k < 6; k++) o->cycles[k] = d.cyc[k];
+  for (int k = 0; k < 7; k++) o->cycles[k] = d.cyc[k];
   o->mu = d.mu; o->alpha = d.alpha; o->r_stat = d.r_stat; o->r_dyn = d.r_dyn; o->r_feas = d.r_feas;
   o->r_kkt = d.r_kkt; o->J = d.J; o->J_c = d.J_c; o->r_p = d.r_p; o->r_d = d.r_d;
 }
@@ -363,8 +367,30 @@ static int solve_common(ptn_solver* s, int method, int B, const int* T_b, const 
   q.args.u_init = u_init;
   q.args.info = s->dinfo;
   q.args.B = B;
-  const bool grid = single && B == 1 && s->opt.grid_min_T > 0 && T_b[0] >= s->opt.grid_min_T;
-  if (grid) {
+  // one instance: a thread-block cluster when the horizon needs 2..16 CTAs, else the
+  // cooperative grid from grid_min_T on, else one CTA
+  int cl_blocks = 0;
+  if (single && B == 1 && s->opt.cluster_max_blocks >= 2) {
+    const long long per = (long long)s->opt.block_threads * s->opt.grid_steps_per_thread;
+    const long long need = (T_b[0] + per - 1) / per;
+    if (need >= 2 && need <= s->opt.cluster_max_blocks) {
+      int maxc = 0;
+      q.tier = 2;
+      q.nthreads = s->opt.block_threads;
+      q.query = 1;
+      q.max_blocks = &maxc;
+      CK(fn(q));
+      q.query = 0;
+      if (need <= maxc) cl_blocks = (int)need;
+    }
+  }
+  const bool grid = !cl_blocks && single && B == 1 && s->opt.grid_min_T > 0 && T_b[0] >= s->opt.grid_min_T;
+  if (cl_blocks) {
+    q.tier = 2;
+    q.nthreads = s->opt.block_threads;
+    q.nblocks = cl_blocks;
+    CK(fn(q));
+  } else if (grid) {
     q.tier = 1;
     q.nthreads = 128;
     int maxb = 0;

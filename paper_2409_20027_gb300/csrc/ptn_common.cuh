@@ -56,7 +56,7 @@ struct OptDev {
   double alpha0, alpha_min, alpha_max, ls_beta, armijo_c1, armijo_eps;
   double roll_tol, polish, armijo_eps32;
   int max_newton, max_outer, ls_count, admm_fixed_iters;
-  int roll_max_iter, method, polish_after, pad1;
+  int roll_max_iter, method, polish_after, init_max_iter;
   long long spin_limit;  // bounded waits in grid barriers
 };
 
@@ -75,8 +75,8 @@ struct InfoDev {
   int exact_passes, pad_;
   double mu, alpha, r_stat, r_dyn, r_feas, r_kkt, J, J_c, r_p, r_d;
   // SM clock cycles spent by group thread 0 per phase (costate, quadratize, value,
-  // state, line search, other)
-  long long cyc[6];
+  // state, line search, initial rollout, other)
+  long long cyc[7];
 };
 
 // ---------------------------------------------------------------------------
@@ -359,10 +359,12 @@ PTN_HD Dual<S, K> operator/(const Dual<S, K>& a, const Dual<S, K>& b) {
 PTN_HD void sc_(double a, double* s, double* c) { sincos(a, s, c); }
 PTN_HD void sc_(float a, float* s, float* c) { sincosf(a, s, c); }
 
+PTN_HD void sincos_ad(double a, double& s, double& c);
+PTN_HD void sincos_ad(float a, float& s, float& c);
 template <class S, int K>
 PTN_HD void sincos_ad(const Dual<S, K>& a, Dual<S, K>& s, Dual<S, K>& c) {
   S sv, cv;
-  sc_(a.v, &sv, &cv);
+  sincos_ad(a.v, sv, cv);
   s.v = sv; c.v = cv;
 #pragma unroll
   for (int k = 0; k < K; k++) { s.d[k] = cv * a.d[k]; c.d[k] = -sv * a.d[k]; }
@@ -497,6 +499,10 @@ PTN_HD void sincos_ad(const Jet<S, K>& a, Jet<S, K>& s, Jet<S, K>& c) {
 // plain scalars share the same interface
 PTN_HD void sincos_ad(double a, double& s, double& c) { sincos(a, &s, &c); }
 PTN_HD void sincos_ad(float a, float& s, float& c) { sincosf(a, &s, &c); }
+template <class S, int K>
+PTN_HD Dual<S, K> operator/(double c, const Dual<S, K>& a) {
+  return recip(a) * Dual<S, K>(S(c));
+}
 PTN_HD double recip(double a) { return 1.0 / a; }
 PTN_HD float recip(float a) { return 1.0f / a; }
 
@@ -514,6 +520,29 @@ PTN_HD S cadd(double c, const S& a) {
   using B = typename base_of<S>::type;
   return B(c) + a;
 }
+// model constants may themselves be AD scalars (parameter derivatives): a constant of
+// the base type, or of the same type, times a value
+template <class B, int K1, int K2>
+PTN_HD Dual<Dual<B, K1>, K2> cmul(const Dual<B, K1>& c, const Dual<Dual<B, K1>, K2>& a) { return c * a; }
+template <class S, int K>
+PTN_HD Dual<S, K> cmul(const Dual<S, K>& c, const Dual<S, K>& a) { return c * a; }
+template <class B, int K1, int K2>
+PTN_HD Dual<Dual<B, K1>, K2> cadd(const Dual<B, K1>& c, const Dual<Dual<B, K1>, K2>& a) { return c + a; }
+template <class S, int K>
+PTN_HD Dual<S, K> cadd(const Dual<S, K>& c, const Dual<S, K>& a) { return c + a; }
+
+// model constants converted once to the evaluation's base scalar (float constants in the
+// FP32 path, so no FP64 arithmetic runs inside the model), or kept as AD scalars when
+// parameter derivatives are taken
+template <class S>
+PTN_HD typename base_of<S>::type pconv(double c) {
+  return typename base_of<S>::type(c);
+}
+template <class S, class B, int K>
+PTN_HD Dual<B, K> pconv(const Dual<B, K>& c) {
+  return c;
+}
+
 template <class S>
 PTN_HD S cst(double c) {
   using B = typename base_of<S>::type;

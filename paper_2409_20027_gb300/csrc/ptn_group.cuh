@@ -14,6 +14,8 @@
 // Grid level: block totals in global memory behind a grid barrier whose wait is
 // bounded (spin_limit); on expiry the group records ST_ETIMEOUT and stops.
 #pragma once
+#include <cooperative_groups.h>
+
 #include "ptn_ops.cuh"
 
 namespace ptn {
@@ -249,6 +251,86 @@ struct GridGroup {
       if (blockIdx.x > 0) ok &= op(*scarry, ex, ex);
     } else {
       if (blockIdx.x + 1 < gridDim.x) ok &= op(ex, *scarry, ex);
+    }
+    __syncthreads();
+    phase ^= 1;
+    return ex;
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Cluster group: the CTAs of one thread-block cluster (up to 16 on GB300) work on one
+// instance.  Block totals are exchanged through distributed shared memory behind the
+// hardware cluster barrier (barrier.cluster arrive/wait), double-buffered by parity.
+struct ClusterGroup {
+  char* sm;    // block scratch (nwarps + 2 scan slots)
+  char* xch;   // this CTA's exchange slots: 2 x max(element bytes, 8 doubles)
+  int xbytes;  // bytes per slot
+  int phase;
+
+  __device__ int nblk() const { return (int)cooperative_groups::this_cluster().num_blocks(); }
+  __device__ int brank() const { return (int)cooperative_groups::this_cluster().block_rank(); }
+  __device__ int rank() const { return brank() * blockDim.x + threadIdx.x; }
+  __device__ int size() const { return nblk() * blockDim.x; }
+  __device__ bool dead() const { return false; }
+  __device__ void sync() { cooperative_groups::this_cluster().sync(); }
+
+  template <int K>
+  __device__ void reduce(double (&v)[K], unsigned maxmask) {
+    static_assert(K <= 8, "at most 8 values per reduction");
+    CtaGroup cg{sm};
+    cg.reduce<K>(v, maxmask);
+    double* mine = reinterpret_cast<double*>(xch + (size_t)phase * xbytes);
+    if (threadIdx.x == 0)
+#pragma unroll
+      for (int k = 0; k < K; k++) mine[k] = v[k];
+    sync();
+    auto cl = cooperative_groups::this_cluster();
+    const int nb = nblk();
+#pragma unroll
+    for (int k = 0; k < K; k++) {
+      double a = cl.map_shared_rank(mine, 0)[k];
+      for (int i = 1; i < nb; i++) {
+        const double o = cl.map_shared_rank(mine, i)[k];
+        a = ((maxmask >> k) & 1u) ? fmax(a, o) : a + o;
+      }
+      v[k] = a;
+    }
+    phase ^= 1;
+  }
+
+  template <class E, class Op>
+  __device__ E scan(E v, const Op& op, bool suffix, bool& ok) {
+    const int nw = blockDim.x >> 5;
+    E* sw = reinterpret_cast<E*>(sm);
+    E* stot = sw + nw;
+    E* scarry = sw + nw + 1;
+    E ex = block_scan_excl(v, op, suffix, ok, sw, stot);
+    E* mine = reinterpret_cast<E*>(xch + (size_t)phase * xbytes);
+    if (threadIdx.x == 0) *mine = *stot;
+    sync();
+    auto cl = cooperative_groups::this_cluster();
+    const int nb = nblk(), br = brank();
+    if (threadIdx.x < 32) {
+      // ordered tree over the totals of the CTAs before (prefix) or after (suffix) this one
+      const int lane = threadIdx.x;
+      const int lo = suffix ? br + 1 : 0;
+      const int hi = suffix ? nb : br;
+      E acc;
+      set_identity(acc);
+      if (lo + lane < hi) acc = *cl.map_shared_rank(mine, lo + lane);
+#pragma unroll 1
+      for (int off = 1; off < 32; off <<= 1) {
+        E o = shfl_down_e(acc, off);
+        if ((lane & (2 * off - 1)) == 0 && lane + off < 32) ok &= op(acc, o, acc);
+      }
+      if (lane == 0) *scarry = acc;
+    }
+    __syncthreads();
+    if (!suffix) {
+      if (br > 0) ok &= op(*scarry, ex, ex);
+    } else {
+      if (br + 1 < nb) ok &= op(ex, *scarry, ex);
     }
     __syncthreads();
     phase ^= 1;

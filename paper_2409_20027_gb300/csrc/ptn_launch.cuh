@@ -23,7 +23,7 @@ inline Work<L> typed(const WorkRaw& r) {
 }
 
 struct LaunchReq {
-  int tier;       // 0: one CTA per instance, 1: cooperative grid on one instance
+  int tier;       // 0: one CTA per instance, 1: cooperative grid, 2: one cluster on one instance
   int precision;  // 0: FP64, 1: FP32 with FP64 solves, 2: FP32
   int nblocks, nthreads;
   int query;      // 1: only report max co-resident grid blocks in *max_blocks
@@ -46,6 +46,38 @@ cudaError_t launch_typed(LaunchReq& q) {
     if (q.query) return cudaSuccess;
     k_solve_cta<M, L, SV><<<q.nblocks, nthreads, smem, q.stream>>>(q.args, typed<L>(q.w));
     return cudaGetLastError();
+  }
+  if (q.tier == 2) {
+    const size_t smc = ((smem + 15) & ~size_t(15)) + cluster_xch_bytes<N, U, L>();
+    cudaError_t e = cudaFuncSetAttribute(k_solve_cluster<M, L, SV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smc);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_solve_cluster<M, L, SV>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return e;
+    if (q.query) {
+      // largest cluster of these CTAs the device can co-schedule (the cluster
+      // dimension in cfg is ignored by the query)
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(16);
+      cfg.blockDim = dim3(nthreads);
+      cfg.dynamicSmemBytes = smc;
+      int maxc = 0;
+      e = cudaOccupancyMaxPotentialClusterSize(&maxc, k_solve_cluster<M, L, SV>, &cfg);
+      *q.max_blocks = maxc;
+      return e;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(q.nblocks);
+    cfg.blockDim = dim3(nthreads);
+    cfg.dynamicSmemBytes = smc;
+    cfg.stream = q.stream;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = q.nblocks;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_solve_cluster<M, L, SV>, q.args, typed<L>(q.w));
   }
   cudaError_t e = cudaFuncSetAttribute(k_solve_grid<M, L, SV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;

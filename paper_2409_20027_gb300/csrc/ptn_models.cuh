@@ -16,11 +16,11 @@ enum : int { INTEG_EULER = 0, INTEG_RK4 = 1 };
 
 // prm = [g, l, m, b]; x = (theta, omega)
 struct Pendulum {
-  static constexpr int NX = 2, NU = 1, ID = MODEL_PENDULUM;
-  template <class S>
-  PTN_HD static void rhs(const double* p, const S* x, const S* u, S* xd) {
-    const double g = p[0], l = p[1], m = p[2], b = p[3];
-    const double iml2 = 1.0 / (m * l * l);
+  static constexpr int NX = 2, NU = 1, NP = 4, ID = MODEL_PENDULUM;
+  template <class S, class PT>
+  PTN_HD static void rhs(const PT* p, const S* x, const S* u, S* xd) {
+    const auto g = pconv<S>(p[0]), l = pconv<S>(p[1]), m = pconv<S>(p[2]), b = pconv<S>(p[3]);
+    const auto iml2 = decltype(g)(1) / (m * l * l);
     S s, c;
     sincos_ad(x[0], s, c);
     xd[0] = x[1];
@@ -30,10 +30,10 @@ struct Pendulum {
 
 // prm = [m_c, m_p, l, g]; x = (p, theta, p', theta'), theta = 0 hanging down
 struct CartPole {
-  static constexpr int NX = 4, NU = 1, ID = MODEL_CARTPOLE;
-  template <class S>
-  PTN_HD static void rhs(const double* p, const S* x, const S* u, S* xd) {
-    const double mc = p[0], mp = p[1], l = p[2], g = p[3];
+  static constexpr int NX = 4, NU = 1, NP = 4, ID = MODEL_CARTPOLE;
+  template <class S, class PT>
+  PTN_HD static void rhs(const PT* p, const S* x, const S* u, S* xd) {
+    const auto mc = pconv<S>(p[0]), mp = pconv<S>(p[1]), l = pconv<S>(p[2]), g = pconv<S>(p[3]);
     S s, c;
     sincos_ad(x[1], s, c);
     const S td2 = x[3] * x[3];
@@ -41,7 +41,8 @@ struct CartPole {
     const S iden = recip(den);
     const S pdd = (u[0] + cmul(mp, s) * (cmul(l, td2) + cmul(g, c))) * iden;
     const S num = -(u[0] * c) - cmul(mp * l, td2 * c * s) - cmul((mc + mp) * g, s);
-    const S tdd = cmul(1.0 / l, num * iden);
+    const S tdd = cmul(decltype(l)(1) / l, num * iden);
+    (void)g;
     xd[0] = x[2];
     xd[1] = x[3];
     xd[2] = pdd;
@@ -53,10 +54,12 @@ struct CartPole {
 // x = (px,py,pz, roll,pitch,yaw, vx,vy,vz, wx,wy,wz); u = rotor thrusts 1..4
 // rotor 1 on +x, 2 on +y, 3 on -x, 4 on -y; yaw torque k_m (f1 - f2 + f3 - f4)
 struct Quadrotor {
-  static constexpr int NX = 12, NU = 4, ID = MODEL_QUADROTOR;
-  template <class S>
-  PTN_HD static void rhs(const double* p, const S* x, const S* u, S* xd) {
-    const double mass = p[0], Ixx = p[1], Iyy = p[2], Izz = p[3], arm = p[4], km = p[5], g = p[6];
+  static constexpr int NX = 12, NU = 4, NP = 7, ID = MODEL_QUADROTOR;
+  template <class S, class PT>
+  PTN_HD static void rhs(const PT* p, const S* x, const S* u, S* xd) {
+    const auto mass = pconv<S>(p[0]), Ixx = pconv<S>(p[1]), Iyy = pconv<S>(p[2]), Izz = pconv<S>(p[3]);
+    const auto arm = pconv<S>(p[4]), km = pconv<S>(p[5]), g = pconv<S>(p[6]);
+    using PC = decltype(g);
     S sph, cph, sth, cth, sps, cps;
     sincos_ad(x[3], sph, cph);
     sincos_ad(x[4], sth, cth);
@@ -64,7 +67,7 @@ struct Quadrotor {
     const S icth = recip(cth);
     const S tth = sth * icth;
     const S fsum = (u[0] + u[1]) + (u[2] + u[3]);
-    const S am = cmul(1.0 / mass, fsum);
+    const S am = cmul(PC(1) / mass, fsum);
     // body z axis in the world frame (third column of Rz Ry Rx)
     const S r13 = cps * (sth * cph) + sps * sph;
     const S r23 = sps * (sth * cph) - cps * sph;
@@ -78,66 +81,53 @@ struct Quadrotor {
     xd[6] = am * r13;
     xd[7] = am * r23;
     xd[8] = cadd(-g, am * r33);
+    (void)mass;
     const S tx = cmul(arm, u[1] - u[3]);
     const S ty = cmul(arm, u[2] - u[0]);
     const S tz = cmul(km, (u[0] + u[2]) - (u[1] + u[3]));
-    xd[9] = cmul(1.0 / Ixx, tx - cmul(Izz - Iyy, x[10] * x[11]));
-    xd[10] = cmul(1.0 / Iyy, ty - cmul(Ixx - Izz, x[11] * x[9]));
-    xd[11] = cmul(1.0 / Izz, tz - cmul(Iyy - Ixx, x[9] * x[10]));
+    xd[9] = cmul(PC(1) / Ixx, tx - cmul(Izz - Iyy, x[10] * x[11]));
+    xd[10] = cmul(PC(1) / Iyy, ty - cmul(Ixx - Izz, x[11] * x[9]));
+    xd[11] = cmul(PC(1) / Izz, tz - cmul(Iyy - Ixx, x[9] * x[10]));
   }
 };
 
-// One discrete step x+ = f(x, u): explicit Euler or classical RK4 with the control
-// held over the step.
-template <class M, class S>
-PTN_HD void step(int integ, double dt, const double* p, const S* x, const S* u, S* xn) {
-  constexpr int N = M::NX;
-  if (integ == INTEG_EULER) {
-    S k[N];
-    M::rhs(p, x, u, k);
-#pragma unroll
-    for (int i = 0; i < N; i++) xn[i] = x[i] + cmul(dt, k[i]);
-    return;
-  }
-  S k[N], acc[N], y[N];
-  M::rhs(p, x, u, k);
-#pragma unroll
-  for (int i = 0; i < N; i++) { acc[i] = k[i]; y[i] = x[i] + cmul(0.5 * dt, k[i]); }
-  M::rhs(p, y, u, k);
-#pragma unroll
-  for (int i = 0; i < N; i++) { acc[i] = acc[i] + cmul(2.0, k[i]); y[i] = x[i] + cmul(0.5 * dt, k[i]); }
-  M::rhs(p, y, u, k);
-#pragma unroll
-  for (int i = 0; i < N; i++) { acc[i] = acc[i] + cmul(2.0, k[i]); y[i] = x[i] + cmul(dt, k[i]); }
-  M::rhs(p, y, u, k);
-#pragma unroll
-  for (int i = 0; i < N; i++) xn[i] = x[i] + cmul(dt / 6.0, acc[i] + k[i]);
-}
-
 // Increment of one discrete step, dx = f(x, u) - x, in scalar S (no identity added, so
 // FP32 keeps the relative precision of the small increment).
-template <class M, class S>
-PTN_HD void step_inc(int integ, double dt, const double* p, const S* x, const S* u, S* dxo) {
+template <class M, class S, class PT = double>
+PTN_HD void step_inc(int integ, double dt, const PT* p, const S* x, const S* u, S* dxo) {
   constexpr int N = M::NX;
+  using B = typename base_of<S>::type;
+  const B h = B(dt), h2 = h * B(0.5), h6 = h / B(6), two = B(2);
   S k[N];
   M::rhs(p, x, u, k);
   if (integ == INTEG_EULER) {
 #pragma unroll
-    for (int i = 0; i < N; i++) dxo[i] = cmul(dt, k[i]);
+    for (int i = 0; i < N; i++) dxo[i] = h * k[i];
     return;
   }
   S acc[N], y[N];
 #pragma unroll
-  for (int i = 0; i < N; i++) { acc[i] = k[i]; y[i] = x[i] + cmul(0.5 * dt, k[i]); }
+  for (int i = 0; i < N; i++) { acc[i] = k[i]; y[i] = x[i] + h2 * k[i]; }
   M::rhs(p, y, u, k);
 #pragma unroll
-  for (int i = 0; i < N; i++) { acc[i] = acc[i] + cmul(2.0, k[i]); y[i] = x[i] + cmul(0.5 * dt, k[i]); }
+  for (int i = 0; i < N; i++) { acc[i] = acc[i] + two * k[i]; y[i] = x[i] + h2 * k[i]; }
   M::rhs(p, y, u, k);
 #pragma unroll
-  for (int i = 0; i < N; i++) { acc[i] = acc[i] + cmul(2.0, k[i]); y[i] = x[i] + cmul(dt, k[i]); }
+  for (int i = 0; i < N; i++) { acc[i] = acc[i] + two * k[i]; y[i] = x[i] + h * k[i]; }
   M::rhs(p, y, u, k);
 #pragma unroll
-  for (int i = 0; i < N; i++) dxo[i] = cmul(dt / 6.0, acc[i] + k[i]);
+  for (int i = 0; i < N; i++) dxo[i] = h6 * (acc[i] + k[i]);
+}
+
+// One discrete step x+ = f(x, u): explicit Euler or classical RK4 with the control
+// held over the step.
+template <class M, class S, class PT = double>
+PTN_HD void step(int integ, double dt, const PT* p, const S* x, const S* u, S* xn) {
+  constexpr int N = M::NX;
+  S d[N];
+  step_inc<M, S, PT>(integ, dt, p, x, u, d);
+#pragma unroll
+  for (int i = 0; i < N; i++) xn[i] = x[i] + d[i];
 }
 
 // Jacobians of the increment: E = d(f - x)/dx (so F = I + E) and G = df/du, plus the
@@ -262,6 +252,40 @@ PTN_HD void step_cl_jac(int integ, double dt, const double* p, const double* x, 
   for (int i = 0; i < N; i++)
 #pragma unroll
     for (int j = 0; j < N; j++) Fcl[i * N + j] = xn[i].d[j];
+}
+
+// Parameter derivatives of one step for the adjoint:
+//   fp  (NX x NP)       df/dprm
+//   Hzp ((NX+NU) x NP)  d2 (lam^T f) / dz dprm
+// by nested forward mode (outer: z = (x, u), inner: prm), in FP64.
+template <class M>
+PTN_HD void step_param_derivs(int integ, double dt, const double* prm, const double* x, const double* u,
+                              const double* lam, double* fp, double* Hzp) {
+  constexpr int N = M::NX, U = M::NU, K = N + U, NP = M::NP;
+  using PD = Dual<double, NP>;
+  using D = Dual<PD, K>;
+  PD p[NP];
+#pragma unroll
+  for (int k = 0; k < NP; k++) { p[k] = PD(prm[k]); p[k].d[k] = 1.0; }
+  D xd[N], ud[U], xn[N];
+#pragma unroll
+  for (int i = 0; i < N; i++) { xd[i] = D(PD(x[i])); xd[i].d[i] = PD(1.0); }
+#pragma unroll
+  for (int i = 0; i < U; i++) { ud[i] = D(PD(u[i])); ud[i].d[N + i] = PD(1.0); }
+  step<M, D, PD>(integ, dt, p, xd, ud, xn);
+#pragma unroll
+  for (int i = 0; i < N; i++)
+#pragma unroll
+    for (int k = 0; k < NP; k++) fp[i * NP + k] = xn[i].v.d[k];
+#pragma unroll
+  for (int j = 0; j < K; j++)
+#pragma unroll
+    for (int k = 0; k < NP; k++) {
+      double h = 0.0;
+#pragma unroll
+      for (int i = 0; i < N; i++) h += lam[i] * xn[i].d[j].d[k];
+      Hzp[j * NP + k] = h;
+    }
 }
 
 }  // namespace ptn

@@ -72,6 +72,65 @@ __device__ void load_prob(ProbS<N, U>& S, const ProbDev& P, const double* xref_o
 }
 
 // ---------------------------------------------------------------------------
+// For large state dimensions (N >= 8) the per-element routines are called through
+// out-of-line wrappers: their operands live in local memory anyway, and compiling
+// them once instead of at every call site keeps build times bounded.
+template <int N>
+struct Big {
+  static constexpr bool value = N >= 8;
+};
+
+template <class SV, int N, class L>
+__device__ __noinline__ bool value_combine_ni(const Val<N, L>& a, const Val<N, L>& b, Val<N, L>& o) {
+  return ValueOp<SV>()(a, b, o);
+}
+template <class SV>
+struct ValueOpSel {
+  template <int N, class L>
+  __device__ __forceinline__ bool operator()(const Val<N, L>& a, const Val<N, L>& b, Val<N, L>& o) const {
+    if constexpr (Big<N>::value) return value_combine_ni<SV, N, L>(a, b, o);
+    else return ValueOp<SV>()(a, b, o);
+  }
+};
+template <int N, int U, class L, class SV>
+__device__ __noinline__ bool value_init_ni(const L* F, const L* G, const L* Pm, const L* Mm, const L* Rm,
+                                           const double* d, double alpha, Val<N, L>& e) {
+  return value_init<N, U, L, SV>(F, G, Pm, Mm, Rm, d, alpha, e);
+}
+template <int N, int U, class L, class SV>
+__device__ __forceinline__ bool value_init_sel(const L* F, const L* G, const L* Pm, const L* Mm, const L* Rm,
+                                               const double* d, double alpha, Val<N, L>& e) {
+  if constexpr (Big<N>::value) return value_init_ni<N, U, L, SV>(F, G, Pm, Mm, Rm, d, alpha, e);
+  else return value_init<N, U, L, SV>(F, G, Pm, Mm, Rm, d, alpha, e);
+}
+template <int N, int U, class L, class SV>
+__device__ __noinline__ bool riccati_step_ni(const L* F, const L* G, const L* Pm, const L* Mm, const L* Rm,
+                                             const double* d, double alpha, L* S, L* s, L* Gam, L* gam) {
+  return riccati_step<N, U, L, SV>(F, G, Pm, Mm, Rm, d, alpha, S, s, Gam, gam);
+}
+template <int N, int U, class L, class SV>
+__device__ __forceinline__ bool riccati_step_sel(const L* F, const L* G, const L* Pm, const L* Mm, const L* Rm,
+                                                 const double* d, double alpha, L* S, L* s, L* Gam, L* gam) {
+  if constexpr (Big<N>::value) return riccati_step_ni<N, U, L, SV>(F, G, Pm, Mm, Rm, d, alpha, S, s, Gam, gam);
+  else return riccati_step<N, U, L, SV>(F, G, Pm, Mm, Rm, d, alpha, S, s, Gam, gam);
+}
+template <class M, class S>
+__device__ __noinline__ void step_hess_ni(int integ, double dt, const double* p, const double* x, const double* u,
+                                          const double* lam, S* Hxx, S* Hxu, S* Huu) {
+  step_hess<M, S>(integ, dt, p, x, u, lam, Hxx, Hxu, Huu);
+}
+template <class M, class S>
+__device__ __noinline__ void inc_jac_ni(int integ, double dt, const double* p, const double* x, const double* u,
+                                        S* dv, S* E, S* G) {
+  inc_jac<M, S>(integ, dt, p, x, u, dv, E, G);
+}
+template <class M, class S>
+__device__ __noinline__ void step_cl_jac_ni(int integ, double dt, const double* p, const double* x,
+                                            const double* u, const S* Gam, S* Fcl) {
+  step_cl_jac<M, S>(integ, dt, p, x, u, Gam, Fcl);
+}
+
+// ---------------------------------------------------------------------------
 // model hooks: generic models use the templated right-hand side and AD scalars;
 // the synthetic model has closed-form derivatives.
 template <class M>
@@ -88,17 +147,20 @@ struct MOps {
   template <class PS, class L>
   __device__ static void hess(const PS& P, const double* x, const double* u, const double* lam, L* Hxx,
                               L* Hxu, L* Huu) {
-    step_hess<M, L>(P.integ, P.dt, P.prm, x, u, lam, Hxx, Hxu, Huu);
+    if constexpr (Big<N>::value) step_hess_ni<M, L>(P.integ, P.dt, P.prm, x, u, lam, Hxx, Hxu, Huu);
+    else step_hess<M, L>(P.integ, P.dt, P.prm, x, u, lam, Hxx, Hxu, Huu);
   }
   template <class PS, class L>
   __device__ static void cl(const PS& P, const double* x, const double* u, const L* Gam, double* xn, L* Fcl) {
-    step_cl_jac<M, L>(P.integ, P.dt, P.prm, x, u, Gam, Fcl);
+    if constexpr (Big<N>::value) step_cl_jac_ni<M, L>(P.integ, P.dt, P.prm, x, u, Gam, Fcl);
+    else step_cl_jac<M, L>(P.integ, P.dt, P.prm, x, u, Gam, Fcl);
     step<M>(P.integ, P.dt, P.prm, x, u, xn);
   }
   // increment Jacobians E = d(f - x)/dx, G = df/du in scalar S (and the increment)
   template <class PS, class S>
   __device__ static void ijac(const PS& P, const double* x, const double* u, S* E, S* G, S* dv = nullptr) {
-    inc_jac<M, S>(P.integ, P.dt, P.prm, x, u, dv, E, G);
+    if constexpr (Big<N>::value) inc_jac_ni<M, S>(P.integ, P.dt, P.prm, x, u, dv, E, G);
+    else inc_jac<M, S>(P.integ, P.dt, P.prm, x, u, dv, E, G);
   }
   // closed-loop increment and its Jacobian in FP32
   template <class PS>
@@ -118,6 +180,12 @@ struct Aug {
   double mu, rho;
   const double* z;  // ADMM, T x nw
   const double* v;
+};
+
+// FP32 copies of the augmentation weights for the FP32 paths
+struct AugF {
+  float mu, rho, irho;
+  __device__ AugF(const Aug& A) : mu(float(A.mu)), rho(float(A.rho)), irho(float(1.0 / A.rho)) {}
 };
 
 template <int N, int U>
@@ -234,13 +302,16 @@ __device__ void stage_grad32(const ProbS<N, U>& P, const Aug& A, int t, const do
   for (int i = 0; i < U; i++) eu[i] = float(u[i] - P.uref[i]);
   mv<N, N>(P.Qs, e, lx);
   mv<U, U>(P.Rs, eu, lu);
+  const AugF F(A);
   for (int r = 0; r < P.nw; r++) {
     const int k = P.idx[r];
     const double zk = P.isx[r] ? x[k] : u[k];
-    const float w = float(P.sgn[r] * (zk - P.bnd[r]));
+    const bool up = P.sgn[r] > 0.0;
+    const float w = float(up ? zk - P.bnd[r] : P.bnd[r] - zk);
     float g1;
-    if (A.kind == AUG_BARRIER) g1 = float(A.mu) * float(P.sgn[r]) / (-w);
-    else g1 = float(A.rho) * (w - float(A.z[(size_t)t * P.nw + r] - A.v[(size_t)t * P.nw + r] / A.rho)) * float(P.sgn[r]);
+    if (A.kind == AUG_BARRIER) g1 = F.mu / (-w);
+    else g1 = F.rho * (w - float(A.z[(size_t)t * P.nw + r])) + float(A.v[(size_t)t * P.nw + r]);
+    if (!up) g1 = -g1;
     if (P.isx[r]) lx[k] += g1;
     else lu[k] += g1;
   }
@@ -267,18 +338,21 @@ __device__ float stage_delta(const ProbS<N, U>& P, const Aug& A, int t, const do
   for (int i = 0; i < N; i++) l += dx[i] * (qe[i] + 0.5f * qd[i]);
 #pragma unroll
   for (int i = 0; i < U; i++) l += du[i] * (re[i] + 0.5f * rd[i]);
+  const AugF F(A);
   for (int r = 0; r < P.nw; r++) {
     const int k = P.idx[r];
     const double z0 = P.isx[r] ? x0[k] : u0[k];
-    const double w0 = P.sgn[r] * (z0 - P.bnd[r]);
-    const float dw = float(P.sgn[r]) * (P.isx[r] ? dx[k] : du[k]);
+    const bool up = P.sgn[r] > 0.0;
+    const float w0 = float(up ? z0 - P.bnd[r] : P.bnd[r] - z0);
+    const float dz = P.isx[r] ? dx[k] : du[k];
+    const float dw = up ? dz : -dz;
     if (A.kind == AUG_BARRIER) {
-      const float ratio = dw / float(-w0);
+      const float ratio = dw / (-w0);
       if (!(ratio < 1.0f)) infeas = true;
-      else l -= float(A.mu) * log1pf(-ratio);
+      else l -= F.mu * log1pf(-ratio);
     } else {
-      const float q0 = float(w0 - A.z[(size_t)t * P.nw + r] + A.v[(size_t)t * P.nw + r] / A.rho);
-      l += float(A.rho) * dw * (q0 + 0.5f * dw);
+      const float q0 = w0 - float(A.z[(size_t)t * P.nw + r]) + float(A.v[(size_t)t * P.nw + r]) * F.irho;
+      l += F.rho * dw * (q0 + 0.5f * dw);
     }
   }
   return l;
@@ -325,6 +399,7 @@ struct Inst {
   double *lam, *d, *F64, *G64;
   L *E, *Gm, *Pm, *Mm, *Rm, *Gam, *gam, *dx, *du;
   double *z, *v;
+  double lamb[N];  // co-state at this chunk's right boundary (from the last co-state pass)
 
   __device__ void setup(const Work<L>& w, const InstDev& id, const double* x0_, int rank, int size, int nw) {
     T = id.T;
@@ -415,6 +490,7 @@ __device__ double costate_exact(Grp& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>
 #pragma unroll
   for (int i = 0; i < N; i++) {
     lam[i] = I.last ? lamT[i] : inc.v[i];
+    I.lamb[i] = lam[i];
     if (I.last) I.lam[(size_t)I.T * N + i] = lam[i];
   }
   double dmax = 0.0;
@@ -524,6 +600,7 @@ __device__ double costate_mixed(Grp& g, Inst<M, float>& I, const ProbS<M::NX, M:
 #pragma unroll
   for (int i = 0; i < N; i++) {
     lam[i] = I.last ? lamT[i] : inc.g[i];
+    I.lamb[i] = lam[i];
     if (I.last) I.lam[(size_t)I.T * N + i] = lam[i];
   }
   double dmax = 0.0;
@@ -568,11 +645,13 @@ __device__ double costate_pass(Grp& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>&
 template <class M, class L, class Grp>
 __device__ void quadratize(Grp& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>& P, const Aug& A) {
   constexpr int N = M::NX, U = M::NU;
+  // lam_{t+1} for t = b-1 belongs to the next chunk; the co-state pass also wrote this
+  // thread's own copy of it (lamb), so no group barrier is needed here
   for (int t = I.a; t < I.b; t++) {
     const double* x = I.xn + (size_t)t * N;
     const double* u = I.un + (size_t)t * U;
     L Pm[N * N], Mm[N * U], Rm[U * U];
-    MOps<M>::hess(P, x, u, I.lam + (size_t)(t + 1) * N, Pm, Mm, Rm);
+    MOps<M>::hess(P, x, u, (t + 1 == I.b) ? I.lamb : I.lam + (size_t)(t + 1) * N, Pm, Mm, Rm);
     stage_hess_add(P, A, x, u, Pm, Rm);
 #pragma unroll (N <= 8 ? N * N : 4)
     for (int i = 0; i < N * N; i++) I.Pm[(size_t)t * N * N + i] = Pm[i];
@@ -585,7 +664,6 @@ __device__ void quadratize(Grp& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>& P, 
 #pragma unroll (N <= 8 ? N * N : 4)
     for (int i = 0; i < N * N; i++) I.Pm[(size_t)I.T * N * N + i] = L(P.Qf[i] + P.Qf[(i % N) * N + i / N]);
   }
-  g.sync();
 }
 
 // pass 3: value suffix scan (Alg. 2) + feedback sweep.  Returns true on success; false
@@ -604,12 +682,12 @@ __device__ bool value_pass(Grp& g, Inst<M, L>& I, double alpha) {
     Val<N, L> e;
     L F[N * N];
     load_F<N>(I.E + (size_t)t * N * N, F);
-    ok &= value_init<N, U, L, SV>(F, I.Gm + (size_t)t * N * U, I.Pm + (size_t)t * N * N, I.Mm + (size_t)t * N * U,
-                                  I.Rm + (size_t)t * U * U, I.d + (size_t)t * U, alpha, e);
+    ok &= value_init_sel<N, U, L, SV>(F, I.Gm + (size_t)t * N * U, I.Pm + (size_t)t * N * N,
+                                      I.Mm + (size_t)t * N * U, I.Rm + (size_t)t * U * U, I.d + (size_t)t * U, alpha, e);
     if (!have) { agg = e; have = true; }
-    else ok &= ValueOp<SV>()(e, agg, agg);
+    else ok &= ValueOpSel<SV>()(e, agg, agg);
   }
-  Val<N, L> inc = g.scan(agg, ValueOp<SV>(), true, ok);
+  Val<N, L> inc = g.scan(agg, ValueOpSel<SV>(), true, ok);
   L S[N * N], s[N];
   if (I.last) {
 #pragma unroll (N <= 8 ? N * N : 4)
@@ -626,8 +704,9 @@ __device__ bool value_pass(Grp& g, Inst<M, L>& I, double alpha) {
   for (int t = I.b - 1; t >= I.a; t--) {
     L Gam[U * N], gam[U], F[N * N];
     load_F<N>(I.E + (size_t)t * N * N, F);
-    ok &= riccati_step<N, U, L, SV>(F, I.Gm + (size_t)t * N * U, I.Pm + (size_t)t * N * N, I.Mm + (size_t)t * N * U,
-                                    I.Rm + (size_t)t * U * U, I.d + (size_t)t * U, alpha, S, s, Gam, gam);
+    ok &= riccati_step_sel<N, U, L, SV>(F, I.Gm + (size_t)t * N * U, I.Pm + (size_t)t * N * N,
+                                        I.Mm + (size_t)t * N * U, I.Rm + (size_t)t * U * U, I.d + (size_t)t * U, alpha,
+                                        S, s, Gam, gam);
 #pragma unroll
     for (int i = 0; i < U * N; i++) I.Gam[(size_t)t * U * N + i] = Gam[i];
 #pragma unroll
@@ -735,13 +814,16 @@ __device__ void state_pass(Grp& g, Inst<M, L>& I, double& G1, double& G2) {
 // solved in parallel by multiple shooting: each thread integrates its chunk from a
 // boundary guess (initially x^ + s dx), and Newton corrections of the boundary
 // states come from a prefix scan of (chunk Jacobian, end defect) elements.
-// Writes the candidate into (xc, uc).  Returns true when converged, finite and (for
-// the barrier) strictly feasible.  *Jm receives the merit: the augmented cost J_c
-// (FP64 mode) or its change J_c(s) - J_c(0) accumulated from FP32 stage differences
-// (mixed modes).
+// Writes the candidate into (xc, uc).  Returns ROLL_OK when converged, finite and (for
+// the barrier) strictly feasible, ROLL_INFEASIBLE when converged but not strictly
+// feasible or with a non-finite merit, ROLL_FAIL otherwise.  *Jm receives the merit:
+// the augmented cost J_c (FP64) or its change J_c(s) - J_c(0) accumulated from FP32
+// stage differences (mixed modes, precise = false).
+enum : int { ROLL_OK = 0, ROLL_FAIL = 1, ROLL_INFEASIBLE = 2 };
+
 template <class M, class L, class Grp>
-__device__ bool rollout(Grp& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>& P, const OptDev& O, const Aug& A,
-                        double s, bool precise, double* Jm, int* iters) {
+__device__ int rollout(Grp& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>& P, const OptDev& O, const Aug& A,
+                       double s, bool precise, double* Jm, int* iters, int max_iter) {
   constexpr int N = M::NX, U = M::NU;
   const bool MIXED = std::is_same<L, float>::value && !precise;
   double X[N];
@@ -752,16 +834,18 @@ __device__ bool rollout(Grp& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>& P, con
     X[i] = first ? I.x0[i] : I.xn[(size_t)I.a * N + i] + s * double(I.dx[(size_t)I.a * N + i]);
   bool conv = false, feas = true;
   double J = INFINITY;
-  for (int it = 0; it < O.roll_max_iter; it++) {
+  // right-hand boundary as this thread predicts it: initially the same guess the
+  // neighbour starts from, afterwards E_j + Phi_j dX_j, which equals the neighbour's
+  // corrected start X_{j+1} + dX_{j+1} (so no boundary exchange through memory)
+  double Xn[N];
+  if (own && !I.last) {
+#pragma unroll
+    for (int i = 0; i < N; i++) Xn[i] = I.xn[(size_t)I.b * N + i] + s * double(I.dx[(size_t)I.b * N + i]);
+  }
+  for (int it = 0; it < max_iter; it++) {
     if (own) {
 #pragma unroll
       for (int i = 0; i < N; i++) I.xc[(size_t)I.a * N + i] = X[i];
-    }
-    g.sync();
-    double Xn[N];
-    if (own && !I.last) {
-#pragma unroll
-      for (int i = 0; i < N; i++) Xn[i] = I.xc[(size_t)I.b * N + i];
     }
     double xt[N], cost = 0.0;
     bool inf = false;
@@ -823,8 +907,14 @@ __device__ bool rollout(Grp& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>& P, con
           for (int i = 0; i < N; i++) I.xc[(size_t)t * N + i] = xt[i];
         }
         cost += stage_cost(P, A, t, xt, ut, inf);
-        double xnext[N];
-        MOps<M>::cl(P, xt, ut, Gam, xnext, Fc);
+        double xnext[N], Fd[N * N], Gd[U * N];
+#pragma unroll
+        for (int i = 0; i < U * N; i++) Gd[i] = double(Gam[i]);
+        // FP64 Jacobian: quadratic convergence of the shooting Newton, so the rollout
+        // reaches the FP64 dynamics to rounding and FP64 merits stay noise-free
+        MOps<M>::cl(P, xt, ut, Gd, xnext, Fd);
+#pragma unroll (N <= 8 ? N * N : 4)
+        for (int i = 0; i < N * N; i++) Fc[i] = L(Fd[i]);
 #pragma unroll
         for (int i = 0; i < N; i++) xt[i] = xnext[i];
       }
@@ -873,7 +963,7 @@ __device__ bool rollout(Grp& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>& P, con
     double red[5] = {rmax, xmax, cost, inf ? 1.0 : 0.0, nonfin ? 1.0 : 0.0};
     g.template reduce<5>(red, 0x1bu);  // max, max, sum, max, max
     if (iters) *iters = it + 1;
-    if (red[4] > 0.0) return false;
+    if (red[4] > 0.0) return ROLL_FAIL;
     const double rtol = MIXED ? fmax(O.roll_tol, 1e-8) : O.roll_tol;
     if (red[0] <= rtol * (1.0 + red[1])) {
       conv = true;
@@ -881,13 +971,21 @@ __device__ bool rollout(Grp& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>& P, con
       J = red[2];
       break;
     }
-    if (!first && own) {
+    if (own) {
+      L d[N], Pd[N];
 #pragma unroll
-      for (int i = 0; i < N; i++) X[i] += double(inc.v[i]);
+      for (int i = 0; i < N; i++) d[i] = first ? L(0) : inc.v[i];
+      mv<N, N>(el.M, d, Pd);
+#pragma unroll
+      for (int i = 0; i < N; i++) {
+        if (!first) X[i] += double(d[i]);
+        if (!I.last) Xn[i] = xt[i] + double(Pd[i]);
+      }
     }
   }
   *Jm = J;
-  return conv && feas && isfinite(J);
+  if (!conv) return ROLL_FAIL;
+  return (feas && isfinite(J)) ? ROLL_OK : ROLL_INFEASIBLE;
 }
 
 // J_c of the current nominal (group sum); *infeas set when the barrier is undefined
@@ -946,7 +1044,7 @@ __device__ int newton_solve(Grp& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>& P,
       st.exact_passes++;
       double mproj;
       int ri = 0;
-      if (rollout(g, I, P, O, A, 0.0, true, &mproj, &ri)) {
+      if (rollout(g, I, P, O, A, 0.0, true, &mproj, &ri, O.roll_max_iter) != ROLL_FAIL) {
         double* t1 = I.xn; I.xn = I.xc; I.xc = t1;
         double* t2 = I.un; I.un = I.uc; I.uc = t2;
       }
@@ -980,7 +1078,7 @@ __device__ int newton_solve(Grp& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>& P,
     for (int k = 0; k < O.ls_count; k++, s *= O.ls_beta) {
       int ri = 0;
       double m;
-      const bool okr = rollout(g, I, P, O, A, s, exact, &m, &ri);
+      const bool okr = rollout(g, I, P, O, A, s, exact, &m, &ri, O.roll_max_iter) == ROLL_OK;
       st.ls_evals++;
       st.roll_iters += ri;
       if (!okr) { st.roll_fails++; continue; }
@@ -1057,32 +1155,56 @@ __device__ void finalize_traj(Grp& g, Inst<M, L>& I) {
   g.sync();
 }
 
+// Error-free sum of two floats (Knuth): s + e == a + b exactly.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
 // initial nominal: x = rollout(x0, u_init) (open loop), integrated sequentially by the
-// group's first thread (FP64 states; FP32 increments in the mixed modes).
+// group's first thread.  In the mixed modes the state is carried as an unevaluated sum
+// of two floats (hi + lo, about 48 significant bits) updated by FP32 increments, so the
+// serial chain stays on the FP32 pipes; FP64 mode integrates in FP64.
 template <class M, class L, class Grp>
 __device__ void initial_rollout(Grp& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>& P) {
   constexpr int N = M::NX, U = M::NU;
   if (g.rank() == 0) {
-    double x[N];
+    if constexpr (std::is_same<L, float>::value) {
+      float hi[N], lo[N], un_next[U];
 #pragma unroll
-    for (int i = 0; i < N; i++) { x[i] = I.x0[i]; I.xn[i] = x[i]; }
-    float un_next[U];
+      for (int i = 0; i < N; i++) {
+        hi[i] = float(I.x0[i]);
+        lo[i] = float(I.x0[i] - double(hi[i]));
+        I.xn[i] = I.x0[i];
+      }
 #pragma unroll
-    for (int i = 0; i < U; i++) un_next[i] = float(I.un[i]);
-    for (int t = 0; t < I.T; t++) {
-      if constexpr (std::is_same<L, float>::value) {
-        float xf[N], uf[U], dv[N];
-#pragma unroll
-        for (int i = 0; i < N; i++) xf[i] = float(x[i]);
+      for (int i = 0; i < U; i++) un_next[i] = float(I.un[i]);
+      for (int t = 0; t < I.T; t++) {
+        float uf[U], dv[N], xf[N];
 #pragma unroll
         for (int i = 0; i < U; i++) {
           uf[i] = un_next[i];
-          if (t + 1 < I.T) un_next[i] = float(I.un[(size_t)(t + 1) * U + i]);  // prefetch
+          if (t + 1 < I.T) un_next[i] = float(I.un[(size_t)(t + 1) * U + i]);
         }
+#pragma unroll
+        for (int i = 0; i < N; i++) xf[i] = hi[i] + lo[i];
         MOps<M>::inc32(P, xf, uf, dv);
 #pragma unroll
-        for (int i = 0; i < N; i++) { x[i] += double(dv[i]); I.xn[(size_t)(t + 1) * N + i] = x[i]; }
-      } else {
+        for (int i = 0; i < N; i++) {
+          float sh, se;
+          two_sum(hi[i], dv[i], sh, se);
+          se += lo[i];
+          hi[i] = sh + se;
+          lo[i] = se - (hi[i] - sh);
+          I.xn[(size_t)(t + 1) * N + i] = double(hi[i]) + double(lo[i]);
+        }
+      }
+    } else {
+      double x[N];
+#pragma unroll
+      for (int i = 0; i < N; i++) { x[i] = I.x0[i]; I.xn[i] = x[i]; }
+      for (int t = 0; t < I.T; t++) {
         double xn[N];
         MOps<M>::f(P, x, I.un + (size_t)t * U, xn);
 #pragma unroll
@@ -1115,10 +1237,11 @@ __device__ void solve_instance(Grp& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>&
   }
   g.sync();
   const long long c_start = clock64();
-  initial_rollout(g, I, P);
   NStats st{0, 0, 0, 0, 0, 0, 0, O.alpha0, {0, 0, 0, 0, 0, 0}};
   Aug A;
   int rc = ST_OK;
+  initial_rollout(g, I, P);
+  st.cyc[5] = clock64() - c_start;
   if (O.method == 0) {
     // ---- primal log-barrier IP (eq. lb-min, lb-step-2) ----
     A.kind = AUG_BARRIER; A.mu = O.mu0; A.rho = 1.0; A.z = nullptr; A.v = nullptr;
@@ -1198,8 +1321,9 @@ __device__ void solve_instance(Grp& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>&
   info.exact_passes = st.exact_passes;
   info.alpha = st.alpha;
   info.r_kkt = fmax(fmax(info.r_stat, info.r_dyn), fmax(info.r_feas, O.method == 0 ? info.mu : 0.0));
-  for (int k = 0; k < 5; k++) info.cyc[k] = st.cyc[k];
-  info.cyc[5] = clock64() - c_start - (st.cyc[0] + st.cyc[1] + st.cyc[2] + st.cyc[3] + st.cyc[4]);
+  for (int k = 0; k < 6; k++) info.cyc[k] = st.cyc[k];
+  info.cyc[6] = clock64() - c_start;
+  for (int k = 0; k < 6; k++) info.cyc[6] -= st.cyc[k];
   if (g.rank() == 0) *info_out = info;
 }
 
@@ -1218,7 +1342,7 @@ struct KArgs {
 };
 
 template <int N, int U, class L>
-constexpr size_t scratch_bytes(int nwarps) {
+__host__ __device__ constexpr size_t scratch_bytes(int nwarps) {
   // largest collective element (value element), nwarps + 2 slots, or 8 doubles per warp
   return ((size_t)(nwarps + 2) * sizeof(Val<N, L>) > (size_t)nwarps * 8 * 8)
              ? (size_t)(nwarps + 2) * sizeof(Val<N, L>)
@@ -1259,6 +1383,33 @@ __global__ void __launch_bounds__(128) k_solve_grid(KArgs args, Work<L> w) {
   Inst<M, L> I;
   I.setup(w, id, args.x0, g.rank(), g.size(), P.nw);
   solve_instance<M, L, SV>(g, I, P, O, args.u_init, args.info);
+}
+
+// one thread-block cluster on one instance (medium horizons)
+template <class M, class L, class SV>
+__global__ void __launch_bounds__(256) k_solve_cluster(KArgs args, Work<L> w) {
+  constexpr int N = M::NX, U = M::NU;
+  extern __shared__ __align__(16) char smem[];
+  ProbS<N, U>& P = *reinterpret_cast<ProbS<N, U>*>(smem);
+  char* scratch = smem + ((sizeof(ProbS<N, U>) + 15) & ~size_t(15));
+  const int nwarps = blockDim.x >> 5;
+  const size_t sbytes = scratch_bytes<N, U, L>(nwarps);
+  constexpr int XB = (int)((sizeof(Val<N, double>) > 64 ? sizeof(Val<N, double>) : 64) + 15) / 16 * 16;
+  char* xch = scratch + ((sbytes + 15) & ~size_t(15));
+  load_prob<N, U>(P, *args.prob, args.xref);
+  const OptDev O = *args.opt;
+  const InstDev id = args.inst[0];
+  ClusterGroup g{scratch, xch, XB, 0};
+  g.sync();  // every CTA of the cluster is running before any DSMEM access
+  Inst<M, L> I;
+  I.setup(w, id, args.x0, g.rank(), g.size(), P.nw);
+  solve_instance<M, L, SV>(g, I, P, O, args.u_init, args.info);
+  g.sync();  // keep this CTA's shared memory alive until every CTA is done reading it
+}
+
+template <int N, int U, class L>
+__host__ __device__ constexpr size_t cluster_xch_bytes() {
+  return 2 * (size_t)(((sizeof(Val<N, double>) > 64 ? sizeof(Val<N, double>) : 64) + 15) / 16 * 16);
 }
 
 }  // namespace ptn

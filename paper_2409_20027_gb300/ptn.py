@@ -36,7 +36,8 @@ class Problem(C.Structure):
 
 
 _OPT_INTS = ["precision", "max_newton", "max_outer", "ls_count", "admm_fixed_iters", "roll_max_iter",
-             "block_threads", "grid_min_T", "grid_steps_per_thread", "polish_after"]
+             "block_threads", "grid_min_T", "grid_steps_per_thread", "polish_after",
+             "cluster_max_blocks", "pad_opt"]
 _OPT_DBLS = ["mu0", "zeta", "mu_final", "tol_inner", "tol_final", "rho", "admm_tol", "alpha0",
              "alpha_min", "alpha_max", "ls_beta", "armijo_c1", "armijo_eps", "roll_tol", "polish",
              "armijo_eps32"]
@@ -52,7 +53,7 @@ class Info(C.Structure):
                                        "exact_passes", "pad"]] + \
                [(k, C.c_double) for k in ["mu", "alpha", "r_stat", "r_dyn", "r_feas", "r_kkt", "J",
                                           "J_c", "r_p", "r_d"]] + \
-               [("cycles", C.c_longlong * 6)]
+               [("cycles", C.c_longlong * 7)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_ if k != "cycles"}
