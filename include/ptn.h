@@ -177,6 +177,38 @@ int ptn_adjoint(ptn_solver* s, int B, const int* T_b, const double* x0, const do
 /* Number of constraint rows nw of the handle's problem. */
 int ptn_num_rows(const ptn_solver* s);
 
+/* Allocation-free single interior-point solve.  The paper has no counterpart: this is
+ * an integration entry point for callers that must not reach the device allocator while
+ * solving (a fixed-rate MPC loop, where cudaMalloc/cudaFree can synchronise the device
+ * and take unbounded time; a plug-in that keeps no handle between calls).
+ *
+ * Same problem, options and results as ptn_solver_create + ptn_solve_ip on a one-CTA
+ * solve (block_threads threads; grid_min_T and cluster_max_blocks are ignored), but no
+ * handle: the problem record, options, report and all workspace arrays live in one
+ * file-scope device array of 4 MiB (the cart-pole model needs about 0.7 KB per step, so
+ * T up to about 5800; the pendulum about 0.3 KB per step).  A T that does not fit is
+ * rejected with PTN_ERR_INVALID_ARG and a message giving the bytes needed.  No device or
+ * pinned memory is allocated and no allocating library call is made.
+ *
+ * The first call on each device does set-up: it looks up the array's device address
+ * (cudaGetSymbolAddress, which loads the module on first use) and caches it.  Make that
+ * first call before any stream capture on that device.
+ *
+ * Nothing in the array has to start at zero: each call copies the problem record,
+ * options and instance entry into it in stream order, and the kernel writes every
+ * workspace entry before it reads it.  All calls on one device share the array, so calls
+ * whose executions can overlap (other host threads, or streams not ordered with each
+ * other) race and corrupt each other's results; serialise them, e.g. on one stream.
+ *
+ * x0 (device, nx doubles), u_init (device, T*nu doubles, or NULL for zeros), x_out
+ * ((T+1)*nx), u_out (T*nu) and lam_out ((T+1)*nx, or NULL) are device buffers owned by
+ * the caller.  opt NULL means the defaults.  err (err_len bytes, may be NULL) receives
+ * a message on failure, "" on success.  Returns PTN_OK or a status code; the call
+ * returns after the solve has finished on `stream`. */
+int ptn_solve_ip_static(const ptn_problem* prob, const ptn_options* opt, const double* x0,
+                        const double* u_init, int T, double* x_out, double* u_out, double* lam_out,
+                        ptn_info* info, char* err, int err_len, void* stream);
+
 /* Library version string. */
 const char* ptn_version(void);
 

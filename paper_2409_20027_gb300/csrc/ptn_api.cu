@@ -3,10 +3,12 @@
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdarg.h>
+#include <stddef.h>
 #include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
 
+#include <mutex>
 #include <vector>
 
 #include "../../include/ptn.h"
@@ -456,4 +458,191 @@ extern "C" int ptn_adjoint(ptn_solver* s, int B, const int* T_b, const double* x
   (void)B; (void)T_b; (void)x0; (void)xref; (void)x_star; (void)u_star; (void)mu; (void)gJ; (void)gx; (void)gu;
   (void)g_x0; (void)g_Qd; (void)g_Rd; (void)g_Qfd; (void)g_prm; (void)stream;
   return fail(s, PTN_ERR_INVALID_ARG, "adjoint not available in this build");
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free single solve.  Some callers must not reach the device allocator on
+// their solve path: a fixed-rate MPC loop, where cudaMalloc / cudaFree may synchronise
+// the whole device and take unbounded time, and hosts that keep no handle between calls
+// (a plug-in called through a plain C function pointer).  For them the problem record,
+// options, instance table, report and every workspace array of one CTA-tier solve live
+// in one file-scope device array of fixed size instead of a handle's cudaMalloc'd
+// workspace; everything else (kernels, launch, options) is the handle's code path.
+namespace {
+
+constexpr size_t kStaticScratchBytes = size_t(4) << 20;  // 4 MiB
+constexpr int kStaticMaxDevices = 64;
+
+struct StaticHead {
+  ProbDev prob;
+  OptDev opt;
+  InstDev inst;
+  InfoDev info;
+};
+
+std::mutex g_static_mu;
+char* g_static_base[kStaticMaxDevices];  // device address of g_static_scratch, per ordinal
+
+int static_fail(char* err, int err_len, int code, const char* fmt, ...) {
+  if (err && err_len > 0) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(err, (size_t)err_len, fmt, ap);
+    va_end(ap);
+  }
+  return code;
+}
+
+}  // namespace
+
+static __device__ __align__(256) char g_static_scratch[kStaticScratchBytes];
+
+extern "C" int ptn_solve_ip_static(const ptn_problem* prob, const ptn_options* opt_in, const double* x0,
+                                   const double* u_init, int T, double* x_out, double* u_out, double* lam_out,
+                                   ptn_info* info, char* err, int err_len, void* stream_) {
+  if (err && err_len > 0) err[0] = 0;
+  if (!prob || !x0 || !x_out || !u_out) return static_fail(err, err_len, PTN_ERR_INVALID_ARG, "NULL argument");
+  if (T < 1) return static_fail(err, err_len, PTN_ERR_INVALID_ARG, "horizon T=%d must be >= 1", T);
+  ptn_options o;
+  if (opt_in) o = *opt_in;
+  else ptn_default_options(&o);
+  {
+    ptn_solver tmp;  // only for the option check's message; holds no device memory
+    tmp.err[0] = 0;
+    const int rc = check_options(&tmp, &o);
+    if (rc) return static_fail(err, err_len, rc, "%s", tmp.err);
+  }
+  // problem record, as the handle builds it
+  int nx, nu;
+  if (model_dims(prob->model, &nx, &nu))
+    return static_fail(err, err_len, PTN_ERR_INVALID_ARG, "unknown or unsupported model id %d", prob->model);
+  if (prob->nx != nx || prob->nu != nu)
+    return static_fail(err, err_len, PTN_ERR_INVALID_ARG, "model %d has nx=%d nu=%d, got %d %d", prob->model, nx, nu,
+                       prob->nx, prob->nu);
+  if (prob->integrator != PTN_EULER && prob->integrator != PTN_RK4)
+    return static_fail(err, err_len, PTN_ERR_INVALID_ARG, "integrator must be PTN_EULER or PTN_RK4");
+  if (!(prob->dt > 0) || !isfinite(prob->dt))
+    return static_fail(err, err_len, PTN_ERR_INVALID_ARG, "dt must be positive");
+  if (!prob->Q || !prob->R || !prob->Qf || !prob->xref || !prob->uref)
+    return static_fail(err, err_len, PTN_ERR_INVALID_ARG, "Q, R, Qf, xref, uref are required");
+  StaticHead h;
+  memset(&h, 0, sizeof(h));
+  ProbDev& P = h.prob;
+  P.model = prob->model;
+  P.nx = nx;
+  P.nu = nu;
+  P.integrator = prob->integrator;
+  P.dt = prob->dt;
+  for (int i = 0; i < 8; i++) P.prm[i] = prob->prm[i];
+  for (int i = 0; i < nx * nx; i++) {
+    if (!isfinite(prob->Q[i]) || !isfinite(prob->Qf[i]))
+      return static_fail(err, err_len, PTN_ERR_INVALID_ARG, "Q/Qf not finite");
+    P.Q[i] = prob->Q[i];
+    P.Qf[i] = prob->Qf[i];
+  }
+  for (int i = 0; i < nu * nu; i++) {
+    if (!isfinite(prob->R[i])) return static_fail(err, err_len, PTN_ERR_INVALID_ARG, "R not finite");
+    P.R[i] = prob->R[i];
+  }
+  for (int i = 0; i < nx; i++) P.xref[i] = prob->xref[i];
+  for (int i = 0; i < nu; i++) P.uref[i] = prob->uref[i];
+  int k = 0;
+  for (int i = 0; i < nx; i++) {
+    if (has_bound(prob->xhi, i)) { P.row_isx[k] = 1; P.row_idx[k] = i; P.row_sgn[k] = 1.0; P.row_bnd[k] = prob->xhi[i]; k++; }
+    if (has_bound(prob->xlo, i)) { P.row_isx[k] = 1; P.row_idx[k] = i; P.row_sgn[k] = -1.0; P.row_bnd[k] = prob->xlo[i]; k++; }
+  }
+  for (int i = 0; i < nu; i++) {
+    if (has_bound(prob->uhi, i)) { P.row_isx[k] = 0; P.row_idx[k] = i; P.row_sgn[k] = 1.0; P.row_bnd[k] = prob->uhi[i]; k++; }
+    if (has_bound(prob->ulo, i)) { P.row_isx[k] = 0; P.row_idx[k] = i; P.row_sgn[k] = -1.0; P.row_bnd[k] = prob->ulo[i]; k++; }
+  }
+  P.nw = k;
+  launch_fn fn = pick_launcher(P.model, o.precision);
+  if (!fn)
+    return static_fail(err, err_len, PTN_ERR_INVALID_ARG, "kernels for model %d, precision %d are not built", P.model,
+                       o.precision);
+  // workspace layout of a one-instance handle with max_T = T, inside the static array
+  const long long S = T, SB = T + 1;
+  const int n = nx, m = nu, nw = k;
+  size_t off = align256(sizeof(StaticHead));
+  size_t o_xB = off; off = align256(off + sizeof(double) * SB * n);
+  size_t o_uB = off; off = align256(off + sizeof(double) * S * m);
+  size_t o_lam = off; off = align256(off + sizeof(double) * SB * n);
+  size_t o_d = off; off = align256(off + sizeof(double) * S * m);
+  size_t o_F64 = off; off = align256(off + sizeof(double) * S * n * n);
+  size_t o_G64 = off; off = align256(off + sizeof(double) * S * n * m);
+  size_t o_E = off; off = align256(off + 8 * S * n * n);
+  size_t o_Gm = off; off = align256(off + 8 * S * n * m);
+  size_t o_Pm = off; off = align256(off + 8 * SB * n * n);
+  size_t o_Mm = off; off = align256(off + 8 * S * n * m);
+  size_t o_Rm = off; off = align256(off + 8 * S * m * m);
+  size_t o_Gam = off; off = align256(off + 8 * S * m * n);
+  size_t o_gam = off; off = align256(off + 8 * S * m);
+  size_t o_dx = off; off = align256(off + 8 * SB * n);
+  size_t o_du = off; off = align256(off + 8 * S * m);
+  size_t o_z = off; off = align256(off + sizeof(double) * S * (nw > 0 ? nw : 1));
+  size_t o_v = off; off = align256(off + sizeof(double) * S * (nw > 0 ? nw : 1));
+  if (off > kStaticScratchBytes)
+    return static_fail(err, err_len, PTN_ERR_INVALID_ARG,
+                       "T=%d needs %zu bytes of static scratch for model %d; the array holds %zu bytes", T, off,
+                       P.model, kStaticScratchBytes);
+  // device set-up, once per device: the symbol's address (loading the module if needed)
+  int dev = 0;
+  cudaError_t ce = cudaGetDevice(&dev);
+  if (ce != cudaSuccess) return static_fail(err, err_len, PTN_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(ce));
+  if (dev < 0 || dev >= kStaticMaxDevices)
+    return static_fail(err, err_len, PTN_ERR_INVALID_ARG, "device ordinal %d outside [0, %d)", dev, kStaticMaxDevices);
+  char* b = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_static_mu);
+    if (!g_static_base[dev]) {
+      void* a = nullptr;
+      ce = cudaGetSymbolAddress(&a, g_static_scratch);
+      if (ce != cudaSuccess)
+        return static_fail(err, err_len, PTN_ERR_CUDA, "cudaGetSymbolAddress: %s", cudaGetErrorString(ce));
+      g_static_base[dev] = static_cast<char*>(a);
+    }
+    b = g_static_base[dev];
+  }
+  StaticHead* dh = reinterpret_cast<StaticHead*>(b);
+  to_optdev(o, PTN_METHOD_IP, &h.opt);
+  h.inst.T = T;
+  h.inst.xoff = 0;
+  h.inst.uoff = 0;
+  h.inst.pad = 0;
+  cudaStream_t st = (cudaStream_t)stream_;
+  // the head is copied from this stack frame in stream order; nothing else needs to be
+  // initialised, because the kernel writes every workspace entry before reading it
+  ce = cudaMemcpyAsync(dh, &h, offsetof(StaticHead, info), cudaMemcpyHostToDevice, st);
+  if (ce != cudaSuccess) return static_fail(err, err_len, PTN_ERR_CUDA, "cudaMemcpyAsync: %s", cudaGetErrorString(ce));
+  LaunchReq q{};
+  q.tier = 0;
+  q.precision = o.precision;
+  q.nthreads = o.block_threads;
+  q.nblocks = 1;
+  q.stream = st;
+  q.w.xA = x_out;
+  q.w.uA = u_out;
+  q.w.xB = (double*)(b + o_xB); q.w.uB = (double*)(b + o_uB);
+  q.w.lam = lam_out ? lam_out : (double*)(b + o_lam);
+  q.w.d = (double*)(b + o_d); q.w.F64 = (double*)(b + o_F64); q.w.G64 = (double*)(b + o_G64);
+  q.w.E = b + o_E; q.w.Gm = b + o_Gm; q.w.Pm = b + o_Pm; q.w.Mm = b + o_Mm; q.w.Rm = b + o_Rm;
+  q.w.Gam = b + o_Gam; q.w.gam = b + o_gam; q.w.dx = b + o_dx; q.w.du = b + o_du;
+  q.w.z = (double*)(b + o_z); q.w.v = (double*)(b + o_v);
+  q.args.prob = &dh->prob;
+  q.args.opt = &dh->opt;
+  q.args.inst = &dh->inst;
+  q.args.x0 = x0;
+  q.args.xref = nullptr;
+  q.args.u_init = u_init;
+  q.args.info = &dh->info;
+  q.args.B = 1;
+  ce = fn(q);
+  if (ce != cudaSuccess) return static_fail(err, err_len, PTN_ERR_CUDA, "launch: %s", cudaGetErrorString(ce));
+  InfoDev hi;
+  ce = cudaMemcpyAsync(&hi, &dh->info, sizeof(InfoDev), cudaMemcpyDeviceToHost, st);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+  if (ce != cudaSuccess) return static_fail(err, err_len, PTN_ERR_CUDA, "solve: %s", cudaGetErrorString(ce));
+  if (info) from_info(hi, info);
+  if (hi.status != 0) return static_fail(err, err_len, hi.status, "solve finished with status %d", hi.status);
+  return PTN_OK;
 }

@@ -18,12 +18,13 @@ LIB_PATH = os.path.join(_HERE, "_build", "libptn.so")
 
 PTN_FP64, PTN_FP32_FP64SOLVE, PTN_FP32 = 0, 1, 2
 METHOD_IP, METHOD_ADMM = 0, 1
+PTN_ERR_INVALID_ARG, PTN_ERR_CUDA = -1, -6
 STATUS = {0: "ok", -1: "invalid argument", -2: "infeasible start", -3: "not converged",
           -4: "numerical failure", -5: "device wait timed out", -6: "CUDA error"}
 
 EXPORTS = ["ptn_default_options", "ptn_solver_create", "ptn_solver_destroy", "ptn_last_error",
            "ptn_set_options", "ptn_solve_ip", "ptn_solve_admm", "ptn_solve_batch", "ptn_adjoint",
-           "ptn_num_rows", "ptn_version"]
+           "ptn_num_rows", "ptn_version", "ptn_solve_ip_static"]
 
 _P = C.POINTER(C.c_double)
 
@@ -88,6 +89,8 @@ def load(path: str = LIB_PATH):
         lib.ptn_adjoint.argtypes = [vp, C.c_int, ip, vp, vp, vp, vp, C.c_double, C.c_double, vp, vp, vp, vp,
                                     vp, vp, vp, vp]
         lib.ptn_num_rows.argtypes = [vp]
+        lib.ptn_solve_ip_static.argtypes = [C.POINTER(Problem), C.POINTER(Options), vp, vp, C.c_int, vp, vp, vp,
+                                            C.POINTER(Info), C.c_char_p, C.c_int, vp]
         lib.ptn_version.restype = C.c_char_p
         _lib = lib
     return _lib
@@ -238,3 +241,49 @@ class Solver:
         if rc != 0:
             raise PtnError(f"ptn_adjoint failed ({rc}): {self.last_error()}")
         return out
+
+
+def _make_problem(prob):
+    """ptn_problem record for `prob`; returns (record, arrays it points into)."""
+    keep = []
+    P = Problem()
+    P.model, P.nx, P.nu, P.integrator = int(prob.model), int(prob.nx), int(prob.nu), int(prob.integrator)
+    P.dt = float(prob.dt)
+    prm = np.zeros(8)
+    prm[:len(prob.prm)] = prob.prm
+    for i in range(8):
+        P.prm[i] = prm[i]
+    for name in ["A", "B", "W", "Q", "R", "Qf", "xref", "uref", "xlo", "xhi", "ulo", "uhi"]:
+        v = getattr(prob, name, None)
+        if v is None:
+            setattr(P, name, None)
+        else:
+            a = np.ascontiguousarray(np.asarray(v, dtype=np.float64).ravel())
+            keep.append(a)
+            setattr(P, name, a.ctypes.data_as(_P))
+    return P, keep
+
+
+def solve_ip_static(prob, x0, T: int, u_init=None, x_out=None, u_out=None, lam_out=None,
+                    options: Options | None = None, stream=None, **opt):
+    """ptn_solve_ip_static: one IP solve with no handle and no device allocation by the
+    library (workspace in a fixed 4 MiB device array shared by all calls on a device).
+    Output tensors are allocated here unless given.  Returns (x, u, lam, info); raises
+    PtnError for invalid arguments and CUDA errors, like a handle's create would."""
+    lib = load()
+    P, keep = _make_problem(prob)
+    o = options if options is not None else default_options(**opt)
+    nx, nu = int(prob.nx), int(prob.nu)
+    import torch
+    mk = lambda r, c: torch.empty((r, c), dtype=torch.float64, device=x0.device)
+    x_out = mk(T + 1, nx) if x_out is None else x_out
+    u_out = mk(T, nu) if u_out is None else u_out
+    lam_out = mk(T + 1, nx) if lam_out is None else lam_out
+    info = Info()
+    err = C.create_string_buffer(512)
+    rc = lib.ptn_solve_ip_static(C.byref(P), C.byref(o), _dptr(x0), _dptr(u_init), int(T), _dptr(x_out),
+                                 _dptr(u_out), _dptr(lam_out), C.byref(info), err, 512, _stream(stream))
+    del keep
+    if rc in (PTN_ERR_INVALID_ARG, PTN_ERR_CUDA):
+        raise PtnError(f"ptn_solve_ip_static failed ({rc}): {err.value.decode()}")
+    return x_out, u_out, lam_out, info.as_dict()
