@@ -150,25 +150,32 @@ int ptn_solve_admm(ptn_solver* s, const double* x0, const double* u_init, int T,
                    void* stream);
 
 /* Solve B independent instances of the same model with horizons T_b (host array) in one
- * launch, one CTA per instance.  x0 is device B x nx; xref is device B x nx (per-instance
- * tracking target) or NULL; u_init is device (sum T_b) x nu or NULL.  Outputs are
- * concatenated in instance order: x_out (sum (T_b+1)) x nx, u_out (sum T_b) x nu,
- * lam_out like x_out or NULL.  info_b is a host array of B records (may be NULL).
- * method is PTN_METHOD_IP or PTN_METHOD_ADMM.  Returns PTN_OK when every instance
- * converged, else the first non-zero instance status. */
-int ptn_solve_batch(ptn_solver* s, int method, int B, const int* T_b, const double* x0,
-                    const double* xref, const double* u_init, double* x_out, double* u_out,
-                    double* lam_out, ptn_info* info_b, void* stream);
+ * launch, one CTA per instance (a batch of one runs like ptn_solve_ip).  dt_b (host, B, or NULL) gives each instance its own time
+ * step: instance b integrates with dt_b[b] and its stage weights Q, R are multiplied by
+ * dt_b[b] / prob.dt (the same continuous-time cost sampled at another rate; Qf is not
+ * scaled) -- the fixed-time, varying-sampling-rate protocol of the paper's experiments
+ * (Sec. IV).  x0 is device B x nx; xref is device B x nx (per-instance tracking target)
+ * or NULL; u_init is device (sum T_b) x nu or NULL.  Outputs are concatenated in
+ * instance order: x_out (sum (T_b+1)) x nx, u_out (sum T_b) x nu, lam_out like x_out or
+ * NULL.  info_b is a host array of B records (may be NULL).  method is PTN_METHOD_IP or
+ * PTN_METHOD_ADMM.  Returns PTN_OK when every instance converged, else the first
+ * non-zero instance status (PTN_ERR_INVALID_ARG for a non-positive dt_b entry). */
+int ptn_solve_batch(ptn_solver* s, int method, int B, const int* T_b, const double* dt_b,
+                    const double* x0, const double* xref, const double* u_init, double* x_out,
+                    double* u_out, double* lam_out, ptn_info* info_b, void* stream);
 
 /* Gradients of the scalar loss  gJ * J* + <gx, x*> + <gu, u*>  at B solutions of the
- * barrier problem with weight mu (J* = optimal barrier objective; x*, u* concatenated as
+ * barrier problem (at the problem's own dt) with weight mu (J* = optimal barrier objective; x*, u* concatenated as
  * in ptn_solve_batch), with respect to x0 (B x nx), diag Q (B x nx), diag R (B x nu),
  * diag Qf (B x nx) and the model constants prm (B x 8).  The J* part follows the
  * envelope theorem on the Lagrangian eq. ocp-lagrangian (gradient in x0 = lam_1); the x*, u*
  * part solves the adjoint LQR (same Hessian as the Newton step, linear terms from
  * gx, gu) with the value and state scans, and its multipliers with the co-state scan.
+ * The adjoint runs in FP64 in every precision mode (one CTA per instance, block_threads
+ * threads): at a solution the reduced Hessian is ill-conditioned near active bounds.
  * All array arguments are device pointers; gx, gu may be NULL (J* part only); any output
- * may be NULL.  xref as in ptn_solve_batch. */
+ * may be NULL.  xref as in ptn_solve_batch.  Returns PTN_ERR_NUMERICAL when the Hessian
+ * is not positive definite on the dynamics at some instance's solution. */
 int ptn_adjoint(ptn_solver* s, int B, const int* T_b, const double* x0, const double* xref,
                 const double* x_star, const double* u_star, double mu, double gJ,
                 const double* gx, const double* gu, double* g_x0, double* g_Qd, double* g_Rd,

@@ -331,7 +331,7 @@ static void from_info(const InfoDev& d, ptn_info* o) {
 
 static int solve_common(ptn_solver* s, int method, int B, const int* T_b, const double* x0, const double* xref,
                         const double* u_init, double* x_out, double* u_out, double* lam_out, double* z_out,
-                        double* v_out, ptn_info* info, bool single, void* stream_) {
+                        double* v_out, ptn_info* info, void* stream_, const double* dt_b = nullptr) {
   if (!s) return PTN_ERR_INVALID_ARG;
   s->err[0] = 0;
   cudaStream_t st = (cudaStream_t)stream_;
@@ -341,10 +341,13 @@ static int solve_common(ptn_solver* s, int method, int B, const int* T_b, const 
   long long steps = 0;
   for (int i = 0; i < B; i++) {
     if (T_b[i] < 1) return fail(s, PTN_ERR_INVALID_ARG, "horizon T_b[%d]=%d must be >= 1", i, T_b[i]);
+    if (dt_b && !(dt_b[i] > 0 && isfinite(dt_b[i])))
+      return fail(s, PTN_ERR_INVALID_ARG, "time step dt_b[%d] must be positive and finite", i);
     s->hinst[i].T = T_b[i];
     s->hinst[i].uoff = (int)steps;
     s->hinst[i].xoff = (int)(steps + i);
     s->hinst[i].pad = 0;
+    s->hinst[i].dt = dt_b ? dt_b[i] : 0.0;
     steps += T_b[i];
   }
   if (steps > s->cap_steps)
@@ -372,7 +375,7 @@ static int solve_common(ptn_solver* s, int method, int B, const int* T_b, const 
   // one instance: a thread-block cluster when the horizon needs 2..16 CTAs, else the
   // cooperative grid from grid_min_T on, else one CTA
   int cl_blocks = 0;
-  if (single && B == 1 && s->opt.cluster_max_blocks >= 2) {
+  if (B == 1 && s->opt.cluster_max_blocks >= 2) {
     const long long per = (long long)s->opt.block_threads * s->opt.grid_steps_per_thread;
     const long long need = (T_b[0] + per - 1) / per;
     if (need >= 2 && need <= s->opt.cluster_max_blocks) {
@@ -386,7 +389,7 @@ static int solve_common(ptn_solver* s, int method, int B, const int* T_b, const 
       if (need <= maxc) cl_blocks = (int)need;
     }
   }
-  const bool grid = !cl_blocks && single && B == 1 && s->opt.grid_min_T > 0 && T_b[0] >= s->opt.grid_min_T;
+  const bool grid = !cl_blocks && B == 1 && s->opt.grid_min_T > 0 && T_b[0] >= s->opt.grid_min_T;
   if (cl_blocks) {
     q.tier = 2;
     q.nthreads = s->opt.block_threads;
@@ -434,30 +437,80 @@ static int solve_common(ptn_solver* s, int method, int B, const int* T_b, const 
 extern "C" int ptn_solve_ip(ptn_solver* s, const double* x0, const double* u_init, int T, double* x_out,
                             double* u_out, double* lam_out, ptn_info* info, void* stream) {
   return solve_common(s, PTN_METHOD_IP, 1, &T, x0, nullptr, u_init, x_out, u_out, lam_out, nullptr, nullptr, info,
-                      true, stream);
+                      stream);
 }
 
 extern "C" int ptn_solve_admm(ptn_solver* s, const double* x0, const double* u_init, int T, double* x_out,
                               double* u_out, double* lam_out, double* z_out, double* v_out, ptn_info* info,
                               void* stream) {
   return solve_common(s, PTN_METHOD_ADMM, 1, &T, x0, nullptr, u_init, x_out, u_out, lam_out, z_out, v_out, info,
-                      true, stream);
+                      stream);
 }
 
-extern "C" int ptn_solve_batch(ptn_solver* s, int method, int B, const int* T_b, const double* x0,
-                               const double* xref, const double* u_init, double* x_out, double* u_out,
-                               double* lam_out, ptn_info* info_b, void* stream) {
-  return solve_common(s, method, B, T_b, x0, xref, u_init, x_out, u_out, lam_out, nullptr, nullptr, info_b, false,
-                      stream);
+extern "C" int ptn_solve_batch(ptn_solver* s, int method, int B, const int* T_b, const double* dt_b,
+                               const double* x0, const double* xref, const double* u_init, double* x_out,
+                               double* u_out, double* lam_out, ptn_info* info_b, void* stream) {
+  return solve_common(s, method, B, T_b, x0, xref, u_init, x_out, u_out, lam_out, nullptr, nullptr, info_b,
+                      stream, dt_b);
 }
 
 extern "C" int ptn_adjoint(ptn_solver* s, int B, const int* T_b, const double* x0, const double* xref,
                            const double* x_star, const double* u_star, double mu, double gJ, const double* gx,
                            const double* gu, double* g_x0, double* g_Qd, double* g_Rd, double* g_Qfd,
-                           double* g_prm, void* stream) {
-  (void)B; (void)T_b; (void)x0; (void)xref; (void)x_star; (void)u_star; (void)mu; (void)gJ; (void)gx; (void)gu;
-  (void)g_x0; (void)g_Qd; (void)g_Rd; (void)g_Qfd; (void)g_prm; (void)stream;
-  return fail(s, PTN_ERR_INVALID_ARG, "adjoint not available in this build");
+                           double* g_prm, void* stream_) {
+  if (!s) return PTN_ERR_INVALID_ARG;
+  s->err[0] = 0;
+  cudaStream_t st = (cudaStream_t)stream_;
+  if (B < 1 || B > s->cap_batch) return fail(s, PTN_ERR_INVALID_ARG, "B=%d outside [1, %d]", B, s->cap_batch);
+  if (!T_b || !x0 || !x_star || !u_star) return fail(s, PTN_ERR_INVALID_ARG, "NULL argument");
+  if (!(mu > 0) || !isfinite(mu) || !isfinite(gJ)) return fail(s, PTN_ERR_INVALID_ARG, "mu must be positive, gJ finite");
+  long long steps = 0;
+  for (int i = 0; i < B; i++) {
+    if (T_b[i] < 1) return fail(s, PTN_ERR_INVALID_ARG, "horizon T_b[%d]=%d must be >= 1", i, T_b[i]);
+    s->hinst[i].T = T_b[i];
+    s->hinst[i].uoff = (int)steps;
+    s->hinst[i].xoff = (int)(steps + i);
+    s->hinst[i].pad = 0;
+    s->hinst[i].dt = 0.0;
+    steps += T_b[i];
+  }
+  if (steps > s->cap_steps)
+    return fail(s, PTN_ERR_INVALID_ARG, "total horizon %lld exceeds the workspace (%lld)", steps, s->cap_steps);
+  // the adjoint LQR runs in FP64 whatever the solver's precision
+  launch_fn fn = pick_launcher(s->hprob.model, PTN_FP64);
+  if (!fn) return fail(s, PTN_ERR_INVALID_ARG, "FP64 kernels for model %d are not built", s->hprob.model);
+  CK(cudaMemcpyAsync(s->dinst, s->hinst, sizeof(InstDev) * B, cudaMemcpyHostToDevice, st));
+  AdjArgs aa{};
+  aa.gx = gx;
+  aa.gu = gu;
+  aa.qx = s->w.xB;  // the candidate-trajectory array is free outside a solve
+  aa.mu = mu;
+  aa.gJ = gJ;
+  aa.g_x0 = g_x0; aa.g_Qd = g_Qd; aa.g_Rd = g_Rd; aa.g_Qfd = g_Qfd; aa.g_prm = g_prm;
+  LaunchReq q{};
+  q.tier = 3;
+  q.precision = PTN_FP64;
+  q.stream = st;
+  q.w = s->w;
+  q.w.xA = const_cast<double*>(x_star);  // read only: the adjoint writes no trajectory
+  q.w.uA = const_cast<double*>(u_star);
+  q.args.prob = s->dprob;
+  q.args.opt = s->dopt;
+  q.args.inst = s->dinst;
+  q.args.x0 = x0;
+  q.args.xref = xref;
+  q.args.info = s->dinfo;
+  q.args.B = B;
+  q.adj = &aa;
+  q.nthreads = s->opt.block_threads;
+  q.nblocks = B;
+  CK(fn(q));
+  CK(cudaMemcpyAsync(s->hinfo, s->dinfo, sizeof(InfoDev) * B, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  for (int i = 0; i < B; i++)
+    if (s->hinfo[i].status != 0)
+      return fail(s, PTN_ERR_NUMERICAL, "instance %d: the Hessian is not positive definite on the dynamics", i);
+  return PTN_OK;
 }
 
 // ---------------------------------------------------------------------------

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
+#include <string.h>
 
 #include <type_traits>
 
@@ -66,6 +67,7 @@ struct InstDev {
   int xoff;     // offset of x_0 in state-major arrays, in steps (sum of previous T+1)
   int uoff;     // offset of u_0 in control-major arrays, in steps (sum of previous T)
   int pad;
+  double dt;    // > 0: this instance's time step (stage weights scaled by dt / problem dt)
 };
 
 // per-instance statistics (device array, copied to the host)
@@ -246,29 +248,109 @@ PTN_HD void chol_solve(const S* L, S* B) {
   }
 }
 
+// LDL^T factorisation of a symmetric positive definite matrix in place: the unit lower
+// factor below the diagonal and the reciprocal pivots 1/D_j on it.  One division per
+// pivot and no square root, which matters where S = double on GB300's FP64 pipe.
+// Returns false when a pivot is not positive and finite (A not positive definite).
+template <int N, class S = double>
+PTN_HD bool ldlt(S* A) {
+  S D[N];
+#pragma unroll
+  for (int j = 0; j < N; j++) {
+    S dj = A[j * N + j];
+#pragma unroll
+    for (int k = 0; k < j; k++) dj -= A[j * N + k] * A[j * N + k] * D[k];
+    if (!(dj > S(0)) || !isfinite(dj)) return false;
+    const S id = S(1) / dj;
+    D[j] = dj;
+    A[j * N + j] = id;
+#pragma unroll
+    for (int i = j + 1; i < N; i++) {
+      S t = A[i * N + j];
+#pragma unroll
+      for (int k = 0; k < j; k++) t -= A[i * N + k] * A[j * N + k] * D[k];
+      A[i * N + j] = t * id;
+    }
+  }
+  return true;
+}
+
+// solve (L D L^T) X = B in place with the factor of ldlt(), B is N x C
+template <int N, int C, class S = double>
+PTN_HD void ldlt_solve(const S* A, S* B) {
+#pragma unroll
+  for (int c = 0; c < C; c++) {
+#pragma unroll
+    for (int i = 0; i < N; i++) {
+      S s = B[i * C + c];
+#pragma unroll
+      for (int k = 0; k < i; k++) s -= A[i * N + k] * B[k * C + c];
+      B[i * C + c] = s;
+    }
+#pragma unroll
+    for (int i = 0; i < N; i++) B[i * C + c] *= A[i * N + i];
+#pragma unroll
+    for (int i = N - 1; i >= 0; i--) {
+      S s = B[i * C + c];
+#pragma unroll
+      for (int k = i + 1; k < N; k++) s -= A[k * N + i] * B[k * C + c];
+      B[i * C + c] = s;
+    }
+  }
+}
+
+// magnitude order key of a float or double from its bit pattern (sign cleared, high word
+// for doubles): integer comparisons, so pivot searches stay off the FP64 pipe
+PTN_HD unsigned mag_key(float x) {
+#ifdef __CUDA_ARCH__
+  return __float_as_uint(x) & 0x7fffffffu;
+#else
+  unsigned u;
+  memcpy(&u, &x, sizeof(u));
+  return u & 0x7fffffffu;
+#endif
+}
+PTN_HD unsigned mag_key(double x) {
+#ifdef __CUDA_ARCH__
+  return (unsigned)((unsigned long long)__double_as_longlong(x) >> 32) & 0x7fffffffu;
+#else
+  unsigned long long u;
+  memcpy(&u, &x, sizeof(u));
+  return (unsigned)(u >> 32) & 0x7fffffffu;
+#endif
+}
+
 // In-place inverse by Gauss-Jordan elimination with partial pivoting (FP64).
 // Returns false when a pivot is zero or not finite.
 template <int N, class S = double>
 PTN_HD bool inv_gj(S* A) {
   int piv[N];
+#pragma unroll
   for (int i = 0; i < N; i++) piv[i] = i;
 #pragma unroll (N <= 8 ? N : 1)
   for (int k = 0; k < N; k++) {
+    // pivot: largest magnitude in column k at or below the diagonal (by bit pattern)
     int p = k;
-    S best = fabs(A[k * N + k]);
+    unsigned best = mag_key(A[k * N + k]);
+#pragma unroll (N <= 8 ? N : 1)
     for (int i = k + 1; i < N; i++) {
-      S v = fabs(A[i * N + k]);
+      const unsigned v = mag_key(A[i * N + k]);
       if (v > best) { best = v; p = i; }
     }
-    if (!(best > S(0)) || !isfinite(best)) return false;
-    if (p != k) {
+    // row swap k <-> p as predicated moves with static indices (registers, not local memory)
+#pragma unroll (N <= 8 ? N : 1)
+    for (int i = k + 1; i < N; i++) {
+      if (i == p) {
 #pragma unroll (N <= 8 ? N : 4)
-      for (int j = 0; j < N; j++) {
-        S t = A[k * N + j]; A[k * N + j] = A[p * N + j]; A[p * N + j] = t;
+        for (int j = 0; j < N; j++) {
+          S t = A[k * N + j]; A[k * N + j] = A[i * N + j]; A[i * N + j] = t;
+        }
+        int t = piv[k]; piv[k] = piv[i]; piv[i] = t;
       }
-      int t = piv[k]; piv[k] = piv[p]; piv[p] = t;
     }
-    S ip = S(1) / A[k * N + k];
+    const S pv = A[k * N + k];
+    if (!(pv != S(0)) || !isfinite(pv)) return false;
+    S ip = S(1) / pv;
     A[k * N + k] = S(1);
 #pragma unroll (N <= 8 ? N : 4)
     for (int j = 0; j < N; j++) A[k * N + j] *= ip;

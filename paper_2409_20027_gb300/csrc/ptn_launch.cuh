@@ -23,7 +23,8 @@ inline Work<L> typed(const WorkRaw& r) {
 }
 
 struct LaunchReq {
-  int tier;       // 0: one CTA per instance, 1: cooperative grid, 2: one cluster on one instance
+  int tier;       // 0: one CTA per instance, 1: cooperative grid, 2: one cluster on one instance,
+                  // 3: adjoint, one CTA per instance
   int precision;  // 0: FP64, 1: FP32 with FP64 solves, 2: FP32
   int nblocks, nthreads;
   int query;      // 1: only report max co-resident grid blocks in *max_blocks
@@ -32,6 +33,7 @@ struct LaunchReq {
   KArgs args;
   WorkRaw w;
   cudaStream_t stream;
+  const AdjArgs* adj;  // tier 3
 };
 
 template <class M, class L, class SV>
@@ -46,6 +48,19 @@ cudaError_t launch_typed(LaunchReq& q) {
     if (q.query) return cudaSuccess;
     k_solve_cta<M, L, SV><<<q.nblocks, nthreads, smem, q.stream>>>(q.args, typed<L>(q.w));
     return cudaGetLastError();
+  }
+  if (q.tier == 3) {
+    // the adjoint is built only in the FP64 units (it runs in FP64 in every mode)
+    if constexpr (std::is_same<L, double>::value) {
+      cudaError_t e =
+          cudaFuncSetAttribute(k_adjoint_cta<M, L, SV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      if (q.query) return cudaSuccess;
+      k_adjoint_cta<M, L, SV><<<q.nblocks, nthreads, smem, q.stream>>>(q.args, typed<L>(q.w), *q.adj);
+      return cudaGetLastError();
+    } else {
+      return cudaErrorNotSupported;
+    }
   }
   if (q.tier == 2) {
     const size_t smc = ((smem + 15) & ~size_t(15)) + cluster_xch_bytes<N, U, L>();

@@ -91,14 +91,18 @@ PTN_HD void symmetrize(L* X) {
 //   b   = A2 K (b1 + C1 eta2) + b2
 //   J   = A1^T K^T J2 A1 + J1      K^T = (I + J2 C1)^{-1} since C, J are symmetric
 //   eta = A1^T K^T (eta2 - J2 b1) + eta1
-// I + C1 J2 is formed and inverted in SV (FP64, or FP32 in the all-FP32 mode); the
-// products run in L.  Returns false when I + C1 J2 is singular.
+// C1 J2 is formed in L, and I + C1 J2 inverted in SV (FP64, or FP32 in the all-FP32
+// mode); the products run in L.  Returns false when I + C1 J2 is singular.
 template <class SV = double>
 struct ValueOp {
   template <int N, class L>
   PTN_HD bool operator()(const Val<N, L>& e1, const Val<N, L>& e2, Val<N, L>& o) const {
+    // I + C1 J2 is formed in L and solved in SV ("FP32 arrays, FP64 solves")
+    L Ml[N * N];
+    mm<N, N, N>(e1.C, e2.J, Ml);
     SV Md[N * N];
-    mm<N, N, N>(e1.C, e2.J, Md);
+#pragma unroll
+    for (int i = 0; i < N * N; i++) Md[i] = SV(Ml[i]);
 #pragma unroll
     for (int i = 0; i < N; i++) Md[i * N + i] += SV(1);
     if (!inv_gj<N, SV>(Md)) return false;
@@ -147,7 +151,7 @@ struct ValueOp {
 // Element initialisation eq. value-fun-elem-init in the P^{-1}-free form
 //   A = F - G R~^{-1} M^T, J = P - M R~^{-1} M^T, C = G R~^{-1} G^T,
 //   eta = M R~^{-1} d, b = -G R~^{-1} d,  R~ = R + alpha I,
-// identical to the printed q_t, r_t form whenever P_t is invertible.  The Cholesky
+// identical to the printed q_t, r_t form whenever P_t is invertible.  The LDL^T
 // factorisation and solve of R~ run in SV; the products in L.
 // Returns false when R~ is not positive definite.
 template <int N, int U, class L, class SV>
@@ -159,7 +163,7 @@ PTN_HD bool value_init(const L* F, const L* G, const L* Pm, const L* Mm, const L
   for (int i = 0; i < U * U; i++) Rt[i] = SV(Rm[i]);
 #pragma unroll
   for (int i = 0; i < U; i++) Rt[i * U + i] += SV(alpha);
-  if (!chol<U, SV>(Rt)) return false;
+  if (!ldlt<U, SV>(Rt)) return false;
 #pragma unroll
   for (int i = 0; i < U; i++) {
 #pragma unroll (N <= 8 ? N : 4)
@@ -169,7 +173,7 @@ PTN_HD bool value_init(const L* F, const L* G, const L* Pm, const L* Mm, const L
     }
     X[i * C + 2 * N] = SV(d[i]);
   }
-  chol_solve<U, C, SV>(Rt, X);
+  ldlt_solve<U, C, SV>(Rt, X);
   L XL[U * C];
 #pragma unroll
   for (int i = 0; i < U * C; i++) XL[i] = L(X[i]);
@@ -242,8 +246,8 @@ PTN_HD bool riccati_step(const L* F, const L* G, const L* Pm, const L* Mm, const
     }
     X[i * (N + 1) + N] = SV(d[i]) + SV(Gs[i]);
   }
-  if (!chol<U, SV>(Q)) return false;
-  chol_solve<U, N + 1, SV>(Q, X);
+  if (!ldlt<U, SV>(Q)) return false;
+  ldlt_solve<U, N + 1, SV>(Q, X);
 #pragma unroll
   for (int i = 0; i < U; i++) {
 #pragma unroll (N <= 8 ? N : 4)

@@ -47,16 +47,19 @@ struct ProbS {
 };
 
 template <int N, int U>
-__device__ void load_prob(ProbS<N, U>& S, const ProbDev& P, const double* xref_override) {
+// dt_inst > 0: the instance's own time step; the stage weights Q, R are scaled by
+// dt_inst / P.dt (the same continuous-time cost at another sampling rate), Qf is not.
+__device__ void load_prob(ProbS<N, U>& S, const ProbDev& P, const double* xref_override, double dt_inst = 0.0) {
+  const double sc = dt_inst > 0.0 ? dt_inst / P.dt : 1.0;
   for (int i = threadIdx.x; i < N * N; i += blockDim.x) {
-    S.Q[i] = P.Q[i];
+    S.Q[i] = sc * P.Q[i];
     S.Qf[i] = P.Qf[i];
-    S.Qs[i] = float(P.Q[i] + P.Q[(i % N) * N + i / N]);
+    S.Qs[i] = float(sc * (P.Q[i] + P.Q[(i % N) * N + i / N]));
     S.Qfs[i] = float(P.Qf[i] + P.Qf[(i % N) * N + i / N]);
   }
   for (int i = threadIdx.x; i < U * U; i += blockDim.x) {
-    S.R[i] = P.R[i];
-    S.Rs[i] = float(P.R[i] + P.R[(i % U) * U + i / U]);
+    S.R[i] = sc * P.R[i];
+    S.Rs[i] = float(sc * (P.R[i] + P.R[(i % U) * U + i / U]));
   }
   for (int i = threadIdx.x; i < N; i += blockDim.x) S.xref[i] = xref_override ? xref_override[i] : P.xref[i];
   for (int i = threadIdx.x; i < U; i += blockDim.x) S.uref[i] = P.uref[i];
@@ -65,7 +68,7 @@ __device__ void load_prob(ProbS<N, U>& S, const ProbDev& P, const double* xref_o
     S.sgn[i] = P.row_sgn[i]; S.bnd[i] = P.row_bnd[i]; S.isx[i] = P.row_isx[i]; S.idx[i] = P.row_idx[i];
   }
   if (threadIdx.x == 0) {
-    S.nw = P.nw; S.integ = P.integrator; S.model = P.model; S.dt = P.dt;
+    S.nw = P.nw; S.integ = P.integrator; S.model = P.model; S.dt = dt_inst > 0.0 ? dt_inst : P.dt;
     S.A = P.A; S.B = P.B; S.W = P.W;
   }
   __syncthreads();
@@ -668,14 +671,22 @@ __device__ void quadratize(Grp& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>& P, 
 
 // pass 3: value suffix scan (Alg. 2) + feedback sweep.  Returns true on success; false
 // (group-uniform) when some R~_t, Q_t is not PD or some I + C J is singular.
+//
+// qx (optional, (T+1) x N, FP64): linear state terms q_t of the LQR stage costs, as the
+// adjoint LQR has them; they enter as eta_t -= q_t (so s_t += q_t).  The Newton step's
+// LQR has none (its state gradient is carried by the co-states).
 template <class M, class L, class SV, class Grp>
-__device__ bool value_pass(Grp& g, Inst<M, L>& I, double alpha) {
+__device__ bool value_pass(Grp& g, Inst<M, L>& I, double alpha, const double* qx = nullptr) {
   constexpr int N = M::NX, U = M::NU;
   bool ok = true, have = false;
   Val<N, L> agg;
   set_identity(agg);
   if (I.last) {
     value_terminal<N, L>(I.Pm + (size_t)I.T * N * N, agg);
+    if (qx) {
+#pragma unroll
+      for (int i = 0; i < N; i++) agg.eta[i] = L(-qx[(size_t)I.T * N + i]);
+    }
     have = true;
   }
   for (int t = I.b - 1; t >= I.a; t--) {
@@ -684,6 +695,10 @@ __device__ bool value_pass(Grp& g, Inst<M, L>& I, double alpha) {
     load_F<N>(I.E + (size_t)t * N * N, F);
     ok &= value_init_sel<N, U, L, SV>(F, I.Gm + (size_t)t * N * U, I.Pm + (size_t)t * N * N,
                                       I.Mm + (size_t)t * N * U, I.Rm + (size_t)t * U * U, I.d + (size_t)t * U, alpha, e);
+    if (qx) {
+#pragma unroll
+      for (int i = 0; i < N; i++) e.eta[i] -= L(qx[(size_t)t * N + i]);
+    }
     if (!have) { agg = e; have = true; }
     else ok &= ValueOpSel<SV>()(e, agg, agg);
   }
@@ -693,7 +708,7 @@ __device__ bool value_pass(Grp& g, Inst<M, L>& I, double alpha) {
 #pragma unroll (N <= 8 ? N * N : 4)
     for (int i = 0; i < N * N; i++) S[i] = I.Pm[(size_t)I.T * N * N + i];
 #pragma unroll
-    for (int i = 0; i < N; i++) s[i] = L(0);
+    for (int i = 0; i < N; i++) s[i] = qx ? L(qx[(size_t)I.T * N + i]) : L(0);
   } else {
     // S_t = J_{t,<|}, s_t = -eta_{t,<|}
 #pragma unroll (N <= 8 ? N * N : 4)
@@ -707,6 +722,10 @@ __device__ bool value_pass(Grp& g, Inst<M, L>& I, double alpha) {
     ok &= riccati_step_sel<N, U, L, SV>(F, I.Gm + (size_t)t * N * U, I.Pm + (size_t)t * N * N,
                                         I.Mm + (size_t)t * N * U, I.Rm + (size_t)t * U * U, I.d + (size_t)t * U, alpha,
                                         S, s, Gam, gam);
+    if (qx) {
+#pragma unroll
+      for (int i = 0; i < N; i++) s[i] += L(qx[(size_t)t * N + i]);
+    }
 #pragma unroll
     for (int i = 0; i < U * N; i++) I.Gam[(size_t)t * U * N + i] = Gam[i];
 #pragma unroll
@@ -1216,6 +1235,248 @@ __device__ void initial_rollout(Grp& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>
 }
 
 // ---------------------------------------------------------------------------
+// Adjoint at a solution (x*, u*) of the barrier problem with weight mu, for the loss
+//   L = gJ J* + <gx, x*> + <gu, u*>   (J* = optimal barrier objective).
+// J* part: envelope theorem on the Lagrangian eq. ocp-lagrangian, dJ*/dx0 = lam_1 and
+// dJ*/dtheta = dL_c/dtheta at (x*, u*, lam*).  x*, u* part: implicit function theorem on
+// the KKT system.  The adjoint LQR  min 1/2 w^T H w - g^T w  s.t. the linearised dynamics
+// and w_{x,1} = 0 (H the Newton-step Hessian with alpha = 0, g = (gx, gu)) is solved by
+// the value and state scans of the Newton step; its multipliers
+//   nu_T = q_T + P_T w_T,  nu_t = q_t + P_t w_t + M_t w_{u,t} + F_t^T nu_{t+1},  q = -gx,
+// come from a co-state-type scan; then dL/dtheta -= w^T d_theta(grad_z L) + nu^T d_theta f.
+// Outputs (per instance): g_x0 (N), g_Qd (N), g_Rd (U), g_Qfd (N), g_prm (PTN_MAXP).
+struct AdjArgs {
+  const double *gx, *gu;  // (sum T+1) x N, (sum T) x U, or NULL
+  double* qx;             // workspace (sum T+1) x N (the linear terms -gx)
+  double mu, gJ;
+  double *g_x0, *g_Qd, *g_Rd, *g_Qfd, *g_prm;  // may be NULL
+};
+
+template <int K, class Grp>
+__device__ void group_sum(Grp& g, double* v) {
+#pragma unroll 1
+  for (int c = 0; c < K; c += 8) {
+    double r[8];
+#pragma unroll
+    for (int i = 0; i < 8; i++) r[i] = (c + i < K) ? v[c + i] : 0.0;
+    g.template reduce<8>(r, 0u);
+#pragma unroll
+    for (int i = 0; i < 8; i++)
+      if (c + i < K) v[c + i] = r[i];
+  }
+}
+
+// nu scan and the parameter contractions, in FP64 (the adjoint runs with L = double in
+// every precision mode: at a solution the reduced Hessian is ill-conditioned near active
+// bounds, where the barrier curvature is large, and an FP32 adjoint LQR is not accurate
+// enough there even with iterative refinement).
+template <class M, class L, class Grp>
+__device__ void adjoint_nu_pass(Grp& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>& P, const double* qx,
+                                double* envp, double* adjp, double* nu0) {
+  static_assert(std::is_same<L, double>::value, "the adjoint runs in FP64");
+  constexpr int N = M::NX, U = M::NU, NP = M::NP;
+  // c_t = q_t + P_t w_t + M_t w_{u,t}
+  auto cterm = [&](int t, double* c) {
+    const double* Pt = I.Pm + (size_t)t * N * N;
+    const double* w = I.dx + (size_t)t * N;
+#pragma unroll
+    for (int i = 0; i < N; i++) {
+      double v = qx[(size_t)t * N + i];
+#pragma unroll
+      for (int j = 0; j < N; j++) v += Pt[i * N + j] * w[j];
+      if (t < I.T) {
+        const double* Mt = I.Mm + (size_t)t * N * U;
+        const double* wu = I.du + (size_t)t * U;
+#pragma unroll
+        for (int j = 0; j < U; j++) v += Mt[i * U + j] * wu[j];
+      }
+      c[i] = v;
+    }
+  };
+  Aff<N, double> agg;
+  set_identity(agg);
+  double nuT[N];
+  if (I.last) {
+    cterm(I.T, nuT);
+#pragma unroll
+    for (int i = 0; i < N; i++) {
+      agg.v[i] = nuT[i];
+#pragma unroll
+      for (int j = 0; j < N; j++) agg.M[i * N + j] = 0.0;
+    }
+  }
+  for (int t = I.b - 1; t >= I.a; t--) {
+    const double* E = I.F64 + (size_t)t * N * N;
+    double c[N], vn[N];
+    cterm(t, c);
+    mtv<N, N>(E, agg.v, vn);
+#pragma unroll
+    for (int i = 0; i < N; i++) agg.v[i] += vn[i] + c[i];
+    if (!I.last) {
+      double Mn[N * N];
+      mtm<N, N, N>(E, agg.M, Mn);
+#pragma unroll (N <= 8 ? N * N : 4)
+      for (int i = 0; i < N * N; i++) agg.M[i] += Mn[i];
+    }
+  }
+  bool ok = true;
+  Aff<N, double> inc = g.scan(agg, CostateOp(), true, ok);
+  double nu[N];
+#pragma unroll
+  for (int i = 0; i < N; i++) nu[i] = I.last ? nuT[i] : inc.v[i];
+  for (int t = I.b - 1; t >= I.a; t--) {
+    const double* x = I.xn + (size_t)t * N;
+    const double* u = I.un + (size_t)t * U;
+    const double* lam1 = (t + 1 == I.b) ? I.lamb : I.lam + (size_t)(t + 1) * N;
+    const double* w = I.dx + (size_t)t * N;
+    const double* wu = I.du + (size_t)t * U;
+    double fp[N * NP], Hzp[(N + U) * NP];
+    step_param_derivs<M>(P.integ, P.dt, P.prm, x, u, lam1, fp, Hzp);
+#pragma unroll
+    for (int k = 0; k < NP; k++) {
+      double e = 0.0, a = 0.0;
+#pragma unroll
+      for (int i = 0; i < N; i++) {
+        e += lam1[i] * fp[i * NP + k];
+        a += nu[i] * fp[i * NP + k] + w[i] * Hzp[i * NP + k];
+      }
+#pragma unroll
+      for (int j = 0; j < U; j++) a += wu[j] * Hzp[(N + j) * NP + k];
+      envp[k] += e;
+      if (adjp) adjp[k] += a;
+    }
+    const double* E = I.F64 + (size_t)t * N * N;
+    double c[N], vn[N];
+    cterm(t, c);
+    mtv<N, N>(E, nu, vn);
+#pragma unroll
+    for (int i = 0; i < N; i++) nu[i] += vn[i] + c[i];
+  }
+  if (I.a == 0 && I.b > 0) {
+#pragma unroll
+    for (int i = 0; i < N; i++) nu0[i] = nu[i];
+  }
+}
+
+// envelope-only parameter term (no trajectory gradients)
+template <class M, class L>
+__device__ void adjoint_env_params(Inst<M, L>& I, const ProbS<M::NX, M::NU>& P, double* envp) {
+  constexpr int N = M::NX, U = M::NU, NP = M::NP;
+  for (int t = I.a; t < I.b; t++) {
+    const double* lam1 = (t + 1 == I.b) ? I.lamb : I.lam + (size_t)(t + 1) * N;
+    double fp[N * NP], Hzp[(N + U) * NP];
+    step_param_derivs<M>(P.integ, P.dt, P.prm, I.xn + (size_t)t * N, I.un + (size_t)t * U, lam1, fp, Hzp);
+#pragma unroll
+    for (int k = 0; k < NP; k++) {
+      double e = 0.0;
+#pragma unroll
+      for (int i = 0; i < N; i++) e += lam1[i] * fp[i * NP + k];
+      envp[k] += e;
+    }
+  }
+}
+
+// returns ST_OK, or ST_ENUM when the Hessian is not positive definite on the dynamics
+template <class M, class L, class SV, class Grp>
+__device__ int adjoint_instance(Grp& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>& P, const AdjArgs& aa,
+                                const InstDev& id, int bi) {
+  constexpr int N = M::NX, U = M::NU, NP = M::NP;
+  Aug A;
+  A.kind = AUG_BARRIER; A.mu = aa.mu; A.rho = 1.0; A.z = nullptr; A.v = nullptr;
+  costate_exact(g, I, P, A);
+  const bool lin = aa.gx || aa.gu;
+  // out = [x0 (N), Qd (N), Rd (U), Qfd (N), prm (NP)] accumulated per thread
+  constexpr int KO = 3 * N + U + NP;
+  double env[KO], adj[KO];
+#pragma unroll
+  for (int i = 0; i < KO; i++) { env[i] = 0.0; adj[i] = 0.0; }
+  for (int t = I.a; t < I.b; t++) {
+#pragma unroll
+    for (int i = 0; i < N; i++) {
+      const double e = I.xn[(size_t)t * N + i] - P.xref[i];
+      env[N + i] += e * e;
+    }
+#pragma unroll
+    for (int i = 0; i < U; i++) {
+      const double e = I.un[(size_t)t * U + i] - P.uref[i];
+      env[2 * N + i] += e * e;
+    }
+  }
+  if (I.last) {
+#pragma unroll
+    for (int i = 0; i < N; i++) {
+      const double e = I.xn[(size_t)I.T * N + i] - P.xref[i];
+      env[2 * N + U + i] = e * e;
+    }
+  }
+  int rc = ST_OK;
+  if (!lin) {
+    adjoint_env_params(I, P, env + 3 * N + U);
+  } else {
+    quadratize(g, I, P, A);
+    // linear terms of the adjoint LQR: d_t = -gu_t, q_t = -gx_t
+    double* qx = aa.qx + (size_t)id.xoff * N;
+    for (int t = I.a; t < I.b; t++) {
+#pragma unroll
+      for (int i = 0; i < U; i++) I.d[(size_t)t * U + i] = aa.gu ? -aa.gu[((size_t)id.uoff + t) * U + i] : 0.0;
+#pragma unroll
+      for (int i = 0; i < N; i++) qx[(size_t)t * N + i] = aa.gx ? -aa.gx[((size_t)id.xoff + t) * N + i] : 0.0;
+    }
+    if (I.last) {
+#pragma unroll
+      for (int i = 0; i < N; i++) qx[(size_t)I.T * N + i] = aa.gx ? -aa.gx[((size_t)id.xoff + I.T) * N + i] : 0.0;
+    }
+    // the value pass reads q of its own chunk and the terminal one, written by the same
+    // thread, and its first group operation orders the rest
+    if (!value_pass<M, L, SV>(g, I, 0.0, qx)) {
+      rc = ST_ENUM;
+    } else {
+      double G1, G2;
+      state_pass(g, I, G1, G2);  // dx = w_x, du = w_u
+      double nu0[N];
+#pragma unroll
+      for (int i = 0; i < N; i++) nu0[i] = 0.0;
+      adjoint_nu_pass(g, I, P, qx, env + 3 * N + U, adj + 3 * N + U, nu0);
+#pragma unroll
+      for (int i = 0; i < N; i++) adj[i] = nu0[i];
+      for (int t = I.a; t < I.b; t++) {
+#pragma unroll
+        for (int i = 0; i < N; i++)
+          adj[N + i] += double(I.dx[(size_t)t * N + i]) * 2.0 * (I.xn[(size_t)t * N + i] - P.xref[i]);
+#pragma unroll
+        for (int i = 0; i < U; i++)
+          adj[2 * N + i] += double(I.du[(size_t)t * U + i]) * 2.0 * (I.un[(size_t)t * U + i] - P.uref[i]);
+      }
+      if (I.last) {
+#pragma unroll
+        for (int i = 0; i < N; i++)
+          adj[2 * N + U + i] =
+              double(I.dx[(size_t)I.T * N + i]) * 2.0 * (I.xn[(size_t)I.T * N + i] - P.xref[i]);
+      }
+    }
+  }
+  double out[KO];
+#pragma unroll
+  for (int i = 0; i < KO; i++) out[i] = aa.gJ * env[i] - adj[i];
+  group_sum<KO>(g, out);  // also orders the co-state writes before lam_1 is read
+  if (g.rank() == 0) {
+#pragma unroll
+    for (int i = 0; i < N; i++) out[i] += aa.gJ * I.lam[i];
+    if (aa.g_x0)
+      for (int i = 0; i < N; i++) aa.g_x0[(size_t)bi * N + i] = out[i];
+    if (aa.g_Qd)
+      for (int i = 0; i < N; i++) aa.g_Qd[(size_t)bi * N + i] = out[N + i];
+    if (aa.g_Rd)
+      for (int i = 0; i < U; i++) aa.g_Rd[(size_t)bi * U + i] = out[2 * N + i];
+    if (aa.g_Qfd)
+      for (int i = 0; i < N; i++) aa.g_Qfd[(size_t)bi * N + i] = out[2 * N + U + i];
+    if (aa.g_prm)
+      for (int k = 0; k < PTN_MAXP; k++) aa.g_prm[(size_t)bi * PTN_MAXP + k] = k < NP ? out[3 * N + U + k] : 0.0;
+  }
+  return rc;
+}
+
+// ---------------------------------------------------------------------------
 // the whole solve of one instance (IP when O.method == 0, ADMM when 1)
 template <class M, class L, class SV, class Grp>
 __device__ void solve_instance(Grp& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>& P, const OptDev& O,
@@ -1358,7 +1619,7 @@ __global__ void __launch_bounds__(256) k_solve_cta(KArgs args, Work<L> w) {
   char* scratch = smem + ((sizeof(ProbS<N, U>) + 15) & ~size_t(15));
   const int bi = blockIdx.x;
   if (bi >= args.B) return;
-  load_prob<N, U>(P, *args.prob, args.xref ? args.xref + (size_t)bi * N : nullptr);
+  load_prob<N, U>(P, *args.prob, args.xref ? args.xref + (size_t)bi * N : nullptr, args.inst[bi].dt);
   const OptDev O = *args.opt;
   const InstDev id = args.inst[bi];
   CtaGroup g{scratch};
@@ -1376,13 +1637,31 @@ __global__ void __launch_bounds__(128) k_solve_grid(KArgs args, Work<L> w) {
   char* scratch = smem + ((sizeof(ProbS<N, U>) + 15) & ~size_t(15));
   __shared__ int sdead;
   if (threadIdx.x == 0) sdead = 0;
-  load_prob<N, U>(P, *args.prob, args.xref);
+  load_prob<N, U>(P, *args.prob, args.xref, args.inst[0].dt);
   const OptDev O = *args.opt;
   const InstDev id = args.inst[0];
   GridGroup g{scratch, args.gs, 0, &sdead};
   Inst<M, L> I;
   I.setup(w, id, args.x0, g.rank(), g.size(), P.nw);
   solve_instance<M, L, SV>(g, I, P, O, args.u_init, args.info);
+}
+
+// adjoint, one CTA per instance
+template <class M, class L, class SV>
+__global__ void __launch_bounds__(256) k_adjoint_cta(KArgs args, Work<L> w, AdjArgs aa) {
+  constexpr int N = M::NX, U = M::NU;
+  extern __shared__ __align__(16) char smem[];
+  ProbS<N, U>& P = *reinterpret_cast<ProbS<N, U>*>(smem);
+  char* scratch = smem + ((sizeof(ProbS<N, U>) + 15) & ~size_t(15));
+  const int bi = blockIdx.x;
+  if (bi >= args.B) return;
+  load_prob<N, U>(P, *args.prob, args.xref ? args.xref + (size_t)bi * N : nullptr, args.inst[bi].dt);
+  const InstDev id = args.inst[bi];
+  CtaGroup g{scratch};
+  Inst<M, L> I;
+  I.setup(w, id, args.x0 + (size_t)bi * N, threadIdx.x, blockDim.x, P.nw);
+  const int rc = adjoint_instance<M, L, SV>(g, I, P, aa, id, bi);
+  if (threadIdx.x == 0) args.info[bi].status = rc;
 }
 
 // one thread-block cluster on one instance (medium horizons)
@@ -1396,7 +1675,7 @@ __global__ void __launch_bounds__(256) k_solve_cluster(KArgs args, Work<L> w) {
   const size_t sbytes = scratch_bytes<N, U, L>(nwarps);
   constexpr int XB = (int)((sizeof(Val<N, double>) > 64 ? sizeof(Val<N, double>) : 64) + 15) / 16 * 16;
   char* xch = scratch + ((sbytes + 15) & ~size_t(15));
-  load_prob<N, U>(P, *args.prob, args.xref);
+  load_prob<N, U>(P, *args.prob, args.xref, args.inst[0].dt);
   const OptDev O = *args.opt;
   const InstDev id = args.inst[0];
   ClusterGroup g{scratch, xch, XB, 0};

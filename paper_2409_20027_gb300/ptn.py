@@ -85,7 +85,8 @@ def load(path: str = LIB_PATH):
         lib.ptn_set_options.argtypes = [vp, C.POINTER(Options)]
         lib.ptn_solve_ip.argtypes = [vp, vp, vp, C.c_int, vp, vp, vp, C.POINTER(Info), vp]
         lib.ptn_solve_admm.argtypes = [vp, vp, vp, C.c_int, vp, vp, vp, vp, vp, C.POINTER(Info), vp]
-        lib.ptn_solve_batch.argtypes = [vp, C.c_int, C.c_int, ip, vp, vp, vp, vp, vp, vp, C.POINTER(Info), vp]
+        lib.ptn_solve_batch.argtypes = [vp, C.c_int, C.c_int, ip, C.POINTER(C.c_double), vp, vp, vp, vp, vp, vp,
+                                         C.POINTER(Info), vp]
         lib.ptn_adjoint.argtypes = [vp, C.c_int, ip, vp, vp, vp, vp, C.c_double, C.c_double, vp, vp, vp, vp,
                                     vp, vp, vp, vp]
         lib.ptn_num_rows.argtypes = [vp]
@@ -210,17 +211,22 @@ class Solver:
         return x, u, lam, info.as_dict()
 
     def solve_batch(self, x0, T_b, xref=None, u_init=None, method: int = METHOD_IP, x_out=None, u_out=None,
-                    lam_out=None, stream=None):
-        """B instances in one launch.  x0: (B, nx) CUDA tensor, T_b: int sequence.
+                    lam_out=None, stream=None, dt_b=None):
+        """B instances in one launch.  x0: (B, nx) CUDA tensor, T_b: int sequence, dt_b:
+        optional per-instance time steps (stage weights scaled by dt_b / prob.dt).
         Returns (x, u, lam, infos) with concatenated trajectories."""
         Tb = np.ascontiguousarray(np.asarray(T_b, dtype=np.int32))
         B = len(Tb)
+        dtb = None if dt_b is None else np.ascontiguousarray(np.asarray(dt_b, dtype=np.float64))
+        if dtb is not None and dtb.shape != (B,):
+            raise ValueError("dt_b must have one entry per instance")
         S = int(Tb.sum())
         x_out = self._out(S + B, self.nx, x0) if x_out is None else x_out
         u_out = self._out(S, self.nu, x0) if u_out is None else u_out
         lam_out = self._out(S + B, self.nx, x0) if lam_out is None else lam_out
         infos = (Info * B)()
-        load().ptn_solve_batch(self._h, int(method), B, Tb.ctypes.data_as(C.POINTER(C.c_int)), _dptr(x0),
+        load().ptn_solve_batch(self._h, int(method), B, Tb.ctypes.data_as(C.POINTER(C.c_int)),
+                               None if dtb is None else dtb.ctypes.data_as(C.POINTER(C.c_double)), _dptr(x0),
                                _dptr(xref), _dptr(u_init), _dptr(x_out), _dptr(u_out), _dptr(lam_out), infos,
                                _stream(stream))
         return x_out, u_out, lam_out, [i.as_dict() for i in infos]
@@ -287,3 +293,74 @@ def solve_ip_static(prob, x0, T: int, u_init=None, x_out=None, u_out=None, lam_o
     if rc in (PTN_ERR_INVALID_ARG, PTN_ERR_CUDA):
         raise PtnError(f"ptn_solve_ip_static failed ({rc}): {err.value.decode()}")
     return x_out, u_out, lam_out, info.as_dict()
+
+
+def theta_of(prob):
+    """Parameter vector [diag Q, diag R, diag Qf, prm (8)] of a problem, as the adjoint
+    orders its gradients."""
+    prm = np.zeros(8)
+    prm[:len(prob.prm)] = prob.prm
+    return np.concatenate([np.diag(np.asarray(prob.Q, dtype=np.float64)),
+                           np.diag(np.asarray(prob.R, dtype=np.float64).reshape(prob.nu, prob.nu)),
+                           np.diag(np.asarray(prob.Qf, dtype=np.float64)), prm])
+
+
+def _solve_ip_function():
+    import torch
+
+    class SolveIP(torch.autograd.Function):
+        """Batched IP solve with gradients from ptn_adjoint (Sec. II-B solution, KKT adjoint).
+
+        forward(x0 (B, nx), theta, solver, T_b, xref) -> (x*, u*, J*): concatenated
+        trajectories as in solve_batch and J* (B,), the barrier objective at mu_final.
+        theta must equal theta_of(solver.prob) (the solver's own parameters); it is an
+        input only so that autograd can route d loss / d theta to it."""
+
+        @staticmethod
+        def forward(ctx, x0, theta, solver, T_b, xref):
+            x, u, _, infos = solver.solve_batch(x0.detach().contiguous(), T_b, xref=xref)
+            bad = [(i, f["status"]) for i, f in enumerate(infos) if f["status"] != 0]
+            if bad:
+                raise PtnError(f"solve failed for instances {bad}: {solver.last_error()}")
+            J = torch.tensor([f["J_c"] for f in infos], dtype=torch.float64, device=x0.device)
+            ctx.solver, ctx.T_b, ctx.xref, ctx.mu = solver, list(T_b), xref, infos[0]["mu"]
+            ctx.save_for_backward(x0.detach(), x, u)
+            return x, u, J
+
+        @staticmethod
+        def backward(ctx, gx, gu, gJ):
+            x0, x, u = ctx.saved_tensors
+            s = ctx.solver
+            B = len(ctx.T_b)
+            # the adjoint is linear in (gJ, gx, gu): one call for the trajectory part and,
+            # since gJ differs per instance, one envelope call with gJ = 1 scaled per row
+            lin = s.adjoint(ctx.T_b, x0, x, u, ctx.mu, 0.0,
+                            None if gx is None else gx.contiguous(), None if gu is None else gu.contiguous(),
+                            xref=ctx.xref) if (gx is not None or gu is not None) else None
+            env = s.adjoint(ctx.T_b, x0, x, u, ctx.mu, 1.0, xref=ctx.xref) if gJ is not None else None
+            tot = {}
+            for k in ["x0", "Qd", "Rd", "Qfd", "prm"]:
+                v = torch.zeros_like((lin or env)[k])
+                if lin is not None:
+                    v = v + lin[k]
+                if env is not None:
+                    v = v + gJ.reshape(B, 1) * env[k]
+                tot[k] = v
+            g_theta = torch.cat([tot["Qd"], tot["Rd"], tot["Qfd"], tot["prm"]], dim=1).sum(0)
+            return tot["x0"], g_theta, None, None, None
+
+    return SolveIP
+
+
+_SOLVE_IP = None
+
+
+def solve_ip_autograd(solver, x0, T_b, theta=None, xref=None):
+    """Differentiable batched IP solve: (x*, u*, J*) with gradients to x0 and theta."""
+    global _SOLVE_IP
+    import torch
+    if _SOLVE_IP is None:
+        _SOLVE_IP = _solve_ip_function()
+    if theta is None:
+        theta = torch.tensor(theta_of(solver.prob), dtype=torch.float64, device=x0.device)
+    return _SOLVE_IP.apply(x0, theta, solver, T_b, xref)

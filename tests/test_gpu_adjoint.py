@@ -1,0 +1,100 @@
+"""Adjoint (gradients of a loss of the solution w.r.t. x0, diag Q, diag R, diag Qf and the
+model constants) on the GPU against the oracle's adjoint at the same solution, and the
+autograd wrapper built on it."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2409_20027_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ptn():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    from paper_2409_20027_gb300 import ptn as m
+    m.load()
+    return m
+
+
+def dev(a):
+    return torch.tensor(np.asarray(a, dtype=np.float64), device="cuda:0")
+
+
+def rel(a, b):
+    a, b = np.asarray(a, dtype=np.float64), np.asarray(b, dtype=np.float64)
+    return float(np.abs(a - b).max() / max(1.0, np.abs(b).max()))
+
+
+KEYS = ["x0", "Qd", "Rd", "Qfd", "prm"]
+
+CASES = [
+    # name, problem, x0 list, T_b, solve precision, tolerance (the adjoint itself runs in
+    # FP64 in every mode, so both compare at the FP64 tolerance)
+    ("pendulum_fp64", W.pendulum, [W.pendulum_x0(0), W.pendulum_x0(1)], [64, 40], 0, 1e-6),
+    ("cartpole_fp32", lambda: W.cartpole(T=256, horizon=2.56), [W.cartpole_x0(0), W.cartpole_x0(2)], [256, 256], 1,
+     1e-6),
+]
+
+
+def solve(ptn, p, x0s, Tb, prec):
+    s = ptn.Solver(p, max_T=max(Tb), max_batch=len(Tb), precision=prec, block_threads=64)
+    x0 = dev(np.stack(x0s))
+    x, u, lam, infos = s.solve_batch(x0, Tb)
+    assert all(i["status"] == 0 for i in infos)
+    return s, x0, x, u, infos
+
+
+@pytest.mark.parametrize("name,mk,x0s,Tb,prec,tol", CASES, ids=[c[0] for c in CASES])
+@pytest.mark.parametrize("with_traj", [False, True], ids=["J_only", "J_and_traj"])
+def test_adjoint_matches_oracle(ptn, name, mk, x0s, Tb, prec, tol, with_traj):
+    p = mk()
+    s, x0, x, u, infos = solve(ptn, p, x0s, Tb, prec)
+    mu = infos[0]["mu"]
+    rng = np.random.default_rng(11)
+    S = sum(Tb)
+    gx = rng.standard_normal((S + len(Tb), p.nx)) if with_traj else None
+    gu = rng.standard_normal((S, p.nu)) if with_traj else None
+    gJ = 0.7
+    out = s.adjoint(Tb, x0, x, u, mu, gJ, None if gx is None else dev(gx), None if gu is None else dev(gu))
+    xs, us = x.cpu().numpy(), u.cpu().numpy()
+    xo = uo = 0
+    for b, T in enumerate(Tb):
+        ref = O.adjoint(p, mu, xs[xo:xo + T + 1], us[uo:uo + T], gJ,
+                        None if gx is None else gx[xo:xo + T + 1], None if gu is None else gu[uo:uo + T])
+        assert ref["status"] == 0
+        for k in KEYS:
+            got = out[k][b].cpu().numpy()
+            assert rel(got, ref[k]) <= tol, (b, k, got, ref[k])
+        xo += T + 1
+        uo += T
+
+
+def test_autograd_wrapper(ptn):
+    p = W.pendulum()
+    Tb = [48, 64]
+    s = ptn.Solver(p, max_T=64, max_batch=2, precision=0, block_threads=64)
+    x0 = dev(np.stack([W.pendulum_x0(2), W.pendulum_x0(3)])).requires_grad_(True)
+    theta = dev(ptn.theta_of(p)).requires_grad_(True)
+    x, u, J = ptn.solve_ip_autograd(s, x0, Tb, theta)
+    rng = np.random.default_rng(5)
+    cx = dev(rng.standard_normal(tuple(x.shape)))
+    cu = dev(rng.standard_normal(tuple(u.shape)))
+    wJ = dev([0.3, 1.7])
+    loss = (wJ * J).sum() + (cx * x).sum() + (cu * u).sum()
+    loss.backward()
+    xs, us = x.detach().cpu().numpy(), u.detach().cpu().numpy()
+    mu = 1e-6
+    gth = np.zeros_like(ptn.theta_of(p))
+    xo = uo = 0
+    for b, T in enumerate(Tb):
+        ref = O.adjoint(p, mu, xs[xo:xo + T + 1], us[uo:uo + T], float(wJ[b]),
+                        cx[xo:xo + T + 1].cpu().numpy(), cu[uo:uo + T].cpu().numpy())
+        assert rel(x0.grad[b].cpu().numpy(), ref["x0"]) <= 1e-6
+        gth += np.concatenate([ref["Qd"], ref["Rd"], ref["Qfd"], ref["prm"]])
+        xo += T + 1
+        uo += T
+    assert rel(theta.grad.cpu().numpy(), gth) <= 1e-6

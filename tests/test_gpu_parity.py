@@ -152,6 +152,24 @@ def test_batch_ragged_matches_individual_oracle_solves(ptn):
         uo += T
 
 
+def test_batch_per_instance_time_steps_match_fixed_horizon_oracle(ptn):
+    # the same 1.28 s horizon sampled at each instance's own rate (Sec. IV protocol)
+    base = W.cartpole()
+    Tb = np.array([64, 90, 128, 200, 75], dtype=np.int32)
+    B = len(Tb)
+    x0s = W.cartpole_batch_x0(B, 5)
+    dtb = 1.28 / Tb
+    s = ptn.Solver(base, max_T=int(Tb.max()), max_batch=B, precision=ptn.PTN_FP64, block_threads=64)
+    X, U, Lm, infos = s.solve_batch(dev(x0s), Tb, dt_b=dtb)
+    xo = uo = 0
+    for b in range(B):
+        T = int(Tb[b])
+        ref = O.solve_ip(W.cartpole(T=T, horizon=1.28), x0s[b], T)
+        check_solution(infos[b], ref, X[xo:xo + T + 1], U[uo:uo + T], Lm[xo:xo + T + 1], FP64_TOL)
+        xo += T + 1
+        uo += T
+
+
 def test_batch_per_instance_targets(ptn):
     # per-instance xref (the waypoint mechanism) on the pendulum
     p = W.pendulum()
@@ -225,8 +243,13 @@ def test_invalid_arguments_are_rejected(ptn):
     assert lib.ptn_solve_ip(*args(9)) == -1          # beyond the workspace (8 steps)
     assert "exceeds" in s.last_error()
     Tb = (C.c_int * 2)(1, 1)
-    assert lib.ptn_solve_batch(s._h, 0, 2, Tb, C.c_void_p(x0.data_ptr()), None, None, C.c_void_p(xo.data_ptr()),
-                               C.c_void_p(uo.data_ptr()), None, None, None) == -1   # B > max_batch
+    assert lib.ptn_solve_batch(s._h, 0, 2, Tb, None, C.c_void_p(x0.data_ptr()), None, None,
+                               C.c_void_p(xo.data_ptr()), C.c_void_p(uo.data_ptr()), None, None, None) == -1  # B > max_batch
+    Tb1 = (C.c_int * 1)(4)
+    dtb = (C.c_double * 1)(-0.01)
+    assert lib.ptn_solve_batch(s._h, 0, 1, Tb1, dtb, C.c_void_p(x0.data_ptr()), None, None,
+                               C.c_void_p(xo.data_ptr()), C.c_void_p(uo.data_ptr()), None, None, None) == -1  # dt < 0
+    assert "dt_b" in s.last_error()
     assert lib.ptn_solve_ip(s._h, None, None, 4, C.c_void_p(xo.data_ptr()), C.c_void_p(uo.data_ptr()), None,
                             C.byref(info), None) == -1   # missing x0
     assert float(xo.abs().max()) == 0.0 and float(uo.abs().max()) == 0.0   # nothing ran
