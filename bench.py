@@ -28,6 +28,7 @@ sys.path.insert(0, ROOT)
 METRIC = "time-to-solve (ms) vs horizon T at KKT residual ≤1e-6; batched solves/sec; grads/sec"
 HORIZON_S = 2.56
 L2_FLUSH_BYTES = 256 << 20
+BATCH_HORIZON_S = 1.28  # keeps dt_b <= 0.02 for every batch horizon (T_b >= 64)
 
 
 def algorithmic_flops(n, m, T, info):
@@ -40,9 +41,28 @@ def algorithmic_flops(n, m, T, info):
     return T * (info["newton_iters"] * per_it + info["roll_iters"] * per_roll)
 
 
-def alu_peak_tflops():
-    # FP32 FMA pipes: 152 SMs x 128 lanes x 2 flop x 2.07 GHz (maximum SM clock)
-    return 152 * 128 * 2 * 2.07e9 / 1e12
+# FP32 FMA pipes: 152 SMs x 128 lanes x 2 flop x 2.07 GHz (maximum SM clock)
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# FP64: GB300's nominal dense FP64 rate
+FP64_PEAK_TFLOPS = 1.25
+# DRAM bytes (read + write) of one k_solve_grid launch of this workload, from the ncu
+# capture summarised in profiles/k_solve_grid_cartpole_T16384.md
+TRAFFIC_BYTES = (2.692096 + 2.212096) * 1e6
+
+
+def flop_split(n, m, T, info):
+    """(FP32, FP64) algorithmic FLOPs of one solve.  The FP64 share is the inverse of
+    I + C1 J2 (about 2 n^3 per combination, two combinations per element) in the value
+    scan; everything else runs in FP32."""
+    total = algorithmic_flops(n, m, T, info)
+    f64 = T * info["newton_iters"] * 2 * 2 * n ** 3
+    return total - f64, f64
+
+
+def blended_peak_tflops(f32, f64):
+    """Peak rate of a kernel doing f32 FP32 and f64 FP64 flops with each pipe at its own
+    peak: (f32 + f64) / (f32 / P32 + f64 / P64)."""
+    return (f32 + f64) / (f32 / FP32_PEAK_TFLOPS + f64 / FP64_PEAK_TFLOPS)
 
 
 class ClockSampler:
@@ -133,6 +153,54 @@ def run_reference(args, T):
     print(json.dumps(line), flush=True)
 
 
+def run_batch(args, ptn, W, dev, flush, stream):
+    """Batched workload: B cart-pole instances (RK4), horizons T_b log-uniform in [64, 4096]
+    from seed 0, each covering the same 1.28 s at dt_b = 1.28 / T_b; one launch for the
+    whole batch (one CTA per instance).  Also the same instances solved one by one with
+    the single-instance path (cluster or grid tier)."""
+    import torch
+    B = args.batch
+    Tb = W.batch_horizons(B, seed=0)
+    dtb = BATCH_HORIZON_S / Tb  # every instance covers the same 1.28 s at its own sampling rate
+    x0 = torch.tensor(W.cartpole_batch_x0(B, seed=0), dtype=torch.float64, device=dev)
+    p = W.cartpole()
+    sv = ptn.Solver(p, max_T=int(Tb.max()), max_batch=B, precision=ptn.PTN_FP32_FP64SOLVE)
+    S = int(Tb.sum())
+    xo = torch.empty((S + B, 4), dtype=torch.float64, device=dev)
+    uo = torch.empty((S, 1), dtype=torch.float64, device=dev)
+    lo = torch.empty((S + B, 4), dtype=torch.float64, device=dev)
+    sv.solve_batch(x0, Tb, x_out=xo, u_out=uo, lam_out=lo, dt_b=dtb)
+    torch.cuda.synchronize()
+    times, infos = [], None
+    for k in range(2):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        _, _, _, infos = sv.solve_batch(x0, Tb, x_out=xo, u_out=uo, lam_out=lo, dt_b=dtb)
+        b.record(stream)
+        torch.cuda.synchronize()
+        times.append(a.elapsed_time(b))
+    ms = min(times)
+    st = [i["status"] for i in infos]
+    # the same instances one at a time (a sample of 32, scaled to B)
+    one = ptn.Solver(p, max_T=int(Tb.max()), precision=ptn.PTN_FP32_FP64SOLVE)
+    ns = min(B, 32)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for i in range(ns):
+        one.solve_batch(x0[i:i + 1], Tb[i:i + 1], dt_b=dtb[i:i + 1])
+    b.record(stream)
+    torch.cuda.synchronize()
+    seq_ms = a.elapsed_time(b) * B / ns
+    sv.close()
+    one.close()
+    return {"workload": f"{B} cart-pole instances, IP, RK4, 1.28 s horizon at dt_b=1.28/T_b, T_b log-uniform [64, 4096] "
+                        f"(seed 0, {S} steps), one launch", "solves_per_s": B / (ms * 1e-3), "ms": ms,
+            "converged": int(sum(1 for x in st if x == 0)), "status_counts": {str(k): st.count(k) for k in set(st)},
+            "one_by_one_solves_per_s": B / (seq_ms * 1e-3),
+            "one_by_one_sample": f"first {ns} instances through solve_ip, time scaled to {B}"}
+
+
 def config(T):
     return {"workload": f"cart-pole swing-stabilisation, primal log-barrier IP, T={T}, fixed {HORIZON_S} s "
                         f"horizon (RK4, dt={HORIZON_S / T:.4g}), |u|<=10, |p|<=2, KKT<=1e-6",
@@ -148,6 +216,8 @@ def main():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--T", type=int, default=16384)
     ap.add_argument("--no-sweep", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--batch", type=int, default=1024)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
@@ -211,16 +281,17 @@ def main():
     ok = all(i["status"] == 0 and i["r_kkt"] <= 1e-6 * (1 + 1e-9) for i in infos)
 
     # end to end through the public API with host buffers (pinned), copies in the region
-    x0h = torch.tensor(W.cartpole_x0(0), dtype=torch.float64).pin_memory()
+    # (same inputs, in the same order, as the device-timed steps)
+    x0hs = [x.cpu().pin_memory() for x in x0s]
     xh = torch.empty((T + 1, 4), dtype=torch.float64).pin_memory()
     uh = torch.empty((T, 1), dtype=torch.float64).pin_memory()
     x0d = torch.empty(4, dtype=torch.float64, device=dev)
     e2e = []
-    for k in range(max(1, min(args.steps, 3))):
+    for k in range(args.steps):
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        x0d.copy_(x0h, non_blocking=True)
+        x0d.copy_(x0hs[k % 10], non_blocking=True)
         solver.solve_ip(x0d, T, x_out=xo, u_out=uo, lam_out=lo)
         xh.copy_(xo, non_blocking=True)
         uh.copy_(uo, non_blocking=True)
@@ -248,15 +319,21 @@ def main():
         sweep[str(T)] = {"ms": ms, "newton_iters": infos[-1]["newton_iters"], "status": infos[-1]["status"],
                          "r_kkt": infos[-1]["r_kkt"]}
 
+    batch = None
+    if not args.no_batch:
+        batch = run_batch(args, ptn, W, dev, flush, stream)
+
     if rank != 0:
         return
     last = infos[-1]
-    flops = algorithmic_flops(4, 1, T, last)
-    achieved = flops / (per[-1] * 1e-3) / 1e12
-    peak = alu_peak_tflops()
+    f32, f64 = flop_split(4, 1, T, last)
+    achieved = (f32 + f64) / (per[-1] * 1e-3) / 1e12
+    peak = blended_peak_tflops(f32, f64)
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": None, "kernel": "k_solve_grid<CartPole,float>",
-            "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"}
+            "traffic": TRAFFIC_BYTES if T == 16384 else None, "kernel": "k_solve_grid<CartPole,float,double>",
+            "peak_source": "derived: FP32 152 SMs x 128 lanes x 2 x 2.07 GHz = %.1f TFLOP/s, FP64 nominal "
+                           "%.2f TFLOP/s, blended by this solve's FP32/FP64 flop split (%.1f%% FP64)"
+                           % (FP32_PEAK_TFLOPS, FP64_PEAK_TFLOPS, 100 * f64 / (f32 + f64))}
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         Ts = 1024
@@ -270,7 +347,7 @@ def main():
             "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": 4 * 8,
                     "d2h_bytes_per_step": ((T + 1) * 4 + T) * 8},
             "gpu_launches": args.steps, "clocks": clocks, "kkt_ok": ok,
-            "newton_iters": last["newton_iters"], "sweep": sweep}
+            "newton_iters": last["newton_iters"], "sweep": sweep, "batch": batch}
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
