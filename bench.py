@@ -198,7 +198,48 @@ def run_batch(args, ptn, W, dev, flush, stream):
                         f"(seed 0, {S} steps), one launch", "solves_per_s": B / (ms * 1e-3), "ms": ms,
             "converged": int(sum(1 for x in st if x == 0)), "status_counts": {str(k): st.count(k) for k in set(st)},
             "one_by_one_solves_per_s": B / (seq_ms * 1e-3),
-            "one_by_one_sample": f"first {ns} instances through solve_ip, time scaled to {B}"}
+            "one_by_one_sample": f"first {ns} instances as single solves (cluster or grid tier), time scaled to {B}"}
+
+
+def run_quadrotor(args, ptn, W, dev, flush, stream):
+    """Quadrotor workload: B instances (n = 12, m = 4, Euler dt = 0.01, T = 1024), hover
+    start at the origin, waypoints uniform in the 2 m cube (seed 0), hover thrust as the
+    strictly feasible initial control; one batched IP solve (wide tier), then the adjoint
+    of J* plus a trajectory loss with respect to x0, diag Q, diag R, diag Qf and the model
+    constants (mass, inertia, arm, yaw coefficient, g).  grads/s counts one gradient of
+    every instance per forward + adjoint."""
+    import torch
+    B, T = args.quad_batch, 1024
+    wps = W.quadrotor_waypoints(B, seed=0)
+    xrefs = torch.tensor(np.stack([W.quadrotor(w).xref for w in wps]), dtype=torch.float64, device=dev)
+    Tb = np.full(B, T, dtype=np.int32)
+    sv = ptn.Solver(W.quadrotor(), max_T=T, max_batch=B, precision=ptn.PTN_FP32_FP64SOLVE)
+    x0 = torch.zeros((B, 12), dtype=torch.float64, device=dev)
+    u0 = torch.full((B * T, 4), W.quadrotor_hover_u(), dtype=torch.float64, device=dev)
+    xo = torch.empty((B * (T + 1), 12), dtype=torch.float64, device=dev)
+    uo = torch.empty((B * T, 4), dtype=torch.float64, device=dev)
+    gx = torch.zeros_like(xo)
+    gx[T::T + 1, :3] = 1.0  # d loss / d final position
+    fw, ad = [], []
+    for k in range(2):
+        flush.zero_()
+        a, b, c = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        a.record(stream)
+        _, _, _, infos = sv.solve_batch(x0, Tb, xref=xrefs, u_init=u0, x_out=xo, u_out=uo)
+        b.record(stream)
+        sv.adjoint(Tb, x0, xo, uo, infos[0]["mu"], 1.0, gx, None, xref=xrefs)
+        c.record(stream)
+        torch.cuda.synchronize()
+        fw.append(a.elapsed_time(b))
+        ad.append(b.elapsed_time(c))
+    st = [i["status"] for i in infos]
+    sv.close()
+    f, g = min(fw), min(ad)
+    return {"workload": f"{B} quadrotor instances (n=12, m=4), T={T}, Euler dt=0.01, waypoints in a 2 m cube, "
+                        "IP fp32 LQR with fp64 solves (wide tier); adjoint in fp64",
+            "forward_ms": f, "adjoint_ms": g, "solves_per_s": B / (f * 1e-3), "grads_per_s": B / ((f + g) * 1e-3),
+            "converged": int(sum(1 for x in st if x == 0)), "status_counts": {str(k): st.count(k) for k in set(st)},
+            "newton_iters_mean": float(np.mean([i["newton_iters"] for i in infos]))}
 
 
 def config(T):
@@ -218,6 +259,8 @@ def main():
     ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--batch", type=int, default=1024)
+    ap.add_argument("--no-quad", action="store_true")
+    ap.add_argument("--quad-batch", type=int, default=256)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
@@ -322,6 +365,9 @@ def main():
     batch = None
     if not args.no_batch:
         batch = run_batch(args, ptn, W, dev, flush, stream)
+    quad = None
+    if not args.no_quad:
+        quad = run_quadrotor(args, ptn, W, dev, flush, stream)
 
     if rank != 0:
         return
@@ -347,7 +393,7 @@ def main():
             "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": 4 * 8,
                     "d2h_bytes_per_step": ((T + 1) * 4 + T) * 8},
             "gpu_launches": args.steps, "clocks": clocks, "kkt_ok": ok,
-            "newton_iters": last["newton_iters"], "sweep": sweep, "batch": batch}
+            "newton_iters": last["newton_iters"], "sweep": sweep, "batch": batch, "quadrotor": quad}
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

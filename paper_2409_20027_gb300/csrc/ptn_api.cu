@@ -375,7 +375,9 @@ static int solve_common(ptn_solver* s, int method, int B, const int* T_b, const 
   // one instance: a thread-block cluster when the horizon needs 2..16 CTAs, else the
   // cooperative grid from grid_min_T on, else one CTA
   int cl_blocks = 0;
-  if (B == 1 && s->opt.cluster_max_blocks >= 2) {
+  // models with n >= 8 run the wide tier (one CTA per instance, one warp per chunk)
+  const bool wide = s->n >= 8;
+  if (!wide && B == 1 && s->opt.cluster_max_blocks >= 2) {
     const long long per = (long long)s->opt.block_threads * s->opt.grid_steps_per_thread;
     const long long need = (T_b[0] + per - 1) / per;
     if (need >= 2 && need <= s->opt.cluster_max_blocks) {
@@ -389,8 +391,13 @@ static int solve_common(ptn_solver* s, int method, int B, const int* T_b, const 
       if (need <= maxc) cl_blocks = (int)need;
     }
   }
-  const bool grid = !cl_blocks && B == 1 && s->opt.grid_min_T > 0 && T_b[0] >= s->opt.grid_min_T;
-  if (cl_blocks) {
+  const bool grid = !wide && !cl_blocks && B == 1 && s->opt.grid_min_T > 0 && T_b[0] >= s->opt.grid_min_T;
+  if (wide) {
+    q.tier = 4;
+    q.nthreads = s->opt.block_threads;
+    q.nblocks = B;
+    CK(fn(q));
+  } else if (cl_blocks) {
     q.tier = 2;
     q.nthreads = s->opt.block_threads;
     q.nblocks = cl_blocks;

@@ -24,7 +24,7 @@ inline Work<L> typed(const WorkRaw& r) {
 
 struct LaunchReq {
   int tier;       // 0: one CTA per instance, 1: cooperative grid, 2: one cluster on one instance,
-                  // 3: adjoint, one CTA per instance
+                  // 3: adjoint, one CTA per instance, 4: wide (n >= 8, one warp per chunk)
   int precision;  // 0: FP64, 1: FP32 with FP64 solves, 2: FP32
   int nblocks, nthreads;
   int query;      // 1: only report max co-resident grid blocks in *max_blocks

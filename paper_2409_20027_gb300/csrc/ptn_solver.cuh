@@ -1038,6 +1038,13 @@ struct NStats {
   long long cyc[6];
 };
 
+// Groups whose passes are always exact (FP64 gradients, rollouts and merits whatever the
+// LQR precision); the Newton loop then skips the FP32-increment phase and its endgame.
+template <class Grp>
+struct exact_only {
+  static constexpr bool value = false;
+};
+
 // Newton iterations (Alg. 4) on the augmented sub-problem until max |d| <= tol.
 // Step acceptance and the alpha rule are the same readings as the CPU oracle's.  In the
 // mixed modes the gradient comes from the FP32-increment co-state pass until, at the
@@ -1045,7 +1052,7 @@ struct NStats {
 template <class M, class L, class SV, class Grp>
 __device__ int newton_solve(Grp& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>& P, const OptDev& O, const Aug& A,
                             double tol, bool final_level, NStats& st, double* rfinal) {
-  constexpr bool MIXED = std::is_same<L, float>::value;
+  constexpr bool MIXED = std::is_same<L, float>::value && !exact_only<Grp>::value;
   bool inf;
   double J0 = nominal_cost(g, I, P, A, &inf, nullptr);
   int rc = ST_ENOTCONV;
