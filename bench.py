@@ -201,6 +201,18 @@ def run_batch(args, ptn, W, dev, flush, stream):
             "one_by_one_sample": f"first {ns} instances as single solves (cluster or grid tier), time scaled to {B}"}
 
 
+PHASES = ["costate", "second_order", "value", "state", "line_search", "initial_rollout", "other"]
+
+
+def phase_share(infos):
+    """Share of SM cycles per phase of the Newton step, summed over instances (the
+    solver's own clock64 counters, first thread of each group)."""
+    tot = np.zeros(7)
+    for i in infos:
+        tot += np.asarray(i["cycles"], dtype=np.float64)
+    return {k: round(float(v / max(tot.sum(), 1.0)), 4) for k, v in zip(PHASES, tot)}
+
+
 def run_quadrotor(args, ptn, W, dev, flush, stream):
     """Quadrotor workload: B instances (n = 12, m = 4, Euler dt = 0.01, T = 1024), hover
     start at the origin, waypoints uniform in the 2 m cube (seed 0), hover thrust as the
@@ -209,7 +221,7 @@ def run_quadrotor(args, ptn, W, dev, flush, stream):
     constants (mass, inertia, arm, yaw coefficient, g).  grads/s counts one gradient of
     every instance per forward + adjoint."""
     import torch
-    B, T = args.quad_batch, 1024
+    B, T = args.quad_batch, args.quad_T
     wps = W.quadrotor_waypoints(B, seed=0)
     xrefs = torch.tensor(np.stack([W.quadrotor(w).xref for w in wps]), dtype=torch.float64, device=dev)
     Tb = np.full(B, T, dtype=np.int32)
@@ -239,7 +251,8 @@ def run_quadrotor(args, ptn, W, dev, flush, stream):
                         "IP fp32 LQR with fp64 solves (wide tier); adjoint in fp64",
             "forward_ms": f, "adjoint_ms": g, "solves_per_s": B / (f * 1e-3), "grads_per_s": B / ((f + g) * 1e-3),
             "converged": int(sum(1 for x in st if x == 0)), "status_counts": {str(k): st.count(k) for k in set(st)},
-            "newton_iters_mean": float(np.mean([i["newton_iters"] for i in infos]))}
+            "newton_iters_mean": float(np.mean([i["newton_iters"] for i in infos])),
+            "phase_share": phase_share(infos)}
 
 
 def config(T):
@@ -261,6 +274,7 @@ def main():
     ap.add_argument("--batch", type=int, default=1024)
     ap.add_argument("--no-quad", action="store_true")
     ap.add_argument("--quad-batch", type=int, default=256)
+    ap.add_argument("--quad-T", type=int, default=1024)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
