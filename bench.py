@@ -407,7 +407,8 @@ def main():
             "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": 4 * 8,
                     "d2h_bytes_per_step": ((T + 1) * 4 + T) * 8},
             "gpu_launches": args.steps, "clocks": clocks, "kkt_ok": ok,
-            "newton_iters": last["newton_iters"], "sweep": sweep, "batch": batch, "quadrotor": quad}
+            "newton_iters": last["newton_iters"], "phase_share": phase_share(infos), "sweep": sweep,
+            "batch": batch, "quadrotor": quad}
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
