@@ -28,6 +28,7 @@ sys.path.insert(0, ROOT)
 METRIC = "time-to-solve (ms) vs horizon T at KKT residual ≤1e-6; batched solves/sec; grads/sec"
 HORIZON_S = 2.56
 L2_FLUSH_BYTES = 256 << 20
+TUNED_TABLE = os.path.join(ROOT, "paper_2409_20027_gb300", "tuned_gb300.json")
 BATCH_HORIZON_S = 1.28  # keeps dt_b <= 0.02 for every batch horizon (T_b >= 64)
 
 
@@ -301,8 +302,11 @@ def main():
         if dist is not None:
             dist.barrier()
 
+    from paper_2409_20027_gb300 import autotune
+    tuned = autotune.load(TUNED_TABLE) if os.path.exists(TUNED_TABLE) else {}
     p = cartpole_instance(T)
     solver = ptn.Solver(p, max_T=T, precision=ptn.PTN_FP32_FP64SOLVE)
+    launch = autotune.apply(solver, tuned, T)
     x0s = [torch.tensor(W.cartpole_x0((k + 100 * rank) % 10 + 0), dtype=torch.float64, device=dev)
            for k in range(10)]
     xo = torch.empty((T + 1, 4), dtype=torch.float64, device=dev)
@@ -361,6 +365,7 @@ def main():
         for Ts in [256, 1024, 4096]:
             ps = cartpole_instance(Ts)
             sv = ptn.Solver(ps, max_T=Ts, precision=ptn.PTN_FP32_FP64SOLVE)
+            autotune.apply(sv, tuned, Ts)
             x0 = x0s[0]
             sv.solve_ip(x0, Ts)
             torch.cuda.synchronize()
@@ -407,7 +412,8 @@ def main():
             "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": 4 * 8,
                     "d2h_bytes_per_step": ((T + 1) * 4 + T) * 8},
             "gpu_launches": args.steps, "clocks": clocks, "kkt_ok": ok,
-            "newton_iters": last["newton_iters"], "phase_share": phase_share(infos), "sweep": sweep,
+            "newton_iters": last["newton_iters"], "launch": launch or "defaults",
+            "phase_share": phase_share(infos), "sweep": sweep,
             "batch": batch, "quadrotor": quad}
     print(json.dumps(line), flush=True)
     if dist is not None:

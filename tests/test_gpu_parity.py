@@ -99,8 +99,17 @@ def test_cartpole_fp64_cta(ptn):
     check_solution(info, ref, x, u, lam, FP64_TOL)
 
 
-@pytest.mark.parametrize("T,grid,prec", [(256, False, 1), (1024, True, 1), (4096, True, 1), (4096, True, 2)])
-def test_cartpole_fp32_matches_oracle(ptn, T, grid, prec):
+# launch options that pin a single solve to one execution tier
+TIERS = {
+    "cta": dict(grid_min_T=0, cluster_max_blocks=0),
+    "cluster": dict(grid_min_T=0, cluster_max_blocks=16),
+    "grid": dict(grid_min_T=512, cluster_max_blocks=0),
+}
+
+
+@pytest.mark.parametrize("T,tier,prec", [(256, "cta", 1), (1024, "grid", 1), (1024, "cluster", 1),
+                                         (4096, "grid", 1), (4096, "cluster", 1), (4096, "cluster", 2)])
+def test_cartpole_fp32_matches_oracle(ptn, T, tier, prec):
     # The reduced Hessian of this single-shooting problem is ill-conditioned, so a
     # 1e-6 stationarity tolerance leaves the controls determined only to ~1e-3: two
     # different iteration paths (FP32 vs FP64 arithmetic) stop at different points of
@@ -108,7 +117,7 @@ def test_cartpole_fp32_matches_oracle(ptn, T, grid, prec):
     # well below the 1e-4 parity bar (the oracle's own noise floor is near 1e-8 here).
     p = W.cartpole(T=T, horizon=2.56)
     x0 = W.cartpole_x0(1)
-    s = ptn.Solver(p, max_T=T, precision=prec, grid_min_T=(512 if grid else 0), tol_final=1e-7)
+    s = ptn.Solver(p, max_T=T, precision=prec, tol_final=1e-7, **TIERS[tier])
     x, u, lam, info = s.solve_ip(dev(x0), T)
     ref = O.solve_ip(p, x0, T, opts=O.Options(tol_final=1e-7))
     check_solution(info, ref, x, u, lam, FP32_TOL, with_lam=False)
@@ -126,11 +135,12 @@ def test_cartpole_fp32_reaches_kkt(ptn, T, prec):
     assert abs(info["J"] - ref["info"]["J"]) / abs(ref["info"]["J"]) <= FP32_TOL
 
 
-def test_grid_tier_fp64_matches_oracle(ptn):
+@pytest.mark.parametrize("tier,spt", [("grid", 3), ("cluster", 3), ("cluster", 1)])
+def test_multi_cta_tiers_fp64_match_oracle(ptn, tier, spt):
     T = 1024
     p = W.cartpole(T=T, horizon=2.56)
     x0 = W.cartpole_x0(2)
-    s = ptn.Solver(p, max_T=T, precision=ptn.PTN_FP64, grid_min_T=512, grid_steps_per_thread=3)
+    s = ptn.Solver(p, max_T=T, precision=ptn.PTN_FP64, grid_steps_per_thread=spt, **TIERS[tier])
     x, u, lam, info = s.solve_ip(dev(x0), T)
     ref = O.solve_ip(p, x0, T)
     check_solution(info, ref, x, u, lam, FP64_TOL)
