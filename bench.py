@@ -256,6 +256,33 @@ def run_quadrotor(args, ptn, W, dev, flush, stream):
             "phase_share": phase_share(infos)}
 
 
+def run_mpc(ptn, W, dev, stream):
+    """Closed-loop MPC: 256 cart-pole loops (initial states as the batch workload), horizon
+    N = 60 at 100 Hz (dt = 0.01, RK4), 100 control periods, each period one batched solve
+    warm-started with the shifted controls of the previous one."""
+    import torch
+    from paper_2409_20027_gb300 import mpc
+    B, N, steps = 256, 60, 100
+    x0 = torch.tensor(W.cartpole_batch_x0(B, seed=1), dtype=torch.float64, device=dev)
+    sv = ptn.Solver(W.cartpole(), max_T=N, max_batch=B, precision=ptn.PTN_FP32_FP64SOLVE, block_threads=64)
+    mpc.closed_loop(sv, x0, N, 2)  # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    res = mpc.closed_loop(sv, x0, N, steps)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    sv.close()
+    st = res["status"]
+    its = res["iters"]
+    return {"workload": f"{B} closed cart-pole loops, N={N}, 100 Hz (dt=0.01, RK4), {steps} periods, shifted warm "
+                        "start, fp32 LQR with fp64 solves, one batched solve per period",
+            "period_ms": 1e3 * wall / steps, "loop_periods_per_s": B * steps / wall,
+            "newton_iters_first": float(its[0].mean()), "newton_iters_warm": float(its[1:].mean()),
+            "converged_share": float((st == 0).mean()),
+            "final_state_max_abs_err": float((res["x"][-1] - torch.tensor([0.0, np.pi, 0.0, 0.0], device=dev))
+                                             .abs().max().item())}
+
+
 def config(T):
     return {"workload": f"cart-pole swing-stabilisation, primal log-barrier IP, T={T}, fixed {HORIZON_S} s "
                         f"horizon (RK4, dt={HORIZON_S / T:.4g}), |u|<=10, |p|<=2, KKT<=1e-6",
@@ -276,6 +303,7 @@ def main():
     ap.add_argument("--no-quad", action="store_true")
     ap.add_argument("--quad-batch", type=int, default=256)
     ap.add_argument("--quad-T", type=int, default=1024)
+    ap.add_argument("--no-mpc", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
@@ -387,6 +415,9 @@ def main():
     quad = None
     if not args.no_quad:
         quad = run_quadrotor(args, ptn, W, dev, flush, stream)
+    mpcl = None
+    if not args.no_mpc:
+        mpcl = run_mpc(ptn, W, dev, stream)
 
     if rank != 0:
         return
@@ -414,7 +445,7 @@ def main():
             "gpu_launches": args.steps, "clocks": clocks, "kkt_ok": ok,
             "newton_iters": last["newton_iters"], "launch": launch or "defaults",
             "phase_share": phase_share(infos), "sweep": sweep,
-            "batch": batch, "quadrotor": quad}
+            "batch": batch, "quadrotor": quad, "mpc": mpcl}
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

@@ -1,0 +1,38 @@
+"""Closed-loop MPC with warm starts: the shift is host logic (CPU); the loop on the GPU
+must follow the same loop run with oracle solves."""
+import numpy as np
+import pytest
+
+from paper_2409_20027_gb300 import workloads as W
+
+
+def test_shift_controls_drops_the_applied_control():
+    torch = pytest.importorskip("torch")
+    from paper_2409_20027_gb300 import mpc
+    u = torch.arange(12, dtype=torch.float64).reshape(6, 2)  # B = 2 loops, T = 3, m = 2
+    v = mpc.shift_controls(u, 3)
+    assert v.tolist() == [[2, 3], [4, 5], [4, 5], [8, 9], [10, 11], [10, 11]]
+
+
+@pytest.mark.gpu
+def test_closed_loop_follows_oracle_loop():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    import oracle as O
+    from paper_2409_20027_gb300 import mpc, ptn
+    p = W.pendulum()
+    T, steps, B = 30, 6, 3
+    x0 = np.stack([W.pendulum_x0(s) for s in range(B)])
+    s = ptn.Solver(p, max_T=T, max_batch=B, precision=ptn.PTN_FP64, block_threads=32)
+    res = mpc.closed_loop(s, torch.tensor(x0, device="cuda:0"), T, steps)
+    assert (res["status"] == 0).all()
+    X = res["x"].cpu().numpy()
+    for b in range(B):
+        x, ui = x0[b], None
+        for k in range(steps):
+            r = O.solve_ip(p, x, T, u_init=ui)
+            assert r["info"]["status"] == 0
+            x = r["x"][1]
+            ui = np.concatenate([r["u"][1:], r["u"][-1:]])
+            assert np.abs(X[k + 1, b] - x).max() <= 1e-6 * max(1.0, np.abs(x).max()), (b, k)
