@@ -283,6 +283,28 @@ def run_mpc(ptn, W, dev, stream):
                                              .abs().max().item())}
 
 
+def run_sequential(args, ptn, W, dev, flush, stream):
+    """The paper's comparison axis on this GPU: the same single cart-pole solve (2.56 s
+    horizon, T = 1024, FP32 LQR with FP64 solves) by the sequential-in-time baseline (one
+    thread running the serial recursions) next to the parallel-in-time solve of the sweep.
+    (Bounded to one solve: the FP64 sequential baseline runs for minutes on this GPU.)"""
+    import torch
+    out = {}
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for T in [1024]:
+        p = cartpole_instance(T)
+        sv = ptn.Solver(p, max_T=T, precision=ptn.PTN_FP32_FP64SOLVE, sequential=1)
+        xs = torch.tensor(W.cartpole_x0(0), dtype=torch.float64, device=dev)
+        flush.zero_()
+        a.record(stream)
+        _, _, _, inf = sv.solve_ip(xs, T)
+        b.record(stream)
+        torch.cuda.synchronize()
+        out[str(T)] = {"ms": a.elapsed_time(b), "newton_iters": inf["newton_iters"], "status": inf["status"]}
+        sv.close()
+    return out
+
+
 def config(T):
     return {"workload": f"cart-pole swing-stabilisation, primal log-barrier IP, T={T}, fixed {HORIZON_S} s "
                         f"horizon (RK4, dt={HORIZON_S / T:.4g}), |u|<=10, |p|<=2, KKT<=1e-6",
@@ -304,6 +326,7 @@ def main():
     ap.add_argument("--quad-batch", type=int, default=256)
     ap.add_argument("--quad-T", type=int, default=1024)
     ap.add_argument("--no-mpc", action="store_true")
+    ap.add_argument("--no-seq", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
@@ -418,6 +441,9 @@ def main():
     mpcl = None
     if not args.no_mpc:
         mpcl = run_mpc(ptn, W, dev, stream)
+    seq = None
+    if not args.no_seq:
+        seq = run_sequential(args, ptn, W, dev, flush, stream)
 
     if rank != 0:
         return
@@ -445,7 +471,7 @@ def main():
             "gpu_launches": args.steps, "clocks": clocks, "kkt_ok": ok,
             "newton_iters": last["newton_iters"], "launch": launch or "defaults",
             "phase_share": phase_share(infos), "sweep": sweep,
-            "batch": batch, "quadrotor": quad, "mpc": mpcl}
+            "batch": batch, "quadrotor": quad, "mpc": mpcl, "sequential": seq}
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

@@ -91,7 +91,8 @@ typedef struct ptn_options {
   int cluster_max_blocks; /* single solves needing 2..cluster_max_blocks CTAs (block_threads
                              threads, grid_steps_per_thread steps each) run on one thread-block
                              cluster (at most 16; 0: never) before the cooperative grid is used */
-  int pad_opt;
+  int sequential;       /* nonzero: the sequential-in-time baseline, one thread per instance
+                           running the serial recursions (n < 8 only); for comparisons */
   double mu0, zeta, mu_final, tol_inner, tol_final, rho, admm_tol;
   double alpha0, alpha_min, alpha_max, ls_beta, armijo_c1, armijo_eps, roll_tol;
   double polish;        /* FP32 modes: exact FP64 gradients once max|d| <= polish * tol_final */

@@ -377,7 +377,7 @@ static int solve_common(ptn_solver* s, int method, int B, const int* T_b, const 
   int cl_blocks = 0;
   // models with n >= 8 run the wide tier (one CTA per instance, one warp per chunk)
   const bool wide = s->n >= 8;
-  if (!wide && B == 1 && s->opt.cluster_max_blocks >= 2) {
+  if (!wide && !s->opt.sequential && B == 1 && s->opt.cluster_max_blocks >= 2) {
     const long long per = (long long)s->opt.block_threads * s->opt.grid_steps_per_thread;
     const long long need = (T_b[0] + per - 1) / per;
     if (need >= 2 && need <= s->opt.cluster_max_blocks) {
@@ -392,7 +392,12 @@ static int solve_common(ptn_solver* s, int method, int B, const int* T_b, const 
     }
   }
   const bool grid = !wide && !cl_blocks && B == 1 && s->opt.grid_min_T > 0 && T_b[0] >= s->opt.grid_min_T;
-  if (wide) {
+  if (s->opt.sequential && !wide) {
+    q.tier = 5;
+    q.nthreads = 32;
+    q.nblocks = (B + 31) / 32;
+    CK(fn(q));
+  } else if (wide) {
     q.tier = 4;
     q.nthreads = s->opt.block_threads;
     q.nblocks = B;

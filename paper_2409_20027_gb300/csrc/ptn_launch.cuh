@@ -24,7 +24,8 @@ inline Work<L> typed(const WorkRaw& r) {
 
 struct LaunchReq {
   int tier;       // 0: one CTA per instance, 1: cooperative grid, 2: one cluster on one instance,
-                  // 3: adjoint, one CTA per instance, 4: wide (n >= 8, one warp per chunk)
+                  // 3: adjoint, one CTA per instance, 4: wide (n >= 8, one warp per chunk),
+                  // 5: sequential-in-time baseline (one thread per instance)
   int precision;  // 0: FP64, 1: FP32 with FP64 solves, 2: FP32
   int nblocks, nthreads;
   int query;      // 1: only report max co-resident grid blocks in *max_blocks
@@ -47,6 +48,11 @@ cudaError_t launch_typed(LaunchReq& q) {
     if (e != cudaSuccess) return e;
     if (q.query) return cudaSuccess;
     k_solve_cta<M, L, SV><<<q.nblocks, nthreads, smem, q.stream>>>(q.args, typed<L>(q.w));
+    return cudaGetLastError();
+  }
+  if (q.tier == 5) {
+    if (q.query) return cudaSuccess;
+    k_solve_seq<M, L, SV><<<q.nblocks, q.nthreads, 0, q.stream>>>(q.args, typed<L>(q.w));
     return cudaGetLastError();
   }
   if (q.tier == 3) {

@@ -689,7 +689,8 @@ __device__ bool value_pass(Grp& g, Inst<M, L>& I, double alpha, const double* qx
     }
     have = true;
   }
-  for (int t = I.b - 1; t >= I.a; t--) {
+  // (a one-member group needs no chunk aggregate: its suffix is the terminal element)
+  for (int t = I.b - 1; t >= I.a && g.size() > 1; t--) {
     Val<N, L> e;
     L F[N * N];
     load_F<N>(I.E + (size_t)t * N * N, F);
@@ -931,9 +932,13 @@ __device__ int rollout(Grp& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>& P, cons
         for (int i = 0; i < U * N; i++) Gd[i] = double(Gam[i]);
         // FP64 Jacobian: quadratic convergence of the shooting Newton, so the rollout
         // reaches the FP64 dynamics to rounding and FP64 merits stay noise-free
-        MOps<M>::cl(P, xt, ut, Gd, xnext, Fd);
+        if (first) {
+          MOps<M>::f(P, xt, ut, xnext);  // the first chunk's map is constant: no Jacobian
+        } else {
+          MOps<M>::cl(P, xt, ut, Gd, xnext, Fd);
 #pragma unroll (N <= 8 ? N * N : 4)
-        for (int i = 0; i < N * N; i++) Fc[i] = L(Fd[i]);
+          for (int i = 0; i < N * N; i++) Fc[i] = L(Fd[i]);
+        }
 #pragma unroll
         for (int i = 0; i < N; i++) xt[i] = xnext[i];
       }
@@ -1669,6 +1674,64 @@ __global__ void __launch_bounds__(256) k_adjoint_cta(KArgs args, Work<L> w, AdjA
   I.setup(w, id, args.x0 + (size_t)bi * N, threadIdx.x, blockDim.x, P.nw);
   const int rc = adjoint_instance<M, L, SV>(g, I, P, aa, id, bi);
   if (threadIdx.x == 0) args.info[bi].status = rc;
+}
+
+// ---------------------------------------------------------------------------
+// Sequential-in-time baseline: one thread per instance.  With a one-member group the
+// scans are identities and each pass is its serial recursion (co-states backward, the
+// Riccati recursion, states forward, plain sequential rollouts).
+struct SeqGroup {
+  __device__ int rank() const { return 0; }
+  __device__ int size() const { return 1; }
+  __device__ bool dead() const { return false; }
+  __device__ void sync() {}
+  template <int K>
+  __device__ void reduce(double (&)[K], unsigned) {}
+  template <class E, class Op>
+  __device__ E scan(E, const Op&, bool, bool&) {
+    E id;
+    set_identity(id);
+    return id;
+  }
+};
+
+// problem record for one thread (as load_prob, without the CTA-wide copy)
+template <int N, int U>
+__device__ void load_prob_thread(ProbS<N, U>& S, const ProbDev& P, const double* xref_override, double dt_inst) {
+  const double sc = dt_inst > 0.0 ? dt_inst / P.dt : 1.0;
+  for (int i = 0; i < N * N; i++) {
+    S.Q[i] = sc * P.Q[i];
+    S.Qf[i] = P.Qf[i];
+    S.Qs[i] = float(sc * (P.Q[i] + P.Q[(i % N) * N + i / N]));
+    S.Qfs[i] = float(P.Qf[i] + P.Qf[(i % N) * N + i / N]);
+  }
+  for (int i = 0; i < U * U; i++) {
+    S.R[i] = sc * P.R[i];
+    S.Rs[i] = float(sc * (P.R[i] + P.R[(i % U) * U + i / U]));
+  }
+  for (int i = 0; i < N; i++) S.xref[i] = xref_override ? xref_override[i] : P.xref[i];
+  for (int i = 0; i < U; i++) S.uref[i] = P.uref[i];
+  for (int i = 0; i < PTN_MAXP; i++) S.prm[i] = P.prm[i];
+  for (int i = 0; i < P.nw; i++) {
+    S.sgn[i] = P.row_sgn[i]; S.bnd[i] = P.row_bnd[i]; S.isx[i] = P.row_isx[i]; S.idx[i] = P.row_idx[i];
+  }
+  S.nw = P.nw; S.integ = P.integrator; S.model = P.model; S.dt = dt_inst > 0.0 ? dt_inst : P.dt;
+  S.A = P.A; S.B = P.B; S.W = P.W;
+}
+
+template <class M, class L, class SV>
+__global__ void __launch_bounds__(64) k_solve_seq(KArgs args, Work<L> w) {
+  constexpr int N = M::NX, U = M::NU;
+  const int bi = blockIdx.x * blockDim.x + threadIdx.x;
+  if (bi >= args.B) return;  // no group barriers below: threads are independent
+  ProbS<N, U> P;
+  load_prob_thread<N, U>(P, *args.prob, args.xref ? args.xref + (size_t)bi * N : nullptr, args.inst[bi].dt);
+  const OptDev O = *args.opt;
+  const InstDev id = args.inst[bi];
+  SeqGroup g;
+  Inst<M, L> I;
+  I.setup(w, id, args.x0 + (size_t)bi * N, 0, 1, P.nw);
+  solve_instance<M, L, SV>(g, I, P, O, args.u_init ? args.u_init + (size_t)id.uoff * U : nullptr, args.info + bi);
 }
 
 // one thread-block cluster on one instance (medium horizons)

@@ -273,3 +273,22 @@ def test_nonfinite_initial_state_does_not_hang(ptn):
     s = ptn.Solver(p, max_T=T, precision=ptn.PTN_FP64)
     x, u, lam, info = s.solve_ip(dev([np.nan, 0.0]), T)
     assert info["status"] != 0
+
+
+def test_sequential_baseline_matches_oracle(ptn):
+    # one thread per instance running the serial recursions: the same algorithm as the
+    # oracle, step for step, so the iteration counts agree too
+    p = W.cartpole()
+    Tb = np.array([1, 7, 40, 64, 100, 33], dtype=np.int32)
+    B = len(Tb)
+    x0s = W.cartpole_batch_x0(B, 9)
+    s = ptn.Solver(p, max_T=int(Tb.max()), max_batch=B, precision=ptn.PTN_FP64, sequential=1)
+    X, U, Lm, infos = s.solve_batch(dev(x0s), Tb)
+    xo = uo = 0
+    for b in range(B):
+        T = int(Tb[b])
+        ref = O.solve_ip(p, x0s[b], T)
+        check_solution(infos[b], ref, X[xo:xo + T + 1], U[uo:uo + T], Lm[xo:xo + T + 1], FP64_TOL)
+        assert infos[b]["newton_iters"] == ref["info"]["newton_iters"]
+        xo += T + 1
+        uo += T
