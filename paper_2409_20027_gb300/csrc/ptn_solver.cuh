@@ -1063,11 +1063,12 @@ __device__ int newton_solve(Grp& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>& P,
   int rc = ST_ENOTCONV;
   double r = INFINITY;
   bool exact = !MIXED;  // FP64 gradients, FP64 rollouts and absolute FP64 merits
+  bool stalled = false;  // the FP32-increment phase ran alpha past alpha_max
   for (int it = 0; it <= O.max_newton; it++) {
     if (g.dead()) return ST_ETIMEOUT;
     long long c0 = clock64();
     r = costate_pass(g, I, P, A, exact);
-    if (MIXED && !exact && final_level && (r <= O.polish * tol || it >= O.polish_after)) {
+    if (MIXED && !exact && (stalled || (final_level && (r <= O.polish * tol || it >= O.polish_after)))) {
       // endgame: below the FP32 noise floor of gradients and merits, switch to FP64.
       // First re-project the nominal onto the FP64 dynamics (one exact rollout with
       // s = 0 under the last feedback), so that FP64 merits compare like with like.
@@ -1132,7 +1133,17 @@ __device__ int newton_solve(Grp& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>& P,
     } else {
       st.ls_rejects++;
       st.alpha *= 10.0;
-      if (st.alpha > O.alpha_max) { rc = ST_ENUM; break; }
+      if (st.alpha > O.alpha_max) {
+        if (MIXED && !exact) {
+          // no descent found with FP32-increment gradients and merits: continue this
+          // level on the exact FP64 path from alpha0 instead of giving up
+          stalled = true;
+          st.alpha = O.alpha0;
+          continue;
+        }
+        rc = ST_ENUM;
+        break;
+      }
     }
   }
   *rfinal = r;

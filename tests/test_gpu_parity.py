@@ -292,3 +292,17 @@ def test_sequential_baseline_matches_oracle(ptn):
         assert infos[b]["newton_iters"] == ref["info"]["newton_iters"]
         xo += T + 1
         uo += T
+
+
+def test_mixed_mode_recovers_when_fp32_phase_stalls(ptn):
+    # a short, coarsely sampled batch instance (T = 82 over 1.28 s) on which the FP32-
+    # increment phase finds no descent; the Newton loop continues on the exact FP64 path
+    T = 82
+    x0 = W.cartpole_batch_x0(1024, 0)[53]
+    p = W.cartpole(T=T, horizon=1.28)
+    s = ptn.Solver(p, max_T=T, precision=ptn.PTN_FP32_FP64SOLVE)
+    x, u, lam, info = s.solve_ip(dev(x0), T)
+    ref = O.solve_ip(p, x0, T)
+    assert info["status"] == 0 and ref["info"]["status"] == 0
+    assert info["r_kkt"] <= 1e-6 * (1 + 1e-9)
+    assert abs(info["J"] - ref["info"]["J"]) / max(1.0, abs(ref["info"]["J"])) <= FP32_TOL
