@@ -210,6 +210,24 @@ def test_admm_fixed_outer_iterations_fp64(ptn):
     assert info["r_p"] == pytest.approx(ref["info"]["r_p"], rel=1e-6, abs=1e-9)
 
 
+@pytest.mark.parametrize("tier", ["cluster", "grid"])
+def test_admm_on_multi_cta_tiers_fp64(ptn, tier):
+    # z and v updates and the primal/dual residual reductions across CTAs.  The sub-
+    # problems are solved to 1e-9: at 1e-6 the ill-conditioned reduced Hessian leaves
+    # the controls pinned only to ~1e-6, and rounding-level path differences show.
+    T = 1024
+    p = W.cartpole(T=T, horizon=2.56)
+    x0 = W.cartpole_x0(3)
+    K = 3
+    s = ptn.Solver(p, max_T=T, precision=ptn.PTN_FP64, admm_fixed_iters=K, tol_final=1e-9, **TIERS[tier])
+    x, u, lam, z, v, info = s.solve_admm(dev(x0), T, with_zv=True)
+    ref = O.solve_admm(p, x0, T, opts=O.Options(admm_fixed_iters=K, tol_final=1e-9))
+    assert info["status"] == 0 and info["outer_iters"] == K
+    for a, b in [(x, ref["x"]), (u, ref["u"]), (z, ref["z"]), (v, ref["v"])]:
+        assert rel(a.cpu().numpy(), b) <= FP64_TOL
+    assert info["r_p"] == pytest.approx(ref["info"]["r_p"], rel=1e-6, abs=1e-9)
+
+
 # FP64 reaches the tighter 1e-4 primal/dual tolerance; the FP32 modes are checked at the
 # 1e-2 stopping rule of the paper's ADMM experiments (Sec. IV): at 1e-4 this instance
 # reaches the accuracy floor of the FP32 Riccati directions and reports status -4.
