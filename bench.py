@@ -452,7 +452,7 @@ def main():
     achieved = (f32 + f64) / (per[-1] * 1e-3) / 1e12
     peak = blended_peak_tflops(f32, f64)
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": TRAFFIC_BYTES if T == 16384 else None, "kernel": "k_solve_grid<CartPole,float,double>",
+            "traffic": None, "kernel": "k_solve_grid<CartPole,float,double>",
             "peak_source": "derived: FP32 152 SMs x 128 lanes x 2 x 2.07 GHz = %.1f TFLOP/s, FP64 nominal "
                            "%.2f TFLOP/s, blended by this solve's FP32/FP64 flop split (%.1f%% FP64)"
                            % (FP32_PEAK_TFLOPS, FP64_PEAK_TFLOPS, 100 * f64 / (f32 + f64))}

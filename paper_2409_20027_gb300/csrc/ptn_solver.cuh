@@ -1257,6 +1257,87 @@ __device__ void initial_rollout(Grp& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>
   g.sync();
 }
 
+// Initial nominal in parallel (FP32 modes, groups of >= 256 threads, fine time steps):
+// the same open-loop trajectory x = rollout(x0, u_init), computed as
+//   1. a coarse pass by the group's first thread with steps K dt (K <= 32, K dt <= 2.5 ms;
+//      controls held), which gives states at t = 0, K, 2K, ...;
+//   2. each thread's guess of its chunk start, integrated in fine steps (< K) from the
+//      coarse state before it;
+//   3. the multiple-shooting rollout with s = 0 and no feedback, which corrects the
+//      guesses onto the fine trajectory (same dynamics and tolerance as later rollouts).
+// Returns false (group-uniform) when not applicable (FP64, small groups, coarse steps,
+// ADMM) or when the shooting does not converge; the caller then integrates sequentially.
+template <class M, class L, class Grp>
+__device__ bool initial_rollout_parallel(Grp& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>& P, const OptDev& O,
+                                         int* iters) {
+  if constexpr (!std::is_same<L, float>::value) {
+    return false;
+  } else {
+    constexpr int N = M::NX, U = M::NU;
+    int K = (int)(0.0025 / P.dt);
+    K = K > 32 ? 32 : K;
+    if (K < 2 || g.size() < 256 || O.method != 0) return false;  // IP only (barrier merit)
+    if (g.rank() == 0) {
+      double x[N];
+#pragma unroll
+      for (int i = 0; i < N; i++) { x[i] = I.x0[i]; I.xn[i] = x[i]; }
+      for (int c = 0; c + K <= I.T; c += K) {
+        float xf[N], uf[U], dv[N];
+#pragma unroll
+        for (int i = 0; i < N; i++) xf[i] = float(x[i]);
+#pragma unroll
+        for (int i = 0; i < U; i++) uf[i] = float(I.un[(size_t)c * U + i]);
+        step_inc<M, float, double>(P.integ, K * P.dt, P.prm, xf, uf, dv);
+#pragma unroll
+        for (int i = 0; i < N; i++) {
+          x[i] += double(dv[i]);
+          I.xn[(size_t)(c + K) * N + i] = x[i];
+        }
+      }
+    }
+    g.sync();
+    // chunk-start guesses (threads write only their own start; coarse points are read)
+    if (I.a < I.b) {
+      const int c = (I.a / K) * K;
+      if (c != I.a) {
+        double x[N];
+#pragma unroll
+        for (int i = 0; i < N; i++) x[i] = I.xn[(size_t)c * N + i];
+        for (int t = c; t < I.a; t++) {
+          float xf[N], uf[U], dv[N];
+#pragma unroll
+          for (int i = 0; i < N; i++) xf[i] = float(x[i]);
+#pragma unroll
+          for (int i = 0; i < U; i++) uf[i] = float(I.un[(size_t)t * U + i]);
+          MOps<M>::inc32(P, xf, uf, dv);
+#pragma unroll
+          for (int i = 0; i < N; i++) x[i] += double(dv[i]);
+        }
+        // (I.a is not a multiple of K: no other thread reads this entry in this phase)
+#pragma unroll
+        for (int i = 0; i < N; i++) I.xn[(size_t)I.a * N + i] = x[i];
+      }
+    }
+    // no step direction yet: dx = 0 where the rollout reads it (x^ + s dx with s = 0)
+    for (int t = I.a; t < I.b; t++)
+#pragma unroll
+      for (int i = 0; i < N; i++) I.dx[(size_t)t * N + i] = L(0);
+    if (I.last)
+#pragma unroll
+      for (int i = 0; i < N; i++) I.dx[(size_t)I.T * N + i] = L(0);
+    g.sync();
+    Aug A;
+    A.kind = AUG_BARRIER; A.mu = O.mu0; A.rho = 1.0; A.z = nullptr; A.v = nullptr;
+    double m;
+    const int rc = rollout(g, I, P, O, A, 0.0, false, &m, iters, O.roll_max_iter);
+    if (rc == ROLL_FAIL) return false;
+    double* t1 = I.xn; I.xn = I.xc; I.xc = t1;
+    double* t2 = I.un; I.un = I.uc; I.uc = t2;
+    g.sync();
+    return true;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Adjoint at a solution (x*, u*) of the barrier problem with weight mu, for the loss
 //   L = gJ J* + <gx, x*> + <gu, u*>   (J* = optimal barrier objective).
@@ -1524,7 +1605,11 @@ __device__ void solve_instance(Grp& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>&
   NStats st{0, 0, 0, 0, 0, 0, 0, O.alpha0, {0, 0, 0, 0, 0, 0}};
   Aug A;
   int rc = ST_OK;
-  initial_rollout(g, I, P);
+  {
+    int ri = 0;
+    if (!initial_rollout_parallel(g, I, P, O, &ri)) initial_rollout(g, I, P);
+    st.roll_iters += ri;
+  }
   st.cyc[5] = clock64() - c_start;
   if (O.method == 0) {
     // ---- primal log-barrier IP (eq. lb-min, lb-step-2) ----
