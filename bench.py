@@ -48,7 +48,7 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 FP64_PEAK_TFLOPS = 1.25
 # DRAM bytes (read + write) of one k_solve_grid launch of this workload, from the ncu
 # capture summarised in profiles/k_solve_grid_cartpole_T16384.md
-TRAFFIC_BYTES = (2.692096 + 2.212096) * 1e6
+TRAFFIC_BYTES = (2.964224 + 1.731072) * 1e6
 
 
 def flop_split(n, m, T, info):
@@ -452,7 +452,7 @@ def main():
     achieved = (f32 + f64) / (per[-1] * 1e-3) / 1e12
     peak = blended_peak_tflops(f32, f64)
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": None, "kernel": "k_solve_grid<CartPole,float,double>",
+            "traffic": TRAFFIC_BYTES if T == 16384 else None, "kernel": "k_solve_grid<CartPole,float,double>",
             "peak_source": "derived: FP32 152 SMs x 128 lanes x 2 x 2.07 GHz = %.1f TFLOP/s, FP64 nominal "
                            "%.2f TFLOP/s, blended by this solve's FP32/FP64 flop split (%.1f%% FP64)"
                            % (FP32_PEAK_TFLOPS, FP64_PEAK_TFLOPS, 100 * f64 / (f32 + f64))}
