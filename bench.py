@@ -154,6 +154,15 @@ def run_reference(args, T):
     print(json.dumps(line), flush=True)
 
 
+def max_over_ranks(value, dist, device):
+    """The largest value over all ranks (every rank gets it): a step takes as long as its
+    slowest replica."""
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def run_batch(args, ptn, W, dev, flush, stream):
     """Batched workload: B cart-pole instances (RK4), horizons T_b log-uniform in [64, 4096]
     from seed 0, each covering the same 1.28 s at dt_b = 1.28 / T_b; one launch for the
@@ -387,9 +396,7 @@ def main():
     per = [a.elapsed_time(b) for a, b in ev]
     ms = sum(per) / len(per)
     if dist is not None:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+        ms = max_over_ranks(ms, dist, dev)
     ok = all(i["status"] == 0 and i["r_kkt"] <= 1e-6 * (1 + 1e-9) for i in infos)
 
     # end to end through the public API with host buffers (pinned), copies in the region
@@ -411,8 +418,11 @@ def main():
         e2e.append((time.perf_counter() - t0) * 1e3)
     e2e_ms = sum(e2e) / len(e2e)
 
+    # the sections below are single-GPU measurements: with N replicas only the headline
+    # solve above is repeated on every GPU
+    single = world == 1
     sweep = {}
-    if not args.no_sweep:
+    if not args.no_sweep and single:
         for Ts in [256, 1024, 4096]:
             ps = cartpole_instance(Ts)
             sv = ptn.Solver(ps, max_T=Ts, precision=ptn.PTN_FP32_FP64SOLVE)
@@ -433,16 +443,16 @@ def main():
                          "r_kkt": infos[-1]["r_kkt"]}
 
     batch = None
-    if not args.no_batch:
+    if not args.no_batch and single:
         batch = run_batch(args, ptn, W, dev, flush, stream)
     quad = None
-    if not args.no_quad:
+    if not args.no_quad and single:
         quad = run_quadrotor(args, ptn, W, dev, flush, stream)
     mpcl = None
-    if not args.no_mpc:
+    if not args.no_mpc and single:
         mpcl = run_mpc(ptn, W, dev, stream)
     seq = None
-    if not args.no_seq:
+    if not args.no_seq and single:
         seq = run_sequential(args, ptn, W, dev, flush, stream)
 
     if rank != 0:
