@@ -194,15 +194,38 @@ struct GridGroup {
 #pragma unroll
       for (int k = 0; k < K; k++) slot[blockIdx.x * 8 + k] = v[k];
     sync();
+    // warp 0 combines the block values: each lane folds blocks lane, lane + 32, ... in
+    // order, then an ordered shuffle tree (the same in every block, so every block gets
+    // bit-identical results); shared memory broadcasts them to the block
+    double* sres = reinterpret_cast<double*>(sm);
+    if (threadIdx.x < 32) {
+      const int lane = threadIdx.x;
+      double a[K];
 #pragma unroll
-    for (int k = 0; k < K; k++) {
-      double a = ((volatile double*)slot)[k];
-      for (int i = 1; i < (int)gridDim.x; i++) {
-        const double o = ((volatile double*)slot)[i * 8 + k];
-        a = ((maxmask >> k) & 1u) ? fmax(a, o) : a + o;
+      for (int k = 0; k < K; k++) a[k] = ((maxmask >> k) & 1u) ? -INFINITY : 0.0;
+      for (int b = lane; b < (int)gridDim.x; b += 32) {
+        double o[K];  // all K loads of a block issued together
+#pragma unroll
+        for (int k = 0; k < K; k++) o[k] = __ldcg(slot + (size_t)b * 8 + k);
+#pragma unroll
+        for (int k = 0; k < K; k++) a[k] = ((maxmask >> k) & 1u) ? fmax(a[k], o[k]) : a[k] + o[k];
       }
-      v[k] = a;
+#pragma unroll
+      for (int off = 1; off < 32; off <<= 1) {
+#pragma unroll
+        for (int k = 0; k < K; k++) {
+          const double o = __shfl_down_sync(PTN_FULL, a[k], off);
+          if ((lane & (2 * off - 1)) == 0) a[k] = ((maxmask >> k) & 1u) ? fmax(a[k], o) : a[k] + o;
+        }
+      }
+      if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < K; k++) sres[k] = a[k];
     }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < K; k++) v[k] = sres[k];
+    __syncthreads();
     phase ^= 1;
   }
 
@@ -285,17 +308,33 @@ struct ClusterGroup {
 #pragma unroll
       for (int k = 0; k < K; k++) mine[k] = v[k];
     sync();
+    // warp 0 reads the CTAs' values (lane i: CTA i) and combines them in an ordered
+    // shuffle tree, the same in every CTA; shared memory broadcasts the result
     auto cl = cooperative_groups::this_cluster();
     const int nb = nblk();
+    double* sres = reinterpret_cast<double*>(sm);
+    if (threadIdx.x < 32) {
+      const int lane = threadIdx.x;
+      double a[K];
 #pragma unroll
-    for (int k = 0; k < K; k++) {
-      double a = cl.map_shared_rank(mine, 0)[k];
-      for (int i = 1; i < nb; i++) {
-        const double o = cl.map_shared_rank(mine, i)[k];
-        a = ((maxmask >> k) & 1u) ? fmax(a, o) : a + o;
+      for (int k = 0; k < K; k++)
+        a[k] = lane < nb ? cl.map_shared_rank(mine, lane)[k] : (((maxmask >> k) & 1u) ? -INFINITY : 0.0);
+#pragma unroll
+      for (int off = 1; off < 32; off <<= 1) {
+#pragma unroll
+        for (int k = 0; k < K; k++) {
+          const double o = __shfl_down_sync(0xffffffffu, a[k], off);
+          if ((lane & (2 * off - 1)) == 0) a[k] = ((maxmask >> k) & 1u) ? fmax(a[k], o) : a[k] + o;
+        }
       }
-      v[k] = a;
+      if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < K; k++) sres[k] = a[k];
     }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < K; k++) v[k] = sres[k];
+    __syncthreads();
     phase ^= 1;
   }
 

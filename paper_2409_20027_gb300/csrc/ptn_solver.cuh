@@ -1728,7 +1728,7 @@ __global__ void __launch_bounds__(256) k_solve_cta(KArgs args, Work<L> w) {
   const int bi = blockIdx.x;
   if (bi >= args.B) return;
   load_prob<N, U>(P, *args.prob, args.xref ? args.xref + (size_t)bi * N : nullptr, args.inst[bi].dt);
-  const OptDev O = *args.opt;
+  const OptDev& O = *args.opt;  // read where used (a local copy would hold ~50 registers)
   const InstDev id = args.inst[bi];
   CtaGroup g{scratch};
   Inst<M, L> I;
@@ -1746,7 +1746,7 @@ __global__ void __launch_bounds__(128) k_solve_grid(KArgs args, Work<L> w) {
   __shared__ int sdead;
   if (threadIdx.x == 0) sdead = 0;
   load_prob<N, U>(P, *args.prob, args.xref, args.inst[0].dt);
-  const OptDev O = *args.opt;
+  const OptDev& O = *args.opt;  // read where used (a local copy would hold ~50 registers)
   const InstDev id = args.inst[0];
   GridGroup g{scratch, args.gs, 0, &sdead};
   Inst<M, L> I;
@@ -1822,7 +1822,7 @@ __global__ void __launch_bounds__(64) k_solve_seq(KArgs args, Work<L> w) {
   if (bi >= args.B) return;  // no group barriers below: threads are independent
   ProbS<N, U> P;
   load_prob_thread<N, U>(P, *args.prob, args.xref ? args.xref + (size_t)bi * N : nullptr, args.inst[bi].dt);
-  const OptDev O = *args.opt;
+  const OptDev& O = *args.opt;  // read where used (a local copy would hold ~50 registers)
   const InstDev id = args.inst[bi];
   SeqGroup g;
   Inst<M, L> I;
@@ -1842,7 +1842,7 @@ __global__ void __launch_bounds__(256) k_solve_cluster(KArgs args, Work<L> w) {
   constexpr int XB = (int)((sizeof(Val<N, double>) > 64 ? sizeof(Val<N, double>) : 64) + 15) / 16 * 16;
   char* xch = scratch + ((sbytes + 15) & ~size_t(15));
   load_prob<N, U>(P, *args.prob, args.xref, args.inst[0].dt);
-  const OptDev O = *args.opt;
+  const OptDev& O = *args.opt;  // read where used (a local copy would hold ~50 registers)
   const InstDev id = args.inst[0];
   ClusterGroup g{scratch, xch, XB, 0};
   g.sync();  // every CTA of the cluster is running before any DSMEM access

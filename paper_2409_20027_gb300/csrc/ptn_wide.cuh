@@ -895,7 +895,7 @@ __global__ void __launch_bounds__(512) k_solve_wide(KArgs args, Work<L> w) {
   const int bi = blockIdx.x;
   if (bi >= args.B) return;
   load_prob<N, U>(P, *args.prob, args.xref ? args.xref + (size_t)bi * N : nullptr, args.inst[bi].dt);
-  const OptDev O = *args.opt;
+  const OptDev& O = *args.opt;  // read where used (a local copy would hold ~50 registers)
   const InstDev id = args.inst[bi];
   Inst<M, L> I;
   I.setup(w, id, args.x0 + (size_t)bi * N, g.warp(), nw, P.nw);
