@@ -280,12 +280,24 @@ def run_mpc(ptn, W, dev, stream):
     res = mpc.closed_loop(sv, x0, N, steps)
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
+    # the same loop with every period replayed from one captured CUDA graph
+    gl = mpc.GraphLoop(sv, x0, N)
+    gl.run(2)  # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    resg = gl.run(steps)
+    torch.cuda.synchronize()
+    wall_g = time.perf_counter() - t0
+    same = bool(torch.equal(res["x"], resg["x"]) and torch.equal(res["u"], resg["u"]))
+    del gl
     sv.close()
     st = res["status"]
     its = res["iters"]
     return {"workload": f"{B} closed cart-pole loops, N={N}, 100 Hz (dt=0.01, RK4), {steps} periods, shifted warm "
                         "start, fp32 LQR with fp64 solves, one batched solve per period",
             "period_ms": 1e3 * wall / steps, "loop_periods_per_s": B * steps / wall,
+            "graph_period_ms": 1e3 * wall_g / steps, "graph_loop_periods_per_s": B * steps / wall_g,
+            "graph_same_trajectories": same,
             "newton_iters_first": float(its[0].mean()), "newton_iters_warm": float(its[1:].mean()),
             "converged_share": float((st == 0).mean()),
             "final_state_max_abs_err": float((res["x"][-1] - torch.tensor([0.0, np.pi, 0.0, 0.0], device=dev))

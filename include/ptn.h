@@ -165,6 +165,30 @@ int ptn_solve_batch(ptn_solver* s, int method, int B, const int* T_b, const doub
                     const double* x0, const double* xref, const double* u_init, double* x_out,
                     double* u_out, double* lam_out, ptn_info* info_b, void* stream);
 
+/* Graph-capturable batch solves.  ptn_batch_prepare validates a batch layout (method, B,
+ * T_b, dt_b as in ptn_solve_batch), fixes the execution tier and launch shape from the
+ * handle's current options, copies the instance table and the options to device buffers
+ * reserved for it, and synchronises `stream`.  The layout stays in force until the next
+ * ptn_batch_prepare on this handle; synchronous solves in between do not change it, and
+ * later option changes reach it only through another prepare.  Returns PTN_OK or
+ * PTN_ERR_INVALID_ARG / PTN_ERR_CUDA (with ptn_last_error). */
+int ptn_batch_prepare(ptn_solver* s, int method, int B, const int* T_b, const double* dt_b,
+                      void* stream);
+
+/* Enqueue one solve of the prepared batch on `stream` and return without waiting: kernel
+ * launches only (for a single instance on the cooperative grid tier, two memsets of its
+ * barrier counters before the kernel), no host<->device copy, no allocation, no
+ * synchronisation -- so the call can be recorded by CUDA stream capture and replayed as a
+ * graph (the pointers are then fixed in the graph; update the inputs in place).  Device
+ * arguments as in ptn_solve_batch.  info_dev: device array of B ptn_info records that the
+ * kernel fills (status, iterations, residuals; read it after the stream has reached the
+ * solve), or NULL to keep them in the handle.  ADMM's z, v stay in the handle's workspace.
+ * Returns PTN_OK when the work was enqueued, PTN_ERR_INVALID_ARG without a prepared batch,
+ * PTN_ERR_CUDA when a launch failed; the solve's own status is in info_dev. */
+int ptn_solve_batch_async(ptn_solver* s, const double* x0, const double* xref, const double* u_init,
+                          double* x_out, double* u_out, double* lam_out, ptn_info* info_dev,
+                          void* stream);
+
 /* Gradients of the scalar loss  gJ * J* + <gx, x*> + <gu, u*>  at B solutions of the
  * barrier problem (at the problem's own dt) with weight mu (J* = optimal barrier objective; x*, u* concatenated as
  * in ptn_solve_batch), with respect to x0 (B x nx), diag Q (B x nx), diag R (B x nu),

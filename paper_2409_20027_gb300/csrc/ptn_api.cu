@@ -60,6 +60,13 @@ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 }  // namespace
 
+// Launch shape of one solve call, fixed on the host before anything is enqueued.
+struct LaunchPlan {
+  launch_fn fn = nullptr;
+  int method = 0, precision = 0, B = 0, tier = 0, nblocks = 0, nthreads = 0;
+  long long steps = 0;
+};
+
 struct ptn_solver {
   ptn_options opt;
   ProbDev hprob;
@@ -77,6 +84,12 @@ struct ptn_solver {
   InfoDev* hinfo = nullptr;  // pinned
   OptDev* hopt = nullptr;    // pinned
   GridScratch gs{};
+  // batch prepared for ptn_solve_batch_async: its own instance table and option record,
+  // so that synchronous solves in between do not change what a captured graph reads
+  InstDev* dinst_a = nullptr;
+  OptDev* dopt_a = nullptr;
+  LaunchPlan plan_a{};
+  bool plan_a_ok = false;
   int grid_cap_blocks = 0;
   int num_sms = 0;
   char err[512];
@@ -167,6 +180,8 @@ extern "C" void ptn_solver_destroy(ptn_solver* s) {
   cudaFree(s->ws);
   cudaFree(s->dinst);
   cudaFree(s->dinfo);
+  cudaFree(s->dinst_a);
+  cudaFree(s->dopt_a);
   cudaFree(s->gs.bar);
   cudaFree(s->gs.err);
   cudaFree(s->gs.red);
@@ -248,6 +263,8 @@ extern "C" int ptn_solver_create(const ptn_problem* prob, const ptn_options* opt
   CK(cudaMalloc(&s->dopt, sizeof(OptDev)));
   CK(cudaMalloc(&s->dinst, sizeof(InstDev) * max_batch));
   CK(cudaMalloc(&s->dinfo, sizeof(InfoDev) * max_batch));
+  CK(cudaMalloc(&s->dinst_a, sizeof(InstDev) * max_batch));
+  CK(cudaMalloc(&s->dopt_a, sizeof(OptDev)));
   CK(cudaMallocHost(&s->hinst, sizeof(InstDev) * max_batch));
   CK(cudaMallocHost(&s->hinfo, sizeof(InfoDev) * max_batch));
   CK(cudaMallocHost(&s->hopt, sizeof(OptDev)));
@@ -329,49 +346,44 @@ static void from_info(const InfoDev& d, ptn_info* o) {
   o->r_kkt = d.r_kkt; o->J = d.J; o->J_c = d.J_c; o->r_p = d.r_p; o->r_d = d.r_d;
 }
 
-static int solve_common(ptn_solver* s, int method, int B, const int* T_b, const double* x0, const double* xref,
-                        const double* u_init, double* x_out, double* u_out, double* lam_out, double* z_out,
-                        double* v_out, ptn_info* info, void* stream_, const double* dt_b = nullptr) {
-  if (!s) return PTN_ERR_INVALID_ARG;
-  s->err[0] = 0;
-  cudaStream_t st = (cudaStream_t)stream_;
-  if (method != PTN_METHOD_IP && method != PTN_METHOD_ADMM) return fail(s, PTN_ERR_INVALID_ARG, "bad method");
+// Validate the horizons (and optional time steps) of a batch and fill the instance table
+// hi: per-instance offsets into the concatenated time axis.  *steps = sum of T_b.
+static int fill_instances(ptn_solver* s, int B, const int* T_b, const double* dt_b, InstDev* hi,
+                          long long* steps_out) {
   if (B < 1 || B > s->cap_batch) return fail(s, PTN_ERR_INVALID_ARG, "B=%d outside [1, %d]", B, s->cap_batch);
-  if (!T_b || !x0 || !x_out || !u_out) return fail(s, PTN_ERR_INVALID_ARG, "NULL argument");
+  if (!T_b) return fail(s, PTN_ERR_INVALID_ARG, "NULL argument");
   long long steps = 0;
   for (int i = 0; i < B; i++) {
     if (T_b[i] < 1) return fail(s, PTN_ERR_INVALID_ARG, "horizon T_b[%d]=%d must be >= 1", i, T_b[i]);
     if (dt_b && !(dt_b[i] > 0 && isfinite(dt_b[i])))
       return fail(s, PTN_ERR_INVALID_ARG, "time step dt_b[%d] must be positive and finite", i);
-    s->hinst[i].T = T_b[i];
-    s->hinst[i].uoff = (int)steps;
-    s->hinst[i].xoff = (int)(steps + i);
-    s->hinst[i].pad = 0;
-    s->hinst[i].dt = dt_b ? dt_b[i] : 0.0;
+    hi[i].T = T_b[i];
+    hi[i].uoff = (int)steps;
+    hi[i].xoff = (int)(steps + i);
+    hi[i].pad = 0;
+    hi[i].dt = dt_b ? dt_b[i] : 0.0;
     steps += T_b[i];
   }
   if (steps > s->cap_steps)
     return fail(s, PTN_ERR_INVALID_ARG, "total horizon %lld exceeds the workspace (%lld)", steps, s->cap_steps);
-  to_optdev(s->opt, method, s->hopt);
-  CK(cudaMemcpyAsync(s->dinst, s->hinst, sizeof(InstDev) * B, cudaMemcpyHostToDevice, st));
-  CK(cudaMemcpyAsync(s->dopt, s->hopt, sizeof(OptDev), cudaMemcpyHostToDevice, st));
+  *steps_out = steps;
+  return PTN_OK;
+}
+
+// Choose the execution tier and launch shape of a solve of B instances (host-side
+// occupancy queries only, no stream work) and set the kernel's function attributes for
+// it, so that the launch itself needs no other runtime call.
+static int plan_launch(ptn_solver* s, int method, int B, const int* T_b, long long steps, LaunchPlan* p) {
   launch_fn fn = pick_launcher(s->hprob.model, s->opt.precision);
   if (!fn) return fail(s, PTN_ERR_INVALID_ARG, "kernels for model %d, precision %d are not built", s->hprob.model, s->opt.precision);
+  *p = LaunchPlan{};
+  p->fn = fn;
+  p->method = method;
+  p->B = B;
+  p->steps = steps;
+  p->precision = s->opt.precision;
   LaunchReq q{};
   q.precision = s->opt.precision;
-  q.stream = st;
-  q.w = s->w;
-  q.w.xA = x_out;
-  q.w.uA = u_out;
-  if (lam_out) q.w.lam = lam_out;
-  q.args.prob = s->dprob;
-  q.args.opt = s->dopt;
-  q.args.inst = s->dinst;
-  q.args.x0 = x0;
-  q.args.xref = xref;
-  q.args.u_init = u_init;
-  q.args.info = s->dinfo;
-  q.args.B = B;
   // one instance: a thread-block cluster when the horizon needs 2..16 CTAs, else the
   // cooperative grid from grid_min_T on, else one CTA
   int cl_blocks = 0;
@@ -387,57 +399,111 @@ static int solve_common(ptn_solver* s, int method, int B, const int* T_b, const 
       q.query = 1;
       q.max_blocks = &maxc;
       CK(fn(q));
-      q.query = 0;
       if (need <= maxc) cl_blocks = (int)need;
     }
   }
   const bool grid = !wide && !cl_blocks && B == 1 && s->opt.grid_min_T > 0 && T_b[0] >= s->opt.grid_min_T;
   if (s->opt.sequential && !wide) {
-    q.tier = 5;
-    q.nthreads = 32;
-    q.nblocks = (B + 31) / 32;
-    CK(fn(q));
+    p->tier = 5;
+    p->nthreads = 32;
+    p->nblocks = (B + 31) / 32;
   } else if (wide) {
-    q.tier = 4;
-    q.nthreads = s->opt.block_threads;
-    q.nblocks = B;
-    CK(fn(q));
+    p->tier = 4;
+    p->nthreads = s->opt.block_threads;
+    p->nblocks = B;
   } else if (cl_blocks) {
-    q.tier = 2;
-    q.nthreads = s->opt.block_threads;
-    q.nblocks = cl_blocks;
-    CK(fn(q));
+    p->tier = 2;
+    p->nthreads = s->opt.block_threads;
+    p->nblocks = cl_blocks;
   } else if (grid) {
+    p->tier = 1;
+    p->nthreads = 128;
+    int maxb = 0;
     q.tier = 1;
     q.nthreads = 128;
-    int maxb = 0;
     q.query = 1;
     q.max_blocks = &maxb;
     CK(fn(q));
-    q.query = 0;
-    int want = (int)((T_b[0] + (long long)q.nthreads * s->opt.grid_steps_per_thread - 1) /
-                     ((long long)q.nthreads * s->opt.grid_steps_per_thread));
+    int want = (int)((T_b[0] + (long long)p->nthreads * s->opt.grid_steps_per_thread - 1) /
+                     ((long long)p->nthreads * s->opt.grid_steps_per_thread));
     int nb = want < maxb ? want : maxb;
     if (nb > s->grid_cap_blocks) nb = s->grid_cap_blocks;
     if (nb < 1) nb = 1;
-    q.nblocks = nb;
+    p->nblocks = nb;
+  } else {
+    p->tier = 0;
+    p->nthreads = s->opt.block_threads;
+    p->nblocks = B;
+  }
+  q = LaunchReq{};
+  q.precision = p->precision;
+  q.tier = p->tier;
+  q.nthreads = p->nthreads;
+  q.nblocks = p->nblocks;
+  q.query = 2;
+  CK(fn(q));
+  return PTN_OK;
+}
+
+// Enqueue a planned solve on st: the kernel launch (preceded, for the cooperative grid
+// tier, by the reset of its barrier counters).  No host<->device copy, no
+// synchronisation, no allocation.
+static int enqueue(ptn_solver* s, const LaunchPlan& p, const OptDev* dopt, const InstDev* dinst, const double* x0,
+                   const double* xref, const double* u_init, double* x_out, double* u_out, double* lam_out,
+                   InfoDev* dinfo, cudaStream_t st) {
+  LaunchReq q{};
+  q.precision = p.precision;
+  q.stream = st;
+  q.tier = p.tier;
+  q.nthreads = p.nthreads;
+  q.nblocks = p.nblocks;
+  q.attrs_set = 1;
+  q.w = s->w;
+  q.w.xA = x_out;
+  q.w.uA = u_out;
+  if (lam_out) q.w.lam = lam_out;
+  q.args.prob = s->dprob;
+  q.args.opt = dopt;
+  q.args.inst = dinst;
+  q.args.x0 = x0;
+  q.args.xref = xref;
+  q.args.u_init = u_init;
+  q.args.info = dinfo;
+  q.args.B = p.B;
+  if (p.tier == 1) {
     q.args.gs = s->gs;
     CK(cudaMemsetAsync(s->gs.bar, 0, 2 * sizeof(unsigned), st));
     CK(cudaMemsetAsync(s->gs.err, 0, sizeof(int), st));
-    CK(fn(q));
-  } else {
-    q.tier = 0;
-    q.nthreads = s->opt.block_threads;
-    q.nblocks = B;
-    CK(fn(q));
   }
+  CK(p.fn(q));
+  return PTN_OK;
+}
+
+static int solve_common(ptn_solver* s, int method, int B, const int* T_b, const double* x0, const double* xref,
+                        const double* u_init, double* x_out, double* u_out, double* lam_out, double* z_out,
+                        double* v_out, ptn_info* info, void* stream_, const double* dt_b = nullptr) {
+  if (!s) return PTN_ERR_INVALID_ARG;
+  s->err[0] = 0;
+  cudaStream_t st = (cudaStream_t)stream_;
+  if (method != PTN_METHOD_IP && method != PTN_METHOD_ADMM) return fail(s, PTN_ERR_INVALID_ARG, "bad method");
+  if (!x0 || !x_out || !u_out) return fail(s, PTN_ERR_INVALID_ARG, "NULL argument");
+  long long steps = 0;
+  int rc = fill_instances(s, B, T_b, dt_b, s->hinst, &steps);
+  if (rc) return rc;
+  LaunchPlan p;
+  rc = plan_launch(s, method, B, T_b, steps, &p);
+  if (rc) return rc;
+  to_optdev(s->opt, method, s->hopt);
+  CK(cudaMemcpyAsync(s->dinst, s->hinst, sizeof(InstDev) * B, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(s->dopt, s->hopt, sizeof(OptDev), cudaMemcpyHostToDevice, st));
+  rc = enqueue(s, p, s->dopt, s->dinst, x0, xref, u_init, x_out, u_out, lam_out, s->dinfo, st);
+  if (rc) return rc;
   CK(cudaMemcpyAsync(s->hinfo, s->dinfo, sizeof(InfoDev) * B, cudaMemcpyDeviceToHost, st));
   if (method == PTN_METHOD_ADMM && s->nw > 0) {
     if (z_out) CK(cudaMemcpyAsync(z_out, s->w.z, sizeof(double) * steps * s->nw, cudaMemcpyDeviceToDevice, st));
     if (v_out) CK(cudaMemcpyAsync(v_out, s->w.v, sizeof(double) * steps * s->nw, cudaMemcpyDeviceToDevice, st));
   }
   CK(cudaStreamSynchronize(st));
-  int rc = PTN_OK;
   for (int i = 0; i < B; i++) {
     if (info) from_info(s->hinfo[i], info + i);
     if (rc == PTN_OK && s->hinfo[i].status != 0) rc = s->hinfo[i].status;
@@ -464,6 +530,45 @@ extern "C" int ptn_solve_batch(ptn_solver* s, int method, int B, const int* T_b,
                                double* u_out, double* lam_out, ptn_info* info_b, void* stream) {
   return solve_common(s, method, B, T_b, x0, xref, u_init, x_out, u_out, lam_out, nullptr, nullptr, info_b,
                       stream, dt_b);
+}
+
+// The kernels write ptn_info records directly into ptn_solve_batch_async's info_dev.
+static_assert(sizeof(InfoDev) == sizeof(ptn_info), "InfoDev must match ptn_info");
+static_assert(offsetof(InfoDev, mu) == offsetof(ptn_info, mu), "InfoDev must match ptn_info");
+static_assert(offsetof(InfoDev, r_d) == offsetof(ptn_info, r_d), "InfoDev must match ptn_info");
+static_assert(offsetof(InfoDev, cyc) == offsetof(ptn_info, cycles), "InfoDev must match ptn_info");
+
+extern "C" int ptn_batch_prepare(ptn_solver* s, int method, int B, const int* T_b, const double* dt_b,
+                                 void* stream) {
+  if (!s) return PTN_ERR_INVALID_ARG;
+  s->err[0] = 0;
+  s->plan_a_ok = false;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (method != PTN_METHOD_IP && method != PTN_METHOD_ADMM) return fail(s, PTN_ERR_INVALID_ARG, "bad method");
+  long long steps = 0;
+  int rc = fill_instances(s, B, T_b, dt_b, s->hinst, &steps);
+  if (rc) return rc;
+  LaunchPlan p;
+  rc = plan_launch(s, method, B, T_b, steps, &p);
+  if (rc) return rc;
+  to_optdev(s->opt, method, s->hopt);
+  CK(cudaMemcpyAsync(s->dinst_a, s->hinst, sizeof(InstDev) * B, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(s->dopt_a, s->hopt, sizeof(OptDev), cudaMemcpyHostToDevice, st));
+  CK(cudaStreamSynchronize(st));
+  s->plan_a = p;
+  s->plan_a_ok = true;
+  return PTN_OK;
+}
+
+extern "C" int ptn_solve_batch_async(ptn_solver* s, const double* x0, const double* xref, const double* u_init,
+                                     double* x_out, double* u_out, double* lam_out, ptn_info* info_dev,
+                                     void* stream) {
+  if (!s) return PTN_ERR_INVALID_ARG;
+  if (!s->plan_a_ok) return fail(s, PTN_ERR_INVALID_ARG, "no batch prepared (ptn_batch_prepare)");
+  if (!x0 || !x_out || !u_out) return fail(s, PTN_ERR_INVALID_ARG, "NULL argument");
+  InfoDev* di = info_dev ? reinterpret_cast<InfoDev*>(info_dev) : s->dinfo;
+  return enqueue(s, s->plan_a, s->dopt_a, s->dinst_a, x0, xref, u_init, x_out, u_out, lam_out, di,
+                 (cudaStream_t)stream);
 }
 
 extern "C" int ptn_adjoint(ptn_solver* s, int B, const int* T_b, const double* x0, const double* xref,

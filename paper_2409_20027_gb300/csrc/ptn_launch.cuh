@@ -28,7 +28,10 @@ struct LaunchReq {
                   // 5: sequential-in-time baseline (one thread per instance)
   int precision;  // 0: FP64, 1: FP32 with FP64 solves, 2: FP32
   int nblocks, nthreads;
-  int query;      // 1: only report max co-resident grid blocks in *max_blocks
+  int query;      // 1: only report max co-resident grid blocks in *max_blocks;
+                  // 2: only set the kernel's function attributes for this launch shape
+  int attrs_set;  // nonzero: the attributes were set by an earlier query 2, launch only
+                  // (no runtime call besides the launch, so that it can be graph-captured)
   int* max_blocks;
   size_t* elem_bytes;  // out: bytes of the largest scan element
   KArgs args;
@@ -44,8 +47,10 @@ cudaError_t launch_typed(LaunchReq& q) {
   const size_t smem = ((sizeof(ProbS<N, U>) + 15) & ~size_t(15)) + scratch_bytes<N, U, L>(nthreads / 32);
   if (q.elem_bytes) *q.elem_bytes = sizeof(Val<N, L>);
   if (q.tier == 0) {
-    cudaError_t e = cudaFuncSetAttribute(k_solve_cta<M, L, SV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
+    if (!q.attrs_set) {
+      cudaError_t e = cudaFuncSetAttribute(k_solve_cta<M, L, SV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+    }
     if (q.query) return cudaSuccess;
     k_solve_cta<M, L, SV><<<q.nblocks, nthreads, smem, q.stream>>>(q.args, typed<L>(q.w));
     return cudaGetLastError();
@@ -70,10 +75,14 @@ cudaError_t launch_typed(LaunchReq& q) {
   }
   if (q.tier == 2) {
     const size_t smc = ((smem + 15) & ~size_t(15)) + cluster_xch_bytes<N, U, L>();
-    cudaError_t e = cudaFuncSetAttribute(k_solve_cluster<M, L, SV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smc);
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_solve_cluster<M, L, SV>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    if (e != cudaSuccess) return e;
+    cudaError_t e = cudaSuccess;
+    if (!q.attrs_set) {
+      e = cudaFuncSetAttribute(k_solve_cluster<M, L, SV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smc);
+      if (e != cudaSuccess) return e;
+      e = cudaFuncSetAttribute(k_solve_cluster<M, L, SV>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+      if (e != cudaSuccess) return e;
+    }
+    if (q.query == 2) return cudaSuccess;
     if (q.query) {
       // largest cluster of these CTAs the device can co-schedule (the cluster
       // dimension in cfg is ignored by the query)
@@ -100,8 +109,12 @@ cudaError_t launch_typed(LaunchReq& q) {
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, k_solve_cluster<M, L, SV>, q.args, typed<L>(q.w));
   }
-  cudaError_t e = cudaFuncSetAttribute(k_solve_grid<M, L, SV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
+  cudaError_t e = cudaSuccess;
+  if (!q.attrs_set) {
+    e = cudaFuncSetAttribute(k_solve_grid<M, L, SV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  if (q.query == 2) return cudaSuccess;
   if (q.query) {
     int dev = 0, per = 0, sms = 0;
     cudaGetDevice(&dev);
@@ -111,10 +124,19 @@ cudaError_t launch_typed(LaunchReq& q) {
     *q.max_blocks = per * sms;
     return cudaSuccess;
   }
-  Work<L> w = typed<L>(q.w);
-  void* params[] = {(void*)&q.args, (void*)&w};
-  return cudaLaunchCooperativeKernel((const void*)k_solve_grid<M, L, SV>, dim3(q.nblocks), dim3(nthreads), params, smem,
-                                     q.stream);
+  // cooperative launch (all CTAs co-resident) through the extensible launch call, which a
+  // stream capture records as a cooperative kernel node
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(q.nblocks);
+  cfg.blockDim = dim3(nthreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = q.stream;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeCooperative;
+  at[0].val.cooperative = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_solve_grid<M, L, SV>, q.args, typed<L>(q.w));
 }
 
 

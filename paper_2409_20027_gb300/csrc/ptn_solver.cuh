@@ -1590,7 +1590,7 @@ __device__ void solve_instance(Grp& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>&
   info.status = ST_OK; info.newton_iters = 0; info.outer_iters = 0; info.ls_rejects = 0;
   info.factor_fails = 0; info.roll_fails = 0; info.roll_iters = 0; info.ls_evals = 0;
   info.mu = 0; info.alpha = 0; info.r_stat = 0; info.r_dyn = 0; info.r_feas = 0; info.r_kkt = 0;
-  info.J = 0; info.J_c = 0; info.r_p = 0; info.r_d = 0;
+  info.J = 0; info.J_c = 0; info.r_p = 0; info.r_d = 0; info.pad_ = 0;
   for (int t = I.a; t < I.b; t++) {
 #pragma unroll
     for (int i = 0; i < U; i++) {

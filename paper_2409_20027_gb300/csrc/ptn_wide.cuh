@@ -1198,14 +1198,17 @@ cudaError_t launch_wide(LaunchReq& q) {
       return cudaErrorNotSupported;
     }
   }
-  if (q.query) {
+  if (q.query == 1) {
     if (q.max_blocks) *q.max_blocks = 0;
     return cudaSuccess;
   }
   const int nw = q.nthreads / 32;
   const size_t smem = wide_smem_bytes<M, L>(nw);
-  cudaError_t e = cudaFuncSetAttribute(k_solve_wide<M, L, SV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
+  if (!q.attrs_set) {
+    cudaError_t e = cudaFuncSetAttribute(k_solve_wide<M, L, SV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  if (q.query == 2) return cudaSuccess;
   k_solve_wide<M, L, SV><<<q.nblocks, q.nthreads, smem, q.stream>>>(q.args, typed<L>(q.w));
   return cudaGetLastError();
 }

@@ -24,7 +24,8 @@ STATUS = {0: "ok", -1: "invalid argument", -2: "infeasible start", -3: "not conv
 
 EXPORTS = ["ptn_default_options", "ptn_solver_create", "ptn_solver_destroy", "ptn_last_error",
            "ptn_set_options", "ptn_solve_ip", "ptn_solve_admm", "ptn_solve_batch", "ptn_adjoint",
-           "ptn_num_rows", "ptn_version", "ptn_solve_ip_static"]
+           "ptn_num_rows", "ptn_version", "ptn_solve_ip_static", "ptn_batch_prepare",
+           "ptn_solve_batch_async"]
 
 _P = C.POINTER(C.c_double)
 
@@ -92,6 +93,8 @@ def load(path: str = LIB_PATH):
         lib.ptn_num_rows.argtypes = [vp]
         lib.ptn_solve_ip_static.argtypes = [C.POINTER(Problem), C.POINTER(Options), vp, vp, C.c_int, vp, vp, vp,
                                             C.POINTER(Info), C.c_char_p, C.c_int, vp]
+        lib.ptn_batch_prepare.argtypes = [vp, C.c_int, C.c_int, ip, C.POINTER(C.c_double), vp]
+        lib.ptn_solve_batch_async.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp]
         lib.ptn_version.restype = C.c_char_p
         _lib = lib
     return _lib
@@ -231,6 +234,49 @@ class Solver:
                                _stream(stream))
         return x_out, u_out, lam_out, [i.as_dict() for i in infos]
 
+    def prepare_batch(self, T_b, method: int = METHOD_IP, dt_b=None, stream=None):
+        """Fix a batch layout (horizons, time steps, method) and its launch shape for
+        solve_batch_async; synchronises the stream.  Raises PtnError on invalid input."""
+        self._prepared = None
+        Tb = np.ascontiguousarray(np.asarray(T_b, dtype=np.int32))
+        B = len(Tb)
+        dtb = None if dt_b is None else np.ascontiguousarray(np.asarray(dt_b, dtype=np.float64))
+        if dtb is not None and dtb.shape != (B,):
+            raise ValueError("dt_b must have one entry per instance")
+        rc = load().ptn_batch_prepare(self._h, int(method), B, Tb.ctypes.data_as(C.POINTER(C.c_int)),
+                                      None if dtb is None else dtb.ctypes.data_as(C.POINTER(C.c_double)),
+                                      _stream(stream))
+        if rc != 0:
+            raise PtnError(f"ptn_batch_prepare: {self.last_error()} ({rc})")
+        self._prepared = (B, int(Tb.sum()))
+
+    def new_info_buffer(self, B: int, device="cuda"):
+        """Device buffer for B ptn_info records (solve_batch_async's info_dev)."""
+        import torch
+        return torch.zeros(B * C.sizeof(Info), dtype=torch.uint8, device=device)
+
+    def solve_batch_async(self, x0, xref=None, u_init=None, x_out=None, u_out=None, lam_out=None,
+                          info_dev=None, stream=None):
+        """Enqueue a solve of the prepared batch without waiting (graph-capturable: kernel
+        launches only).  Outputs are allocated when not given (inside a capture they come
+        from the graph's pool).  Returns (x, u, lam, info_dev); decode info_dev with
+        infos_from_device once the stream has passed the solve."""
+        if getattr(self, "_prepared", None) is None:
+            raise PtnError("no batch prepared (prepare_batch)")
+        B, S = self._prepared
+        x_out = self._out(S + B, self.nx, x0) if x_out is None else x_out
+        u_out = self._out(S, self.nu, x0) if u_out is None else u_out
+        lam_out = self._out(S + B, self.nx, x0) if lam_out is None else lam_out
+        info_dev = self.new_info_buffer(B, x0.device) if info_dev is None else info_dev
+        if info_dev.numel() < B * C.sizeof(Info) or not info_dev.is_cuda or not info_dev.is_contiguous():
+            raise ValueError("info_dev must be a contiguous CUDA buffer of B ptn_info records")
+        rc = load().ptn_solve_batch_async(self._h, _dptr(x0), _dptr(xref), _dptr(u_init), _dptr(x_out),
+                                          _dptr(u_out), _dptr(lam_out), C.c_void_p(info_dev.data_ptr()),
+                                          _stream(stream))
+        if rc != 0:
+            raise PtnError(f"ptn_solve_batch_async: {self.last_error()} ({rc})")
+        return x_out, u_out, lam_out, info_dev
+
     def adjoint(self, T_b, x0, x_star, u_star, mu: float, gJ: float = 1.0, gx=None, gu=None, xref=None,
                 stream=None):
         """Gradients of gJ J* + <gx, x*> + <gu, u*> w.r.t. x0, diag Q, diag R, diag Qf, prm."""
@@ -247,6 +293,19 @@ class Solver:
         if rc != 0:
             raise PtnError(f"ptn_adjoint failed ({rc}): {self.last_error()}")
         return out
+
+
+def infos_from_device(info_dev, B: int):
+    """Decode B ptn_info records from a device (or host) byte buffer into dicts (copies to
+    the host, so it waits for the work that writes them)."""
+    raw = info_dev[: B * C.sizeof(Info)].cpu().numpy().tobytes()
+    return [r.as_dict() for r in (Info * B).from_buffer_copy(raw)]
+
+
+def status_view(info_dev, B: int):
+    """(B, 2) int32 device view of the status and Newton-iteration fields of the records."""
+    import torch
+    return info_dev[: B * C.sizeof(Info)].view(-1).view(torch.int32).reshape(B, -1)[:, :2]
 
 
 def _make_problem(prob):

@@ -36,3 +36,22 @@ def test_closed_loop_follows_oracle_loop():
             x = r["x"][1]
             ui = np.concatenate([r["u"][1:], r["u"][-1:]])
             assert np.abs(X[k + 1, b] - x).max() <= 1e-6 * max(1.0, np.abs(x).max()), (b, k)
+
+
+@pytest.mark.gpu
+def test_closed_loop_graph_replays_the_same_loop():
+    # each period replayed from one captured CUDA graph: the same states, controls and
+    # iteration counts as the loop that calls the synchronous batched solve
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    from paper_2409_20027_gb300 import mpc, ptn
+    p = W.cartpole()
+    T, steps, B = 40, 8, 6
+    x0 = torch.tensor(W.cartpole_batch_x0(B, 4), device="cuda:0")
+    s = ptn.Solver(p, max_T=T, max_batch=B, precision=ptn.PTN_FP32_FP64SOLVE, block_threads=32)
+    a = mpc.closed_loop(s, x0, T, steps)
+    b = mpc.closed_loop_graph(s, x0, T, steps)
+    assert (a["status"] == 0).all() and (b["status"] == 0).all()
+    assert torch.equal(a["x"], b["x"]) and torch.equal(a["u"], b["u"])
+    assert (a["iters"] == b["iters"]).all()
