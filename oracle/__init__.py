@@ -61,7 +61,8 @@ class _Options(C.Structure):
     _fields_ = [(k, C.c_double) for k in
                 ["mu0", "zeta", "mu_final", "tol_inner", "tol_final", "rho", "admm_tol",
                  "alpha0", "alpha_min", "alpha_max", "ls_beta", "armijo_c1", "armijo_eps"]] + \
-               [(k, C.c_int) for k in ["max_newton", "max_outer", "ls_count", "admm_fixed_iters"]]
+               [(k, C.c_int) for k in ["max_newton", "max_outer", "ls_count", "admm_fixed_iters",
+                                       "costate_mode"]]
 
 
 class _Aug(C.Structure):
@@ -92,6 +93,9 @@ class Options:
     max_outer: int = 2000
     ls_count: int = 10
     admm_fixed_iters: int = 0
+    # 0: co-states by the backward recursion (Sec. III-B); 1: multiplier form, a variant
+    # that updates multipliers of the dynamics by the LQR duals (no recursion through F^T)
+    costate_mode: int = 0
 
     def _c(self) -> _Options:
         o = _Options()
@@ -244,6 +248,23 @@ def newton_direction(prob, x, u, alpha, aug="barrier", mu=0.1, rho=1.0, z=None, 
     keys = ["lam", "d", "S", "s", "Gam", "gam", "dx", "du", "P", "M", "R", "F", "G"]
     st = lib().orc_newton_direction(b.ref(), C.byref(a), C.c_int(T), _ptr(x), _ptr(u),
                                     C.c_double(alpha), *[_ptr(out[k]) for k in keys], _ptr(g12))
+    out["G1"], out["G2"], out["status"] = g12[0], g12[1], int(st)
+    return out
+
+
+def newton_direction_mult(prob, x, u, nu, alpha, aug="barrier", mu=0.1, rho=1.0, z=None, v=None):
+    """One Newton step of the multiplier form (a variant, not in the paper: multipliers nu
+    of the dynamics instead of the co-state recursion of Sec. III-B) at (x, u, nu): dict
+    with q, d, dx, du, dnu (dual step S_t dx_t + s_t), G1, G2 and status."""
+    b = _Bound(prob); x = _arr(x); u = _arr(u); T = u.shape[0]; n, m = b.n, b.m
+    nu = _arr(nu, (T + 1, n))
+    a, keep = _aug(aug, mu, rho, z, v, num_rows(prob))
+    out = dict(q=np.zeros((T + 1, n)), d=np.zeros((T, m)), dx=np.zeros((T + 1, n)),
+               du=np.zeros((T, m)), dnu=np.zeros((T + 1, n)))
+    g12 = np.zeros(2)
+    st = lib().orc_newton_direction_mult(b.ref(), C.byref(a), C.c_int(T), _ptr(x), _ptr(u), _ptr(nu),
+                                         C.c_double(alpha), _ptr(out["q"]), _ptr(out["d"]),
+                                         _ptr(out["dx"]), _ptr(out["du"]), _ptr(out["dnu"]), _ptr(g12))
     out["G1"], out["G2"], out["status"] = g12[0], g12[1], int(st)
     return out
 

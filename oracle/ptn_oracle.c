@@ -58,6 +58,8 @@ typedef struct orc_options {
     double mu0, zeta, mu_final, tol_inner, tol_final, rho, admm_tol;
     double alpha0, alpha_min, alpha_max, ls_beta, armijo_c1, armijo_eps;
     int max_newton, max_outer, ls_count, admm_fixed_iters;
+    int costate_mode; /* 0: co-states by the backward recursion (Sec. III-B);
+                         1: multiplier form (dynamics multipliers updated by the LQR duals) */
 } orc_options;
 
 typedef struct orc_aug {
@@ -632,6 +634,61 @@ static double costate_pass(const orc_problem *P, const rows_t *R, const orc_aug 
     return dmax;
 }
 
+/* Multiplier form of the first-order terms (a variant of the method, not in the paper:
+ * it replaces the co-state recursion of Sec. III-B, whose products of F_t^T grow without
+ * bound on long horizons of an unstable system).  nu holds multipliers of the dynamics
+ * constraints; with the Lagrangian
+ *   L = sum_t l_t(x_t, u_t) + l_{N+1}(x_{N+1}) + sum_t nu_{t+1}^T (f(x_t, u_t) - x_{t+1})
+ * the gradients are d_t = dL/du_t = dl_t/du + G_t^T nu_{t+1} and
+ *   q_t = dL/dx_t = dl_t/dx + F_t^T nu_{t+1} - nu_t   (t = 2..N),
+ *   q_{N+1} = dl_{N+1}/dx - nu_{N+1},   q_1 = 0 (x_1 is fixed).
+ * Each term is local in t: no recursion.  W->lam is set to nu, so the second-order terms
+ * contract the model Hessians with nu_{t+1}.  At q = 0, nu is the co-state of Sec. III-B.
+ * Returns max(max_t |d_t|_inf, max_t |q_t|_inf). */
+static double multiplier_pass(const orc_problem *P, const rows_t *R, const orc_aug *G, int T,
+                              const double *x, const double *u, double *nu, newton_ws *W,
+                              double *q)
+{
+    int n = P->nx, m = P->nu;
+    double lx[ORC_MAXN], lu[ORC_MAXM], lxx[ORC_MAXN * ORC_MAXN], lxu[ORC_MAXN * ORC_MAXM],
+        luu[ORC_MAXM * ORC_MAXM], gT[ORC_MAXN];
+    memcpy(W->lam, nu, sizeof(double) * (T + 1) * n);
+    double r = 0.0;
+    terminal_grad(P, x + T * n, gT, NULL);
+    for (int i = 0; i < n; i++) {
+        q[T * n + i] = gT[i] - nu[T * n + i];
+        if (!(fabs(q[T * n + i]) <= r)) r = isfinite(q[T * n + i]) ? fabs(q[T * n + i]) : INFINITY;
+    }
+    for (int t = 0; t < T; t++) {
+        double *F = W->F + (size_t)t * n * n, *Gm = W->G + (size_t)t * n * m;
+        orc_jac(P, x + t * n, u + t * m, F, Gm);
+        stage_derivs(P, R, G, t, x + t * n, u + t * m, lx, lu, lxx, lxu, luu);
+        const double *nn = nu + (t + 1) * n;
+        for (int i = 0; i < n; i++) {
+            double v = lx[i];
+            for (int k = 0; k < n; k++) v += F[k * n + i] * nn[k];
+            if (t == 0) {
+                /* x_1 is fixed: its multiplier is defined by one step of the co-state
+                 * relation (it is the gradient of the cost in x0), q_1 = 0 */
+                nu[i] = v;
+                W->lam[i] = v;
+                q[i] = 0.0;
+                continue;
+            }
+            v -= nu[t * n + i];
+            q[t * n + i] = v;
+            if (!(fabs(v) <= r)) r = isfinite(v) ? fabs(v) : INFINITY;
+        }
+        for (int i = 0; i < m; i++) {
+            double v = lu[i];
+            for (int k = 0; k < n; k++) v += Gm[k * m + i] * nn[k];
+            W->d[t * m + i] = v;
+            if (!(fabs(v) <= r)) r = isfinite(v) ? fabs(v) : INFINITY;
+        }
+    }
+    return r;
+}
+
 /* Second-order expansion of the Lagrangian (Sec. III-C):
  *   P_t = l_xx + c_xx + lam_{t+1}.f_xx,  M_t = l_xu + c_xu + lam_{t+1}.f_xu,
  *   R_t = l_uu + c_uu + lam_{t+1}.f_uu,  P_{N+1} = d2 l_{N+1}/dx2.  */
@@ -760,6 +817,29 @@ static void forward_pass(int n, int m, int T, newton_ws *W)
     W->G2 = G2;
 }
 
+/* Multiplier form, first-order model term: G1 += sum_t q_t^T dx_t.  The multiplier
+ * terms of the Lagrangian telescope away along the linearised dynamics (dx_1 = 0), so
+ * G1 stays the cost's directional derivative along (dx, du). */
+static void mult_g1(int n, int T, const double *q, newton_ws *W)
+{
+    for (int t = 1; t <= T; t++)
+        for (int i = 0; i < n; i++) W->G1 += q[t * n + i] * W->dx[t * n + i];
+}
+
+/* Multiplier form, dual step: dnu_t = S_t dx_t + s_t, the gradient of the LQR value
+ * function at dx_t (the multiplier of the linearised dynamics into step t). */
+static void mult_dual(int n, int T, const newton_ws *W, double *dnu)
+{
+    for (int t = 0; t <= T; t++) {
+        const double *S = W->S + (size_t)t * n * n, *sv = W->s + t * n, *dx = W->dx + t * n;
+        for (int i = 0; i < n; i++) {
+            double v = sv[i];
+            for (int j = 0; j < n; j++) v += S[i * n + j] * dx[j];
+            dnu[t * n + i] = v;
+        }
+    }
+}
+
 /* Public: one full Newton direction at the nominal (x, u) for regularisation alpha.
  * Outputs (any may be NULL): lam (T+1)xn, d Txm, S (T+1)xnxn, s (T+1)xn, Gam Txmxn,
  * gam Txm, dx (T+1)xn, du Txm, P (T+1)xnxn, M Txnxm, R Txmxm, F Txnxn, G Txnxm, g12[2].
@@ -794,6 +874,41 @@ int orc_newton_direction(const orc_problem *P, const orc_aug *G, int T, const do
     CP(Gm, W.G, T * n * m);
 #undef CP
     if (g12) { g12[0] = W.G1; g12[1] = W.G2; }
+    ws_free(&W);
+    return st;
+}
+
+/* Public: one Newton direction of the multiplier form at (x, u) with multipliers nu
+ * ((T+1) x n; row 0 is replaced by its local definition, see multiplier_pass).
+ * Outputs (any may be NULL): q (T+1)xn, d Txm, dx (T+1)xn, du Txm, dnu (T+1)xn (the dual
+ * step S_t dx_t + s_t), g12[2] = (G1, G2).  Returns 0, or 1 when R~ or Q is not positive
+ * definite. */
+int orc_newton_direction_mult(const orc_problem *P, const orc_aug *G, int T, const double *x,
+                              const double *u, const double *nu_in, double alpha, double *q_out,
+                              double *d, double *dx, double *du, double *dnu, double *g12)
+{
+    int n = P->nx, m = P->nu;
+    rows_t R;
+    build_rows(P, &R);
+    newton_ws W;
+    ws_alloc(&W, T, n, m);
+    double *nu = malloc(sizeof(double) * (T + 1) * n), *q = calloc((size_t)(T + 1) * n, sizeof(double));
+    memcpy(nu, nu_in, sizeof(double) * (T + 1) * n);
+    multiplier_pass(P, &R, G, T, x, u, nu, &W, q);
+    quadratize(P, &R, G, T, x, u, &W);
+    int st = riccati(n, m, T, &W, alpha, q);
+    if (!st) {
+        forward_pass(n, m, T, &W);
+        mult_g1(n, T, q, &W);
+        if (dnu) mult_dual(n, T, &W, dnu);
+    }
+    if (q_out) memcpy(q_out, q, sizeof(double) * (T + 1) * n);
+    if (d) memcpy(d, W.d, sizeof(double) * T * m);
+    if (dx) memcpy(dx, W.dx, sizeof(double) * (T + 1) * n);
+    if (du) memcpy(du, W.du, sizeof(double) * T * m);
+    if (g12) { g12[0] = W.G1; g12[1] = W.G2; }
+    free(nu);
+    free(q);
     ws_free(&W);
     return st;
 }
@@ -1057,26 +1172,28 @@ typedef struct { int iters, ls_rejects, factor_fails; double alpha; } nstats;
  * alpha = max(10 alpha, 1e-8) and retries; no accepted step multiplies alpha by 10. */
 static int newton_solve(const orc_problem *P, const rows_t *R, const orc_aug *G,
                         const orc_options *o, int T, double *x, double *u, double tol,
-                        nstats *st, double *rfinal)
+                        nstats *st, double *rfinal, double *nu)
 {
     int n = P->nx, m = P->nu, rc = ORC_ENOTCONV;
     newton_ws W;
     ws_alloc(&W, T, n, m);
     double *xc = malloc(sizeof(double) * (T + 1) * n), *uc = malloc(sizeof(double) * (T * m + 1));
+    double *q = nu ? calloc((size_t)(T + 1) * n, sizeof(double)) : NULL;
     double J0 = traj_cost(P, R, G, T, x, u, NULL);
     double r = INFINITY;
     for (int it = 0; it <= o->max_newton; it++) {
-        r = costate_pass(P, R, G, T, x, u, &W);
+        r = nu ? multiplier_pass(P, R, G, T, x, u, nu, &W, q) : costate_pass(P, R, G, T, x, u, &W);
         if (r <= tol) { rc = ORC_OK; break; }
         if (it == o->max_newton || !isfinite(r) || !isfinite(J0)) break;
         st->iters++;
         quadratize(P, R, G, T, x, u, &W);
-        while (riccati(n, m, T, &W, st->alpha, NULL)) {
+        while (riccati(n, m, T, &W, st->alpha, q)) {
             st->factor_fails++;
             st->alpha = fmax(10.0 * st->alpha, 1e-8);
             if (st->alpha > o->alpha_max) { rc = ORC_ENUM; goto done; }
         }
         forward_pass(n, m, T, &W);
+        if (q) mult_g1(n, T, q, &W);
         int accepted = 0;
         double s = 1.0, Js = INFINITY;
         for (int k = 0; k < o->ls_count; k++, s *= o->ls_beta) {
@@ -1097,6 +1214,13 @@ static int newton_solve(const orc_problem *P, const rows_t *R, const orc_aug *G,
             memcpy(x, xc, sizeof(double) * (T + 1) * n);
             memcpy(u, uc, sizeof(double) * T * m);
             J0 = Js;
+            if (nu) {
+                /* multipliers := the duals of the LQR's linearised dynamics, nu + dnu
+                 * (the full dual step whatever the primal step s: the LQR duals are the
+                 * multiplier estimate at the linearisation point) */
+                mult_dual(n, T, &W, q);
+                for (int i = 0; i < (T + 1) * n; i++) nu[i] += q[i];
+            }
         } else {
             st->ls_rejects++;
             st->alpha *= 10.0;
@@ -1107,6 +1231,7 @@ done:
     if (rfinal) *rfinal = r;
     free(xc);
     free(uc);
+    free(q);
     ws_free(&W);
     return rc;
 }
@@ -1115,12 +1240,17 @@ done:
  *  0 status  1 newton iterations  2 outer iterations  3 mu  4 alpha  5 r_stat  6 r_dyn
  *  7 r_feas  8 r_kkt  9 J  10 J_c  11 r_p  12 r_d  13 line-search rejects  14 factor fails */
 static void residuals(const orc_problem *P, const rows_t *R, const orc_aug *G, int T,
-                      const double *x, const double *u, double *lam_out, double *info)
+                      const double *x, const double *u, double *lam_out, double *info,
+                      double *nu)
 {
     int n = P->nx, m = P->nu;
     newton_ws W;
     ws_alloc(&W, T, n, m);
-    double rs = costate_pass(P, R, G, T, x, u, &W);
+    double *q = nu ? calloc((size_t)(T + 1) * n, sizeof(double)) : NULL;
+    /* multiplier form: stationarity of the Lagrangian in u and x (both gradients), and
+     * the multipliers as the co-states */
+    double rs = nu ? multiplier_pass(P, R, G, T, x, u, nu, &W, q) : costate_pass(P, R, G, T, x, u, &W);
+    free(q);
     double rd = 0.0, rf = 0.0, xn[ORC_MAXN];
     for (int t = 0; t < T; t++) {
         orc_step(P, x + t * n, u + t * m, xn);
@@ -1169,19 +1299,22 @@ int orc_solve_ip(const orc_problem *P, const orc_options *o, const double *x0,
     orc_rollout(P, x0, u, T, x);
     if (!check_feasible(P, &R, T, x, u)) { info[0] = ORC_EINFEAS; return ORC_EINFEAS; }
     nstats st = {0, 0, 0, o->alpha0};
+    /* multiplier form: nu starts at zero (no recursion through F^T at the start either) */
+    double *nu = o->costate_mode == 1 ? calloc((size_t)(T + 1) * n, sizeof(double)) : NULL;
     double mu = o->mu0;
     int rc = ORC_OK, level = 0;
     orc_aug G = {AUG_BARRIER, R.nw, mu, 0.0, NULL, NULL};
     for (;;) {
         int last = mu <= o->mu_final * (1.0 + 1e-9);
         G.mu = mu;
-        rc = newton_solve(P, &R, &G, o, T, x, u, last ? o->tol_final : o->tol_inner, &st, NULL);
+        rc = newton_solve(P, &R, &G, o, T, x, u, last ? o->tol_final : o->tol_inner, &st, NULL, nu);
         level++;
         if (rc == ORC_ENUM || last) break;
         mu = o->mu0 * pow(o->zeta, level);
         if (mu < o->mu_final) mu = o->mu_final;
     }
-    residuals(P, &R, &G, T, x, u, lam, info);
+    residuals(P, &R, &G, T, x, u, lam, info, nu);
+    free(nu);
     info[0] = rc;
     info[1] = st.iters;
     info[2] = level;
@@ -1208,8 +1341,10 @@ int orc_solve_fixed_mu(const orc_problem *P, const orc_options *o, double mu, do
     if (!check_feasible(P, &R, T, x, u)) { info[0] = ORC_EINFEAS; return ORC_EINFEAS; }
     nstats st = {0, 0, 0, o->alpha0};
     orc_aug G = {AUG_BARRIER, R.nw, mu, 0.0, NULL, NULL};
-    int rc = newton_solve(P, &R, &G, o, T, x, u, tol, &st, NULL);
-    residuals(P, &R, &G, T, x, u, lam, info);
+    double *nu = o->costate_mode == 1 ? calloc((size_t)(T + 1) * P->nx, sizeof(double)) : NULL;
+    int rc = newton_solve(P, &R, &G, o, T, x, u, tol, &st, NULL, nu);
+    residuals(P, &R, &G, T, x, u, lam, info, nu);
+    free(nu);
     info[0] = rc;
     info[1] = st.iters;
     info[3] = mu;
@@ -1245,12 +1380,13 @@ int orc_solve_admm(const orc_problem *P, const orc_options *o, const double *x0,
             vi[t * nw + r] = 0.0;
         }
     nstats st = {0, 0, 0, o->alpha0};
+    double *nu = o->costate_mode == 1 ? calloc((size_t)(T + 1) * n, sizeof(double)) : NULL;
     orc_aug G = {AUG_ADMM, nw, 0.0, o->rho, zi, vi};
     int rc = ORC_ENOTCONV, k;
     double rp = INFINITY, rdl = INFINITY;
     int kmax = o->admm_fixed_iters > 0 ? o->admm_fixed_iters : o->max_outer;
     for (k = 0; k < kmax; k++) {
-        int s = newton_solve(P, &R, &G, o, T, x, u, o->tol_final, &st, NULL);
+        int s = newton_solve(P, &R, &G, o, T, x, u, o->tol_final, &st, NULL, nu);
         if (s == ORC_ENUM) { rc = ORC_ENUM; k++; break; }
         memcpy(zp, zi, sizeof(double) * T * nw);
         rp = 0.0;
@@ -1268,7 +1404,8 @@ int orc_solve_admm(const orc_problem *P, const orc_options *o, const double *x0,
         if (o->admm_fixed_iters <= 0 && rp <= o->admm_tol && rdl <= o->admm_tol) { rc = ORC_OK; k++; break; }
     }
     if (o->admm_fixed_iters > 0 && rc != ORC_ENUM) rc = ORC_OK;
-    residuals(P, &R, &G, T, x, u, lam, info);
+    residuals(P, &R, &G, T, x, u, lam, info, nu);
+    free(nu);
     info[0] = rc;
     info[1] = st.iters;
     info[2] = k;
