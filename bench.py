@@ -211,6 +211,55 @@ def run_batch(args, ptn, W, dev, flush, stream):
             "one_by_one_sample": f"first {ns} instances as single solves (cluster or grid tier), time scaled to {B}"}
 
 
+def run_multiplier(args, ptn, W, dev, flush, stream, tuned, x0, sweep):
+    """The multiplier form of the co-states (option costate_mode = 1, a variant of the
+    method: dynamics multipliers moved to the LQR duals, no co-state scan) on the same
+    single solves as the sweep (same launch shapes, same x0) and on the batch workload.
+    It ends at the same KKT point; reported beside the co-state form's numbers."""
+    import torch
+    from paper_2409_20027_gb300 import autotune
+    out = {"single": {}}
+    for Ts in [1024, 4096, args.T]:
+        ps = cartpole_instance(Ts)
+        sv = ptn.Solver(ps, max_T=Ts, precision=ptn.PTN_FP32_FP64SOLVE, costate_mode=1)
+        autotune.apply(sv, tuned, Ts)
+        sv.solve_ip(x0, Ts)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        flush.zero_()
+        a.record(stream)
+        _, _, _, inf = sv.solve_ip(x0, Ts)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ref = sweep.get(str(Ts), {})
+        out["single"][str(Ts)] = {"ms": a.elapsed_time(b), "newton_iters": inf["newton_iters"],
+                                  "status": inf["status"], "r_kkt": inf["r_kkt"],
+                                  "costate_form_ms": ref.get("ms"), "costate_form_newton_iters": ref.get("newton_iters")}
+        sv.close()
+    B = args.batch
+    Tb = W.batch_horizons(B, seed=0)
+    dtb = BATCH_HORIZON_S / Tb
+    xb = torch.tensor(W.cartpole_batch_x0(B, seed=0), dtype=torch.float64, device=dev)
+    sv = ptn.Solver(W.cartpole(), max_T=int(Tb.max()), max_batch=B, precision=ptn.PTN_FP32_FP64SOLVE, costate_mode=1)
+    sv.solve_batch(xb, Tb, dt_b=dtb)
+    torch.cuda.synchronize()
+    flush.zero_()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    _, _, _, infos = sv.solve_batch(xb, Tb, dt_b=dtb)
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b)
+    st = [i["status"] for i in infos]
+    out["batch"] = {"solves_per_s": B / (ms * 1e-3), "ms": ms,
+                    "status_counts": {str(k): st.count(k) for k in set(st)},
+                    "newton_iters_mean": float(np.mean([i["newton_iters"] for i in infos]))}
+    sv.close()
+    out["workload"] = ("cart-pole IP as the sweep (2.56 s horizon, tuned launch) and the batch workload, "
+                       "multiplier form of the co-states")
+    return out
+
+
 PHASES = ["costate", "second_order", "value", "state", "line_search", "initial_rollout", "other"]
 
 
@@ -348,6 +397,7 @@ def main():
     ap.add_argument("--quad-T", type=int, default=1024)
     ap.add_argument("--no-mpc", action="store_true")
     ap.add_argument("--no-seq", action="store_true")
+    ap.add_argument("--no-mult", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
@@ -466,6 +516,9 @@ def main():
     seq = None
     if not args.no_seq and single:
         seq = run_sequential(args, ptn, W, dev, flush, stream)
+    mult = None
+    if not args.no_mult and single and not args.no_sweep:
+        mult = run_multiplier(args, ptn, W, dev, flush, stream, tuned, x0s[0], sweep)
 
     if rank != 0:
         return
@@ -493,7 +546,8 @@ def main():
             "gpu_launches": args.steps, "clocks": clocks, "kkt_ok": ok,
             "newton_iters": last["newton_iters"], "launch": launch or "defaults",
             "phase_share": phase_share(infos), "sweep": sweep,
-            "batch": batch, "quadrotor": quad, "mpc": mpcl, "sequential": seq}
+            "batch": batch, "quadrotor": quad, "mpc": mpcl, "sequential": seq,
+            "multiplier_form": mult}
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

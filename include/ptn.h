@@ -93,6 +93,14 @@ typedef struct ptn_options {
                              cluster (at most 16; 0: never) before the cooperative grid is used */
   int sequential;       /* nonzero: the sequential-in-time baseline, one thread per instance
                            running the serial recursions (n < 8 only); for comparisons */
+  int costate_mode;     /* 0: co-states by the suffix scan of Alg. 1 (the paper's method);
+                           1: multiplier form, a variant: multipliers nu of the dynamics take
+                           the duals of each Newton step's LQR (nu_t += S_t dx_t + s_t), the
+                           Lagrangian's gradients d_t, q_t are local in t (no product of
+                           F_t^T is formed), the LQR carries q_t as a linear state term, and
+                           the stopping test is max(|d|, |q|) <= tol; lam_out returns nu.
+                           Same KKT point as mode 0.  Not built for nx >= 8
+                           (PTN_ERR_INVALID_ARG). */
   double mu0, zeta, mu_final, tol_inner, tol_final, rho, admm_tol;
   double alpha0, alpha_min, alpha_max, ls_beta, armijo_c1, armijo_eps, roll_tol;
   double polish;        /* FP32 modes: exact FP64 gradients once max|d| <= polish * tol_final */

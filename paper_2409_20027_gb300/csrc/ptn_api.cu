@@ -161,6 +161,8 @@ static int check_options(ptn_solver* s, const ptn_options* o) {
   if (o->grid_steps_per_thread < 1) return fail(s, PTN_ERR_INVALID_ARG, "grid_steps_per_thread must be >= 1");
   if (o->cluster_max_blocks < 0 || o->cluster_max_blocks > 16)
     return fail(s, PTN_ERR_INVALID_ARG, "cluster_max_blocks must be in [0, 16]");
+  if (o->costate_mode != 0 && o->costate_mode != 1)
+    return fail(s, PTN_ERR_INVALID_ARG, "costate_mode must be 0 (co-state scan) or 1 (multiplier form)");
   return PTN_OK;
 }
 
@@ -291,6 +293,10 @@ extern "C" int ptn_solver_create(const ptn_problem* prob, const ptn_options* opt
   size_t o_du = off; off = align256(off + 8 * S * m);
   size_t o_z = off; off = align256(off + sizeof(double) * S * (nw > 0 ? nw : 1));
   size_t o_v = off; off = align256(off + sizeof(double) * S * (nw > 0 ? nw : 1));
+  size_t o_q = off; off = align256(off + sizeof(double) * SB * n);
+  size_t o_dnu = off; off = align256(off + sizeof(double) * SB * n);
+  size_t o_Sv = off; off = align256(off + 8 * SB * n * n);
+  size_t o_sv = off; off = align256(off + 8 * SB * n);
   CK(cudaMalloc(&s->ws, off));
   char* b = s->ws;
   s->w.xB = (double*)(b + o_xB); s->w.uB = (double*)(b + o_uB); s->w.lam = (double*)(b + o_lam);
@@ -299,6 +305,7 @@ extern "C" int ptn_solver_create(const ptn_problem* prob, const ptn_options* opt
   s->w.Pm = b + o_Pm; s->w.Mm = b + o_Mm; s->w.Rm = b + o_Rm; s->w.Gam = b + o_Gam; s->w.gam = b + o_gam;
   s->w.dx = b + o_dx; s->w.du = b + o_du;
   s->w.z = (double*)(b + o_z); s->w.v = (double*)(b + o_v);
+  s->w.q = (double*)(b + o_q); s->w.dnu = (double*)(b + o_dnu); s->w.Sv = b + o_Sv; s->w.sv = b + o_sv;
   // grid-tier scratch, sized for 4 co-resident blocks per SM
   s->grid_cap_blocks = 4 * s->num_sms;
   CK(cudaMalloc(&s->gs.bar, 2 * sizeof(unsigned)));
@@ -334,6 +341,7 @@ static void to_optdev(const ptn_options& o, int method, OptDev* d) {
   d->init_max_iter = 64;
   d->max_newton = o.max_newton; d->max_outer = o.max_outer; d->ls_count = o.ls_count;
   d->admm_fixed_iters = o.admm_fixed_iters; d->roll_max_iter = o.roll_max_iter; d->method = method;
+  d->costate_mode = o.costate_mode;
   d->spin_limit = 1ll << 26;
 }
 
@@ -389,6 +397,8 @@ static int plan_launch(ptn_solver* s, int method, int B, const int* T_b, long lo
   int cl_blocks = 0;
   // models with n >= 8 run the wide tier (one CTA per instance, one warp per chunk)
   const bool wide = s->n >= 8;
+  if (wide && s->opt.costate_mode == 1)
+    return fail(s, PTN_ERR_INVALID_ARG, "the multiplier form (costate_mode 1) is not built for the wide tier (nx >= 8)");
   if (!wide && !s->opt.sequential && B == 1 && s->opt.cluster_max_blocks >= 2) {
     const long long per = (long long)s->opt.block_threads * s->opt.grid_steps_per_thread;
     const long long need = (T_b[0] + per - 1) / per;
@@ -686,6 +696,9 @@ extern "C" int ptn_solve_ip_static(const ptn_problem* prob, const ptn_options* o
   int nx, nu;
   if (model_dims(prob->model, &nx, &nu))
     return static_fail(err, err_len, PTN_ERR_INVALID_ARG, "unknown or unsupported model id %d", prob->model);
+  if (nx >= 8 && o.costate_mode == 1)
+    return static_fail(err, err_len, PTN_ERR_INVALID_ARG,
+                       "the multiplier form (costate_mode 1) is not built for the wide tier (nx >= 8)");
   if (prob->nx != nx || prob->nu != nu)
     return static_fail(err, err_len, PTN_ERR_INVALID_ARG, "model %d has nx=%d nu=%d, got %d %d", prob->model, nx, nu,
                        prob->nx, prob->nu);
@@ -751,6 +764,12 @@ extern "C" int ptn_solve_ip_static(const ptn_problem* prob, const ptn_options* o
   size_t o_du = off; off = align256(off + 8 * S * m);
   size_t o_z = off; off = align256(off + sizeof(double) * S * (nw > 0 ? nw : 1));
   size_t o_v = off; off = align256(off + sizeof(double) * S * (nw > 0 ? nw : 1));
+  // the multiplier form's arrays only when it is selected
+  const bool mult = o.costate_mode == 1;
+  size_t o_q = off; off = align256(off + (mult ? sizeof(double) * SB * n : 0));
+  size_t o_dnu = off; off = align256(off + (mult ? sizeof(double) * SB * n : 0));
+  size_t o_Sv = off; off = align256(off + (mult ? 8 * SB * n * n : 0));
+  size_t o_sv = off; off = align256(off + (mult ? 8 * SB * n : 0));
   if (off > kStaticScratchBytes)
     return static_fail(err, err_len, PTN_ERR_INVALID_ARG,
                        "T=%d needs %zu bytes of static scratch for model %d; the array holds %zu bytes", T, off,
@@ -798,6 +817,9 @@ extern "C" int ptn_solve_ip_static(const ptn_problem* prob, const ptn_options* o
   q.w.E = b + o_E; q.w.Gm = b + o_Gm; q.w.Pm = b + o_Pm; q.w.Mm = b + o_Mm; q.w.Rm = b + o_Rm;
   q.w.Gam = b + o_Gam; q.w.gam = b + o_gam; q.w.dx = b + o_dx; q.w.du = b + o_du;
   q.w.z = (double*)(b + o_z); q.w.v = (double*)(b + o_v);
+  if (mult) {
+    q.w.q = (double*)(b + o_q); q.w.dnu = (double*)(b + o_dnu); q.w.Sv = b + o_Sv; q.w.sv = b + o_sv;
+  }
   q.args.prob = &dh->prob;
   q.args.opt = &dh->opt;
   q.args.inst = &dh->inst;

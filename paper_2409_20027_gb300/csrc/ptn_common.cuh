@@ -58,6 +58,7 @@ struct OptDev {
   double roll_tol, polish, armijo_eps32;
   int max_newton, max_outer, ls_count, admm_fixed_iters;
   int roll_max_iter, method, polish_after, init_max_iter;
+  int costate_mode, pad_;  // 0: co-state scan (Alg. 1); 1: multiplier form
   long long spin_limit;  // bounded waits in grid barriers
 };
 

@@ -10,6 +10,8 @@ struct WorkRaw {
   double *xA, *uA, *xB, *uB, *lam, *d, *F64, *G64;
   void *E, *Gm, *Pm, *Mm, *Rm, *Gam, *gam, *dx, *du;
   double *z, *v;
+  double *q, *dnu;  // multiplier form (may be null when it is not used)
+  void *Sv, *sv;
 };
 
 template <class L>
@@ -19,6 +21,7 @@ inline Work<L> typed(const WorkRaw& r) {
   w.d = r.d; w.F64 = r.F64; w.G64 = r.G64; w.E = (L*)r.E; w.Gm = (L*)r.Gm;
   w.Pm = (L*)r.Pm; w.Mm = (L*)r.Mm; w.Rm = (L*)r.Rm; w.Gam = (L*)r.Gam; w.gam = (L*)r.gam;
   w.dx = (L*)r.dx; w.du = (L*)r.du; w.z = r.z; w.v = r.v;
+  w.q = r.q; w.dnu = r.dnu; w.Sv = (L*)r.Sv; w.sv = (L*)r.sv;
   return w;
 }
 

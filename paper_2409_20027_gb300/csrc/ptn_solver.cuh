@@ -389,6 +389,8 @@ struct Work {
   L *Gam, *gam;         // (sum T) x U*N, x U
   L *dx, *du;           // (sum T+1) x N, (sum T) x U
   double *z, *v;        // (sum T) x nw (ADMM)
+  double *q, *dnu;      // (sum T+1) x N  multiplier form: x-gradient q_t, dual step
+  L *Sv, *sv;           // (sum T+1) x N*N, x N  multiplier form: LQR value S_t, s_t
 };
 
 template <class M, class L>
@@ -402,6 +404,8 @@ struct Inst {
   double *lam, *d, *F64, *G64;
   L *E, *Gm, *Pm, *Mm, *Rm, *Gam, *gam, *dx, *du;
   double *z, *v;
+  double *q, *dnu;
+  L *Sv, *sv;
   double lamb[N];  // co-state at this chunk's right boundary (from the last co-state pass)
 
   __device__ void setup(const Work<L>& w, const InstDev& id, const double* x0_, int rank, int size, int nw) {
@@ -423,6 +427,8 @@ struct Inst {
     dx = w.dx + xo * N; du = w.du + uo * U;
     z = w.z ? w.z + uo * nw : nullptr;
     v = w.v ? w.v + uo * nw : nullptr;
+    q = w.q + xo * N; dnu = w.dnu + xo * N;
+    Sv = w.Sv + xo * N * N; sv = w.sv + xo * N;
   }
 };
 
@@ -644,6 +650,149 @@ __device__ double costate_pass(Grp& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>&
   return costate_exact(g, I, P, A);
 }
 
+// pass 1, multiplier form (option costate_mode = 1; a variant of the method, not in the
+// paper): the co-state suffix scan is replaced by multipliers nu of the dynamics, held in
+// I.lam and moved to the LQR duals after each accepted step.  Both gradients of the
+// Lagrangian  sum_t l_t + l_{N+1} + sum_t nu_{t+1}^T (f(x_t, u_t) - x_{t+1})  are local in t:
+//   d_t = dl/du + G_t^T nu_{t+1},   q_t = dl/dx + F_t^T nu_{t+1} - nu_t   (t >= 1),
+//   q_T = dl_T/dx - nu_T,   and nu_0 (x_0 is fixed) := dl/dx + F_0^T nu_1 with q_0 = 0,
+// so no product of F_t^T is ever formed.  Jacobians in FP64 (forward-mode AD), stored as
+// the exact co-state pass stores them.  Returns max(max |d|, max |q|) over the group.
+template <class M, class L, class Grp>
+__device__ __noinline__ double multiplier_pass(Grp& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>& P, const Aug& A) {
+  constexpr int N = M::NX, U = M::NU;
+  double rmax = 0.0;
+  for (int t = I.a; t < I.b; t++) {
+    double E[N * N], G[N * U], lx[N], lu[U], nv[N], Et[N], Gt[U];
+    const double* x = I.xn + (size_t)t * N;
+    const double* u = I.un + (size_t)t * U;
+    MOps<M>::ijac(P, x, u, E, G);
+#pragma unroll (N <= 8 ? N * N : 4)
+    for (int i = 0; i < N * N; i++) { I.F64[(size_t)t * N * N + i] = E[i]; I.E[(size_t)t * N * N + i] = L(E[i]); }
+#pragma unroll
+    for (int i = 0; i < N * U; i++) { I.G64[(size_t)t * N * U + i] = G[i]; I.Gm[(size_t)t * N * U + i] = L(G[i]); }
+    stage_grad(P, A, t, x, u, lx, lu);
+#pragma unroll
+    for (int i = 0; i < N; i++) nv[i] = I.lam[(size_t)(t + 1) * N + i];
+    mtv<N, N>(E, nv, Et);  // F^T nu = nu + E^T nu
+    mtv<N, U>(G, nv, Gt);
+#pragma unroll
+    for (int i = 0; i < U; i++) {
+      const double d = lu[i] + Gt[i];
+      I.d[(size_t)t * U + i] = d;
+      const double ad = fabs(d);
+      rmax = (ad <= rmax) ? rmax : (isfinite(ad) ? ad : INFINITY);
+    }
+#pragma unroll
+    for (int i = 0; i < N; i++) {
+      double v = lx[i] + nv[i] + Et[i];
+      if (t == 0) {
+        I.lam[i] = v;
+        I.q[i] = 0.0;
+        continue;
+      }
+      v -= I.lam[(size_t)t * N + i];
+      I.q[(size_t)t * N + i] = v;
+      const double av = fabs(v);
+      rmax = (av <= rmax) ? rmax : (isfinite(av) ? av : INFINITY);
+    }
+  }
+  if (I.last) {
+    double gT[N];
+    terminal_grad(P, I.xn + (size_t)I.T * N, gT);
+#pragma unroll
+    for (int i = 0; i < N; i++) {
+      const double v = gT[i] - I.lam[(size_t)I.T * N + i];
+      I.q[(size_t)I.T * N + i] = v;
+      const double av = fabs(v);
+      rmax = (av <= rmax) ? rmax : (isfinite(av) ? av : INFINITY);
+    }
+  }
+  // nu at the chunk's right boundary for the second-order terms (the next chunk's first
+  // multiplier, which this pass does not write unless it is nu_0 of an empty chunk)
+  if (I.a < I.b) {
+#pragma unroll
+    for (int i = 0; i < N; i++) I.lamb[i] = I.lam[(size_t)I.b * N + i];
+  }
+  double red[1] = {rmax};
+  g.template reduce<1>(red, 1u);
+  return red[0];
+}
+
+// Multiplier form, mixed precision (L = float, before the FP64 endgame): the same terms
+// with the Jacobian increments E = F - I, G and the stage gradients from FP32 AD, as the
+// FP32-increment co-state pass has them.  Only the increment terms carry FP32 error:
+//   q_t = (dl/dx + E^T nu_{t+1}) [FP32] + (nu_{t+1} - nu_t) [FP64].
+template <class M, class Grp>
+__device__ __noinline__ double multiplier_mixed(Grp& g, Inst<M, float>& I, const ProbS<M::NX, M::NU>& P,
+                                                const Aug& A) {
+  constexpr int N = M::NX, U = M::NU;
+  double rmax = 0.0;
+  for (int t = I.a; t < I.b; t++) {
+    float E[N * N], G[N * U], lx[N], lu[U], nf[N], Et[N], Gt[U];
+    double nv[N];
+    const double* x = I.xn + (size_t)t * N;
+    const double* u = I.un + (size_t)t * U;
+    MOps<M>::ijac(P, x, u, E, G);
+#pragma unroll (N <= 8 ? N * N : 4)
+    for (int i = 0; i < N * N; i++) I.E[(size_t)t * N * N + i] = E[i];
+#pragma unroll
+    for (int i = 0; i < N * U; i++) I.Gm[(size_t)t * N * U + i] = G[i];
+    stage_grad32(P, A, t, x, u, lx, lu);
+#pragma unroll
+    for (int i = 0; i < N; i++) {
+      nv[i] = I.lam[(size_t)(t + 1) * N + i];
+      nf[i] = float(nv[i]);
+    }
+    mtv<N, N>(E, nf, Et);
+    mtv<N, U>(G, nf, Gt);
+#pragma unroll
+    for (int i = 0; i < U; i++) {
+      const double d = double(lu[i] + Gt[i]);
+      I.d[(size_t)t * U + i] = d;
+      const double ad = fabs(d);
+      rmax = (ad <= rmax) ? rmax : (isfinite(ad) ? ad : INFINITY);
+    }
+#pragma unroll
+    for (int i = 0; i < N; i++) {
+      const double inc = double(lx[i] + Et[i]);
+      if (t == 0) {
+        I.lam[i] = nv[i] + inc;
+        I.q[i] = 0.0;
+        continue;
+      }
+      const double v = inc + (nv[i] - I.lam[(size_t)t * N + i]);
+      I.q[(size_t)t * N + i] = v;
+      const double av = fabs(v);
+      rmax = (av <= rmax) ? rmax : (isfinite(av) ? av : INFINITY);
+    }
+  }
+  if (I.last) {
+    double gT[N];
+    terminal_grad(P, I.xn + (size_t)I.T * N, gT);
+#pragma unroll
+    for (int i = 0; i < N; i++) {
+      const double v = gT[i] - I.lam[(size_t)I.T * N + i];
+      I.q[(size_t)I.T * N + i] = v;
+      const double av = fabs(v);
+      rmax = (av <= rmax) ? rmax : (isfinite(av) ? av : INFINITY);
+    }
+  }
+  if (I.a < I.b) {
+#pragma unroll
+    for (int i = 0; i < N; i++) I.lamb[i] = I.lam[(size_t)I.b * N + i];
+  }
+  double red[1] = {rmax};
+  g.template reduce<1>(red, 1u);
+  return red[0];
+}
+
+// Groups on which the multiplier form is built (all but the wide tier).
+template <class Grp>
+struct multiplier_form_ok {
+  static constexpr bool value = true;
+};
+
 // pass 2: second-order expansion (Sec. III-C).  Needs lam from pass 1 (group-synced).
 template <class M, class L, class Grp>
 __device__ void quadratize(Grp& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>& P, const Aug& A) {
@@ -675,8 +824,12 @@ __device__ void quadratize(Grp& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>& P, 
 // qx (optional, (T+1) x N, FP64): linear state terms q_t of the LQR stage costs, as the
 // adjoint LQR has them; they enter as eta_t -= q_t (so s_t += q_t).  The Newton step's
 // LQR has none (its state gradient is carried by the co-states).
+//
+// Sv, sv (optional, (T+1) x N*N and x N): receive S_t and s_t of the LQR value function
+// V_t(dx) = 1/2 dx^T S_t dx + s_t^T dx (the multiplier form's dual step needs them).
 template <class M, class L, class SV, class Grp>
-__device__ bool value_pass(Grp& g, Inst<M, L>& I, double alpha, const double* qx = nullptr) {
+__device__ bool value_pass(Grp& g, Inst<M, L>& I, double alpha, const double* qx = nullptr, L* Sv = nullptr,
+                           L* sv = nullptr) {
   constexpr int N = M::NX, U = M::NU;
   bool ok = true, have = false;
   Val<N, L> agg;
@@ -710,6 +863,12 @@ __device__ bool value_pass(Grp& g, Inst<M, L>& I, double alpha, const double* qx
     for (int i = 0; i < N * N; i++) S[i] = I.Pm[(size_t)I.T * N * N + i];
 #pragma unroll
     for (int i = 0; i < N; i++) s[i] = qx ? L(qx[(size_t)I.T * N + i]) : L(0);
+    if (Sv) {
+#pragma unroll (N <= 8 ? N * N : 4)
+      for (int i = 0; i < N * N; i++) Sv[(size_t)I.T * N * N + i] = S[i];
+#pragma unroll
+      for (int i = 0; i < N; i++) sv[(size_t)I.T * N + i] = s[i];
+    }
   } else {
     // S_t = J_{t,<|}, s_t = -eta_{t,<|}
 #pragma unroll (N <= 8 ? N * N : 4)
@@ -727,6 +886,12 @@ __device__ bool value_pass(Grp& g, Inst<M, L>& I, double alpha, const double* qx
 #pragma unroll
       for (int i = 0; i < N; i++) s[i] += L(qx[(size_t)t * N + i]);
     }
+    if (Sv) {
+#pragma unroll (N <= 8 ? N * N : 4)
+      for (int i = 0; i < N * N; i++) Sv[(size_t)t * N * N + i] = S[i];
+#pragma unroll
+      for (int i = 0; i < N; i++) sv[(size_t)t * N + i] = s[i];
+    }
 #pragma unroll
     for (int i = 0; i < U * N; i++) I.Gam[(size_t)t * U * N + i] = Gam[i];
 #pragma unroll
@@ -737,10 +902,30 @@ __device__ bool value_pass(Grp& g, Inst<M, L>& I, double alpha, const double* qx
   return red[0] == 0.0;
 }
 
+// multiplier form, per step t: g1 += q_t^T dx_t and dnu_t = S_t dx_t + s_t
+template <int N, class L>
+__device__ __noinline__ void mult_terms(int t, const L* dx, const double* qx, const L* Sv, const L* sv,
+                                        double* dnu, double& g1) {
+  const L* S = Sv + (size_t)t * N * N;
+#pragma unroll
+  for (int i = 0; i < N; i++) {
+    g1 += qx[(size_t)t * N + i] * double(dx[i]);
+    double v = double(sv[(size_t)t * N + i]);
+#pragma unroll
+    for (int j = 0; j < N; j++) v += double(S[i * N + j]) * double(dx[j]);
+    dnu[(size_t)t * N + i] = v;
+  }
+}
+
 // pass 4: state prefix scan (Alg. 3).  dx_1 = 0, du = Gam dx + gam, dx+ = F dx + G du.
 // Returns the model terms G1, G2 (R without the alpha shift).
+//
+// Multiplier form (qx, Sv, sv, dnu given): G1 also carries sum_t q_t^T dx_t (the
+// multiplier terms of the Lagrangian telescope along the linearised dynamics, so G1 stays
+// the cost's directional derivative), and dnu_t = S_t dx_t + s_t is the dual step.
 template <class M, class L, class Grp>
-__device__ void state_pass(Grp& g, Inst<M, L>& I, double& G1, double& G2) {
+__device__ void state_pass(Grp& g, Inst<M, L>& I, double& G1, double& G2, const double* qx = nullptr,
+                           const L* Sv = nullptr, const L* sv = nullptr, double* dnu = nullptr) {
   constexpr int N = M::NX, U = M::NU;
   Aff<N, L> agg;
   set_identity(agg);
@@ -793,6 +978,7 @@ __device__ void state_pass(Grp& g, Inst<M, L>& I, double& G1, double& G2) {
     }
 #pragma unroll
     for (int i = 0; i < N; i++) I.dx[(size_t)t * N + i] = dx[i];
+    if (qx) mult_terms<N>(t, dx, qx, Sv, sv, dnu, g1);
     L Pd[N], Md[N], Rd[U];
     mv<N, N>(Pm, dx, Pd);
     mv<N, U>(Mm, du, Md);
@@ -810,6 +996,7 @@ __device__ void state_pass(Grp& g, Inst<M, L>& I, double& G1, double& G2) {
     for (int i = 0; i < N; i++) dx[i] += Edx[i] + Gdu[i];
   }
   if (I.last) {
+    if (qx) mult_terms<N>(I.T, dx, qx, Sv, sv, dnu, g1);
     const L* PT = I.Pm + (size_t)I.T * N * N;
     L Pd[N];
     mv<N, N>(PT, dx, Pd);
@@ -1057,7 +1244,22 @@ struct exact_only {
 template <class M, class L, class SV, class Grp>
 __device__ int newton_solve(Grp& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>& P, const OptDev& O, const Aug& A,
                             double tol, bool final_level, NStats& st, double* rfinal) {
+  constexpr int N = M::NX;
   constexpr bool MIXED = std::is_same<L, float>::value && !exact_only<Grp>::value;
+  constexpr bool CAN_MULT = multiplier_form_ok<Grp>::value;
+  const bool MULT = CAN_MULT && O.costate_mode == 1;
+  // first-order terms: the co-state scan, or the multiplier form's local gradients
+  auto first_order = [&](bool ex) -> double {
+    if constexpr (CAN_MULT) {
+      if (MULT) {
+        if constexpr (std::is_same<L, float>::value) {
+          if (!ex) return multiplier_mixed(g, I, P, A);
+        }
+        return multiplier_pass(g, I, P, A);
+      }
+    }
+    return costate_pass(g, I, P, A, ex);
+  };
   bool inf;
   double J0 = nominal_cost(g, I, P, A, &inf, nullptr);
   int rc = ST_ENOTCONV;
@@ -1067,7 +1269,7 @@ __device__ int newton_solve(Grp& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>& P,
   for (int it = 0; it <= O.max_newton; it++) {
     if (g.dead()) return ST_ETIMEOUT;
     long long c0 = clock64();
-    r = costate_pass(g, I, P, A, exact);
+    r = first_order(exact);
     if (MIXED && !exact && (stalled || (final_level && (r <= O.polish * tol || it >= O.polish_after)))) {
       // endgame: below the FP32 noise floor of gradients and merits, switch to FP64.
       // First re-project the nominal onto the FP64 dynamics (one exact rollout with
@@ -1081,7 +1283,7 @@ __device__ int newton_solve(Grp& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>& P,
         double* t2 = I.un; I.un = I.uc; I.uc = t2;
       }
       st.roll_iters += ri;
-      r = costate_pass(g, I, P, A, true);
+      r = first_order(true);
       J0 = nominal_cost(g, I, P, A, &inf, nullptr);
     } else if (exact && MIXED) {
       st.exact_passes++;
@@ -1094,7 +1296,15 @@ __device__ int newton_solve(Grp& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>& P,
     quadratize(g, I, P, A);
     long long c2 = clock64();
     st.cyc[1] += c2 - c1;
-    while (!value_pass<M, L, SV>(g, I, st.alpha)) {
+    auto vpass = [&]() -> bool {
+      if constexpr (CAN_MULT) {
+        return value_pass<M, L, SV>(g, I, st.alpha, MULT ? I.q : nullptr, MULT ? I.Sv : nullptr,
+                                    MULT ? I.sv : nullptr);
+      } else {
+        return value_pass<M, L, SV>(g, I, st.alpha);
+      }
+    };
+    while (!vpass()) {
       st.factor_fails++;
       st.alpha = fmax(10.0 * st.alpha, 1e-8);
       if (st.alpha > O.alpha_max || g.dead()) { *rfinal = r; return g.dead() ? ST_ETIMEOUT : ST_ENUM; }
@@ -1102,7 +1312,12 @@ __device__ int newton_solve(Grp& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>& P,
     long long c3 = clock64();
     st.cyc[2] += c3 - c2;
     double G1, G2;
-    state_pass(g, I, G1, G2);
+    if constexpr (CAN_MULT) {
+      state_pass(g, I, G1, G2, MULT ? I.q : nullptr, MULT ? I.Sv : nullptr, MULT ? I.sv : nullptr,
+                 MULT ? I.dnu : nullptr);
+    } else {
+      state_pass(g, I, G1, G2);
+    }
     long long c4 = clock64();
     st.cyc[3] += c4 - c3;
     bool accepted = false;
@@ -1130,6 +1345,19 @@ __device__ int newton_solve(Grp& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>& P,
       double* t1 = I.xn; I.xn = I.xc; I.xc = t1;
       double* t2 = I.un; I.un = I.uc; I.uc = t2;
       J0 = Js;
+      if constexpr (CAN_MULT) {
+        if (MULT) {
+          // multipliers := the duals of the LQR's linearised dynamics (full dual step
+          // whatever s); the next pass reads the neighbouring chunk's nu, hence the sync
+          for (int t = I.a; t < I.b; t++)
+#pragma unroll
+            for (int i = 0; i < N; i++) I.lam[(size_t)t * N + i] += I.dnu[(size_t)t * N + i];
+          if (I.last)
+#pragma unroll
+            for (int i = 0; i < N; i++) I.lam[(size_t)I.T * N + i] += I.dnu[(size_t)I.T * N + i];
+          g.sync();
+        }
+      }
     } else {
       st.ls_rejects++;
       st.alpha *= 10.0;
@@ -1151,10 +1379,16 @@ __device__ int newton_solve(Grp& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>& P,
 }
 
 // final residuals: r_stat (max |d|, exact pass), r_dyn, r_feas, J, J_c; lam of the final point
+// (multiplier form: r_stat = max(|d|, |q|), the Lagrangian's gradients, and lam = nu)
 template <class M, class L, class Grp>
-__device__ void residuals(Grp& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>& P, const Aug& A, InfoDev& info) {
+__device__ void residuals(Grp& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>& P, const Aug& A, InfoDev& info,
+                          bool mult = false) {
   constexpr int N = M::NX, U = M::NU;
-  info.r_stat = costate_pass(g, I, P, A, true);
+  if constexpr (multiplier_form_ok<Grp>::value) {
+    info.r_stat = mult ? multiplier_pass(g, I, P, A) : costate_pass(g, I, P, A, true);
+  } else {
+    info.r_stat = costate_pass(g, I, P, A, true);
+  }
   double rd = 0.0, rf = -INFINITY;
   for (int t = I.a; t < I.b; t++) {
     double xn[N];
@@ -1599,7 +1833,13 @@ __device__ void solve_instance(Grp& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>&
     }
 #pragma unroll
     for (int i = 0; i < U * N; i++) I.Gam[(size_t)t * U * N + i] = L(0);
+    if (O.costate_mode == 1)
+#pragma unroll
+      for (int i = 0; i < N; i++) I.lam[(size_t)t * N + i] = 0.0;  // multipliers start at zero
   }
+  if (O.costate_mode == 1 && I.last)
+#pragma unroll
+    for (int i = 0; i < N; i++) I.lam[(size_t)I.T * N + i] = 0.0;
   g.sync();
   const long long c_start = clock64();
   NStats st{0, 0, 0, 0, 0, 0, 0, O.alpha0, {0, 0, 0, 0, 0, 0}};
@@ -1678,7 +1918,7 @@ __device__ void solve_instance(Grp& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>&
     info.r_d = rdl;
   }
   if (g.dead()) rc = ST_ETIMEOUT;
-  if (rc != ST_EINFEAS && rc != ST_ETIMEOUT) residuals(g, I, P, A, info);
+  if (rc != ST_EINFEAS && rc != ST_ETIMEOUT) residuals(g, I, P, A, info, O.costate_mode == 1);
   finalize_traj(g, I);
   info.status = rc;
   info.newton_iters = st.iters;

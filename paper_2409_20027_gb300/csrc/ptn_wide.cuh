@@ -56,6 +56,10 @@ struct WideGroup {
 };
 
 template <>
+struct multiplier_form_ok<WideGroup> {
+  static constexpr bool value = false;
+};
+template <>
 struct exact_only<WideGroup> {
   static constexpr bool value = true;
 };
