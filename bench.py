@@ -211,52 +211,58 @@ def run_batch(args, ptn, W, dev, flush, stream):
             "one_by_one_sample": f"first {ns} instances as single solves (cluster or grid tier), time scaled to {B}"}
 
 
-def run_multiplier(args, ptn, W, dev, flush, stream, tuned, x0, sweep):
-    """The multiplier form of the co-states (option costate_mode = 1, a variant of the
-    method: dynamics multipliers moved to the LQR duals, no co-state scan) on the same
-    single solves as the sweep (same launch shapes, same x0) and on the batch workload.
-    It ends at the same KKT point; reported beside the co-state form's numbers."""
+def run_multiplier(args, ptn, W, dev, flush, stream, tuned, x0):
+    """The multiplier form of the co-states (option costate_mode; a variant of the method:
+    dynamics multipliers moved to the LQR duals instead of the co-state scan), pure (1) and
+    restarted from the scan's co-states at every barrier level (2), beside the co-state
+    form (0) on the same single solves (same x0, same tuned launch shapes), and modes 1, 2
+    on the batch workload.  All forms end at the same KKT point."""
     import torch
     from paper_2409_20027_gb300 import autotune
     out = {"single": {}}
     for Ts in [1024, 4096, args.T]:
         ps = cartpole_instance(Ts)
-        sv = ptn.Solver(ps, max_T=Ts, precision=ptn.PTN_FP32_FP64SOLVE, costate_mode=1)
-        autotune.apply(sv, tuned, Ts)
-        sv.solve_ip(x0, Ts)
-        torch.cuda.synchronize()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        flush.zero_()
-        a.record(stream)
-        _, _, _, inf = sv.solve_ip(x0, Ts)
-        b.record(stream)
-        torch.cuda.synchronize()
-        ref = sweep.get(str(Ts), {})
-        out["single"][str(Ts)] = {"ms": a.elapsed_time(b), "newton_iters": inf["newton_iters"],
-                                  "status": inf["status"], "r_kkt": inf["r_kkt"],
-                                  "costate_form_ms": ref.get("ms"), "costate_form_newton_iters": ref.get("newton_iters")}
-        sv.close()
+        row = {}
+        for mode in [0, 1, 2]:
+            sv = ptn.Solver(ps, max_T=Ts, precision=ptn.PTN_FP32_FP64SOLVE, costate_mode=mode)
+            autotune.apply(sv, tuned, Ts)
+            sv.solve_ip(x0, Ts)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            flush.zero_()
+            a.record(stream)
+            _, _, _, inf = sv.solve_ip(x0, Ts)
+            b.record(stream)
+            torch.cuda.synchronize()
+            row[f"mode{mode}"] = {"ms": a.elapsed_time(b), "newton_iters": inf["newton_iters"],
+                                  "status": inf["status"], "r_kkt": inf["r_kkt"]}
+            sv.close()
+        out["single"][str(Ts)] = row
     B = args.batch
     Tb = W.batch_horizons(B, seed=0)
     dtb = BATCH_HORIZON_S / Tb
     xb = torch.tensor(W.cartpole_batch_x0(B, seed=0), dtype=torch.float64, device=dev)
-    sv = ptn.Solver(W.cartpole(), max_T=int(Tb.max()), max_batch=B, precision=ptn.PTN_FP32_FP64SOLVE, costate_mode=1)
-    sv.solve_batch(xb, Tb, dt_b=dtb)
-    torch.cuda.synchronize()
-    flush.zero_()
-    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a.record(stream)
-    _, _, _, infos = sv.solve_batch(xb, Tb, dt_b=dtb)
-    b.record(stream)
-    torch.cuda.synchronize()
-    ms = a.elapsed_time(b)
-    st = [i["status"] for i in infos]
-    out["batch"] = {"solves_per_s": B / (ms * 1e-3), "ms": ms,
-                    "status_counts": {str(k): st.count(k) for k in set(st)},
-                    "newton_iters_mean": float(np.mean([i["newton_iters"] for i in infos]))}
-    sv.close()
-    out["workload"] = ("cart-pole IP as the sweep (2.56 s horizon, tuned launch) and the batch workload, "
-                       "multiplier form of the co-states")
+    out["batch"] = {}
+    for mode in [1, 2]:
+        sv = ptn.Solver(W.cartpole(), max_T=int(Tb.max()), max_batch=B, precision=ptn.PTN_FP32_FP64SOLVE,
+                        costate_mode=mode)
+        sv.solve_batch(xb, Tb, dt_b=dtb)
+        torch.cuda.synchronize()
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        _, _, _, infos = sv.solve_batch(xb, Tb, dt_b=dtb)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b)
+        st = [i["status"] for i in infos]
+        out["batch"][f"mode{mode}"] = {"solves_per_s": B / (ms * 1e-3), "ms": ms,
+                                       "status_counts": {str(k): st.count(k) for k in set(st)},
+                                       "newton_iters_mean": float(np.mean([i["newton_iters"] for i in infos]))}
+        sv.close()
+    out["workload"] = ("cart-pole IP as the sweep (2.56 s horizon, tuned launch, x0 seed 0) in co-state forms "
+                       "0 (scan), 1 (multiplier), 2 (multiplier restarted per barrier level); the batch "
+                       "workload in forms 1 and 2 (form 0: the batch section)")
     return out
 
 
@@ -517,8 +523,8 @@ def main():
     if not args.no_seq and single:
         seq = run_sequential(args, ptn, W, dev, flush, stream)
     mult = None
-    if not args.no_mult and single and not args.no_sweep:
-        mult = run_multiplier(args, ptn, W, dev, flush, stream, tuned, x0s[0], sweep)
+    if not args.no_mult and single:
+        mult = run_multiplier(args, ptn, W, dev, flush, stream, tuned, x0s[0])
 
     if rank != 0:
         return

@@ -99,7 +99,12 @@ typedef struct ptn_options {
                            Lagrangian's gradients d_t, q_t are local in t (no product of
                            F_t^T is formed), the LQR carries q_t as a linear state term, and
                            the stopping test is max(|d|, |q|) <= tol; lam_out returns nu.
-                           Same KKT point as mode 0.  Not built for nx >= 8
+                           Same KKT point as mode 0.
+                           2: as 1, but every Newton sub-problem (barrier level, ADMM
+                           iteration) restarts the multipliers from the co-states of the
+                           scan; more robust than 1 far from the solution (where the
+                           pure form can stall), still fewer Newton iterations than 0 on
+                           long horizons.  Modes 1, 2 are not built for nx >= 8
                            (PTN_ERR_INVALID_ARG). */
   double mu0, zeta, mu_final, tol_inner, tol_final, rho, admm_tol;
   double alpha0, alpha_min, alpha_max, ls_beta, armijo_c1, armijo_eps, roll_tol;

@@ -94,7 +94,8 @@ class Options:
     ls_count: int = 10
     admm_fixed_iters: int = 0
     # 0: co-states by the backward recursion (Sec. III-B); 1: multiplier form, a variant
-    # that updates multipliers of the dynamics by the LQR duals (no recursion through F^T)
+    # that updates multipliers of the dynamics by the LQR duals (no recursion through F^T);
+    # 2: the multiplier form restarted from the recursion's co-states at every sub-problem
     costate_mode: int = 0
 
     def _c(self) -> _Options:

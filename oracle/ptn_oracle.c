@@ -59,7 +59,9 @@ typedef struct orc_options {
     double alpha0, alpha_min, alpha_max, ls_beta, armijo_c1, armijo_eps;
     int max_newton, max_outer, ls_count, admm_fixed_iters;
     int costate_mode; /* 0: co-states by the backward recursion (Sec. III-B);
-                         1: multiplier form (dynamics multipliers updated by the LQR duals) */
+                         1: multiplier form (dynamics multipliers updated by the LQR duals);
+                         2: multiplier form whose multipliers restart from the co-states of
+                            the recursion at the start of every Newton sub-problem */
 } orc_options;
 
 typedef struct orc_aug {
@@ -1179,6 +1181,12 @@ static int newton_solve(const orc_problem *P, const rows_t *R, const orc_aug *G,
     ws_alloc(&W, T, n, m);
     double *xc = malloc(sizeof(double) * (T + 1) * n), *uc = malloc(sizeof(double) * (T * m + 1));
     double *q = nu ? calloc((size_t)(T + 1) * n, sizeof(double)) : NULL;
+    if (nu && o->costate_mode == 2) {
+        /* hybrid: each sub-problem (barrier level, ADMM iteration) starts from the
+         * co-states of the recursion; multiplier steps take over from there */
+        costate_pass(P, R, G, T, x, u, &W);
+        memcpy(nu, W.lam, sizeof(double) * (T + 1) * n);
+    }
     double J0 = traj_cost(P, R, G, T, x, u, NULL);
     double r = INFINITY;
     for (int it = 0; it <= o->max_newton; it++) {
@@ -1300,7 +1308,7 @@ int orc_solve_ip(const orc_problem *P, const orc_options *o, const double *x0,
     if (!check_feasible(P, &R, T, x, u)) { info[0] = ORC_EINFEAS; return ORC_EINFEAS; }
     nstats st = {0, 0, 0, o->alpha0};
     /* multiplier form: nu starts at zero (no recursion through F^T at the start either) */
-    double *nu = o->costate_mode == 1 ? calloc((size_t)(T + 1) * n, sizeof(double)) : NULL;
+    double *nu = o->costate_mode != 0 ? calloc((size_t)(T + 1) * n, sizeof(double)) : NULL;
     double mu = o->mu0;
     int rc = ORC_OK, level = 0;
     orc_aug G = {AUG_BARRIER, R.nw, mu, 0.0, NULL, NULL};
@@ -1341,7 +1349,7 @@ int orc_solve_fixed_mu(const orc_problem *P, const orc_options *o, double mu, do
     if (!check_feasible(P, &R, T, x, u)) { info[0] = ORC_EINFEAS; return ORC_EINFEAS; }
     nstats st = {0, 0, 0, o->alpha0};
     orc_aug G = {AUG_BARRIER, R.nw, mu, 0.0, NULL, NULL};
-    double *nu = o->costate_mode == 1 ? calloc((size_t)(T + 1) * P->nx, sizeof(double)) : NULL;
+    double *nu = o->costate_mode != 0 ? calloc((size_t)(T + 1) * P->nx, sizeof(double)) : NULL;
     int rc = newton_solve(P, &R, &G, o, T, x, u, tol, &st, NULL, nu);
     residuals(P, &R, &G, T, x, u, lam, info, nu);
     free(nu);
@@ -1380,7 +1388,7 @@ int orc_solve_admm(const orc_problem *P, const orc_options *o, const double *x0,
             vi[t * nw + r] = 0.0;
         }
     nstats st = {0, 0, 0, o->alpha0};
-    double *nu = o->costate_mode == 1 ? calloc((size_t)(T + 1) * n, sizeof(double)) : NULL;
+    double *nu = o->costate_mode != 0 ? calloc((size_t)(T + 1) * n, sizeof(double)) : NULL;
     orc_aug G = {AUG_ADMM, nw, 0.0, o->rho, zi, vi};
     int rc = ORC_ENOTCONV, k;
     double rp = INFINITY, rdl = INFINITY;

@@ -161,8 +161,10 @@ static int check_options(ptn_solver* s, const ptn_options* o) {
   if (o->grid_steps_per_thread < 1) return fail(s, PTN_ERR_INVALID_ARG, "grid_steps_per_thread must be >= 1");
   if (o->cluster_max_blocks < 0 || o->cluster_max_blocks > 16)
     return fail(s, PTN_ERR_INVALID_ARG, "cluster_max_blocks must be in [0, 16]");
-  if (o->costate_mode != 0 && o->costate_mode != 1)
-    return fail(s, PTN_ERR_INVALID_ARG, "costate_mode must be 0 (co-state scan) or 1 (multiplier form)");
+  if (o->costate_mode < 0 || o->costate_mode > 2)
+    return fail(s, PTN_ERR_INVALID_ARG,
+                "costate_mode must be 0 (co-state scan), 1 (multiplier form) or 2 (multiplier form restarted "
+                "from the co-states at each sub-problem)");
   return PTN_OK;
 }
 
@@ -397,8 +399,8 @@ static int plan_launch(ptn_solver* s, int method, int B, const int* T_b, long lo
   int cl_blocks = 0;
   // models with n >= 8 run the wide tier (one CTA per instance, one warp per chunk)
   const bool wide = s->n >= 8;
-  if (wide && s->opt.costate_mode == 1)
-    return fail(s, PTN_ERR_INVALID_ARG, "the multiplier form (costate_mode 1) is not built for the wide tier (nx >= 8)");
+  if (wide && s->opt.costate_mode != 0)
+    return fail(s, PTN_ERR_INVALID_ARG, "the multiplier form (costate_mode 1, 2) is not built for the wide tier (nx >= 8)");
   if (!wide && !s->opt.sequential && B == 1 && s->opt.cluster_max_blocks >= 2) {
     const long long per = (long long)s->opt.block_threads * s->opt.grid_steps_per_thread;
     const long long need = (T_b[0] + per - 1) / per;
@@ -696,9 +698,9 @@ extern "C" int ptn_solve_ip_static(const ptn_problem* prob, const ptn_options* o
   int nx, nu;
   if (model_dims(prob->model, &nx, &nu))
     return static_fail(err, err_len, PTN_ERR_INVALID_ARG, "unknown or unsupported model id %d", prob->model);
-  if (nx >= 8 && o.costate_mode == 1)
+  if (nx >= 8 && o.costate_mode != 0)
     return static_fail(err, err_len, PTN_ERR_INVALID_ARG,
-                       "the multiplier form (costate_mode 1) is not built for the wide tier (nx >= 8)");
+                       "the multiplier form (costate_mode 1, 2) is not built for the wide tier (nx >= 8)");
   if (prob->nx != nx || prob->nu != nu)
     return static_fail(err, err_len, PTN_ERR_INVALID_ARG, "model %d has nx=%d nu=%d, got %d %d", prob->model, nx, nu,
                        prob->nx, prob->nu);
@@ -765,7 +767,7 @@ extern "C" int ptn_solve_ip_static(const ptn_problem* prob, const ptn_options* o
   size_t o_z = off; off = align256(off + sizeof(double) * S * (nw > 0 ? nw : 1));
   size_t o_v = off; off = align256(off + sizeof(double) * S * (nw > 0 ? nw : 1));
   // the multiplier form's arrays only when it is selected
-  const bool mult = o.costate_mode == 1;
+  const bool mult = o.costate_mode != 0;
   size_t o_q = off; off = align256(off + (mult ? sizeof(double) * SB * n : 0));
   size_t o_dnu = off; off = align256(off + (mult ? sizeof(double) * SB * n : 0));
   size_t o_Sv = off; off = align256(off + (mult ? 8 * SB * n * n : 0));

@@ -1247,7 +1247,7 @@ __device__ int newton_solve(Grp& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>& P,
   constexpr int N = M::NX;
   constexpr bool MIXED = std::is_same<L, float>::value && !exact_only<Grp>::value;
   constexpr bool CAN_MULT = multiplier_form_ok<Grp>::value;
-  const bool MULT = CAN_MULT && O.costate_mode == 1;
+  const bool MULT = CAN_MULT && O.costate_mode != 0;
   // first-order terms: the co-state scan, or the multiplier form's local gradients
   auto first_order = [&](bool ex) -> double {
     if constexpr (CAN_MULT) {
@@ -1265,6 +1265,12 @@ __device__ int newton_solve(Grp& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>& P,
   int rc = ST_ENOTCONV;
   double r = INFINITY;
   bool exact = !MIXED;  // FP64 gradients, FP64 rollouts and absolute FP64 merits
+  if (MULT && O.costate_mode == 2) {
+    // hybrid multiplier form: this sub-problem's multipliers start from the co-states of
+    // the scan (written to I.lam; the pass ends with a group reduction, so they are
+    // visible to the neighbouring chunks), multiplier steps take over from there
+    costate_pass(g, I, P, A, exact);
+  }
   bool stalled = false;  // the FP32-increment phase ran alpha past alpha_max
   for (int it = 0; it <= O.max_newton; it++) {
     if (g.dead()) return ST_ETIMEOUT;
@@ -1833,11 +1839,11 @@ __device__ void solve_instance(Grp& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>&
     }
 #pragma unroll
     for (int i = 0; i < U * N; i++) I.Gam[(size_t)t * U * N + i] = L(0);
-    if (O.costate_mode == 1)
+    if (O.costate_mode != 0)
 #pragma unroll
       for (int i = 0; i < N; i++) I.lam[(size_t)t * N + i] = 0.0;  // multipliers start at zero
   }
-  if (O.costate_mode == 1 && I.last)
+  if (O.costate_mode != 0 && I.last)
 #pragma unroll
     for (int i = 0; i < N; i++) I.lam[(size_t)I.T * N + i] = 0.0;
   g.sync();
@@ -1918,7 +1924,7 @@ __device__ void solve_instance(Grp& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>&
     info.r_d = rdl;
   }
   if (g.dead()) rc = ST_ETIMEOUT;
-  if (rc != ST_EINFEAS && rc != ST_ETIMEOUT) residuals(g, I, P, A, info, O.costate_mode == 1);
+  if (rc != ST_EINFEAS && rc != ST_ETIMEOUT) residuals(g, I, P, A, info, O.costate_mode != 0);
   finalize_traj(g, I);
   info.status = rc;
   info.newton_iters = st.iters;

@@ -58,13 +58,14 @@ CASES = {
 }
 
 
+@pytest.mark.parametrize("mode", [1, 2])
 @pytest.mark.parametrize("case", list(CASES))
-def test_fp64_cta_matches_oracle_multiplier_form(ptn, case):
+def test_fp64_cta_matches_oracle_multiplier_form(ptn, case, mode):
     p, x0, T, threads = CASES[case]
     s = ptn.Solver(p, max_T=T, precision=ptn.PTN_FP64, block_threads=threads, grid_min_T=0,
-                   cluster_max_blocks=0, costate_mode=1)
+                   cluster_max_blocks=0, costate_mode=mode)
     x, u, lam, info = s.solve_ip(dev(x0), T)
-    ref = O.solve_ip(p, x0, T, opts=MULT)
+    ref = O.solve_ip(p, x0, T, opts=O.Options(costate_mode=mode))
     check(info, ref, x, u, lam, FP64_TOL)
     # and it is the co-state form's KKT point
     ref0 = O.solve_ip(p, x0, T)
@@ -86,25 +87,25 @@ TIERS = {
 }
 
 
-@pytest.mark.parametrize("T,tier", [(1024, "cluster"), (1024, "grid")])
-def test_fp64_multi_cta_tiers(ptn, T, tier):
+@pytest.mark.parametrize("T,tier,mode", [(1024, "cluster", 1), (1024, "grid", 1), (1024, "grid", 2)])
+def test_fp64_multi_cta_tiers(ptn, T, tier, mode):
     p = W.cartpole(T=T, horizon=2.56)
     x0 = W.cartpole_x0(1)
-    s = ptn.Solver(p, max_T=T, precision=ptn.PTN_FP64, costate_mode=1, **TIERS[tier])
+    s = ptn.Solver(p, max_T=T, precision=ptn.PTN_FP64, costate_mode=mode, **TIERS[tier])
     x, u, lam, info = s.solve_ip(dev(x0), T)
-    ref = O.solve_ip(p, x0, T, opts=MULT)
+    ref = O.solve_ip(p, x0, T, opts=O.Options(costate_mode=mode))
     check(info, ref, x, u, lam, FP64_TOL)
 
 
-@pytest.mark.parametrize("T,tier,prec", [(256, "cta", 1), (1024, "cluster", 1), (4096, "grid", 1),
-                                         (4096, "cluster", 2)])
-def test_fp32_matches_oracle(ptn, T, tier, prec):
+@pytest.mark.parametrize("T,tier,prec,mode", [(256, "cta", 1, 1), (1024, "cluster", 1, 1), (4096, "grid", 1, 1),
+                                              (4096, "cluster", 2, 1), (1024, "cluster", 1, 2), (4096, "grid", 1, 2)])
+def test_fp32_matches_oracle(ptn, T, tier, prec, mode):
     # both sides solved to 1e-7, as in the co-state form's FP32 parity tests
     p = W.cartpole(T=T, horizon=2.56)
     x0 = W.cartpole_x0(1)
-    s = ptn.Solver(p, max_T=T, precision=prec, tol_final=1e-7, costate_mode=1, **TIERS[tier])
+    s = ptn.Solver(p, max_T=T, precision=prec, tol_final=1e-7, costate_mode=mode, **TIERS[tier])
     x, u, lam, info = s.solve_ip(dev(x0), T)
-    ref = O.solve_ip(p, x0, T, opts=O.Options(tol_final=1e-7, costate_mode=1))
+    ref = O.solve_ip(p, x0, T, opts=O.Options(tol_final=1e-7, costate_mode=mode))
     check(info, ref, x, u, lam, FP32_TOL, with_lam=False)
     assert info["r_stat"] <= 1e-7
 
@@ -122,6 +123,31 @@ def test_batch_ragged_matches_oracle(ptn):
         T = int(Tb[b])
         ref = O.solve_ip(p, x0s[b], T, opts=MULT)
         check(infos[b], ref, X[xo:xo + T + 1], U[uo:uo + T], Lm[xo:xo + T + 1], FP64_TOL)
+        xo += T + 1
+        uo += T
+
+
+def test_hybrid_form_on_batch_instances_where_the_pure_form_stalls(ptn):
+    # batch workload instances (1.28 s horizon at dt_b = 1.28 / T_b): in mode 2 the GPU
+    # batch matches the oracle's mode 2, which reaches the co-state form's KKT point
+    Tb_all = W.batch_horizons(1024, seed=0)
+    ks = [310, 236, 519, 58]
+    Tb = Tb_all[ks].astype(np.int32)
+    dtb = 1.28 / Tb
+    x0s = W.cartpole_batch_x0(1024, seed=0)[ks]
+    base = W.cartpole()
+    s = ptn.Solver(base, max_T=int(Tb.max()), max_batch=len(ks), precision=ptn.PTN_FP64, block_threads=64,
+                   costate_mode=2)
+    X, U, Lm, infos = s.solve_batch(dev(x0s), Tb, dt_b=dtb)
+    xo = uo = 0
+    for b in range(len(ks)):
+        T = int(Tb[b])
+        sc = float(dtb[b]) / base.dt
+        p = base.replace(dt=float(dtb[b]), Q=base.Q * sc, R=base.R * sc)
+        ref = O.solve_ip(p, x0s[b], T, opts=O.Options(costate_mode=2))
+        check(infos[b], ref, X[xo:xo + T + 1], U[uo:uo + T], Lm[xo:xo + T + 1], FP64_TOL)
+        ref0 = O.solve_ip(p, x0s[b], T)
+        assert rel(U[uo:uo + T].cpu().numpy(), ref0["u"]) <= FP64_TOL
         xo += T + 1
         uo += T
 
