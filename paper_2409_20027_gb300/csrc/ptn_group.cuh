@@ -129,6 +129,14 @@ struct CtaGroup {
   __device__ E scan(E v, const Op& op, bool suffix, bool& ok) {
     return block_scan_excl(v, op, suffix, ok, reinterpret_cast<E*>(sm), (E*)nullptr);
   }
+
+  // scan followed by a reduction of K values (one group barrier each within a CTA)
+  template <class E, class Op, int K>
+  __device__ E scan_reduce(E v, const Op& op, bool suffix, bool& ok, double (&red)[K], unsigned maxmask) {
+    E r = scan(v, op, suffix, ok);
+    reduce<K>(red, maxmask);
+    return r;
+  }
 };
 
 // ---------------------------------------------------------------------------
@@ -184,6 +192,68 @@ struct GridGroup {
     __syncthreads();
   }
 
+  // Warp 0 combines the K block values of every block (written before the barrier):
+  // each lane folds blocks lane, lane + 32, ... in order, all K loads of a block issued
+  // together, then an ordered shuffle tree -- the same in every block, so every block gets
+  // bit-identical results; lane 0 stores them to sres.
+  template <int K>
+  __device__ void totals_warp0(const double* rslot, unsigned maxmask, double* sres) const {
+    const int lane = threadIdx.x;
+    double a[K];
+#pragma unroll
+    for (int k = 0; k < K; k++) a[k] = ((maxmask >> k) & 1u) ? -INFINITY : 0.0;
+    for (int b = lane; b < (int)gridDim.x; b += 32) {
+      double o[K];
+#pragma unroll
+      for (int k = 0; k < K; k++) o[k] = __ldcg(rslot + (size_t)b * 8 + k);
+#pragma unroll
+      for (int k = 0; k < K; k++) a[k] = ((maxmask >> k) & 1u) ? fmax(a[k], o[k]) : a[k] + o[k];
+    }
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+#pragma unroll
+      for (int k = 0; k < K; k++) {
+        const double o = __shfl_down_sync(PTN_FULL, a[k], off);
+        if ((lane & (2 * off - 1)) == 0) a[k] = ((maxmask >> k) & 1u) ? fmax(a[k], o) : a[k] + o;
+      }
+    }
+    if (lane == 0)
+#pragma unroll
+      for (int k = 0; k < K; k++) sres[k] = a[k];
+  }
+
+  // Warp 0 folds the totals of the blocks before (prefix) or after (suffix) this one: each
+  // lane folds a contiguous range, then an ordered tree; lane 0 stores the carry.
+  template <class E, class Op>
+  __device__ void carry_warp0(const E* slot, const Op& op, bool suffix, bool& ok, E* scarry) const {
+    const int lane = threadIdx.x;
+    const int lo = suffix ? blockIdx.x + 1 : 0;
+    const int hi = suffix ? gridDim.x : blockIdx.x;
+    const int cnt = hi - lo;
+    const int per = (cnt + 31) / 32;
+    E acc;
+    set_identity(acc);
+    const int b0 = lo + lane * per;
+    const int b1 = min(hi, b0 + per);
+    for (int b = b0; b < b1; b++) {
+      E t;
+      const char* src = reinterpret_cast<const char*>(slot) + (size_t)b * gs.elem_bytes;
+      // volatile-free copy through L2 (written before the barrier by another block)
+      const unsigned* s4 = reinterpret_cast<const unsigned*>(src);
+      unsigned* d4 = reinterpret_cast<unsigned*>(&t);
+#pragma unroll
+      for (int i = 0; i < (int)(sizeof(E) / 4); i++) d4[i] = __ldcg(s4 + i);
+      if (b == b0) acc = t;
+      else ok &= op(acc, t, acc);
+    }
+#pragma unroll 1
+    for (int off = 1; off < 32; off <<= 1) {
+      E o = shfl_down_e(acc, off);
+      if ((lane & (2 * off - 1)) == 0 && lane + off < 32) ok &= op(acc, o, acc);
+    }
+    if (lane == 0) *scarry = acc;
+  }
+
   template <int K>
   __device__ void reduce(double (&v)[K], unsigned maxmask) {
     static_assert(K <= 8, "at most 8 values per reduction");
@@ -194,34 +264,8 @@ struct GridGroup {
 #pragma unroll
       for (int k = 0; k < K; k++) slot[blockIdx.x * 8 + k] = v[k];
     sync();
-    // warp 0 combines the block values: each lane folds blocks lane, lane + 32, ... in
-    // order, then an ordered shuffle tree (the same in every block, so every block gets
-    // bit-identical results); shared memory broadcasts them to the block
     double* sres = reinterpret_cast<double*>(sm);
-    if (threadIdx.x < 32) {
-      const int lane = threadIdx.x;
-      double a[K];
-#pragma unroll
-      for (int k = 0; k < K; k++) a[k] = ((maxmask >> k) & 1u) ? -INFINITY : 0.0;
-      for (int b = lane; b < (int)gridDim.x; b += 32) {
-        double o[K];  // all K loads of a block issued together
-#pragma unroll
-        for (int k = 0; k < K; k++) o[k] = __ldcg(slot + (size_t)b * 8 + k);
-#pragma unroll
-        for (int k = 0; k < K; k++) a[k] = ((maxmask >> k) & 1u) ? fmax(a[k], o[k]) : a[k] + o[k];
-      }
-#pragma unroll
-      for (int off = 1; off < 32; off <<= 1) {
-#pragma unroll
-        for (int k = 0; k < K; k++) {
-          const double o = __shfl_down_sync(PTN_FULL, a[k], off);
-          if ((lane & (2 * off - 1)) == 0) a[k] = ((maxmask >> k) & 1u) ? fmax(a[k], o) : a[k] + o;
-        }
-      }
-      if (lane == 0)
-#pragma unroll
-        for (int k = 0; k < K; k++) sres[k] = a[k];
-    }
+    if (threadIdx.x < 32) totals_warp0<K>(slot, maxmask, sres);
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < K; k++) v[k] = sres[k];
@@ -239,35 +283,44 @@ struct GridGroup {
     E* slot = reinterpret_cast<E*>(gs.xs + (size_t)phase * gridDim.x * gs.elem_bytes);
     if (threadIdx.x == 0) *reinterpret_cast<E*>(reinterpret_cast<char*>(slot) + (size_t)blockIdx.x * gs.elem_bytes) = *stot;
     sync();
-    // carry = fold of the totals of the blocks before (prefix) or after (suffix) this one,
-    // computed by warp 0: each lane folds a contiguous range, then an ordered tree.
-    if (threadIdx.x < 32) {
-      const int lane = threadIdx.x;
-      const int lo = suffix ? blockIdx.x + 1 : 0;
-      const int hi = suffix ? gridDim.x : blockIdx.x;
-      const int cnt = hi - lo;
-      const int per = (cnt + 31) / 32;
-      E acc;
-      set_identity(acc);
-      const int b0 = lo + lane * per;
-      const int b1 = min(hi, b0 + per);
-      for (int b = b0; b < b1; b++) {
-        E t;
-        const char* src = reinterpret_cast<const char*>(slot) + (size_t)b * gs.elem_bytes;
-        // volatile-free copy through L2 (written before the barrier by another block)
-        const unsigned* s4 = reinterpret_cast<const unsigned*>(src);
-        unsigned* d4 = reinterpret_cast<unsigned*>(&t);
+    if (threadIdx.x < 32) carry_warp0(slot, op, suffix, ok, scarry);
+    __syncthreads();
+    if (!suffix) {
+      if (blockIdx.x > 0) ok &= op(*scarry, ex, ex);
+    } else {
+      if (blockIdx.x + 1 < gridDim.x) ok &= op(ex, *scarry, ex);
+    }
+    __syncthreads();
+    phase ^= 1;
+    return ex;
+  }
+
+  // scan (as scan) and a reduction of K values (as reduce) behind one grid barrier: the
+  // block reduces its values first, then scans, and thread 0 publishes both; warp 0 then
+  // computes the carry and the totals from the same barrier.  Needs block scratch for
+  // nwarps + 2 elements plus 8 + 8 K bytes.
+  template <class E, class Op, int K>
+  __device__ E scan_reduce(E v, const Op& op, bool suffix, bool& ok, double (&red)[K], unsigned maxmask) {
+    static_assert(K <= 8, "at most 8 values per reduction");
+    CtaGroup cg{sm};
+    cg.reduce<K>(red, maxmask);  // ends with a block barrier, so the scratch is free again
+    const int nw = blockDim.x >> 5;
+    E* sw = reinterpret_cast<E*>(sm);
+    E* stot = sw + nw;
+    E* scarry = sw + nw + 1;
+    double* sres = reinterpret_cast<double*>((reinterpret_cast<size_t>(scarry + 1) + 7) & ~size_t(7));
+    E ex = block_scan_excl(v, op, suffix, ok, sw, stot);
+    E* slot = reinterpret_cast<E*>(gs.xs + (size_t)phase * gridDim.x * gs.elem_bytes);
+    double* rslot = gs.red + (size_t)phase * gridDim.x * 8;
+    if (threadIdx.x == 0) {
+      *reinterpret_cast<E*>(reinterpret_cast<char*>(slot) + (size_t)blockIdx.x * gs.elem_bytes) = *stot;
 #pragma unroll
-        for (int i = 0; i < (int)(sizeof(E) / 4); i++) d4[i] = __ldcg(s4 + i);
-        if (b == b0) acc = t;
-        else ok &= op(acc, t, acc);
-      }
-#pragma unroll 1
-      for (int off = 1; off < 32; off <<= 1) {
-        E o = shfl_down_e(acc, off);
-        if ((lane & (2 * off - 1)) == 0 && lane + off < 32) ok &= op(acc, o, acc);
-      }
-      if (lane == 0) *scarry = acc;
+      for (int k = 0; k < K; k++) rslot[blockIdx.x * 8 + k] = red[k];
+    }
+    sync();
+    if (threadIdx.x < 32) {
+      carry_warp0(slot, op, suffix, ok, scarry);
+      totals_warp0<K>(rslot, maxmask, sres);
     }
     __syncthreads();
     if (!suffix) {
@@ -275,6 +328,8 @@ struct GridGroup {
     } else {
       if (blockIdx.x + 1 < gridDim.x) ok &= op(ex, *scarry, ex);
     }
+#pragma unroll
+    for (int k = 0; k < K; k++) red[k] = sres[k];
     __syncthreads();
     phase ^= 1;
     return ex;
@@ -374,6 +429,14 @@ struct ClusterGroup {
     __syncthreads();
     phase ^= 1;
     return ex;
+  }
+
+  // scan followed by a reduction of K values (the cluster barrier is cheap: no fusion)
+  template <class E, class Op, int K>
+  __device__ E scan_reduce(E v, const Op& op, bool suffix, bool& ok, double (&red)[K], unsigned maxmask) {
+    E r = scan(v, op, suffix, ok);
+    reduce<K>(red, maxmask);
+    return r;
   }
 };
 

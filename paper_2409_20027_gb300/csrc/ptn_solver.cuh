@@ -827,9 +827,12 @@ __device__ void quadratize(Grp& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>& P, 
 //
 // Sv, sv (optional, (T+1) x N*N and x N): receive S_t and s_t of the LQR value function
 // V_t(dx) = 1/2 dx^T S_t dx + s_t^T dx (the multiplier form's dual step needs them).
+//
+// group_ok = false: return this thread's flag without the group reduction (the caller
+// folds it into a later reduction).
 template <class M, class L, class SV, class Grp>
 __device__ bool value_pass(Grp& g, Inst<M, L>& I, double alpha, const double* qx = nullptr, L* Sv = nullptr,
-                           L* sv = nullptr) {
+                           L* sv = nullptr, bool group_ok = true) {
   constexpr int N = M::NX, U = M::NU;
   bool ok = true, have = false;
   Val<N, L> agg;
@@ -897,6 +900,7 @@ __device__ bool value_pass(Grp& g, Inst<M, L>& I, double alpha, const double* qx
 #pragma unroll
     for (int i = 0; i < U; i++) I.gam[(size_t)t * U + i] = gam[i];
   }
+  if (!group_ok) return ok;
   double red[1] = {ok ? 0.0 : 1.0};
   g.template reduce<1>(red, 1u);
   return red[0] == 0.0;
@@ -923,9 +927,13 @@ __device__ __noinline__ void mult_terms(int t, const L* dx, const double* qx, co
 // Multiplier form (qx, Sv, sv, dnu given): G1 also carries sum_t q_t^T dx_t (the
 // multiplier terms of the Lagrangian telescope along the linearised dynamics, so G1 stays
 // the cost's directional derivative), and dnu_t = S_t dx_t + s_t is the dual step.
+//
+// fail (optional): a per-thread flag (0 or 1) reduced by maximum with G1, G2; on return
+// the group's flag (the value pass's factorisation result, without a reduction of its own).
 template <class M, class L, class Grp>
 __device__ void state_pass(Grp& g, Inst<M, L>& I, double& G1, double& G2, const double* qx = nullptr,
-                           const L* Sv = nullptr, const L* sv = nullptr, double* dnu = nullptr) {
+                           const L* Sv = nullptr, const L* sv = nullptr, double* dnu = nullptr,
+                           double* fail = nullptr) {
   constexpr int N = M::NX, U = M::NU;
   Aff<N, L> agg;
   set_identity(agg);
@@ -1007,6 +1015,14 @@ __device__ void state_pass(Grp& g, Inst<M, L>& I, double& G1, double& G2, const 
       q += L(0.5) * dx[i] * Pd[i];
     }
     g2 += double(q);
+  }
+  if (fail) {
+    double red[3] = {g1, g2, *fail};
+    g.template reduce<3>(red, 4u);
+    G1 = red[0];
+    G2 = red[1];
+    *fail = red[2];
+    return;
   }
   double red[2] = {g1, g2};
   g.template reduce<2>(red, 0u);
@@ -1170,9 +1186,10 @@ __device__ int rollout(Grp& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>& P, cons
     }
     if (nonfin) rmax = INFINITY;
     bool ok = true;
-    Aff<N, L> inc = g.scan(el, StateOp(), false, ok);
     double red[5] = {rmax, xmax, cost, inf ? 1.0 : 0.0, nonfin ? 1.0 : 0.0};
-    g.template reduce<5>(red, 0x1bu);  // max, max, sum, max, max
+    // boundary corrections (prefix scan) and convergence/merit sums (max, max, sum, max,
+    // max) behind one group barrier
+    Aff<N, L> inc = g.scan_reduce(el, StateOp(), false, ok, red, 0x1bu);
     if (iters) *iters = it + 1;
     if (red[4] > 0.0) return ROLL_FAIL;
     const double rtol = MIXED ? fmax(O.roll_tol, 1e-8) : O.roll_tol;
@@ -1302,30 +1319,40 @@ __device__ int newton_solve(Grp& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>& P,
     quadratize(g, I, P, A);
     long long c2 = clock64();
     st.cyc[1] += c2 - c1;
-    auto vpass = [&]() -> bool {
-      if constexpr (CAN_MULT) {
-        return value_pass<M, L, SV>(g, I, st.alpha, MULT ? I.q : nullptr, MULT ? I.Sv : nullptr,
-                                    MULT ? I.sv : nullptr);
-      } else {
-        return value_pass<M, L, SV>(g, I, st.alpha);
-      }
-    };
-    while (!vpass()) {
-      st.factor_fails++;
-      st.alpha = fmax(10.0 * st.alpha, 1e-8);
-      if (st.alpha > O.alpha_max || g.dead()) { *rfinal = r; return g.dead() ? ST_ETIMEOUT : ST_ENUM; }
-    }
-    long long c3 = clock64();
-    st.cyc[2] += c3 - c2;
     double G1, G2;
+    long long c4;
     if constexpr (CAN_MULT) {
-      state_pass(g, I, G1, G2, MULT ? I.q : nullptr, MULT ? I.Sv : nullptr, MULT ? I.sv : nullptr,
-                 MULT ? I.dnu : nullptr);
+      // value pass, then the state pass, whose group reduction also carries the value
+      // pass's factorisation flag (one group reduction fewer per step); a failure anywhere
+      // redoes both with a larger alpha (the state pass's results are then discarded)
+      for (;;) {
+        const bool okl = value_pass<M, L, SV>(g, I, st.alpha, MULT ? I.q : nullptr, MULT ? I.Sv : nullptr,
+                                              MULT ? I.sv : nullptr, false);
+        const long long c3 = clock64();
+        st.cyc[2] += c3 - c2;
+        double fail = okl ? 0.0 : 1.0;
+        state_pass(g, I, G1, G2, MULT ? I.q : nullptr, MULT ? I.Sv : nullptr, MULT ? I.sv : nullptr,
+                   MULT ? I.dnu : nullptr, &fail);
+        c4 = clock64();
+        st.cyc[3] += c4 - c3;
+        if (fail == 0.0) break;
+        st.factor_fails++;
+        st.alpha = fmax(10.0 * st.alpha, 1e-8);
+        if (st.alpha > O.alpha_max || g.dead()) { *rfinal = r; return g.dead() ? ST_ETIMEOUT : ST_ENUM; }
+        c2 = clock64();
+      }
     } else {
+      while (!value_pass<M, L, SV>(g, I, st.alpha)) {
+        st.factor_fails++;
+        st.alpha = fmax(10.0 * st.alpha, 1e-8);
+        if (st.alpha > O.alpha_max || g.dead()) { *rfinal = r; return g.dead() ? ST_ETIMEOUT : ST_ENUM; }
+      }
+      const long long c3 = clock64();
+      st.cyc[2] += c3 - c2;
       state_pass(g, I, G1, G2);
+      c4 = clock64();
+      st.cyc[3] += c4 - c3;
     }
-    long long c4 = clock64();
-    st.cyc[3] += c4 - c3;
     bool accepted = false;
     double s = 1.0, Js = INFINITY, dJ = INFINITY;
     for (int k = 0; k < O.ls_count; k++, s *= O.ls_beta) {
@@ -1958,10 +1985,12 @@ struct KArgs {
 
 template <int N, int U, class L>
 __host__ __device__ constexpr size_t scratch_bytes(int nwarps) {
-  // largest collective element (value element), nwarps + 2 slots, or 8 doubles per warp
-  return ((size_t)(nwarps + 2) * sizeof(Val<N, L>) > (size_t)nwarps * 8 * 8)
-             ? (size_t)(nwarps + 2) * sizeof(Val<N, L>)
-             : (size_t)nwarps * 8 * 8;
+  // largest collective element (value element), nwarps + 2 slots, or 8 doubles per warp;
+  // a fused scan + reduction of state elements needs nwarps + 2 slots and 8 + 64 bytes
+  const size_t a = (size_t)(nwarps + 2) * sizeof(Val<N, L>);
+  const size_t b = (size_t)nwarps * 8 * 8;
+  const size_t c = (size_t)(nwarps + 2) * sizeof(Aff<N, L>) + 72;
+  return a > b ? (a > c ? a : c) : (b > c ? b : c);
 }
 
 // one CTA per instance (batches and short horizons)
@@ -2034,6 +2063,10 @@ struct SeqGroup {
     E id;
     set_identity(id);
     return id;
+  }
+  template <class E, class Op, int K>
+  __device__ E scan_reduce(E v, const Op& op, bool suffix, bool& ok, double (&)[K], unsigned) {
+    return scan(v, op, suffix, ok);
   }
 };
 
