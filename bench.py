@@ -48,7 +48,7 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 FP64_PEAK_TFLOPS = 1.25
 # DRAM bytes (read + write) of one k_solve_grid launch of this workload, from the ncu
 # capture summarised in profiles/k_solve_grid_cartpole_T16384.md
-TRAFFIC_BYTES = (2.869248 + 1.680896) * 1e6
+TRAFFIC_BYTES = (2.443776 + 1.739264) * 1e6
 
 
 def flop_split(n, m, T, info):

@@ -6,7 +6,7 @@
  *     l_{N+1}(x_{N+1}) + sum_{t=1..N} l_t(x_t, u_t)
  * subject to x_{t+1} = f(x_t, u_t), g(x_t) <= 0, h(u_t) <= 0, x_1 = x0.
  * Here N = T, l_t(x,u) = (x-xref)^T Q (x-xref) + (u-uref)^T R (u-uref) (no 1/2),
- * l_{N+1}(x) = (x-xref)^T Qf (x-xref), f is one of the built-in models and g, h are
+ * l_{N+1}(x) = (x-xref)^T Qf (x-xref), f is a built-in or user-registered model and g, h are
  * box bounds (each finite bound is one constraint row).
  *
  * Solvers: primal log-barrier interior point (Sec. II-B, eq. lb-min / lb-step-2) and
@@ -126,6 +126,12 @@ typedef struct ptn_info {
 } ptn_info;
 
 typedef struct ptn_solver ptn_solver;
+
+/* Dimensions of model id `model`: a built-in model (pendulum, cart-pole, quadrotor) or one
+ * registered from a user unit linked into this library (ids >= 64, see
+ * ptn_user_model.cuh).  Writes *nx, *nu and returns 0, or returns PTN_ERR_INVALID_ARG for
+ * an id this library does not know.  Needs no GPU. */
+int ptn_model_dims(int model, int* nx, int* nu);
 
 /* Fill *opt with the defaults listed above. */
 void ptn_default_options(ptn_options* opt);

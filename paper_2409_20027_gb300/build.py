@@ -47,17 +47,36 @@ def _stale(obj: str, src: str, headers: list[str]) -> bool:
     return any(os.path.getmtime(f) > t for f in [src] + headers)
 
 
-def build(force: bool = False, jobs: int | None = None, verbose: bool = False) -> str:
+def build(force: bool = False, jobs: int | None = None, verbose: bool = False, extra=None,
+          out: str | None = None) -> str:
+    """Compile the library; returns the path of libptn.so.
+
+    extra: .cu files with user models (ptn_user_model.cuh), compiled with the kernel
+    sources on the include path and linked into a library of their own in `out` (the
+    package's objects are built as usual and reused).  PTN_USER_MODELS (comma list of
+    paths) adds such files to the default build."""
     os.makedirs(OUT, exist_ok=True)
     nvcc = _nvcc()
     headers = glob.glob(os.path.join(CSRC, "*.cuh")) + [os.path.join(HERE, "..", "include", "ptn.h")]
     srcs = sources()
     objs = [os.path.join(OUT, os.path.basename(s)[:-3] + ".o") for s in srcs]
+    extra = list(extra or [])
+    env_extra = [x for x in os.environ.get("PTN_USER_MODELS", "").split(",") if x.strip()]
+    if env_extra and out is None:
+        extra += env_extra
+    lib = LIB if not extra or out is None else os.path.join(out, "libptn.so")
+    if extra:
+        edir = out or OUT
+        os.makedirs(edir, exist_ok=True)
+        for e in extra:
+            e = os.path.abspath(e)
+            srcs.append(e)
+            objs.append(os.path.join(edir, "user_" + os.path.basename(e)[:-3] + ".o"))
     todo = [(s, o) for s, o in zip(srcs, objs) if force or _stale(o, s, headers)]
 
     def comp(so):
         s, o = so
-        cmd = [nvcc, *ARCH, *FLAGS, "-c", s, "-o", o + ".tmp"]
+        cmd = [nvcc, *ARCH, *FLAGS, "-I", CSRC, "-c", s, "-o", o + ".tmp"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed for {os.path.basename(s)}:\n{r.stderr[-4000:]}")
@@ -68,13 +87,15 @@ def build(force: bool = False, jobs: int | None = None, verbose: bool = False) -
     if todo:
         with ThreadPoolExecutor(max_workers=jobs or min(len(todo), os.cpu_count() or 4)) as ex:
             list(ex.map(comp, todo))
-    if todo or not os.path.exists(LIB):
-        tmp = LIB + f".{os.getpid()}.tmp"
+    # relink when anything was compiled or an object is newer than the library (another
+    # build, e.g. one with user models, may have refreshed the shared objects)
+    if todo or not os.path.exists(lib) or any(os.path.getmtime(o) > os.path.getmtime(lib) for o in objs):
+        tmp = lib + f".{os.getpid()}.tmp"
         r = subprocess.run([nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"], capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("link failed:\n" + r.stderr[-4000:])
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

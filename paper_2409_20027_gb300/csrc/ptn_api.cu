@@ -13,6 +13,7 @@
 
 #include "../../include/ptn.h"
 #include "ptn_launch.cuh"
+#include "ptn_user_model.cuh"
 
 using namespace ptn;
 
@@ -35,13 +36,33 @@ typedef cudaError_t (*launch_fn)(LaunchReq&);
 #define PTN_PICK(m) \
   (precision == PTN_FP64 ? ptn_launch_##m##_f64 : precision == PTN_FP32_FP64SOLVE ? ptn_launch_##m##_f32d : ptn_launch_##m##_f32)
 
+// models registered from outside the library (ptn_user_model.cuh); filled by static
+// initialisers of the user units while the library loads, read-only afterwards
+struct UserModel {
+  int id, nx, nu;
+  launch_fn f64, f32d, f32;
+};
+constexpr int kMaxUserModels = 32;
+UserModel g_user_models[kMaxUserModels];
+int g_num_user_models = 0;
+
+const UserModel* find_user_model(int id) {
+  for (int i = 0; i < g_num_user_models; i++)
+    if (g_user_models[i].id == id) return &g_user_models[i];
+  return nullptr;
+}
+
 launch_fn pick_launcher(int model, int precision) {
   switch (model) {
     case PTN_MODEL_PENDULUM: return PTN_PICK(pendulum);
     case PTN_MODEL_CARTPOLE: return PTN_PICK(cartpole);
     case PTN_MODEL_QUADROTOR: return PTN_PICK(quadrotor);
     case PTN_MODEL_SYNTH_TANH: return PTN_PICK(synth);
-    default: return nullptr;
+    default: {
+      const UserModel* um = find_user_model(model);
+      if (!um) return nullptr;
+      return precision == PTN_FP64 ? um->f64 : precision == PTN_FP32_FP64SOLVE ? um->f32d : um->f32;
+    }
   }
 }
 
@@ -50,11 +71,30 @@ int model_dims(int model, int* nx, int* nu) {
     case PTN_MODEL_PENDULUM: *nx = 2; *nu = 1; return 0;
     case PTN_MODEL_CARTPOLE: *nx = 4; *nu = 1; return 0;
     case PTN_MODEL_QUADROTOR: *nx = 12; *nu = 4; return 0;
-    default: return -1;
+    default: {
+      const UserModel* um = find_user_model(model);
+      if (!um) return -1;
+      *nx = um->nx;
+      *nu = um->nu;
+      return 0;
+    }
   }
 }
 
 bool has_bound(const double* b, int i) { return b && isfinite(b[i]) && fabs(b[i]) < 1e300; }
+
+}  // namespace
+
+namespace ptn {
+int register_model(int id, int nx, int nu, user_launch_fn f64, user_launch_fn f32d, user_launch_fn f32) {
+  if (id < PTN_USER_MODEL_MIN || nx < 1 || nx > PTN_MAXN || nu < 1 || nu > PTN_MAXM) return -1;
+  if (find_user_model(id) || g_num_user_models >= kMaxUserModels) return -1;
+  g_user_models[g_num_user_models++] = UserModel{id, nx, nu, f64, f32d, f32};
+  return 0;
+}
+}  // namespace ptn
+
+namespace {
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
@@ -110,6 +150,11 @@ static int fail(ptn_solver* s, int code, const char* fmt, ...) {
     cudaError_t e_ = (call);                                                                 \
     if (e_ != cudaSuccess) return fail(s, PTN_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
   } while (0)
+
+extern "C" int ptn_model_dims(int model, int* nx, int* nu) {
+  if (!nx || !nu) return PTN_ERR_INVALID_ARG;
+  return model_dims(model, nx, nu) == 0 ? PTN_OK : PTN_ERR_INVALID_ARG;
+}
 
 extern "C" void ptn_default_options(ptn_options* o) {
   memset(o, 0, sizeof(*o));

@@ -14,7 +14,8 @@ from dataclasses import dataclass
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_build", "libptn.so")
+# PTN_LIB selects another build of the library (e.g. one with user models linked in)
+LIB_PATH = os.environ.get("PTN_LIB") or os.path.join(_HERE, "_build", "libptn.so")
 
 PTN_FP64, PTN_FP32_FP64SOLVE, PTN_FP32 = 0, 1, 2
 METHOD_IP, METHOD_ADMM = 0, 1
@@ -25,7 +26,7 @@ STATUS = {0: "ok", -1: "invalid argument", -2: "infeasible start", -3: "not conv
 EXPORTS = ["ptn_default_options", "ptn_solver_create", "ptn_solver_destroy", "ptn_last_error",
            "ptn_set_options", "ptn_solve_ip", "ptn_solve_admm", "ptn_solve_batch", "ptn_adjoint",
            "ptn_num_rows", "ptn_version", "ptn_solve_ip_static", "ptn_batch_prepare",
-           "ptn_solve_batch_async"]
+           "ptn_solve_batch_async", "ptn_model_dims"]
 
 _P = C.POINTER(C.c_double)
 
@@ -95,6 +96,7 @@ def load(path: str = LIB_PATH):
                                             C.POINTER(Info), C.c_char_p, C.c_int, vp]
         lib.ptn_batch_prepare.argtypes = [vp, C.c_int, C.c_int, ip, C.POINTER(C.c_double), vp]
         lib.ptn_solve_batch_async.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp]
+        lib.ptn_model_dims.argtypes = [C.c_int, ip, ip]
         lib.ptn_version.restype = C.c_char_p
         _lib = lib
     return _lib
@@ -293,6 +295,14 @@ class Solver:
         if rc != 0:
             raise PtnError(f"ptn_adjoint failed ({rc}): {self.last_error()}")
         return out
+
+
+def model_dims(model: int):
+    """(nx, nu) of a model id known to the loaded library (built-in or user-registered),
+    or None."""
+    nx, nu = C.c_int(), C.c_int()
+    rc = load().ptn_model_dims(int(model), C.byref(nx), C.byref(nu))
+    return (nx.value, nu.value) if rc == 0 else None
 
 
 def infos_from_device(info_dev, B: int):
