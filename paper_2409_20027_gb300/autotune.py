@@ -22,6 +22,10 @@ CANDIDATES = [
     {"block_threads": 128, "grid_steps_per_thread": 4, "cluster_max_blocks": 16},
     {"block_threads": 128, "grid_steps_per_thread": 2, "cluster_max_blocks": 0},
     {"block_threads": 128, "grid_steps_per_thread": 1, "cluster_max_blocks": 0},
+    {"block_threads": 128, "grid_steps_per_thread": 4, "cluster_max_blocks": 0},
+    {"block_threads": 32, "grid_steps_per_thread": 2, "cluster_max_blocks": 16},
+    {"block_threads": 64, "grid_steps_per_thread": 1, "cluster_max_blocks": 16},
+    {"block_threads": 128, "grid_steps_per_thread": 1, "cluster_max_blocks": 16},
 ]
 
 

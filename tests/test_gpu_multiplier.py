@@ -185,3 +185,12 @@ def test_wide_tier_rejects_the_multiplier_form(ptn):
     assert "multiplier form" in s.last_error()
     with pytest.raises(ptn.PtnError, match="multiplier form"):
         ptn.solve_ip_static(p, dev(np.zeros(12)), T, u_init=u0, precision=ptn.PTN_FP64, costate_mode=1)
+
+
+def test_sequential_tier(ptn):
+    # one thread per instance: the serial recursions with the multiplier form's terms
+    p, x0, T = W.pendulum(), W.pendulum_x0(2), 64
+    s = ptn.Solver(p, max_T=T, precision=ptn.PTN_FP64, sequential=1, costate_mode=1)
+    x, u, lam, info = s.solve_ip(dev(x0), T)
+    ref = O.solve_ip(p, x0, T, opts=MULT)
+    check(info, ref, x, u, lam, FP64_TOL)
