@@ -73,12 +73,12 @@ typedef struct ptn_problem {
 /* Solver settings; ptn_default_options() fills the defaults:
  *   precision FP32_FP64SOLVE, mu 1e-1 -> 1e-6 (x0.1), tol_inner 1e-4, tol_final 1e-6,
  *   block_threads 128, grid_min_T 512, grid_steps_per_thread 2, polish 100, polish_after 50,
- *   cluster_max_blocks 16,
+ *   cluster_max_blocks 16, sequential 0, costate_mode 0 (the co-state scan),
  *   max_newton 500 per barrier level, ADMM rho 1, admm_tol 1e-2, max_outer 2000,
  *   alpha0 1e-6 in [1e-10, 1e10], ten step sizes 1, 1/2, ..., Armijo c1 1e-4,
  *   rollout: at most 30 multiple-shooting Newton iterations to relative defect 1e-12. */
 typedef struct ptn_options {
-  int precision;        /* PTN_FP64 or PTN_FP32_FP64SOLVE */
+  int precision;        /* PTN_FP64, PTN_FP32_FP64SOLVE or PTN_FP32 */
   int max_newton;       /* Newton iterations per barrier level / ADMM sub-problem */
   int max_outer;        /* ADMM outer iterations */
   int ls_count;         /* candidate step sizes 1, beta, beta^2, ... */
