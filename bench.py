@@ -266,6 +266,34 @@ def run_multiplier(args, ptn, W, dev, flush, stream, tuned, x0):
     return out
 
 
+def run_admm(args, ptn, W, dev, flush, stream, tuned, x0):
+    """ADMM (Sec. II-C) on the cart-pole sweep: rho = 1, the paper's stopping rule
+    max|w - z| <= 1e-2 and max|z - z_prev| <= 1e-2, each sub-problem solved by Newton to
+    the final tolerance; same horizons, x0 and tuned launch shapes as the IP sweep."""
+    import torch
+    from paper_2409_20027_gb300 import autotune
+    out = {}
+    for Ts in [256, 1024, 4096, args.T]:
+        ps = cartpole_instance(Ts)
+        sv = ptn.Solver(ps, max_T=Ts, precision=ptn.PTN_FP32_FP64SOLVE, rho=1.0, admm_tol=1e-2, max_outer=200)
+        autotune.apply(sv, tuned, Ts)
+        sv.solve_admm(x0, Ts)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        flush.zero_()
+        a.record(stream)
+        _, _, _, inf = sv.solve_admm(x0, Ts)
+        b.record(stream)
+        torch.cuda.synchronize()
+        out[str(Ts)] = {"ms": a.elapsed_time(b), "status": inf["status"], "outer_iters": inf["outer_iters"],
+                        "newton_iters": inf["newton_iters"], "r_p": inf["r_p"], "r_d": inf["r_d"],
+                        "r_stat": inf["r_stat"]}
+        sv.close()
+    out["workload"] = ("cart-pole ADMM (rho 1) on the 2.56 s horizon, stop at max|w-z|, max|z-z_prev| <= 1e-2, "
+                       "Newton sub-problems to 1e-6, FP32 LQR with FP64 solves")
+    return out
+
+
 PHASES = ["costate", "second_order", "value", "state", "line_search", "initial_rollout", "other"]
 
 
@@ -404,6 +432,7 @@ def main():
     ap.add_argument("--no-mpc", action="store_true")
     ap.add_argument("--no-seq", action="store_true")
     ap.add_argument("--no-mult", action="store_true")
+    ap.add_argument("--no-admm", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
@@ -522,6 +551,9 @@ def main():
     seq = None
     if not args.no_seq and single:
         seq = run_sequential(args, ptn, W, dev, flush, stream)
+    admm = None
+    if not args.no_admm and single:
+        admm = run_admm(args, ptn, W, dev, flush, stream, tuned, x0s[0])
     mult = None
     if not args.no_mult and single:
         mult = run_multiplier(args, ptn, W, dev, flush, stream, tuned, x0s[0])
@@ -553,7 +585,7 @@ def main():
             "newton_iters": last["newton_iters"], "launch": launch or "defaults",
             "phase_share": phase_share(infos), "sweep": sweep,
             "batch": batch, "quadrotor": quad, "mpc": mpcl, "sequential": seq,
-            "multiplier_form": mult}
+            "multiplier_form": mult, "admm": admm}
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
