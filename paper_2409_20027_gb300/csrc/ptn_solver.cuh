@@ -1259,8 +1259,12 @@ struct exact_only {
 // mixed modes the gradient comes from the FP32-increment co-state pass until, at the
 // final tolerance, it falls below polish * tol; from then on the exact FP64 pass decides.
 template <class M, class L, class SV, class Grp>
+//
+// sticky_exact (optional): once a call switches to the exact FP64 path it sets the flag,
+// and later calls start on that path (ADMM: every sub-problem is warm-started next to its
+// solution, where the FP32-increment phase only adds iterations before the endgame).
 __device__ int newton_solve(Grp& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>& P, const OptDev& O, const Aug& A,
-                            double tol, bool final_level, NStats& st, double* rfinal) {
+                            double tol, bool final_level, NStats& st, double* rfinal, bool* sticky_exact = nullptr) {
   constexpr int N = M::NX;
   constexpr bool MIXED = std::is_same<L, float>::value && !exact_only<Grp>::value;
   constexpr bool CAN_MULT = multiplier_form_ok<Grp>::value;
@@ -1281,7 +1285,7 @@ __device__ int newton_solve(Grp& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>& P,
   double J0 = nominal_cost(g, I, P, A, &inf, nullptr);
   int rc = ST_ENOTCONV;
   double r = INFINITY;
-  bool exact = !MIXED;  // FP64 gradients, FP64 rollouts and absolute FP64 merits
+  bool exact = !MIXED || (sticky_exact && *sticky_exact);  // FP64 gradients, rollouts and merits
   if (MULT && O.costate_mode == 2) {
     // hybrid multiplier form: this sub-problem's multipliers start from the co-states of
     // the scan (written to I.lam; the pass ends with a group reduction, so they are
@@ -1298,6 +1302,7 @@ __device__ int newton_solve(Grp& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>& P,
       // First re-project the nominal onto the FP64 dynamics (one exact rollout with
       // s = 0 under the last feedback), so that FP64 merits compare like with like.
       exact = true;
+      if (sticky_exact) *sticky_exact = true;
       st.exact_passes++;
       double mproj;
       int ri = 0;
@@ -1922,9 +1927,10 @@ __device__ void solve_instance(Grp& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>&
     rc = ST_ENOTCONV;
     int k;
     double rp = INFINITY, rdl = INFINITY;
+    bool admm_exact = false;  // sub-problems after the first FP64 endgame start exact
     for (k = 0; k < kmax; k++) {
       double r;
-      const int s = newton_solve<M, L, SV>(g, I, P, O, A, O.tol_final, true, st, &r);
+      const int s = newton_solve<M, L, SV>(g, I, P, O, A, O.tol_final, true, st, &r, &admm_exact);
       if (s == ST_ENUM || s == ST_ETIMEOUT) { rc = s; k++; break; }
       double lrp = 0.0, lrd = 0.0;
       for (int t = I.a; t < I.b; t++)
