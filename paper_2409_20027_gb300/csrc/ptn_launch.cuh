@@ -1,8 +1,24 @@
 // ptn_launch.cuh -- host-side launch of the solver kernels for one model type.
 #pragma once
+#include <mutex>
+
 #include "ptn_solver.cuh"
 
 namespace ptn {
+
+// Raise, never lower, a kernel's dynamic shared-memory limit (a per-function, process-wide
+// attribute): a launch recorded earlier with a larger size -- in a captured CUDA graph, or
+// prepared by ptn_batch_prepare -- stays valid after launches of smaller shapes.
+template <auto Kernel>
+cudaError_t raise_smem_limit(size_t bytes) {
+  static std::mutex mu;
+  static size_t limit = 0;
+  std::lock_guard<std::mutex> lk(mu);
+  if (bytes <= limit) return cudaSuccess;
+  const cudaError_t e = cudaFuncSetAttribute(Kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) limit = bytes;
+  return e;
+}
 
 // untyped workspace pointers (LQR arrays are allocated with 8 bytes per entry so that
 // either precision fits)
@@ -51,7 +67,7 @@ cudaError_t launch_typed(LaunchReq& q) {
   if (q.elem_bytes) *q.elem_bytes = sizeof(Val<N, L>);
   if (q.tier == 0) {
     if (!q.attrs_set) {
-      cudaError_t e = cudaFuncSetAttribute(k_solve_cta<M, L, SV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      cudaError_t e = raise_smem_limit<k_solve_cta<M, L, SV>>(smem);
       if (e != cudaSuccess) return e;
     }
     if (q.query) return cudaSuccess;
@@ -66,8 +82,7 @@ cudaError_t launch_typed(LaunchReq& q) {
   if (q.tier == 3) {
     // the adjoint is built only in the FP64 units (it runs in FP64 in every mode)
     if constexpr (std::is_same<L, double>::value) {
-      cudaError_t e =
-          cudaFuncSetAttribute(k_adjoint_cta<M, L, SV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      cudaError_t e = raise_smem_limit<k_adjoint_cta<M, L, SV>>(smem);
       if (e != cudaSuccess) return e;
       if (q.query) return cudaSuccess;
       k_adjoint_cta<M, L, SV><<<q.nblocks, nthreads, smem, q.stream>>>(q.args, typed<L>(q.w), *q.adj);
@@ -80,7 +95,7 @@ cudaError_t launch_typed(LaunchReq& q) {
     const size_t smc = ((smem + 15) & ~size_t(15)) + cluster_xch_bytes<N, U, L>();
     cudaError_t e = cudaSuccess;
     if (!q.attrs_set) {
-      e = cudaFuncSetAttribute(k_solve_cluster<M, L, SV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smc);
+      e = raise_smem_limit<k_solve_cluster<M, L, SV>>(smc);
       if (e != cudaSuccess) return e;
       e = cudaFuncSetAttribute(k_solve_cluster<M, L, SV>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
       if (e != cudaSuccess) return e;
@@ -114,7 +129,7 @@ cudaError_t launch_typed(LaunchReq& q) {
   }
   cudaError_t e = cudaSuccess;
   if (!q.attrs_set) {
-    e = cudaFuncSetAttribute(k_solve_grid<M, L, SV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = raise_smem_limit<k_solve_grid<M, L, SV>>(smem);
     if (e != cudaSuccess) return e;
   }
   if (q.query == 2) return cudaSuccess;

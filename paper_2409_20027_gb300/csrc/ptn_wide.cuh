@@ -1193,8 +1193,7 @@ cudaError_t launch_wide(LaunchReq& q) {
       if (q.query) return cudaSuccess;
       const int nw = q.nthreads / 32;
       const size_t smem = wide_smem_bytes<M, double>(nw);
-      cudaError_t e =
-          cudaFuncSetAttribute(k_adjoint_wide<M, SV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      cudaError_t e = raise_smem_limit<k_adjoint_wide<M, SV>>(smem);
       if (e != cudaSuccess) return e;
       k_adjoint_wide<M, SV><<<q.nblocks, q.nthreads, smem, q.stream>>>(q.args, typed<double>(q.w), *q.adj);
       return cudaGetLastError();
@@ -1209,7 +1208,7 @@ cudaError_t launch_wide(LaunchReq& q) {
   const int nw = q.nthreads / 32;
   const size_t smem = wide_smem_bytes<M, L>(nw);
   if (!q.attrs_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_solve_wide<M, L, SV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = raise_smem_limit<k_solve_wide<M, L, SV>>(smem);
     if (e != cudaSuccess) return e;
   }
   if (q.query == 2) return cudaSuccess;

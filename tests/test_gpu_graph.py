@@ -162,3 +162,31 @@ def test_async_argument_errors(ptn):
     s._prepared = (2, 32)
     with pytest.raises(ptn.PtnError, match="no batch prepared"):
         s.solve_batch_async(x0)
+
+
+def test_graph_replay_survives_smaller_launches_of_the_same_kernel(ptn):
+    # a kernel's dynamic shared-memory limit only grows: a solve with fewer threads per CTA
+    # after the capture must leave the captured, larger launch valid
+    p = W.cartpole()
+    Tb = np.array([40, 64], dtype=np.int32)
+    s = ptn.Solver(p, max_T=64, max_batch=2, precision=ptn.PTN_FP64, block_threads=256)
+    s.prepare_batch(Tb)
+    x0 = dev(W.cartpole_batch_x0(2, 1))
+    X = torch.empty((int(Tb.sum()) + 2, 4), dtype=torch.float64, device="cuda:0")
+    U = torch.empty((int(Tb.sum()), 1), dtype=torch.float64, device="cuda:0")
+    info = s.new_info_buffer(2)
+    s.solve_batch_async(x0, x_out=X, u_out=U, info_dev=info)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        s.solve_batch_async(x0, x_out=X, u_out=U, info_dev=info)
+    small = ptn.Solver(p, max_T=64, max_batch=2, precision=ptn.PTN_FP64, block_threads=32)
+    _, _, _, si = small.solve_batch(x0, Tb)  # the same kernel with less shared memory
+    assert all(i["status"] == 0 for i in si)
+    X.zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    Xs, Us, _, infos = s.solve_batch(x0, Tb)
+    assert all(i["status"] == 0 for i in infos)
+    assert same(X, Xs) and same(U, Us)
+    assert report(ptn.infos_from_device(info, 2)) == report(infos)
