@@ -43,3 +43,28 @@ def test_binding_fails_loudly_without_the_library(tmp_path):
     from paper_2409_20027_gb300 import ptn
     with pytest.raises(OSError):
         ptn._open(str(tmp_path / "libptn.so"))
+
+
+def test_entry_points_refuse_null_handles_and_pointers_without_a_gpu():
+    # argument checks come before any CUDA call, so they answer on a machine without a GPU
+    from paper_2409_20027_gb300 import ptn
+    lib = ptn.load()
+    INVALID = -1
+    nx, nu = ctypes.c_int(), ctypes.c_int()
+    assert lib.ptn_model_dims(1, ctypes.byref(nx), ctypes.byref(nu)) == 0 and (nx.value, nu.value) == (4, 1)
+    assert lib.ptn_model_dims(1, None, None) == INVALID
+    assert lib.ptn_model_dims(3, ctypes.byref(nx), ctypes.byref(nu)) == INVALID  # no GPU kernels for it
+    assert lib.ptn_model_dims(999, ctypes.byref(nx), ctypes.byref(nu)) == INVALID
+    tb = (ctypes.c_int * 1)(8)
+    assert lib.ptn_batch_prepare(None, 0, 1, tb, None, None) == INVALID
+    assert lib.ptn_solve_batch_async(None, None, None, None, None, None, None, None, None) == INVALID
+    assert lib.ptn_solve_ip(None, None, None, 8, None, None, None, None, None) == INVALID
+    assert lib.ptn_set_options(None, None) == INVALID
+    assert lib.ptn_last_error(None) is not None
+    opt = ptn.Options()
+    lib.ptn_default_options(ctypes.byref(opt))
+    assert opt.costate_mode == 0 and opt.precision == ptn.PTN_FP32_FP64SOLVE
+    # the static entry point checks its arguments first as well
+    err = ctypes.create_string_buffer(256)
+    rc = lib.ptn_solve_ip_static(None, None, None, None, 8, None, None, None, None, err, 256, None)
+    assert rc == INVALID and b"NULL" in err.value
