@@ -1,9 +1,12 @@
-"""The kernels' model code on the host: ptn_models.cuh is written __host__ __device__, so a
-host build of the same templates (tests/host_models/ptn_host_models.cu, compiled with
-nvcc, run on the CPU) gives the GPU path's step map, its forward-mode Jacobians and its
-lam-contracted Hessians.  They must agree with the oracle's models, which are separate
+"""The kernels' model code and scan operators on the host: ptn_models.cuh and ptn_ops.cuh
+are written __host__ __device__, so a host build of the same templates
+(tests/host_models/*.cu, compiled with nvcc, run on the CPU) gives the GPU path's step
+map, its forward-mode Jacobians and its lam-contracted Hessians.  They must agree with the oracle's models, which are separate
 code (hyper-dual numbers, pinned by finite differences in test_oracle_models), for every
-model and integrator the kernels use -- without a GPU."""
+model and integrator the kernels use -- without a GPU.  Likewise the kernels' value,
+co-state and state combines and the value-element initialisation against the oracle's
+operators (pinned by the scan identities in test_oracle_scans), in FP64 and in the FP32
+form with FP64 solves."""
 import os
 import shutil
 import subprocess
@@ -16,22 +19,24 @@ from paper_2409_20027_gb300 import workloads as W
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "tests", "host_models", "ptn_host_models.cu")
+SRC_OPS = os.path.join(ROOT, "tests", "host_models", "ptn_host_ops.cu")
 CSRC = os.path.join(ROOT, "paper_2409_20027_gb300", "csrc")
 EXE = os.path.join(ROOT, "paper_2409_20027_gb300", "_build", "host_models")
+EXE_OPS = os.path.join(ROOT, "paper_2409_20027_gb300", "_build", "host_ops")
 
 
-def _harness():
+def _harness(src=SRC, exe=EXE):
     nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
     if not os.path.exists(nvcc):
         pytest.skip("nvcc not available")
-    deps = [SRC] + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cuh")]
-    if not os.path.exists(EXE) or any(os.path.getmtime(d) > os.path.getmtime(EXE) for d in deps):
-        os.makedirs(os.path.dirname(EXE), exist_ok=True)
-        tmp = EXE + f".{os.getpid()}.tmp"
+    deps = [src] + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cuh")]
+    if not os.path.exists(exe) or any(os.path.getmtime(d) > os.path.getmtime(exe) for d in deps):
+        os.makedirs(os.path.dirname(exe), exist_ok=True)
+        tmp = exe + f".{os.getpid()}.tmp"
         subprocess.run([nvcc, "-x", "cu", "-std=c++17", "-O2", "-gencode", "arch=compute_103a,code=sm_103a",
-                        "-I", CSRC, SRC, "-o", tmp], check=True, capture_output=True)
-        os.replace(tmp, EXE)
-    return EXE
+                        "-I", CSRC, src, "-o", tmp], check=True, capture_output=True)
+        os.replace(tmp, exe)
+    return exe
 
 
 def _cases():
@@ -76,3 +81,51 @@ def test_model_code_of_the_kernels_matches_the_oracle_models():
         for name, a, b in zip(["x+", "F", "G", "Hxx", "Hxu", "Huu"], [xn, F, G, Hxx, Hxu, Huu], ref):
             scale = max(1.0, float(np.abs(b).max()))
             assert np.abs(a - b).max() <= 1e-12 * scale, (prob.name, name, a, b)
+
+
+def _val(rng):
+    """A well-conditioned value element (A, b, C, eta, J): C, J symmetric PSD."""
+    X = rng.normal(size=(4, 4)); Y = rng.normal(size=(4, 4))
+    return (np.eye(4) + 0.2 * rng.normal(size=(4, 4)), rng.normal(size=4), 0.3 * X @ X.T,
+            rng.normal(size=4), 0.3 * Y @ Y.T)
+
+
+def _f32(a):
+    return np.asarray(a, dtype=np.float32).astype(np.float64)
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-12), (1, 3e-5)], ids=["fp64", "fp32_fp64solve"])
+def test_scan_operators_of_the_kernels_match_the_oracle_operators(prec, tol):
+    exe = _harness(SRC_OPS, EXE_OPS)
+    rng = np.random.default_rng(41 + prec)
+    rnd = _f32 if prec else (lambda a: np.asarray(a, dtype=np.float64))
+    lines, refs = [], []
+    for _ in range(6):
+        e1 = tuple(rnd(z) for z in _val(rng))
+        e2 = tuple(rnd(z) for z in _val(rng))
+        lines.append("V %d " % prec + " ".join(repr(float(v)) for z in e1 + e2 for v in np.ravel(z)))
+        refs.append(np.concatenate([np.ravel(z) for z in O.value_combine(e1, e2)]))
+        F = rnd(np.eye(4) + 0.1 * rng.normal(size=(4, 4))); G = rnd(rng.normal(size=(4, 1)))
+        Pq = rng.normal(size=(4, 4)); P = rnd(Pq @ Pq.T + np.eye(4)); M = rnd(0.1 * rng.normal(size=(4, 1)))
+        R = rnd(np.array([[0.5 + rng.random()]])); d = rng.normal(size=1)
+        lines.append("I %d " % prec + " ".join(repr(float(v)) for v in
+                                              np.concatenate([F.ravel(), G.ravel(), P.ravel(), M.ravel(), R.ravel(),
+                                                              d, [1e-3]])))
+        refs.append(np.concatenate([np.ravel(z) for z in O.value_init(F, G, P, M, R, d, 1e-3)]))
+    for _ in range(4):
+        g1, g2 = rng.normal(size=4), rng.normal(size=4)
+        A1, A2 = np.eye(4) + 0.2 * rng.normal(size=(4, 4)), np.eye(4) + 0.2 * rng.normal(size=(4, 4))
+        lines.append("C 0 " + " ".join(repr(float(v)) for v in np.concatenate([g1, A1.ravel(), g2, A2.ravel()])))
+        g, Ft = O.costate_combine(g1, A1, g2, A2)
+        refs.append(np.concatenate([np.ravel(g), np.ravel(Ft)]))
+        lines.append("S 0 " + " ".join(repr(float(v)) for v in np.concatenate([A1.ravel(), g1, A2.ravel(), g2])))
+        F, e = O.state_combine(A1, g1, A2, g2)
+        refs.append(np.concatenate([np.ravel(e), np.ravel(F)]))
+    r = subprocess.run([exe], input="\n".join(lines) + "\n", capture_output=True, text=True, check=True)
+    outs = r.stdout.strip().splitlines()
+    assert len(outs) == len(refs)
+    for line, ref, inp in zip(outs, refs, lines):
+        assert "FAIL" not in line, inp[:2]
+        got = np.array([float(t) for t in line.split()])
+        t = tol if inp[0] in "VI" else 1e-12
+        assert np.abs(got - ref).max() <= t * max(1.0, float(np.abs(ref).max())), (inp[:2], got, ref)
