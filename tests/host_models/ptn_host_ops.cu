@@ -5,6 +5,8 @@
 //   I  value element init:       F(16) G(4) P(16) M(4) R(1) d(1) alpha
 //   C  co-state combine (Alg. 1): g1(4) Ft1(16) g2(4) Ft2(16)
 //   S  state combine (Alg. 3):    F1(16) e1(4) F2(16) e2(4)
+//   R  Riccati step with feedback: F(16) G(4) P(16) M(4) R(1) d(1) alpha S(16) s(4)
+//      -> Gam(4) gam(1) S_t(16) s_t(4)
 // for n = 4, m = 1, and LQR precision 0 (FP64) or 1 (FP32 data, FP64 solves); the output
 // line is the resulting element (value elements as A b C eta J).
 #include <cstdio>
@@ -66,6 +68,23 @@ static bool value_init_op(const double* in) {
   return true;
 }
 
+template <class L>
+static bool riccati_op(const double* in) {
+  L F[16], G[4], P[16], M[4], R[1], S[16], sv[4], Gam[4], gam[1];
+  for (int i = 0; i < 16; i++) { F[i] = L(in[i]); P[i] = L(in[20 + i]); S[i] = L(in[43 + i]); }
+  for (int i = 0; i < 4; i++) { G[i] = L(in[16 + i]); M[i] = L(in[36 + i]); sv[i] = L(in[59 + i]); }
+  R[0] = L(in[40]);
+  const double d[1] = {in[41]};
+  if (!riccati_step<N, U, L, double>(F, G, P, M, R, d, in[42], S, sv, Gam, gam)) return false;
+  double o[25];
+  for (int i = 0; i < 4; i++) o[i] = double(Gam[i]);
+  o[4] = double(gam[0]);
+  for (int i = 0; i < 16; i++) o[5 + i] = double(S[i]);
+  for (int i = 0; i < 4; i++) o[21 + i] = double(sv[i]);
+  pr(o, 25);
+  return true;
+}
+
 int main() {
   char op[4];
   int prec;
@@ -78,6 +97,9 @@ int main() {
     } else if (op[0] == 'I') {
       if (!rd(in, 43)) return 1;
       ok = prec ? value_init_op<float>(in) : value_init_op<double>(in);
+    } else if (op[0] == 'R') {
+      if (!rd(in, 63)) return 1;
+      ok = prec ? riccati_op<float>(in) : riccati_op<double>(in);
     } else if (op[0] == 'C' || op[0] == 'S') {
       if (!rd(in, 40)) return 1;
       Aff<N, double> a, b, o;

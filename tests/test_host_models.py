@@ -129,3 +129,32 @@ def test_scan_operators_of_the_kernels_match_the_oracle_operators(prec, tol):
         got = np.array([float(t) for t in line.split()])
         t = tol if inp[0] in "VI" else 1e-12
         assert np.abs(got - ref).max() <= t * max(1.0, float(np.abs(ref).max())), (inp[:2], got, ref)
+
+
+def test_riccati_step_of_the_kernels_matches_the_oracle_recursion():
+    # one backward step of the kernels' sweep from the oracle's (S, s)_{t+1} reproduces the
+    # oracle's Gam_t, gam_t and (S, s)_t (eq. value-fun-feedback with M^T), on the
+    # cart-pole's Newton step at a barrier weight where the LQR has curvature from all terms
+    exe = _harness(SRC_OPS, EXE_OPS)
+    p = W.cartpole()
+    T = 6
+    rng = np.random.default_rng(9)
+    u = rng.normal(scale=0.5, size=(T, 1))
+    x = O.rollout(p, W.cartpole_x0(2), u)
+    alpha = 1e-3
+    nd = O.newton_direction(p, x, u, alpha, "barrier", mu=1e-2)
+    assert nd["status"] == 0
+    lines, refs = [], []
+    for t in range(T):
+        vals = np.concatenate([nd["F"][t].ravel(), nd["G"][t].ravel(), nd["P"][t].ravel(), nd["M"][t].ravel(),
+                               nd["R"][t].ravel(), nd["d"][t].ravel(), [alpha], nd["S"][t + 1].ravel(),
+                               nd["s"][t + 1]])
+        lines.append("R 0 " + " ".join(repr(float(v)) for v in vals))
+        refs.append(np.concatenate([nd["Gam"][t].ravel(), nd["gam"][t].ravel(), nd["S"][t].ravel(), nd["s"][t]]))
+    r = subprocess.run([exe], input="\n".join(lines) + "\n", capture_output=True, text=True, check=True)
+    outs = r.stdout.strip().splitlines()
+    assert len(outs) == T
+    for t, (line, ref) in enumerate(zip(outs, refs)):
+        assert "FAIL" not in line, t
+        got = np.array([float(v) for v in line.split()])
+        assert np.abs(got - ref).max() <= 1e-10 * max(1.0, float(np.abs(ref).max())), (t, got, ref)
