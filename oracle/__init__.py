@@ -206,6 +206,14 @@ def param_jac(prob, x, u):
     return out
 
 
+def param_hess(prob, x, u, lam):
+    """d2 (lam . f) / dz dprm with z = (x, u), shape (nx + nu, 8)."""
+    b = _Bound(prob); x = _arr(x); u = _arr(u); lam = _arr(lam)
+    out = np.zeros((b.n + b.m, MAXP))
+    lib().orc_param_hess(b.ref(), _ptr(x), _ptr(u), _ptr(lam), _ptr(out))
+    return out
+
+
 def rollout(prob, x0, u):
     b = _Bound(prob); x0 = _arr(x0); u = _arr(u)
     T = u.shape[0]

@@ -1,8 +1,9 @@
 // Host build of the kernels' model code (ptn_models.cuh is __host__ __device__): for each
 // line of input "model integ dt p0..p7 x.. u.. lam.." it prints the step x+ = f(x, u), its
 // Jacobians F, G (forward-mode Dual numbers) and the lam-contracted second derivatives
-// Hxx, Hxu, Huu (Jet numbers) -- the same templates the solver kernels instantiate --
-// so that a test can compare them with the oracle's models without a GPU.
+// Hxx, Hxu, Huu (Jet numbers), and the adjoint's parameter derivatives df/dprm and
+// d2(lam . f)/dz dprm (nested Dual numbers) -- the same templates the solver kernels
+// instantiate -- so that a test can compare them with the oracle's models without a GPU.
 #include <cstdio>
 
 #include "ptn_models.cuh"
@@ -21,6 +22,10 @@ static void eval(int integ, double dt, const double* p, const double* x, const d
   for (double v : Hxx) printf("%.17g ", v);
   for (double v : Hxu) printf("%.17g ", v);
   for (double v : Huu) printf("%.17g ", v);
+  double fp[N * M::NP], Hzp[(N + U) * M::NP];
+  step_param_derivs<M>(integ, dt, p, x, u, lam, fp, Hzp);
+  for (double v : fp) printf("%.17g ", v);
+  for (double v : Hzp) printf("%.17g ", v);
   printf("\n");
 }
 

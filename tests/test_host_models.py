@@ -1,7 +1,8 @@
 """The kernels' model code and scan operators on the host: ptn_models.cuh and ptn_ops.cuh
 are written __host__ __device__, so a host build of the same templates
 (tests/host_models/*.cu, compiled with nvcc, run on the CPU) gives the GPU path's step
-map, its forward-mode Jacobians and its lam-contracted Hessians.  They must agree with the oracle's models, which are separate
+map, its forward-mode Jacobians, its lam-contracted Hessians and the adjoint's parameter
+derivatives.  They must agree with the oracle's models, which are separate
 code (hyper-dual numbers, pinned by finite differences in test_oracle_models), for every
 model and integrator the kernels use -- without a GPU.  Likewise the kernels' value,
 co-state and state combines and the value-element initialisation against the oracle's
@@ -71,14 +72,17 @@ def test_model_code_of_the_kernels_matches_the_oracle_models():
     assert len(outs) == len(cases)
     for (prob, x, u, lam), line in zip(cases, outs):
         n, m = prob.nx, prob.nu
+        npm = {W.PENDULUM: 4, W.CARTPOLE: 4, W.QUADROTOR: 7}[prob.model]  # model constants used
         v = np.array([float(t) for t in line.split()])
-        sizes = [n, n * n, n * m, n * n, n * m, m * m]
+        sizes = [n, n * n, n * m, n * n, n * m, m * m, n * npm, (n + m) * npm]
         parts = np.split(v, np.cumsum(sizes)[:-1])
-        xn, F, G, Hxx, Hxu, Huu = parts
+        xn, F, G, Hxx, Hxu, Huu, fp, Hzp = parts
         F0, G0 = O.jac(prob, x, u)
         H0 = O.hess(prob, x, u, lam)
-        ref = [O.step(prob, x, u), F0.ravel(), G0.ravel(), H0[0].ravel(), H0[1].ravel(), H0[2].ravel()]
-        for name, a, b in zip(["x+", "F", "G", "Hxx", "Hxu", "Huu"], [xn, F, G, Hxx, Hxu, Huu], ref):
+        ref = [O.step(prob, x, u), F0.ravel(), G0.ravel(), H0[0].ravel(), H0[1].ravel(), H0[2].ravel(),
+               O.param_jac(prob, x, u)[:, :npm].ravel(), O.param_hess(prob, x, u, lam)[:, :npm].ravel()]
+        for name, a, b in zip(["x+", "F", "G", "Hxx", "Hxu", "Huu", "df/dprm", "d2(lam.f)/dz dprm"],
+                              [xn, F, G, Hxx, Hxu, Huu, fp, Hzp], ref):
             scale = max(1.0, float(np.abs(b).max()))
             assert np.abs(a - b).max() <= 1e-12 * scale, (prob.name, name, a, b)
 
