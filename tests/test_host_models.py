@@ -21,9 +21,11 @@ from paper_2409_20027_gb300 import workloads as W
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "tests", "host_models", "ptn_host_models.cu")
 SRC_OPS = os.path.join(ROOT, "tests", "host_models", "ptn_host_ops.cu")
+SRC_SYN = os.path.join(ROOT, "tests", "host_models", "ptn_host_synth.cu")
 CSRC = os.path.join(ROOT, "paper_2409_20027_gb300", "csrc")
 EXE = os.path.join(ROOT, "paper_2409_20027_gb300", "_build", "host_models")
 EXE_OPS = os.path.join(ROOT, "paper_2409_20027_gb300", "_build", "host_ops")
+EXE_SYN = os.path.join(ROOT, "paper_2409_20027_gb300", "_build", "host_synth")
 
 
 def _harness(src=SRC, exe=EXE):
@@ -162,3 +164,29 @@ def test_riccati_step_of_the_kernels_matches_the_oracle_recursion():
         assert "FAIL" not in line, t
         got = np.array([float(v) for v in line.split()])
         assert np.abs(got - ref).max() <= 1e-10 * max(1.0, float(np.abs(ref).max())), (t, got, ref)
+
+
+@pytest.mark.parametrize("n,m", [(32, 8), (6, 2)])
+def test_synthetic_map_closed_forms_match_the_oracle(n, m):
+    # x+ = A x + B u + c tanh(W x) (the n = 32, m = 8 workload's model): step, F, G and
+    # lam . f_xx in closed form (ptn_synth.cuh) against the oracle's hyper-dual evaluation
+    exe = _harness(SRC_SYN, EXE_SYN)
+    rng = np.random.default_rng(7 + n)
+    lines, refs = [], []
+    for seed in range(3):
+        p = W.synth(seed, nx=n, nu=m)
+        x = rng.normal(size=n)
+        u = rng.normal(size=m)
+        lam = rng.normal(scale=3.0, size=n)
+        vals = np.concatenate([p.A.ravel(), p.B.ravel(), p.W.ravel(), x, u, lam])
+        lines.append(f"{n} {m} {float(p.prm[0])!r} " + " ".join(repr(float(v)) for v in vals))
+        F0, G0 = O.jac(p, x, u)
+        Hxx, Hxu, Huu = O.hess(p, x, u, lam)
+        assert np.abs(Hxu).max() == 0.0 and np.abs(Huu).max() == 0.0
+        refs.append(np.concatenate([O.step(p, x, u), F0.ravel(), G0.ravel(), Hxx.ravel()]))
+    r = subprocess.run([exe], input="\n".join(lines) + "\n", capture_output=True, text=True, check=True)
+    outs = r.stdout.strip().splitlines()
+    assert len(outs) == len(refs)
+    for line, ref in zip(outs, refs):
+        got = np.array([float(t) for t in line.split()])
+        assert np.abs(got - ref).max() <= 1e-12 * max(1.0, float(np.abs(ref).max()))
