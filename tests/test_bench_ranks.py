@@ -41,3 +41,21 @@ def test_max_over_two_gloo_ranks():
         p.join(timeout=60)
         assert p.exitcode == 0
     assert out == {0: 15.0, 1: 15.0}
+
+
+def test_reference_arm_prints_the_json_contract_on_the_cpu():
+    # the reference arm times the oracle on the host cores: one JSON line with the keys the
+    # contract names, higher_is_better false for a time, and e2e / cpu_baseline describing it
+    import json
+    import subprocess
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                        "--warmup", "3", "--T", "256"], capture_output=True, text=True, timeout=300, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    line = json.loads(r.stdout.strip().splitlines()[-1])
+    for k in ["metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "scaling",
+              "vs_baseline", "dtype", "data", "config", "impl", "cpu_baseline", "e2e"]:
+        assert k in line, k
+    assert line["impl"] == "reference" and line["higher_is_better"] is False
+    assert line["unit"] == "ms" and line["value"] > 0 and line["steps"] == 1 and line["warmup"] == 3
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
+    assert line["e2e"]["value"] == line["value"] and line["e2e"]["h2d_bytes_per_step"] == 0
