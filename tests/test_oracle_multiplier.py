@@ -139,3 +139,26 @@ def test_multiplier_form_admm_fixed_outer_count():
     # Newton sub-problem)
     for k in ["x", "u", "z", "v"]:
         assert rel(b[k], a[k]) <= 1e-8, k
+
+
+def test_multiplier_form_solves_where_the_costate_recursion_breaks_down():
+    # synthetic x+ = A x + B u + c tanh(W x), n = 6, m = 2, seed 9: the Jacobian at the
+    # origin has spectral radius 1.017, so the co-state recursion's products of F_t^T grow
+    # like 1.017^T.  At T = 512 both forms reach the same KKT point; at T = 1024 the
+    # recursion-based Newton step breaks down while the multiplier form converges, to the
+    # same cost (the state has settled by step 512, so the longer horizon adds nothing)
+    p = W.synth(9, nx=6, nu=2)
+    rho = max(abs(np.linalg.eigvals(p.A + p.prm[0] * p.W)))
+    assert rho > 1.01
+    x0 = W.synth_x0(9, nx=6)
+    a = O.solve_ip(p, x0, 512)
+    b = O.solve_ip(p, x0, 512, opts=O.Options(costate_mode=1))
+    assert a["info"]["status"] == 0 and b["info"]["status"] == 0
+    assert rel(b["u"], a["u"]) <= 1e-9 and b["info"]["J"] == pytest.approx(a["info"]["J"], rel=1e-12)
+    c = O.solve_ip(p, x0, 1024)
+    assert c["info"]["status"] != 0
+    d = O.solve_ip(p, x0, 1024, opts=O.Options(costate_mode=1))
+    i = d["info"]
+    assert i["status"] == 0 and i["r_stat"] <= 1e-6 and i["r_dyn"] <= 1e-9 and i["r_feas"] == 0.0
+    assert np.abs(d["lam"]).max() < 1e3
+    assert i["J"] == pytest.approx(a["info"]["J"], rel=1e-6)
