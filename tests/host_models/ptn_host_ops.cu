@@ -7,6 +7,8 @@
 //   S  state combine (Alg. 3):    F1(16) e1(4) F2(16) e2(4)
 //   R  Riccati step with feedback: F(16) G(4) P(16) M(4) R(1) d(1) alpha S(16) s(4)
 //      -> Gam(4) gam(1) S_t(16) s_t(4)
+//   K  pivot keys: x -> mag_key(double x) mag_key(float x)
+//   G  FP64 Gauss-Jordan inverse with partial pivoting: A(16) -> A^{-1}(16)
 // for n = 4, m = 1, and LQR precision 0 (FP64) or 1 (FP32 data, FP64 solves); the output
 // line is the resulting element (value elements as A b C eta J).
 #include <cstdio>
@@ -100,6 +102,13 @@ int main() {
     } else if (op[0] == 'R') {
       if (!rd(in, 63)) return 1;
       ok = prec ? riccati_op<float>(in) : riccati_op<double>(in);
+    } else if (op[0] == 'K') {
+      if (!rd(in, 1)) return 1;
+      printf("%u %u", mag_key(in[0]), mag_key(float(in[0])));
+    } else if (op[0] == 'G') {
+      if (!rd(in, 16)) return 1;
+      ok = inv_gj<N, double>(in);
+      if (ok) pr(in, 16);
     } else if (op[0] == 'C' || op[0] == 'S') {
       if (!rd(in, 40)) return 1;
       Aff<N, double> a, b, o;

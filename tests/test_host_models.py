@@ -190,3 +190,43 @@ def test_synthetic_map_closed_forms_match_the_oracle(n, m):
     for line, ref in zip(outs, refs):
         got = np.array([float(t) for t in line.split()])
         assert np.abs(got - ref).max() <= 1e-12 * max(1.0, float(np.abs(ref).max()))
+
+
+def test_pivot_keys_and_the_fp64_inverse():
+    # the integer pivot key orders by magnitude (doubles: by the high word, so monotone with
+    # ties below 2^-20 relative and among subnormals; floats: strictly), and the Gauss-Jordan
+    # inverse of the value
+    # combine matches numpy's inverse, with pivoting exercised and a singular matrix refused
+    exe = _harness(SRC_OPS, EXE_OPS)
+    rng = np.random.default_rng(3)
+    xs = np.concatenate([rng.normal(size=40) * 10.0 ** rng.integers(-30, 30, size=40),
+                         [0.0, -0.0, 1.0, -1.0, 1.0 + 2.0 ** -40, 5e-324, -5e-324, 3e38, -3e38]])
+    lines = ["K 0 %r" % float(v) for v in xs]
+    mats = [rng.normal(size=(4, 4)) for _ in range(6)]
+    mats.append(np.array([[1e-9, 1, 2, 3], [4, 5, 6, 7.5], [8, 9.5, 10, 11], [12, 13, 14.5, 16]]))  # pivoting
+    mats.append(np.diag([1e-6, 1.0, 1e3, 5.0]) + 1e-3 * rng.normal(size=(4, 4)))  # ill-scaled
+    lines += ["G 0 " + " ".join(repr(float(v)) for v in A.ravel()) for A in mats]
+    lines.append("G 0 " + " ".join(["1.0", "2.0", "3.0", "4.0"] * 4))  # singular
+    r = subprocess.run([exe], input="\n".join(lines) + "\n", capture_output=True, text=True, check=True)
+    outs = r.stdout.strip().splitlines()
+    assert len(outs) == len(lines)
+    kd = np.array([int(o.split()[0]) for o in outs[:len(xs)]])
+    kf = np.array([int(o.split()[1]) for o in outs[:len(xs)]])
+    a = np.abs(xs)
+    af = np.abs(xs.astype(np.float32).astype(np.float64))
+    for i in range(len(xs)):
+        for j in range(len(xs)):
+            if a[i] < a[j]:
+                assert kd[i] <= kd[j], (xs[i], xs[j])
+            if a[i] < a[j] * (1.0 - 2.0 ** -19) and a[j] >= np.finfo(np.float64).tiny:
+                # strict between normal magnitudes (the high word resolves 2^-20 relative;
+                # below the normal range all keys are 0)
+                assert kd[i] < kd[j], (xs[i], xs[j])
+            if af[i] < af[j]:
+                assert kf[i] < kf[j], (xs[i], xs[j])
+    for A, o in zip(mats, outs[len(xs):len(xs) + len(mats)]):
+        got = np.array([float(t) for t in o.split()]).reshape(4, 4)
+        ref = np.linalg.inv(A)
+        tol = 1e-15 * np.linalg.cond(A) * 16
+        assert np.abs(got - ref).max() <= tol * max(1.0, float(np.abs(ref).max())), (A, got, ref)
+    assert outs[-1].strip() == "FAIL" or "FAIL" in outs[-1]
