@@ -9,6 +9,7 @@
 //      -> Gam(4) gam(1) S_t(16) s_t(4)
 //   K  pivot keys: x -> mag_key(double x) mag_key(float x)
 //   G  FP64 Gauss-Jordan inverse with partial pivoting: A(16) -> A^{-1}(16)
+//   L  LDL^T factorisation and solve: A(16, symmetric) B(4 x 3) -> X = A^{-1} B (12)
 // for n = 4, m = 1, and LQR precision 0 (FP64) or 1 (FP32 data, FP64 solves); the output
 // line is the resulting element (value elements as A b C eta J).
 #include <cstdio>
@@ -105,6 +106,13 @@ int main() {
     } else if (op[0] == 'K') {
       if (!rd(in, 1)) return 1;
       printf("%u %u", mag_key(in[0]), mag_key(float(in[0])));
+    } else if (op[0] == 'L') {
+      if (!rd(in, 28)) return 1;
+      ok = ldlt<N, double>(in);
+      if (ok) {
+        ldlt_solve<N, 3, double>(in, in + 16);
+        pr(in + 16, 12);
+      }
     } else if (op[0] == 'G') {
       if (!rd(in, 16)) return 1;
       ok = inv_gj<N, double>(in);

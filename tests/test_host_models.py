@@ -230,3 +230,28 @@ def test_pivot_keys_and_the_fp64_inverse():
         tol = 1e-15 * np.linalg.cond(A) * 16
         assert np.abs(got - ref).max() <= tol * max(1.0, float(np.abs(ref).max())), (A, got, ref)
     assert outs[-1].strip() == "FAIL" or "FAIL" in outs[-1]
+
+
+def test_ldlt_factorisation_and_solve():
+    # LDL^T with reciprocal pivots (R~ and Q_uu of the value pass): solves SPD systems like
+    # numpy's solver, ill-conditioned ones to the conditioning bound, and refuses a matrix
+    # that is not positive definite
+    exe = _harness(SRC_OPS, EXE_OPS)
+    rng = np.random.default_rng(17)
+    cases = []
+    for k in range(5):
+        Xq = rng.normal(size=(4, 4))
+        A = Xq @ Xq.T + (10.0 ** -k) * np.eye(4)  # conditioning up to ~1e5
+        cases.append((A, rng.normal(size=(4, 3))))
+    indef = np.diag([1.0, 2.0, -0.5, 3.0])
+    lines = ["L 0 " + " ".join(repr(float(v)) for v in np.concatenate([A.ravel(), Bm.ravel()])) for A, Bm in cases]
+    lines.append("L 0 " + " ".join(repr(float(v)) for v in np.concatenate([indef.ravel(), np.ones(12)])))
+    r = subprocess.run([exe], input="\n".join(lines) + "\n", capture_output=True, text=True, check=True)
+    outs = r.stdout.strip().splitlines()
+    assert len(outs) == len(lines)
+    for (A, Bm), o in zip(cases, outs):
+        got = np.array([float(t) for t in o.split()]).reshape(4, 3)
+        ref = np.linalg.solve(A, Bm)
+        tol = 1e-15 * np.linalg.cond(A) * 32
+        assert np.abs(got - ref).max() <= tol * max(1.0, float(np.abs(ref).max()))
+    assert "FAIL" in outs[-1]
