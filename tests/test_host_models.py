@@ -255,3 +255,18 @@ def test_ldlt_factorisation_and_solve():
         tol = 1e-15 * np.linalg.cond(A) * 32
         assert np.abs(got - ref).max() <= tol * max(1.0, float(np.abs(ref).max()))
     assert "FAIL" in outs[-1]
+
+
+def test_element_operators_refuse_singular_and_indefinite_inputs():
+    # value combine with I + C1 J2 singular (C1 J2 = -I), and element init with R~ < 0:
+    # both report failure (the solver then raises alpha) instead of returning garbage
+    exe = _harness(SRC_OPS, EXE_OPS)
+    eye = np.eye(4)
+    e1 = (eye, np.zeros(4), eye, np.zeros(4), eye)      # C1 = I
+    e2 = (eye, np.zeros(4), eye, np.zeros(4), -eye)     # J2 = -I
+    v = "V 0 " + " ".join(repr(float(x)) for z in e1 + e2 for x in np.ravel(z))
+    i = "I 0 " + " ".join(repr(float(x)) for x in np.concatenate(
+        [eye.ravel(), np.ones(4), eye.ravel(), np.zeros(4), [-1.0], [0.5], [1e-3]]))
+    r = subprocess.run([exe], input=v + "\n" + i + "\n", capture_output=True, text=True, check=True)
+    outs = r.stdout.strip().splitlines()
+    assert len(outs) == 2 and "FAIL" in outs[0] and "FAIL" in outs[1]
