@@ -26,6 +26,21 @@ static void eval(int integ, double dt, const double* p, const double* x, const d
   step_param_derivs<M>(integ, dt, p, x, u, lam, fp, Hzp);
   for (double v : fp) printf("%.17g ", v);
   for (double v : Hzp) printf("%.17g ", v);
+  // increment f - x in FP64 and FP32 (the mixed rollouts' form)
+  double d64[N];
+  float xf[N], uf[U], d32[N];
+  step_inc<M, double>(integ, dt, p, x, u, d64);
+  for (int i = 0; i < N; i++) xf[i] = float(x[i]);
+  for (int i = 0; i < U; i++) uf[i] = float(u[i]);
+  step_inc<M, float>(integ, dt, p, xf, uf, d32);
+  for (double v : d64) printf("%.17g ", v);
+  for (float v : d32) printf("%.9g ", double(v));
+  // closed-loop Jacobian F + G Gam with Gam = lam[0..U) in every row (a fixed test gain)
+  double Gam[U * N], Fcl[N * N];
+  for (int i = 0; i < U; i++)
+    for (int j = 0; j < N; j++) Gam[i * N + j] = 0.1 * lam[j] / double(i + 1);
+  step_cl_jac<M, double>(integ, dt, p, x, u, Gam, Fcl);
+  for (double v : Fcl) printf("%.17g ", v);
   printf("\n");
 }
 

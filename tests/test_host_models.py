@@ -1,8 +1,8 @@
 """The kernels' model code and scan operators on the host: ptn_models.cuh and ptn_ops.cuh
 are written __host__ __device__, so a host build of the same templates
 (tests/host_models/*.cu, compiled with nvcc, run on the CPU) gives the GPU path's step
-map, its forward-mode Jacobians, its lam-contracted Hessians and the adjoint's parameter
-derivatives.  They must agree with the oracle's models, which are separate
+map and its increment (FP64 and FP32), its forward-mode and closed-loop Jacobians, its
+lam-contracted Hessians and the adjoint's parameter derivatives.  They must agree with the oracle's models, which are separate
 code (hyper-dual numbers, pinned by finite differences in test_oracle_models), for every
 model and integrator the kernels use -- without a GPU.  Likewise the kernels' value,
 co-state and state combines and the value-element initialisation against the oracle's
@@ -76,9 +76,9 @@ def test_model_code_of_the_kernels_matches_the_oracle_models():
         n, m = prob.nx, prob.nu
         npm = {W.PENDULUM: 4, W.CARTPOLE: 4, W.QUADROTOR: 7}[prob.model]  # model constants used
         v = np.array([float(t) for t in line.split()])
-        sizes = [n, n * n, n * m, n * n, n * m, m * m, n * npm, (n + m) * npm]
+        sizes = [n, n * n, n * m, n * n, n * m, m * m, n * npm, (n + m) * npm, n, n, n * n]
         parts = np.split(v, np.cumsum(sizes)[:-1])
-        xn, F, G, Hxx, Hxu, Huu, fp, Hzp = parts
+        xn, F, G, Hxx, Hxu, Huu, fp, Hzp, d64, d32, Fcl = parts
         F0, G0 = O.jac(prob, x, u)
         H0 = O.hess(prob, x, u, lam)
         ref = [O.step(prob, x, u), F0.ravel(), G0.ravel(), H0[0].ravel(), H0[1].ravel(), H0[2].ravel(),
@@ -87,6 +87,17 @@ def test_model_code_of_the_kernels_matches_the_oracle_models():
                               [xn, F, G, Hxx, Hxu, Huu, fp, Hzp], ref):
             scale = max(1.0, float(np.abs(b).max()))
             assert np.abs(a - b).max() <= 1e-12 * scale, (prob.name, name, a, b)
+        # the increment f - x: FP64 to rounding of x+, FP32 to FP32 precision of the
+        # increment itself (evaluated at the FP32-rounded point, as the mixed rollouts do)
+        inc = O.step(prob, x, u) - x
+        assert np.abs(d64 - inc).max() <= 1e-13 * max(1.0, float(np.abs(x).max()))
+        xf = x.astype(np.float32).astype(np.float64)
+        uf = u.astype(np.float32).astype(np.float64)
+        inc32 = O.step(prob, xf, uf) - xf
+        assert np.abs(d32 - inc32).max() <= 2e-5 * max(1e-3, float(np.abs(inc32).max())), (prob.name, d32, inc32)
+        # closed-loop Jacobian F + G Gam
+        Gam = np.array([[0.1 * lam[j] / (i + 1) for j in range(n)] for i in range(m)])
+        assert np.abs(Fcl - (F0 + G0 @ Gam).ravel()).max() <= 1e-12 * max(1.0, float(np.abs(F0).max()))
 
 
 def _val(rng):
