@@ -10,12 +10,14 @@
 //   K  pivot keys: x -> mag_key(double x) mag_key(float x)
 //   G  FP64 Gauss-Jordan inverse with partial pivoting: A(16) -> A^{-1}(16)
 //   L  LDL^T factorisation and solve: A(16, symmetric) B(4 x 3) -> X = A^{-1} B (12)
+//   D  co-state combine on FP32 increments (mixed mode): ga(4) Da(16) gb(4) Db(16)
+//      -> g(4) D(16), the elements being (g, I + D)
 // for n = 4, m = 1, and LQR precision 0 (FP64) or 1 (FP32 data, FP64 solves); the output
 // line is the resulting element (value elements as A b C eta J).
 #include <cstdio>
 #include <cstring>
 
-#include "ptn_ops.cuh"
+#include "ptn_solver.cuh"
 
 using namespace ptn;
 constexpr int N = 4, U = 1;
@@ -106,6 +108,14 @@ int main() {
     } else if (op[0] == 'K') {
       if (!rd(in, 1)) return 1;
       printf("%u %u", mag_key(in[0]), mag_key(float(in[0])));
+    } else if (op[0] == 'D') {
+      if (!rd(in, 40)) return 1;
+      IncAff<N> a, b, o;
+      for (int i = 0; i < 4; i++) { a.g[i] = in[i]; b.g[i] = in[20 + i]; }
+      for (int i = 0; i < 16; i++) { a.D[i] = float(in[4 + i]); b.D[i] = float(in[24 + i]); }
+      IncCostateOp()(a, b, o);
+      pr(o.g, 4);
+      for (int i = 0; i < 16; i++) printf("%.9g ", double(o.D[i]));
     } else if (op[0] == 'L') {
       if (!rd(in, 28)) return 1;
       ok = ldlt<N, double>(in);

@@ -281,3 +281,25 @@ def test_element_operators_refuse_singular_and_indefinite_inputs():
     r = subprocess.run([exe], input=v + "\n" + i + "\n", capture_output=True, text=True, check=True)
     outs = r.stdout.strip().splitlines()
     assert len(outs) == 2 and "FAIL" in outs[0] and "FAIL" in outs[1]
+
+
+def test_mixed_costate_operator_matches_the_oracle_combine():
+    # the FP32-increment co-state element (g, I + D) of the mixed mode: composition as the
+    # oracle's co-state combine of (g, I + D), to FP32 precision in the increment terms
+    exe = _harness(SRC_OPS, EXE_OPS)
+    rng = np.random.default_rng(23)
+    lines, refs = [], []
+    for _ in range(6):
+        ga, gb = rng.normal(size=4) * 10, rng.normal(size=4) * 10
+        Da = (0.05 * rng.normal(size=(4, 4))).astype(np.float32).astype(np.float64)
+        Db = (0.05 * rng.normal(size=(4, 4))).astype(np.float32).astype(np.float64)
+        lines.append("D 0 " + " ".join(repr(float(v)) for v in np.concatenate([ga, Da.ravel(), gb, Db.ravel()])))
+        g, Ft = O.costate_combine(ga, np.eye(4) + Da, gb, np.eye(4) + Db)
+        refs.append((g, Ft - np.eye(4)))
+    r = subprocess.run([exe], input="\n".join(lines) + "\n", capture_output=True, text=True, check=True)
+    outs = r.stdout.strip().splitlines()
+    assert len(outs) == len(refs)
+    for o, (g, D) in zip(outs, refs):
+        v = np.array([float(t) for t in o.split()])
+        assert np.abs(v[:4] - g).max() <= 1e-6 * max(1.0, float(np.abs(g).max()))
+        assert np.abs(v[4:] - D.ravel()).max() <= 1e-6 * max(1e-3, float(np.abs(D).max()))
