@@ -132,6 +132,47 @@ def oracle_solve_ms(T, seed):
     return (time.perf_counter() - t0) * 1e3, r["info"]
 
 
+def _oracle_batch_instance(k):
+    """One instance of the batch workload solved by the oracle (run in a worker process)."""
+    import oracle as O
+    from paper_2409_20027_gb300 import workloads as W
+    Tb = W.batch_horizons(1024, seed=0)
+    base = W.cartpole()
+    dt = BATCH_HORIZON_S / float(Tb[k])
+    sc = dt / base.dt
+    p = base.replace(dt=dt, Q=base.Q * sc, R=base.R * sc)
+    r = O.solve_ip(p, W.cartpole_batch_x0(1024, seed=0)[k], int(Tb[k]))
+    return int(Tb[k]), int(r["info"]["status"])
+
+
+def cpu_batch_baseline(n_sample=16):
+    """The oracle on a sample of the batch workload, one instance per worker process over
+    all host cores (a spawn pool, so it is safe after CUDA is initialised): solves/s of the
+    sample, which scales to the batch as its mean horizon does.  Never raises: a failure is
+    reported in the result instead."""
+    import multiprocessing as mp
+    import numpy as np
+    from paper_2409_20027_gb300 import workloads as W
+    try:
+        cores = os.cpu_count() or 1
+        rng = np.random.default_rng(7)
+        ks = sorted(int(k) for k in rng.choice(1024, size=n_sample, replace=False))
+        Tb = W.batch_horizons(1024, seed=0)
+        ctx = mp.get_context("spawn")
+        with ctx.Pool(processes=min(cores, n_sample)) as pool:
+            pool.map(_oracle_batch_instance, ks[:1])  # start-up (imports, oracle build) outside the timing
+            t0 = time.perf_counter()
+            res = pool.map(_oracle_batch_instance, ks)
+            wall = time.perf_counter() - t0
+        steps = sum(t for t, _ in res)
+        return {"solves_per_s": n_sample / wall, "unit": "solves/s", "cores": min(cores, n_sample), "kind": "oracle",
+                "sample": f"{n_sample} instances of the batch workload (seed 7 draw), {steps} steps; the whole "
+                          f"batch has {int(Tb.sum())} steps, one instance per process",
+                "converged": sum(1 for _, st in res if st == 0)}
+    except Exception as e:  # the GPU numbers must not depend on the host baseline
+        return {"error": f"{type(e).__name__}: {e}"}
+
+
 def run_reference(args, T):
     """The serial FP64 CPU oracle on a bounded sample of the workload: a T_s = 1024
     solve of the same problem family, scaled by T / T_s (the oracle's cost per Newton
@@ -542,6 +583,8 @@ def main():
     batch = None
     if not args.no_batch and single:
         batch = run_batch(args, ptn, W, dev, flush, stream)
+        if not args.no_cpu_baseline:
+            batch["cpu_baseline"] = cpu_batch_baseline()
     quad = None
     if not args.no_quad and single:
         quad = run_quadrotor(args, ptn, W, dev, flush, stream)
