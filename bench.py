@@ -159,10 +159,11 @@ def cpu_batch_baseline(n_sample=16):
         ks = sorted(int(k) for k in rng.choice(1024, size=n_sample, replace=False))
         Tb = W.batch_horizons(1024, seed=0)
         ctx = mp.get_context("spawn")
-        with ctx.Pool(processes=min(cores, n_sample)) as pool:
-            pool.map(_oracle_batch_instance, ks[:1])  # start-up (imports, oracle build) outside the timing
+        with ctx.Pool(processes=min(cores, n_sample)) as pool:  # leaving the block terminates it
+            # start-up (imports, library load) outside the timing; bounded waits throughout
+            pool.map_async(_oracle_batch_instance, ks[:1]).get(timeout=300)
             t0 = time.perf_counter()
-            res = pool.map(_oracle_batch_instance, ks)
+            res = pool.map_async(_oracle_batch_instance, ks).get(timeout=300)
             wall = time.perf_counter() - t0
         steps = sum(t for t, _ in res)
         return {"solves_per_s": n_sample / wall, "unit": "solves/s", "cores": min(cores, n_sample), "kind": "oracle",
