@@ -30,6 +30,7 @@ HORIZON_S = 2.56
 L2_FLUSH_BYTES = 256 << 20
 TUNED_TABLE = os.path.join(ROOT, "paper_2409_20027_gb300", "tuned_gb300.json")
 BATCH_HORIZON_S = 1.28  # keeps dt_b <= 0.02 for every batch horizon (T_b >= 64)
+SWEEP_T = [256, 1024, 4096, 16384, 32768, 65536]
 
 
 def algorithmic_flops(n, m, T, info):
@@ -42,10 +43,6 @@ def algorithmic_flops(n, m, T, info):
     return T * (info["newton_iters"] * per_it + info["roll_iters"] * per_roll)
 
 
-# FP32 FMA pipes: 152 SMs x 128 lanes x 2 flop x 2.07 GHz (maximum SM clock)
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
-# FP64: GB300's nominal dense FP64 rate
-FP64_PEAK_TFLOPS = 1.25
 # DRAM bytes (read + write) of one k_solve_grid launch of this workload, from the ncu
 # capture summarised in profiles/k_solve_grid_cartpole_T16384.md
 TRAFFIC_BYTES = (2.443776 + 1.739264) * 1e6
@@ -60,10 +57,34 @@ def flop_split(n, m, T, info):
     return total - f64, f64
 
 
-def blended_peak_tflops(f32, f64):
+def measured_fma_peaks():
+    """FP32 and FP64 FMA throughput of this GPU (TFLOP/s), measured by the probe kernel of
+    include/ptn_peaks.h (full occupancy, 8 independent chains per thread, CUDA-event timed),
+    with the SM count of the device; None where the probe is unavailable."""
+    import ctypes as C
+    from paper_2409_20027_gb300 import build as B
+    try:
+        lib = C.CDLL(B.build_peaks())
+        lib.ptn_peak_fma.argtypes = [C.c_int, C.c_int, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)]
+        out = {}
+        for name, fp64, iters in [("fp32", 0, 200000), ("fp64", 1, 2000)]:
+            best = 0.0
+            for _ in range(3):
+                tf, ms = C.c_double(), C.c_double()
+                rc = lib.ptn_peak_fma(fp64, 8, iters, C.byref(tf), C.byref(ms))
+                if rc != 0:
+                    return None
+                best = max(best, tf.value)
+            out[name] = best
+        return out
+    except (OSError, RuntimeError):
+        return None
+
+
+def blended_peak_tflops(f32, f64, p32, p64):
     """Peak rate of a kernel doing f32 FP32 and f64 FP64 flops with each pipe at its own
     peak: (f32 + f64) / (f32 / P32 + f64 / P64)."""
-    return (f32 + f64) / (f32 / FP32_PEAK_TFLOPS + f64 / FP64_PEAK_TFLOPS)
+    return (f32 + f64) / (f32 / p32 + f64 / p64)
 
 
 class ClockSampler:
@@ -123,70 +144,124 @@ def cartpole_instance(T):
     return W.cartpole(T=T, horizon=HORIZON_S)
 
 
-def oracle_solve_ms(T, seed):
+def _oracle_ref(job):
+    """One oracle solve of a benchmark workload (also run in spawn-pool workers): the
+    solution arrays, the oracle's report and the solve's wall time in ms.  Jobs:
+    ("cartpole", T, seed) the single-solve workload at horizon T; ("pendulum", seed) the
+    pendulum at T = 64; ("batch", k) instance k of the batch workload; ("quad", b, T)
+    instance b of the quadrotor workload."""
     import oracle as O
     from paper_2409_20027_gb300 import workloads as W
-    p = cartpole_instance(T)
+    kind = job[0]
+    if kind == "cartpole":
+        _, T, seed = job
+        args = (W.cartpole(T=T, horizon=HORIZON_S), W.cartpole_x0(seed), T)
+        kw = {}
+    elif kind == "pendulum":
+        args = (W.pendulum(), W.pendulum_x0(job[1]), 64)
+        kw = {}
+    elif kind == "batch":
+        k = job[1]
+        T = int(W.batch_horizons(1024, seed=0)[k])
+        args = (W.cartpole(T=T, horizon=BATCH_HORIZON_S), W.cartpole_batch_x0(1024, seed=0)[k], T)
+        kw = {}
+    elif kind == "quad":
+        _, b, T = job
+        args = (W.quadrotor(W.quadrotor_waypoints(b + 1, seed=0)[b]), np.zeros(12), T)
+        kw = {"u_init": np.full((T, 4), W.quadrotor_hover_u())}
+    else:
+        raise ValueError(job)
     t0 = time.perf_counter()
-    r = O.solve_ip(p, W.cartpole_x0(seed), T)
-    return (time.perf_counter() - t0) * 1e3, r["info"]
+    r = O.solve_ip(*args, **kw)
+    r["ms"] = (time.perf_counter() - t0) * 1e3
+    return r
 
 
-def _oracle_batch_instance(k):
-    """One instance of the batch workload solved by the oracle (run in a worker process)."""
-    import oracle as O
-    from paper_2409_20027_gb300 import workloads as W
-    Tb = W.batch_horizons(1024, seed=0)
-    base = W.cartpole()
-    dt = BATCH_HORIZON_S / float(Tb[k])
-    sc = dt / base.dt
-    p = base.replace(dt=dt, Q=base.Q * sc, R=base.R * sc)
-    r = O.solve_ip(p, W.cartpole_batch_x0(1024, seed=0)[k], int(Tb[k]))
-    return int(Tb[k]), int(r["info"]["status"])
+def err_vs_oracle(ref, x, u, lam, J):
+    """Relative error of a GPU result against the oracle's, max|a - b| / max(1, max|b|) for
+    x, u, lam and |J - J_o| / max(1, |J_o|), with the oracle's status and iteration count."""
+    def rel(a, b):
+        a = np.asarray(a)
+        b = np.asarray(b)
+        return float(np.abs(a - b).max() / max(1.0, np.abs(b).max()))
+    return {"x": rel(x, ref["x"]), "u": rel(u, ref["u"]),
+            "lam": None if lam is None else rel(lam, ref["lam"]),
+            "J": abs(J - ref["info"]["J"]) / max(1.0, abs(ref["info"]["J"])),
+            "oracle_status": ref["info"]["status"], "oracle_newton_iters": ref["info"]["newton_iters"]}
 
 
-def cpu_batch_baseline(n_sample=16):
-    """The oracle on a sample of the batch workload, one instance per worker process over
-    all host cores (a spawn pool, so it is safe after CUDA is initialised): solves/s of the
-    sample, which scales to the batch as its mean horizon does.  Never raises: a failure is
-    reported in the result instead."""
+def oracle_pool(jobs, timeout=900):
+    """Oracle solves of `jobs` in a spawn pool over the host cores (safe after CUDA is
+    initialised), one job per process; returns (results in job order, processes used)."""
     import multiprocessing as mp
-    import numpy as np
+    procs = max(1, min(os.cpu_count() or 1, len(jobs)))
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(processes=procs) as pool:  # leaving the block terminates it
+        return pool.map_async(_oracle_ref, jobs, chunksize=1).get(timeout=timeout), procs
+
+
+BATCH_SAMPLE = 16
+
+
+def batch_sample_indices():
+    rng = np.random.default_rng(7)
+    return sorted(int(k) for k in rng.choice(1024, size=BATCH_SAMPLE, replace=False))
+
+
+def cpu_batch_baseline():
+    """The oracle on a sample of the batch workload, one instance per worker process over
+    the host cores: solves/s of the sample (which scales to the batch as its mean horizon
+    does) and the sample's solutions.  Never raises: a failure is reported instead."""
     from paper_2409_20027_gb300 import workloads as W
     try:
-        cores = os.cpu_count() or 1
-        rng = np.random.default_rng(7)
-        ks = sorted(int(k) for k in rng.choice(1024, size=n_sample, replace=False))
+        ks = batch_sample_indices()
         Tb = W.batch_horizons(1024, seed=0)
-        ctx = mp.get_context("spawn")
-        with ctx.Pool(processes=min(cores, n_sample)) as pool:  # leaving the block terminates it
-            # start-up (imports, library load) outside the timing; bounded waits throughout
-            pool.map_async(_oracle_batch_instance, ks[:1]).get(timeout=300)
-            t0 = time.perf_counter()
-            res = pool.map_async(_oracle_batch_instance, ks).get(timeout=300)
-            wall = time.perf_counter() - t0
-        steps = sum(t for t, _ in res)
-        return {"solves_per_s": n_sample / wall, "unit": "solves/s", "cores": min(cores, n_sample), "kind": "oracle",
-                "sample": f"{n_sample} instances of the batch workload (seed 7 draw), {steps} steps; the whole "
+        oracle_pool([("batch", ks[0])])  # start-up (imports, library build) outside the timing
+        t0 = time.perf_counter()
+        res, procs = oracle_pool([("batch", k) for k in ks])
+        wall = time.perf_counter() - t0
+        steps = sum(int(Tb[k]) for k in ks)
+        return {"solves_per_s": len(ks) / wall, "unit": "solves/s", "cores": procs, "kind": "oracle",
+                "sample": f"{len(ks)} instances of the batch workload (seed 7 draw), {steps} steps; the whole "
                           f"batch has {int(Tb.sum())} steps, one instance per process",
-                "converged": sum(1 for _, st in res if st == 0)}
+                "converged": sum(1 for r in res if r["info"]["status"] == 0)}, dict(zip(ks, res))
     except Exception as e:  # the GPU numbers must not depend on the host baseline
-        return {"error": f"{type(e).__name__}: {e}"}
+        return {"error": f"{type(e).__name__}: {e}"}, {}
+
+
+def host_cpu():
+    """Model name of the host CPU (Linux /proc/cpuinfo, lscpu-style keys), or the machine."""
+    import platform
+    try:
+        for line in open("/proc/cpuinfo"):
+            k = line.split(":")[0].strip().lower()
+            if k in ("model name", "cpu model", "hardware"):
+                return line.split(":", 1)[1].strip()
+        r = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10)
+        for line in r.stdout.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return platform.machine()
 
 
 def run_reference(args, T):
-    """The serial FP64 CPU oracle on a bounded sample of the workload: a T_s = 1024
-    solve of the same problem family, scaled by T / T_s (the oracle's cost per Newton
-    iteration is linear in T and its iteration count does not grow with T)."""
-    Ts = min(T, 1024)
+    """The serial FP64 CPU oracle on the benchmark's workload itself: every timed step is
+    one complete oracle solve of the T = 16384 cart-pole (seed = step index mod 10), single
+    thread.  The warm-up steps are T = 1024 solves of the same problem family (the oracle
+    has no compilation step; warm-up only pages in its code and data)."""
     for k in range(args.warmup):
-        oracle_solve_ms(Ts, k % 10)
-    times = []
+        _oracle_ref(("cartpole", min(T, 1024), k % 10))
+    times, iters = [], []
     for k in range(args.steps):
-        ms, info = oracle_solve_ms(Ts, k % 10)
-        times.append(ms * T / Ts)
+        r = _oracle_ref(("cartpole", T, k % 10))
+        times.append(r["ms"])
+        iters.append(r["info"]["newton_iters"])
     v = sum(times) / len(times)
-    sample = f"oracle IP solve at T={Ts} (same 2.56 s horizon), time scaled x{T / Ts:g} to T={T}"
+    sample = (f"one complete oracle IP solve of the workload per step (T={T}, seed = step mod 10), "
+              f"single thread on {host_cpu()}; warm-up steps are T=1024 solves; mean Newton iterations "
+              f"{sum(iters) / len(iters):.1f}")
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "ms", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": v, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -203,6 +278,41 @@ def max_over_ranks(value, dist, device):
     t = torch.tensor([float(value)], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def run_pendulum(ptn, W, dev, flush, stream, tuned):
+    """The pendulum swing-up (n = 2, m = 1, Euler dt = 0.05, T = 64, |u| <= 5, mu 1e-1 ->
+    1e-6), FP64 throughout, seeds 0-9 (x0 = N(0, 0.05^2) per component), tuned launch shape;
+    each seed's solve timed with CUDA events after warm-up, L2 flushed before each."""
+    import torch
+    from paper_2409_20027_gb300 import autotune
+    T = 64
+    sv = ptn.Solver(W.pendulum(), max_T=T, precision=ptn.PTN_FP64)
+    launch = autotune.apply(sv, tuned, T)
+    x0s = [torch.tensor(W.pendulum_x0(sd), dtype=torch.float64, device=dev) for sd in range(10)]
+    for x in x0s[:3]:
+        sv.solve_ip(x, T)
+    torch.cuda.synchronize()
+    ms, its, st, infos, outs = [], [], [], [], {}
+    for sd, x in enumerate(x0s):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        xs, us, ls, inf = sv.solve_ip(x, T)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+        its.append(inf["newton_iters"])
+        st.append(inf["status"])
+        infos.append(inf)
+        outs[("pendulum", sd)] = (xs.cpu().numpy(), us.cpu().numpy(), ls.cpu().numpy(), inf["J"])
+    sv.close()
+    return {"workload": "pendulum swing-up, IP, T=64 (Euler dt=0.05), |u|<=5, FP64, seeds 0-9, KKT<=1e-6",
+            "ms_median": float(np.median(ms)), "ms_mean": float(np.mean(ms)), "ms": ms,
+            "newton_iters_mean": float(np.mean(its)),
+            "us_per_newton_iter": float(1e3 * np.sum(ms) / max(np.sum(its), 1)),
+            "status_counts": {str(k): st.count(k) for k in set(st)}, "launch": launch or "defaults",
+            "phase_share": phase_share(infos)}, outs
 
 
 def run_batch(args, ptn, W, dev, flush, stream):
@@ -234,6 +344,12 @@ def run_batch(args, ptn, W, dev, flush, stream):
         times.append(a.elapsed_time(b))
     ms = min(times)
     st = [i["status"] for i in infos]
+    # the solutions of the instances the CPU leg also solves (for the error against it)
+    xoff = np.concatenate([[0], np.cumsum(Tb + 1)])
+    uoff = np.concatenate([[0], np.cumsum(Tb)])
+    xs, us, ls = xo.cpu().numpy(), uo.cpu().numpy(), lo.cpu().numpy()
+    outs = {k: (xs[xoff[k]:xoff[k + 1]], us[uoff[k]:uoff[k + 1]], ls[xoff[k]:xoff[k + 1]], infos[k]["J"])
+            for k in batch_sample_indices() if k < B}
     # the same instances one at a time (a sample of 32, scaled to B)
     one = ptn.Solver(p, max_T=int(Tb.max()), precision=ptn.PTN_FP32_FP64SOLVE)
     ns = min(B, 32)
@@ -250,7 +366,7 @@ def run_batch(args, ptn, W, dev, flush, stream):
                         f"(seed 0, {S} steps), one launch", "solves_per_s": B / (ms * 1e-3), "ms": ms,
             "converged": int(sum(1 for x in st if x == 0)), "status_counts": {str(k): st.count(k) for k in set(st)},
             "one_by_one_solves_per_s": B / (seq_ms * 1e-3),
-            "one_by_one_sample": f"first {ns} instances as single solves (cluster or grid tier), time scaled to {B}"}
+            "one_by_one_sample": f"first {ns} instances as single solves (cluster or grid tier), time scaled to {B}"}, outs
 
 
 def run_multiplier(args, ptn, W, dev, flush, stream, tuned, x0):
@@ -348,6 +464,9 @@ def phase_share(infos):
     return {k: round(float(v / max(tot.sum(), 1.0)), 4) for k, v in zip(PHASES, tot)}
 
 
+QUAD_ORACLE_SAMPLE = 2
+
+
 def run_quadrotor(args, ptn, W, dev, flush, stream):
     """Quadrotor workload: B instances (n = 12, m = 4, Euler dt = 0.01, T = 1024), hover
     start at the origin, waypoints uniform in the 2 m cube (seed 0), hover thrust as the
@@ -372,7 +491,7 @@ def run_quadrotor(args, ptn, W, dev, flush, stream):
         flush.zero_()
         a, b, c = (torch.cuda.Event(enable_timing=True) for _ in range(3))
         a.record(stream)
-        _, _, _, infos = sv.solve_batch(x0, Tb, xref=xrefs, u_init=u0, x_out=xo, u_out=uo)
+        _, _, lq, infos = sv.solve_batch(x0, Tb, xref=xrefs, u_init=u0, x_out=xo, u_out=uo)
         b.record(stream)
         sv.adjoint(Tb, x0, xo, uo, infos[0]["mu"], 1.0, gx, None, xref=xrefs)
         c.record(stream)
@@ -380,6 +499,10 @@ def run_quadrotor(args, ptn, W, dev, flush, stream):
         fw.append(a.elapsed_time(b))
         ad.append(b.elapsed_time(c))
     st = [i["status"] for i in infos]
+    xs, us, ls = xo.cpu().numpy(), uo.cpu().numpy(), lq.cpu().numpy()
+    outs = {b: (xs[b * (T + 1):(b + 1) * (T + 1)], us[b * T:(b + 1) * T], ls[b * (T + 1):(b + 1) * (T + 1)],
+                infos[b]["J"])
+            for b in range(min(B, QUAD_ORACLE_SAMPLE))}
     sv.close()
     f, g = min(fw), min(ad)
     return {"workload": f"{B} quadrotor instances (n=12, m=4), T={T}, Euler dt=0.01, waypoints in a 2 m cube, "
@@ -387,25 +510,24 @@ def run_quadrotor(args, ptn, W, dev, flush, stream):
             "forward_ms": f, "adjoint_ms": g, "solves_per_s": B / (f * 1e-3), "grads_per_s": B / ((f + g) * 1e-3),
             "converged": int(sum(1 for x in st if x == 0)), "status_counts": {str(k): st.count(k) for k in set(st)},
             "newton_iters_mean": float(np.mean([i["newton_iters"] for i in infos])),
-            "phase_share": phase_share(infos)}
+            "phase_share": phase_share(infos)}, outs
 
 
-def run_mpc(ptn, W, dev, stream):
-    """Closed-loop MPC: 256 cart-pole loops (initial states as the batch workload), horizon
-    N = 60 at 100 Hz (dt = 0.01, RK4), 100 control periods, each period one batched solve
-    warm-started with the shifted controls of the previous one."""
+def _mpc_loop(ptn, W, prob, x0, target, steps):
+    """One closed-loop experiment: B loops from the rows of x0, horizon N at the problem's
+    rate, `steps` periods, each one batched solve warm-started with the shifted controls;
+    synchronous solves, then the same loop replayed period by period from one CUDA graph."""
     import torch
     from paper_2409_20027_gb300 import mpc
-    B, N, steps = 256, 60, 100
-    x0 = torch.tensor(W.cartpole_batch_x0(B, seed=1), dtype=torch.float64, device=dev)
-    sv = ptn.Solver(W.cartpole(), max_T=N, max_batch=B, precision=ptn.PTN_FP32_FP64SOLVE, block_threads=64)
+    B = x0.shape[0]
+    N = W.PAPER_MPC["horizon"]
+    sv = ptn.Solver(prob, max_T=N, max_batch=B, precision=ptn.PTN_FP32_FP64SOLVE, block_threads=64)
     mpc.closed_loop(sv, x0, N, 2)  # warm-up
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     res = mpc.closed_loop(sv, x0, N, steps)
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
-    # the same loop with every period replayed from one captured CUDA graph
     gl = mpc.GraphLoop(sv, x0, N)
     gl.run(2)  # warm-up
     torch.cuda.synchronize()
@@ -416,17 +538,36 @@ def run_mpc(ptn, W, dev, stream):
     same = bool(torch.equal(res["x"], resg["x"]) and torch.equal(res["u"], resg["u"]))
     del gl
     sv.close()
-    st = res["status"]
-    its = res["iters"]
-    return {"workload": f"{B} closed cart-pole loops, N={N}, 100 Hz (dt=0.01, RK4), {steps} periods, shifted warm "
-                        "start, fp32 LQR with fp64 solves, one batched solve per period",
+    st, its = res["status"], res["iters"]
+    err = (res["x"][-1] - torch.tensor(target, device=x0.device)).abs()
+    lim = float(prob.uhi[0])
+    return {"loops": B, "periods": steps, "horizon": N, "dt": prob.dt,
             "period_ms": 1e3 * wall / steps, "loop_periods_per_s": B * steps / wall,
             "graph_period_ms": 1e3 * wall_g / steps, "graph_loop_periods_per_s": B * steps / wall_g,
             "graph_same_trajectories": same,
             "newton_iters_first": float(its[0].mean()), "newton_iters_warm": float(its[1:].mean()),
             "converged_share": float((st == 0).mean()),
-            "final_state_max_abs_err": float((res["x"][-1] - torch.tensor([0.0, np.pi, 0.0, 0.0], device=dev))
-                                             .abs().max().item())}
+            "final_state_abs_err_max": err.max(dim=0).values.tolist(),
+            "final_state_abs_err_median": err.median(dim=0).values.tolist(),
+            "max_abs_control": float(res["u"].abs().max().item()), "control_limit": lim}
+
+
+def run_mpc(ptn, W, dev, stream):
+    """Closed-loop MPC as the paper's experiment (Sec. IV-C): 4 s at 100 Hz (400 periods),
+    horizon N = 60, Euler, the paper's pendulum (|tau| <= 5) and cart-pole (m_c = 10, m_p = 1,
+    |F| <= 60), target upright (and the cart at the origin); 256 loops per system."""
+    import torch
+    m = W.PAPER_MPC
+    steps = int(round(m["duration_s"] * m["rate_hz"]))
+    B = 256
+    xc = torch.tensor(W.cartpole_batch_x0(B, seed=1), dtype=torch.float64, device=dev)
+    xp = torch.tensor(np.stack([W.pendulum_upright_x0(1000 + b) for b in range(B)]), dtype=torch.float64, device=dev)
+    return {"workload": f"{B} closed loops per system, {m['duration_s']:g} s at {m['rate_hz']} Hz (Euler), N="
+                        f"{m['horizon']}, the paper's pendulum (|tau|<=5) and cart-pole (m_c=10, m_p=1, |F|<=60, "
+                        "R=1e-4), both from near upright, shifted warm start, fp32 LQR with fp64 solves, one "
+                        "batched solve per period",
+            "cartpole": _mpc_loop(ptn, W, W.cartpole_paper(), xc, [0.0, np.pi, 0.0, 0.0], steps),
+            "pendulum": _mpc_loop(ptn, W, W.pendulum_paper(), xp, [np.pi, 0.0], steps)}
 
 
 def run_sequential(args, ptn, W, dev, flush, stream):
@@ -476,6 +617,7 @@ def main():
     ap.add_argument("--no-mult", action="store_true")
     ap.add_argument("--no-admm", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-pend", action="store_true")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -557,12 +699,18 @@ def main():
         e2e.append((time.perf_counter() - t0) * 1e3)
     e2e_ms = sum(e2e) / len(e2e)
 
+    # the solution of the seed-0 solve, for the error against the oracle
+    _, _, _, info0 = solver.solve_ip(x0s[0], T, x_out=xo, u_out=uo, lam_out=lo)
+    gpu_out = {("cartpole", T, 0): (xo.cpu().numpy(), uo.cpu().numpy(), lo.cpu().numpy(), info0["J"])}
+
     # the sections below are single-GPU measurements: with N replicas only the headline
     # solve above is repeated on every GPU
     single = world == 1
     sweep = {}
     if not args.no_sweep and single:
-        for Ts in [256, 1024, 4096]:
+        for Ts in SWEEP_T:
+            if Ts == T:
+                continue
             ps = cartpole_instance(Ts)
             sv = ptn.Solver(ps, max_T=Ts, precision=ptn.PTN_FP32_FP64SOLVE)
             autotune.apply(sv, tuned, Ts)
@@ -572,23 +720,33 @@ def main():
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             flush.zero_()
             a.record(stream)
-            _, _, _, inf = sv.solve_ip(x0, Ts)
+            xs_, us_, ls_, inf = sv.solve_ip(x0, Ts)
             b.record(stream)
             torch.cuda.synchronize()
             sweep[str(Ts)] = {"ms": a.elapsed_time(b), "newton_iters": inf["newton_iters"], "status": inf["status"],
-                              "r_kkt": inf["r_kkt"]}
+                              "r_kkt": inf["r_kkt"], "us_per_newton_iter": 1e3 * a.elapsed_time(b) /
+                              max(inf["newton_iters"], 1)}
+            gpu_out[("cartpole", Ts, 0)] = (xs_.cpu().numpy(), us_.cpu().numpy(), ls_.cpu().numpy(), inf["J"])
             sv.close()
         sweep[str(T)] = {"ms": ms, "newton_iters": infos[-1]["newton_iters"], "status": infos[-1]["status"],
-                         "r_kkt": infos[-1]["r_kkt"]}
+                         "r_kkt": infos[-1]["r_kkt"], "us_per_newton_iter": 1e3 * ms / max(infos[-1]["newton_iters"], 1),
+                         "note": "the headline solves (mean over the timed steps)"}
+        sweep["workload"] = ("cart-pole IP on the fixed 2.56 s horizon (dt = 2.56/T, RK4), x0 seed 0, tuned launch "
+                             "shape per T, fp32 LQR with fp64 solves, KKT <= 1e-6")
+
+    pend = None
+    if not args.no_pend and single:
+        pend, pend_out = run_pendulum(ptn, W, dev, flush, stream, tuned)
+        gpu_out.update(pend_out)
 
     batch = None
+    batch_out = {}
     if not args.no_batch and single:
-        batch = run_batch(args, ptn, W, dev, flush, stream)
-        if not args.no_cpu_baseline:
-            batch["cpu_baseline"] = cpu_batch_baseline()
+        batch, batch_out = run_batch(args, ptn, W, dev, flush, stream)
     quad = None
+    quad_out = {}
     if not args.no_quad and single:
-        quad = run_quadrotor(args, ptn, W, dev, flush, stream)
+        quad, quad_out = run_quadrotor(args, ptn, W, dev, flush, stream)
     mpcl = None
     if not args.no_mpc and single:
         mpcl = run_mpc(ptn, W, dev, stream)
@@ -601,38 +759,99 @@ def main():
     mult = None
     if not args.no_mult and single:
         mult = run_multiplier(args, ptn, W, dev, flush, stream, tuned, x0s[0])
+    peaks = measured_fma_peaks() if rank == 0 else None
 
     if rank != 0:
         return
     last = infos[-1]
     f32, f64 = flop_split(4, 1, T, last)
     achieved = (f32 + f64) / (per[-1] * 1e-3) / 1e12
-    peak = blended_peak_tflops(f32, f64)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    if peaks:
+        p32, p64 = peaks["fp32"], peaks["fp64"]
+        src = "measured"
+        how = ("measured on this GPU by the FMA-throughput probe (include/ptn_peaks.h): FP32 %.1f TFLOP/s, FP64 "
+               "%.2f TFLOP/s" % (p32, p64))
+    else:
+        p32 = sms * 128 * 2 * 2.07e9 / 1e12
+        p64 = 1.25
+        src = "nominal"
+        how = "nominal: FP32 %d SMs x 128 lanes x 2 x 2.07 GHz = %.1f TFLOP/s, FP64 1.25 TFLOP/s" % (sms, p32)
+    peak = blended_peak_tflops(f32, f64, p32, p64)
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
             "traffic": TRAFFIC_BYTES if T == 16384 else None, "kernel": "k_solve_grid<CartPole,float,double>",
-            "peak_source": "derived: FP32 152 SMs x 128 lanes x 2 x 2.07 GHz = %.1f TFLOP/s, FP64 nominal "
-                           "%.2f TFLOP/s, blended by this solve's FP32/FP64 flop split (%.1f%% FP64)"
-                           % (FP32_PEAK_TFLOPS, FP64_PEAK_TFLOPS, 100 * f64 / (f32 + f64))}
+            "peak_source": "%s; blended by this solve's FP32/FP64 flop split (%.1f%% FP64); %d SMs"
+                           % (how, 100 * f64 / (f32 + f64), sms),
+            "peak_kind": src, "fp32_peak": p32, "fp64_peak": p64}
     cpu = None
+    errs = {}
     if not args.no_cpu_baseline and world == 1:
-        Ts = 1024
-        t_ms, _ = oracle_solve_ms(Ts, 0)
-        cpu = {"value": t_ms * T / Ts, "unit": "ms", "cores": 1, "kind": "oracle",
-               "sample": f"one oracle IP solve at T={Ts} (same horizon), time scaled x{T // Ts} to T={T}"}
+        # the oracle on the headline workload itself (one full solve, single thread) ...
+        r16 = _oracle_ref(("cartpole", T, 0))
+        cpu = {"value": r16["ms"], "unit": "ms", "cores": 1, "kind": "oracle",
+               "sample": f"one complete oracle IP solve of the workload (T={T}, seed 0), single thread on "
+                         f"{host_cpu()}", "oracle_newton_iters": r16["info"]["newton_iters"]}
+        refs = {("cartpole", T, 0): r16}
+        # ... and every other result's reference solve, in parallel over the host cores
+        jobs = [k for k in gpu_out if k not in refs]
+        jobs += [("quad", b, args.quad_T) for b in quad_out]
+        if batch is not None:
+            bc, bref = cpu_batch_baseline()
+            batch["cpu_baseline"] = bc
+            refs.update({("batch", k): r for k, r in bref.items()})
+        try:
+            res, _ = oracle_pool(jobs)
+            refs.update(dict(zip(jobs, res)))
+        except Exception as e:  # the GPU numbers must not depend on the host references
+            errs["error"] = f"{type(e).__name__}: {e}"
+        outs = dict(gpu_out)
+        outs.update({("quad", b, args.quad_T): v for b, v in quad_out.items()})
+        outs.update({("batch", k): v for k, v in batch_out.items()})
+        for key, (x, u, lam, J) in outs.items():
+            if key in refs:
+                errs["/".join(str(v) for v in key)] = err_vs_oracle(refs[key], x, u, lam, J)
+        if pend is not None:
+            pend["oracle_ms_median"] = float(np.median([refs[("pendulum", sd)]["ms"] for sd in range(10)
+                                                        if ("pendulum", sd) in refs] or [np.nan]))
+    head_err = errs.get(f"cartpole/{T}/0")
+    if not args.no_sweep and single and errs:
+        for Ts in SWEEP_T:
+            e = errs.get(f"cartpole/{Ts}/0")
+            if e is not None:
+                sweep[str(Ts)]["err_vs_oracle"] = e
+    if pend is not None and errs:
+        pend["err_vs_oracle_max"] = max_err([errs.get(f"pendulum/{sd}") for sd in range(10)])
+    if batch is not None and errs:
+        batch["err_vs_oracle_max"] = max_err([v for k, v in errs.items() if k.startswith("batch/")])
+        batch["err_vs_oracle_sample"] = "the instances of cpu_baseline's sample"
+    if quad is not None and errs:
+        quad["err_vs_oracle_max"] = max_err([v for k, v in errs.items() if k.startswith("quad/")])
+        quad["err_vs_oracle_sample"] = f"instances 0..{QUAD_ORACLE_SAMPLE - 1}"
     line = {"metric": METRIC, "value": ms, "unit": "ms", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic", "config": config(T),
             "roofline": roof, "cpu_baseline": cpu,
             "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": 4 * 8,
                     "d2h_bytes_per_step": ((T + 1) * 4 + T) * 8},
-            "gpu_launches": args.steps, "clocks": clocks, "kkt_ok": ok,
+            "gpu_launches": args.steps, "clocks": clocks, "kkt_ok": ok, "err_vs_oracle": head_err,
             "newton_iters": last["newton_iters"], "launch": launch or "defaults",
-            "phase_share": phase_share(infos), "sweep": sweep,
+            "phase_share": phase_share(infos), "sweep": sweep, "pendulum": pend,
             "batch": batch, "quadrotor": quad, "mpc": mpcl, "sequential": seq,
             "multiplier_form": mult, "admm": admm}
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+
+
+def max_err(es):
+    """Component-wise maximum of err_vs_oracle records (None entries skipped)."""
+    es = [e for e in es if e]
+    if not es:
+        return None
+    out = {k: max((e[k] for e in es if e.get(k) is not None), default=None) for k in ("x", "u", "lam", "J")}
+    out["instances"] = len(es)
+    out["oracle_not_converged"] = sum(1 for e in es if e["oracle_status"] != 0)
+    return out
 
 
 if __name__ == "__main__":

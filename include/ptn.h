@@ -234,16 +234,23 @@ int ptn_num_rows(const ptn_solver* s);
  * and take unbounded time; a plug-in that keeps no handle between calls).
  *
  * Same problem, options and results as ptn_solver_create + ptn_solve_ip on a one-CTA
- * solve (block_threads threads; grid_min_T and cluster_max_blocks are ignored), but no
- * handle: the problem record, options, report and all workspace arrays live in one
- * file-scope device array of 4 MiB (the cart-pole model needs about 0.7 KB per step, so
- * T up to about 5800; the pendulum about 0.3 KB per step).  A T that does not fit is
- * rejected with PTN_ERR_INVALID_ARG and a message giving the bytes needed.  No device or
- * pinned memory is allocated and no allocating library call is made.
+ * solve (block_threads threads; grid_min_T and cluster_max_blocks are ignored; option
+ * sequential must be 0, else PTN_ERR_INVALID_ARG), but no handle: the problem record,
+ * options, report and all workspace arrays live in one file-scope device array of 4 MiB
+ * (the cart-pole model needs about 0.7 KB per step, so T up to about 5800; the pendulum
+ * about 0.3 KB per step; the quadrotor about 5.7 KB per step, so T up to about 740).
+ * A T that does not fit is rejected with PTN_ERR_INVALID_ARG and a message giving the
+ * bytes needed.  No device or pinned memory is allocated and no allocating library call
+ * is made.
  *
- * The first call on each device does set-up: it looks up the array's device address
- * (cudaGetSymbolAddress, which loads the module on first use) and caches it.  Make that
- * first call before any stream capture on that device.
+ * Set-up: the array's device address belongs to the CUDA context that loaded the module.
+ * A call whose stream is not being captured looks it up in the calling thread's current
+ * context (cudaGetSymbolAddress, which loads the module on first use and makes the
+ * device's primary context current when the thread has none) and remembers it for that
+ * context.  A call made while its stream is being captured uses the remembered address
+ * and fails with PTN_ERR_INVALID_ARG when this context has none, so make the first call
+ * in each context (the first on each device, and the first after cudaDeviceReset) before
+ * any stream capture.
  *
  * Nothing in the array has to start at zero: each call copies the problem record,
  * options and instance entry into it in stream order, and the kernel writes every

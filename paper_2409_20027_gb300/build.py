@@ -98,5 +98,25 @@ def build(force: bool = False, jobs: int | None = None, verbose: bool = False, e
     return lib
 
 
+PEAKS_SRC = os.path.join(HERE, "peaks", "ptn_peaks.cu")
+PEAKS_LIB = os.path.join(OUT, "libptn_peaks.so")
+
+
+def build_peaks(force: bool = False) -> str:
+    """Compile the FMA-throughput probe (include/ptn_peaks.h) into its own library,
+    _build/libptn_peaks.so: benchmark infrastructure, not linked into libptn.so."""
+    os.makedirs(OUT, exist_ok=True)
+    hdr = os.path.join(HERE, "..", "include", "ptn_peaks.h")
+    if force or _stale(PEAKS_LIB, PEAKS_SRC, [hdr]):
+        tmp = PEAKS_LIB + f".{os.getpid()}.tmp"
+        r = subprocess.run([_nvcc(), *ARCH, *FLAGS, "-shared", "-o", tmp, PEAKS_SRC, "-lcudart"],
+                           capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError("nvcc failed for ptn_peaks.cu:\n" + r.stderr[-4000:])
+        os.replace(tmp, PEAKS_LIB)
+    return PEAKS_LIB
+
+
 if __name__ == "__main__":
     print(build(force="--force" in sys.argv, verbose=True))
+    print(build_peaks(force="--force" in sys.argv))

@@ -698,7 +698,7 @@ extern "C" int ptn_adjoint(ptn_solver* s, int B, const int* T_b, const double* x
 namespace {
 
 constexpr size_t kStaticScratchBytes = size_t(4) << 20;  // 4 MiB
-constexpr int kStaticMaxDevices = 64;
+constexpr int kStaticMaxContexts = 64;
 
 struct StaticHead {
   ProbDev prob;
@@ -707,8 +707,37 @@ struct StaticHead {
   InfoDev info;
 };
 
+// The device address of g_static_scratch belongs to the CUDA context that loaded the
+// module: a non-primary context, or a primary context created again after
+// cudaDeviceReset, has its own.  So the address is looked up again on every call whose
+// stream is not being captured (cudaGetSymbolAddress is a host-side lookup: no stream
+// work, no allocation once the module is loaded), and remembered per context for calls
+// made while a capture is recording, when no module may be loaded.
+struct StaticCtxAddr {
+  void* ctx;
+  char* base;
+};
 std::mutex g_static_mu;
-char* g_static_base[kStaticMaxDevices];  // device address of g_static_scratch, per ordinal
+StaticCtxAddr g_static_addr[kStaticMaxContexts];
+int g_static_naddr = 0;
+
+typedef int (*ctx_get_current_fn)(void**);  // cuCtxGetCurrent(CUcontext*)
+
+// Current context of the calling thread (nullptr if none or the query is unavailable),
+// through the driver entry point, so that the library does not link libcuda itself.
+void* static_current_ctx() {
+  static ctx_get_current_fn fn = [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      f = nullptr;
+    return reinterpret_cast<ctx_get_current_fn>(f);
+  }();
+  void* c = nullptr;
+  if (!fn || fn(&c) != 0) return nullptr;
+  return c;
+}
 
 int static_fail(char* err, int err_len, int code, const char* fmt, ...) {
   if (err && err_len > 0) {
@@ -746,6 +775,9 @@ extern "C" int ptn_solve_ip_static(const ptn_problem* prob, const ptn_options* o
   if (nx >= 8 && o.costate_mode != 0)
     return static_fail(err, err_len, PTN_ERR_INVALID_ARG,
                        "the multiplier form (costate_mode 1, 2) is not built for the wide tier (nx >= 8)");
+  if (o.sequential != 0)
+    return static_fail(err, err_len, PTN_ERR_INVALID_ARG,
+                       "the sequential-in-time baseline (option sequential) is not offered without a handle");
   if (prob->nx != nx || prob->nu != nu)
     return static_fail(err, err_len, PTN_ERR_INVALID_ARG, "model %d has nx=%d nu=%d, got %d %d", prob->model, nx, nu,
                        prob->nx, prob->nu);
@@ -821,23 +853,37 @@ extern "C" int ptn_solve_ip_static(const ptn_problem* prob, const ptn_options* o
     return static_fail(err, err_len, PTN_ERR_INVALID_ARG,
                        "T=%d needs %zu bytes of static scratch for model %d; the array holds %zu bytes", T, off,
                        P.model, kStaticScratchBytes);
-  // device set-up, once per device: the symbol's address (loading the module if needed)
-  int dev = 0;
-  cudaError_t ce = cudaGetDevice(&dev);
-  if (ce != cudaSuccess) return static_fail(err, err_len, PTN_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(ce));
-  if (dev < 0 || dev >= kStaticMaxDevices)
-    return static_fail(err, err_len, PTN_ERR_INVALID_ARG, "device ordinal %d outside [0, %d)", dev, kStaticMaxDevices);
+  // the array's address in the calling thread's current context (see g_static_addr)
+  cudaStream_t st = (cudaStream_t)stream_;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  cudaError_t ce = cudaStreamIsCapturing(st, &cap);
+  const bool capturing = ce != cudaSuccess || cap != cudaStreamCaptureStatusNone;
+  if (ce != cudaSuccess) (void)cudaGetLastError();  // e.g. the legacy stream during a global capture
   char* b = nullptr;
   {
     std::lock_guard<std::mutex> lk(g_static_mu);
-    if (!g_static_base[dev]) {
-      void* a = nullptr;
+    void* a = nullptr;
+    if (!capturing) {
+      // also makes the device's primary context current when the thread has none
       ce = cudaGetSymbolAddress(&a, g_static_scratch);
       if (ce != cudaSuccess)
         return static_fail(err, err_len, PTN_ERR_CUDA, "cudaGetSymbolAddress: %s", cudaGetErrorString(ce));
-      g_static_base[dev] = static_cast<char*>(a);
     }
-    b = g_static_base[dev];
+    void* ctx = static_current_ctx();
+    int slot = -1;
+    for (int i = 0; i < g_static_naddr; i++)
+      if (g_static_addr[i].ctx == ctx) slot = i;
+    if (!capturing) {
+      if (slot < 0) {
+        slot = g_static_naddr < kStaticMaxContexts ? g_static_naddr++ : kStaticMaxContexts - 1;
+        g_static_addr[slot].ctx = ctx;
+      }
+      g_static_addr[slot].base = static_cast<char*>(a);
+    } else if (slot < 0) {
+      return static_fail(err, err_len, PTN_ERR_INVALID_ARG,
+                         "no earlier call in this CUDA context: make one call before capturing the stream");
+    }
+    b = g_static_addr[slot].base;
   }
   StaticHead* dh = reinterpret_cast<StaticHead*>(b);
   to_optdev(o, PTN_METHOD_IP, &h.opt);
@@ -845,7 +891,6 @@ extern "C" int ptn_solve_ip_static(const ptn_problem* prob, const ptn_options* o
   h.inst.xoff = 0;
   h.inst.uoff = 0;
   h.inst.pad = 0;
-  cudaStream_t st = (cudaStream_t)stream_;
   // the head is copied from this stack frame in stream order; nothing else needs to be
   // initialised, because the kernel writes every workspace entry before reading it
   ce = cudaMemcpyAsync(dh, &h, offsetof(StaticHead, info), cudaMemcpyHostToDevice, st);

@@ -126,6 +126,21 @@ def _dptr(t):
     return C.c_void_p(t.data_ptr())
 
 
+def _check_buf(t, numel, name, min_only=False):
+    """Refuse a buffer that the kernel would read or write out of bounds, or that lives on
+    another device than the current one (None passes: the argument is optional)."""
+    if t is None:
+        return
+    import torch
+    if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise ValueError(f"{name}: expected a contiguous float64 CUDA tensor")
+    if t.device.index != torch.cuda.current_device():
+        raise ValueError(f"{name} is on cuda:{t.device.index}, the current device is cuda:{torch.cuda.current_device()}")
+    n = t.numel()
+    if n < numel if min_only else n != numel:
+        raise ValueError(f"{name} has {n} elements, expected {numel}")
+
+
 def _stream(stream):
     import torch
     s = torch.cuda.current_stream() if stream is None else stream
@@ -196,6 +211,7 @@ class Solver:
         x_out = self._out(T + 1, self.nx, x0) if x_out is None else x_out
         u_out = self._out(T, self.nu, x0) if u_out is None else u_out
         lam_out = self._out(T + 1, self.nx, x0) if lam_out is None else lam_out
+        _check_solve_bufs(T, self.nx, self.nu, x0, u_init, x_out, u_out, lam_out)
         info = Info()
         load().ptn_solve_ip(self._h, _dptr(x0), _dptr(u_init), int(T), _dptr(x_out), _dptr(u_out),
                             _dptr(lam_out), C.byref(info), _stream(stream))
@@ -318,6 +334,19 @@ def status_view(info_dev, B: int):
     return info_dev[: B * C.sizeof(Info)].view(-1).view(torch.int32).reshape(B, -1)[:, :2]
 
 
+def _check_solve_bufs(T, nx, nu, x0, u_init, x_out, u_out, lam_out):
+    """Sizes and device of a single solve's buffers (x0: nx, u_init: T*nu, x_out and
+    lam_out: (T+1)*nx, u_out: T*nu)."""
+    T = int(T)
+    if T < 1:
+        return  # the library reports the invalid horizon
+    _check_buf(x0, nx, "x0")
+    _check_buf(u_init, T * nu, "u_init")
+    _check_buf(x_out, (T + 1) * nx, "x_out")
+    _check_buf(u_out, T * nu, "u_out")
+    _check_buf(lam_out, (T + 1) * nx, "lam_out")
+
+
 def _make_problem(prob):
     """ptn_problem record for `prob`; returns (record, arrays it points into)."""
     keep = []
@@ -354,6 +383,7 @@ def solve_ip_static(prob, x0, T: int, u_init=None, x_out=None, u_out=None, lam_o
     x_out = mk(T + 1, nx) if x_out is None else x_out
     u_out = mk(T, nu) if u_out is None else u_out
     lam_out = mk(T + 1, nx) if lam_out is None else lam_out
+    _check_solve_bufs(T, nx, nu, x0, u_init, x_out, u_out, lam_out)
     info = Info()
     err = C.create_string_buffer(512)
     rc = lib.ptn_solve_ip_static(C.byref(P), C.byref(o), _dptr(x0), _dptr(u_init), int(T), _dptr(x_out),
@@ -382,11 +412,17 @@ def _solve_ip_function():
 
         forward(x0 (B, nx), theta, solver, T_b, xref) -> (x*, u*, J*): concatenated
         trajectories as in solve_batch and J* (B,), the barrier objective at mu_final.
-        theta must equal theta_of(solver.prob) (the solver's own parameters); it is an
-        input only so that autograd can route d loss / d theta to it."""
+        theta must equal theta_of(solver.prob) (the solver's own parameters; anything
+        else raises ValueError); it is an input only so that autograd can route
+        d loss / d theta to it."""
 
         @staticmethod
         def forward(ctx, x0, theta, solver, T_b, xref):
+            want = theta_of(solver.prob)
+            got = theta.detach().to("cpu", torch.float64).reshape(-1).numpy()
+            if got.shape != want.shape or not np.array_equal(got, want):
+                raise ValueError("theta must equal theta_of(solver.prob): the solve and its gradients use the "
+                                 "solver's own parameters; build a Solver for other parameters")
             x, u, _, infos = solver.solve_batch(x0.detach().contiguous(), T_b, xref=xref)
             bad = [(i, f["status"]) for i, f in enumerate(infos) if f["status"] != 0]
             if bad:

@@ -124,6 +124,43 @@ def cartpole_batch_x0(B: int, seed: int = 0) -> np.ndarray:
                      for b in range(B)])
 
 
+# ---------------------------------------------------------------- the paper's own settings
+# Sec. IV prints the model constants, Euler integration, the barrier schedule (mu from 0.1,
+# times 0.2 until mu <= 1e-4, i.e. a last level of 0.1 * 0.2^5), the ADMM penalties and
+# stopping rule, and the closed-loop experiment (4 s at 100 Hz, N = 60, |tau| < 5 Nm,
+# |F| < 60 N).  It prints no cost weights, horizon length in seconds or trajectory-
+# optimisation bounds: those are the readings of pendulum() and cartpole() above.
+PAPER_IP = {"mu0": 0.1, "zeta": 0.2, "mu_stop": 1e-4, "mu_final": 0.1 * 0.2 ** 5}
+PAPER_ADMM = {"pendulum_rho": 1.0, "cartpole_rho": 0.5, "tol": 1e-2}
+PAPER_MPC = {"duration_s": 4.0, "rate_hz": 100, "horizon": 60, "torque_limit": 5.0, "force_limit": 60.0}
+
+
+def pendulum_paper(dt: float = 1.0 / PAPER_MPC["rate_hz"]) -> Problem:
+    """The paper's pendulum (Sec. IV-A): g=9.81, l=1, m=1, b=1e-3, Euler step dt, with the
+    closed-loop experiment's torque limit |tau| <= 5 (Sec. IV-C); weights as pendulum()."""
+    t = PAPER_MPC["torque_limit"]
+    return pendulum(dt=dt, b=1e-3).replace(ulo=_f([-t]), uhi=_f([t]), name="pendulum_paper")
+
+
+def cartpole_paper(dt: float = 1.0 / PAPER_MPC["rate_hz"]) -> Problem:
+    """The paper's cart-pole (Sec. IV-B): m_c=10, m_p=1, l=0.5, g=9.81, Euler step dt, with
+    the closed-loop experiment's force limit |F| <= 60 (Sec. IV-C) and no cart-position
+    bound.  Q and Qf as cartpole(); R = 1e-4, so that the force limit rather than the force
+    weight bounds the 10 kg cart (at R = 0.01 the loop leaves the cart 2.6 m from the
+    origin after 4 s)."""
+    f = PAPER_MPC["force_limit"]
+    return cartpole(dt=dt).replace(integrator=EULER, prm=_f([10.0, 1.0, 0.5, 9.81]), R=np.array([[1e-4]]),
+                                   ulo=_f([-f]), uhi=_f([f]), xlo=np.full(4, -INF), xhi=np.full(4, INF),
+                                   name="cartpole_paper")
+
+
+def pendulum_upright_x0(seed: int) -> np.ndarray:
+    """theta ~ U[pi-0.3, pi+0.3], omega 0: near upright (the closed-loop experiment
+    stabilises the upright position, Sec. IV-C)."""
+    r = np.random.default_rng(seed)
+    return _f([r.uniform(np.pi - 0.3, np.pi + 0.3), 0.0])
+
+
 # ---------------------------------------------------------------- quadrotor
 QUAD_MASS = 0.5
 QUAD_G = 9.81

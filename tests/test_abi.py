@@ -1,5 +1,6 @@
 """The C-ABI library builds for sm_103a, loads, and exports every function that
-include/ptn.h declares (no compute calls: this runs without a GPU)."""
+include/ptn.h declares, and so does the benchmark's FMA-rate probe for include/ptn_peaks.h
+(no compute calls: this runs without a GPU)."""
 import ctypes
 import os
 import re
@@ -10,8 +11,8 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 HEADER = os.path.join(ROOT, "include", "ptn.h")
 
 
-def declared_functions():
-    txt = open(HEADER).read()
+def declared_functions(header=HEADER):
+    txt = open(header).read()
     txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
     names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\**\s+\**\s*(ptn_[a-z0-9_]+)\s*\(", txt, flags=re.M)
     return sorted(set(names))
@@ -31,6 +32,19 @@ def test_library_exports_every_declared_symbol():
         assert hasattr(lib, name), f"{name} declared in ptn.h but not exported"
     assert set(declared_functions()) <= set(ptn.EXPORTS)
     assert lib is not None
+
+
+def test_peaks_library_exports_its_header():
+    from paper_2409_20027_gb300 import build
+    names = declared_functions(os.path.join(ROOT, "include", "ptn_peaks.h"))
+    assert names == ["ptn_peak_fma"]
+    lib = ctypes.CDLL(build.build_peaks())
+    for name in names:
+        assert hasattr(lib, name)
+    # invalid arguments are refused before any CUDA call
+    lib.ptn_peak_fma.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
+    assert lib.ptn_peak_fma(2, 8, 10, None, None) == -1
+    assert lib.ptn_peak_fma(0, 0, 10, None, None) == -1
 
 
 def test_version_string_without_gpu():

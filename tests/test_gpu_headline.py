@@ -1,0 +1,128 @@
+"""GPU parity at the launch shapes the benchmark times, against the FP64 CPU oracle.
+
+- the cart-pole at T = 16384 (fixed 2.56 s horizon, RK4, FP32 LQR with FP64 solves) in the
+  tuned launch shape of the benchmark: the cooperative grid, 64 CTAs x 128 threads x 2
+  steps, so that the fold of several CTA totals per lane in the grid scan and reduction
+  (more than 32 CTAs) is exercised;
+- an FP64 grid solve with 64 CTAs (one step per thread), at the FP64 tolerance;
+- two instances of the quadrotor workload at its benchmark horizon T = 1024;
+- a slice of the 1024-instance batch workload that holds its longest horizon.
+
+Tolerances as in test_gpu_parity: FP64 path 1e-6, FP32 paths 1e-4 (relative), with both
+sides converged to max|d| <= 1e-7 in the FP32 cases (at 1e-6 the ill-conditioned reduced
+Hessian leaves the controls determined only to about 1e-3).  On the fixed 2.56 s horizon
+the gradient d_t of the cost with respect to u_t scales with dt = 2.56 / T, and so does the
+reduced Hessian: at T = 16384 a solve stopped at max|d| <= 1e-7 pins u only to about
+1e-7 / (2 R dt / 0.01) ~ 3e-4.  The oracle's quadratic endgame lands far below its
+tolerance (its u moves by 6e-8 between tolerances 1e-7 and 1e-9), the FP32 path's linear
+endgame (FP32 LQR directions) stops just below it; the FP32 side of that case is therefore
+solved to 1e-9.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2409_20027_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-6
+FP32_TOL = 1e-4
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def rel(a, b):
+    a = np.asarray(a)
+    b = np.asarray(b)
+    return float(np.abs(a - b).max() / max(1.0, np.abs(b).max()))
+
+
+@pytest.fixture(scope="module")
+def ptn():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_2409_20027_gb300 import build, ptn as P
+    build.build()
+    P.load()
+    return P
+
+
+def dev(a):
+    return torch.tensor(np.asarray(a, dtype=np.float64), device="cuda:0")
+
+
+def check(info, ref, x, u, lam, tol, with_lam=True):
+    assert info["status"] == 0, info
+    assert ref["info"]["status"] == 0, ref["info"]
+    ex, eu = rel(x.cpu().numpy(), ref["x"]), rel(u.cpu().numpy(), ref["u"])
+    el = rel(lam.cpu().numpy(), ref["lam"]) if with_lam else 0.0
+    eJ = abs(info["J"] - ref["info"]["J"]) / max(1.0, abs(ref["info"]["J"]))
+    assert max(ex, eu, el, eJ) <= tol, dict(x=ex, u=eu, lam=el, J=eJ)
+    assert info["r_stat"] <= 1e-6 and info["r_dyn"] <= 1e-6 and info["r_feas"] == 0.0
+
+
+def test_cartpole_headline_shape_fp32_matches_oracle(ptn):
+    from paper_2409_20027_gb300 import autotune
+    T = 16384
+    p = W.cartpole(T=T, horizon=2.56)
+    x0 = W.cartpole_x0(0)
+    s = ptn.Solver(p, max_T=T, precision=ptn.PTN_FP32_FP64SOLVE, tol_final=1e-9)
+    launch = autotune.apply(s, autotune.load(os.path.join(ROOT, "paper_2409_20027_gb300", "tuned_gb300.json")), T)
+    # the benchmark's tier and shape: T >= grid_min_T with more CTAs than a cluster holds
+    per = s.options.block_threads * s.options.grid_steps_per_thread
+    assert s.options.grid_min_T <= T and (T + per - 1) // per > s.options.cluster_max_blocks, launch
+    x, u, lam, info = s.solve_ip(dev(x0), T)
+    ref = O.solve_ip(p, x0, T, opts=O.Options(tol_final=1e-7))
+    check(info, ref, x, u, lam, FP32_TOL)
+
+
+def test_grid_fp64_64_ctas_matches_oracle(ptn):
+    # 8192 steps at 128 threads x 1 step per thread: 64 CTAs on the cooperative grid
+    T = 8192
+    p = W.cartpole(T=T, horizon=2.56)
+    x0 = W.cartpole_x0(2)
+    s = ptn.Solver(p, max_T=T, precision=ptn.PTN_FP64, grid_min_T=512, cluster_max_blocks=0,
+                   grid_steps_per_thread=1)
+    x, u, lam, info = s.solve_ip(dev(x0), T)
+    ref = O.solve_ip(p, x0, T)
+    check(info, ref, x, u, lam, FP64_TOL)
+    assert info["newton_iters"] == ref["info"]["newton_iters"]
+
+
+def test_quadrotor_bench_horizon_matches_oracle(ptn):
+    # two instances of the quadrotor workload (waypoints seed 0) at T = 1024, one launch
+    B, T = 2, 1024
+    wps = W.quadrotor_waypoints(256, seed=0)[:B]
+    probs = [W.quadrotor(w) for w in wps]
+    xrefs = dev(np.stack([q.xref for q in probs]))
+    hover = W.quadrotor_hover_u()
+    s = ptn.Solver(W.quadrotor(), max_T=T, max_batch=B, precision=ptn.PTN_FP32_FP64SOLVE, tol_final=1e-7)
+    X, U, Lm, infos = s.solve_batch(dev(np.zeros((B, 12))), [T] * B, xref=xrefs,
+                                    u_init=dev(np.full((B * T, 4), hover)))
+    for b in range(B):
+        ref = O.solve_ip(probs[b], np.zeros(12), T, u_init=np.full((T, 4), hover), opts=O.Options(tol_final=1e-7))
+        sl, su = slice(b * (T + 1), (b + 1) * (T + 1)), slice(b * T, (b + 1) * T)
+        check(infos[b], ref, X[sl], U[su], Lm[sl], FP32_TOL)
+
+
+def test_batch_slice_with_longest_horizon_matches_oracle(ptn):
+    # instances of the batch workload (horizons log-uniform in [64, 4096], seed 0, each over
+    # 1.28 s at dt_b = 1.28 / T_b): the longest one and two others, in one launch
+    Tall = W.batch_horizons(1024, seed=0)
+    x0all = W.cartpole_batch_x0(1024, seed=0)
+    ks = [int(np.argmax(Tall)), 0, 1]
+    Tb = Tall[ks].astype(np.int32)
+    assert Tb[0] > 4000
+    x0s = x0all[ks]
+    s = ptn.Solver(W.cartpole(), max_T=int(Tb.max()), max_batch=len(ks), precision=ptn.PTN_FP32_FP64SOLVE,
+                   tol_final=1e-7)
+    X, U, Lm, infos = s.solve_batch(dev(x0s), Tb, dt_b=1.28 / Tb)
+    xo = uo = 0
+    for b, T in enumerate(Tb.tolist()):
+        ref = O.solve_ip(W.cartpole(T=T, horizon=1.28), x0s[b], T, opts=O.Options(tol_final=1e-7))
+        check(infos[b], ref, X[xo:xo + T + 1], U[uo:uo + T], Lm[xo:xo + T + 1], FP32_TOL)
+        xo += T + 1
+        uo += T

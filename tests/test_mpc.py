@@ -55,3 +55,32 @@ def test_closed_loop_graph_replays_the_same_loop():
     assert (a["status"] == 0).all() and (b["status"] == 0).all()
     assert torch.equal(a["x"], b["x"]) and torch.equal(a["u"], b["u"])
     assert (a["iters"] == b["iters"]).all()
+
+
+@pytest.mark.gpu
+def test_paper_cartpole_loop_follows_oracle_loop():
+    # the paper's closed-loop experiment (Sec. IV-C): its cart-pole (m_c = 10, m_p = 1,
+    # Euler), |F| <= 60, N = 60 at 100 Hz, from near upright; the first periods use the
+    # force limit, so the barrier terms are active
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    import oracle as O
+    from paper_2409_20027_gb300 import mpc, ptn
+    p = W.cartpole_paper()
+    T, steps, B = W.PAPER_MPC["horizon"], 10, 3
+    x0 = W.cartpole_batch_x0(B, seed=1)
+    s = ptn.Solver(p, max_T=T, max_batch=B, precision=ptn.PTN_FP64, block_threads=64)
+    res = mpc.closed_loop(s, torch.tensor(x0, device="cuda:0"), T, steps)
+    assert (res["status"] == 0).all()
+    X = res["x"].cpu().numpy()
+    U = res["u"].cpu().numpy()
+    for b in range(B):
+        x, ui = x0[b], None
+        for k in range(steps):
+            r = O.solve_ip(p, x, T, u_init=ui)
+            assert r["info"]["status"] == 0
+            assert np.abs(U[k, b] - r["u"][0]).max() <= 1e-6 * max(1.0, np.abs(r["u"][0]).max()), (b, k)
+            x = r["x"][1]
+            ui = np.concatenate([r["u"][1:], r["u"][-1:]])
+            assert np.abs(X[k + 1, b] - x).max() <= 1e-6 * max(1.0, np.abs(x).max()), (b, k)
