@@ -165,6 +165,10 @@ def _oracle_ref(job):
         T = int(W.batch_horizons(1024, seed=0)[k])
         args = (W.cartpole(T=T, horizon=BATCH_HORIZON_S), W.cartpole_batch_x0(1024, seed=0)[k], T)
         kw = {}
+    elif kind == "synth":
+        _, T, k = job
+        args = (W.synth(0), W.synth_x0(k), T)
+        kw = {"opts": O.Options(costate_mode=1)}
     elif kind == "quad":
         _, b, T = job
         args = (W.quadrotor(W.quadrotor_waypoints(b + 1, seed=0)[b]), np.zeros(12), T)
@@ -424,31 +428,45 @@ def run_multiplier(args, ptn, W, dev, flush, stream, tuned, x0):
     return out
 
 
-def run_admm(args, ptn, W, dev, flush, stream, tuned, x0):
-    """ADMM (Sec. II-C) on the cart-pole sweep: rho = 1, the paper's stopping rule
-    max|w - z| <= 1e-2 and max|z - z_prev| <= 1e-2, each sub-problem solved by Newton to
-    the final tolerance; same horizons, x0 and tuned launch shapes as the IP sweep."""
+def _admm_solve(ptn, prob, T, x0, stream, flush, tuned, **opt):
     import torch
     from paper_2409_20027_gb300 import autotune
-    out = {}
-    for Ts in [256, 1024, 4096, args.T]:
-        ps = cartpole_instance(Ts)
-        sv = ptn.Solver(ps, max_T=Ts, precision=ptn.PTN_FP32_FP64SOLVE, rho=1.0, admm_tol=1e-2, max_outer=200)
-        autotune.apply(sv, tuned, Ts)
-        sv.solve_admm(x0, Ts)
-        torch.cuda.synchronize()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        flush.zero_()
-        a.record(stream)
-        _, _, _, inf = sv.solve_admm(x0, Ts)
-        b.record(stream)
-        torch.cuda.synchronize()
-        out[str(Ts)] = {"ms": a.elapsed_time(b), "status": inf["status"], "outer_iters": inf["outer_iters"],
-                        "newton_iters": inf["newton_iters"], "r_p": inf["r_p"], "r_d": inf["r_d"],
-                        "r_stat": inf["r_stat"]}
-        sv.close()
-    out["workload"] = ("cart-pole ADMM (rho 1) on the 2.56 s horizon, stop at max|w-z|, max|z-z_prev| <= 1e-2, "
-                       "Newton sub-problems to 1e-6, FP32 LQR with FP64 solves")
+    sv = ptn.Solver(prob, max_T=T, precision=ptn.PTN_FP32_FP64SOLVE, **opt)
+    autotune.apply(sv, tuned, T)
+    sv.solve_admm(x0, T)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    flush.zero_()
+    a.record(stream)
+    _, _, _, inf = sv.solve_admm(x0, T)
+    b.record(stream)
+    torch.cuda.synchronize()
+    sv.close()
+    return {"ms": a.elapsed_time(b), "status": inf["status"], "outer_iters": inf["outer_iters"],
+            "newton_iters": inf["newton_iters"], "r_p": inf["r_p"], "r_d": inf["r_d"], "r_stat": inf["r_stat"]}
+
+
+def run_admm(args, ptn, W, dev, flush, stream, tuned, x0):
+    """ADMM (Sec. II-C) with the paper's stopping rule max|w - z| <= 1e-2 and max|z - z_prev|
+    <= 1e-2, at most 2000 outer iterations (the oracle's own cap), each sub-problem solved by
+    Newton to 1e-6, FP32 LQR with FP64 solves:
+      - the paper's pendulum (g, l, m, b = 1e-3, Euler, |tau| <= 5; rho = 1 as the paper sets
+        it) on a fixed 3.2 s horizon, T = 256 ... 16384: time-to-solve at the rule;
+      - the configuration's cart-pole (rho = 1, 2.56 s horizon) at T = 256, 1024, which does not
+        meet the rule within 2000 outer iterations, on the GPU or in the oracle."""
+    import torch
+    out = {"pendulum_paper": {}, "cartpole": {}}
+    xp = torch.tensor(W.pendulum_x0(0), dtype=torch.float64, device=dev)
+    for Ts in [256, 1024, 4096, 16384]:
+        out["pendulum_paper"][str(Ts)] = _admm_solve(ptn, W.pendulum_paper(dt=3.2 / Ts), Ts, xp, stream, flush, tuned,
+                                                     rho=W.PAPER_ADMM["pendulum_rho"], admm_tol=W.PAPER_ADMM["tol"],
+                                                     max_outer=2000)
+    for Ts in [256, 1024]:
+        out["cartpole"][str(Ts)] = _admm_solve(ptn, cartpole_instance(Ts), Ts, x0, stream, flush, tuned, rho=1.0,
+                                               admm_tol=1e-2, max_outer=2000)
+    out["workload"] = ("ADMM, stop at max|w-z|, max|z-z_prev| <= 1e-2 or 2000 outer iterations; the paper's pendulum "
+                       "(rho 1) on 3.2 s at dt = 3.2/T, x0 seed 0; the cart-pole of the sweep (rho 1, 2.56 s, x0 seed "
+                       "0); Newton sub-problems to 1e-6, FP32 LQR with FP64 solves")
     return out
 
 
@@ -570,6 +588,107 @@ def run_mpc(ptn, W, dev, stream):
             "pendulum": _mpc_loop(ptn, W, W.pendulum_paper(), xp, [np.pi, 0.0], steps)}
 
 
+def run_synth(args, ptn, W, dev, flush, stream):
+    """The synthetic scaling workload x+ = A x + B u + 0.1 tanh(W x) (n = 32, m = 8; A 0.98 x
+    Haar orthogonal, B ~ N(0, 1/m), W ~ N(0, 1/n), random SPD Q, R = 0.1 I, |u| <= 1, x0 ~
+    N(0, I); matrices from seed 0), IP with the multiplier form of the co-states (the co-state
+    products of A + 0.1 W grow like 1.0167^T at this seed), FP32 LQR data with FP64 solves,
+    wide tier: one instance at T = 65536 on the cooperative grid, and a batch of 64 instances
+    with T uniform in [1024, 8192] (seed 0), one CTA each."""
+    import torch
+    p = W.synth(0)
+    out = {"workload": "synthetic x+ = A x + B u + 0.1 tanh(W x), n=32, m=8 (seed 0), |u|<=1, IP, multiplier "
+                       "form of the co-states, fp32 LQR with fp64 solves, wide tier",
+           "spectral_radius_A_plus_cW": float(np.abs(np.linalg.eigvals(p.A + 0.1 * p.W)).max())}
+    T = args.synth_T
+    sv = ptn.Solver(p, max_T=T, precision=ptn.PTN_FP32_FP64SOLVE, costate_mode=1)
+    x0 = torch.tensor(W.synth_x0(0), dtype=torch.float64, device=dev)
+    flush.zero_()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    xs, us, ls, inf = sv.solve_ip(x0, T)
+    b.record(stream)
+    torch.cuda.synchronize()
+    out["single"] = {"T": T, "ms": a.elapsed_time(b), "status": inf["status"], "newton_iters": inf["newton_iters"],
+                     "r_kkt": inf["r_kkt"], "r_stat": inf["r_stat"], "r_dyn": inf["r_dyn"], "J": inf["J"],
+                     "us_per_newton_iter": 1e3 * a.elapsed_time(b) / max(inf["newton_iters"], 1),
+                     "phase_share": phase_share([inf]), "note": "one solve, cold (the first of this model)"}
+    sv.close()
+    B = args.synth_batch
+    Tb = W.uniform_horizons(B, seed=0, lo=1024, hi=8192)
+    S = int(Tb.sum())
+    sb = ptn.Solver(p, max_T=(S + B - 1) // B, max_batch=B, precision=ptn.PTN_FP32_FP64SOLVE, costate_mode=1)
+    xb = torch.tensor(np.stack([W.synth_x0(k) for k in range(B)]), dtype=torch.float64, device=dev)
+    flush.zero_()
+    a.record(stream)
+    X, U, _, infos = sb.solve_batch(xb, Tb)
+    b.record(stream)
+    torch.cuda.synchronize()
+    st = [i["status"] for i in infos]
+    k = int(np.argmin(Tb))
+    xoff = int(np.sum(Tb[:k] + 1))
+    uoff = int(np.sum(Tb[:k]))
+    sample = (X[xoff:xoff + int(Tb[k]) + 1].cpu().numpy(), U[uoff:uoff + int(Tb[k])].cpu().numpy(), None,
+              infos[k]["J"])
+    out["batch"] = {"instances": B, "steps": S, "ms": a.elapsed_time(b), "solves_per_s": B / (a.elapsed_time(b) * 1e-3),
+                    "status_counts": {str(v): st.count(v) for v in set(st)},
+                    "newton_iters_mean": float(np.mean([i["newton_iters"] for i in infos])),
+                    "horizons": "uniform in [1024, 8192], seed 0", "x0": "synth_x0(b) for instance b"}
+    sb.close()
+    return out, {("synth", int(Tb[k]), k): sample}
+
+
+LITERAL_T = [256, 1024, 4096, 16384]
+
+
+def run_literal_dt(args, ptn, W, dev, flush, stream, tuned):
+    """The cart-pole at the configuration's literal time step dt = 0.01 for every T (the
+    horizon grows to 163.84 s): the co-state form (0) and the multiplier form (1), FP32 LQR
+    with FP64 solves, tuned launch shape per T; status, Newton iterations and time."""
+    import torch
+    from paper_2409_20027_gb300 import autotune
+    out = {"workload": "cart-pole IP at dt = 0.01 for every T (horizon 0.01 T s), x0 seed 0, FP32 LQR with FP64 "
+                       "solves; the open-loop co-state map of the upright cart-pole grows like 1.0476^T"}
+    x0 = torch.tensor(W.cartpole_x0(0), dtype=torch.float64, device=dev)
+    for T in LITERAL_T:
+        row = {}
+        for mode in [0, 1]:
+            sv = ptn.Solver(W.cartpole(dt=0.01), max_T=T, precision=ptn.PTN_FP32_FP64SOLVE, costate_mode=mode)
+            autotune.apply(sv, tuned, T)
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            _, _, _, inf = sv.solve_ip(x0, T)
+            b.record(stream)
+            torch.cuda.synchronize()
+            row[f"mode{mode}"] = {"ms": a.elapsed_time(b), "status": inf["status"], "newton_iters": inf["newton_iters"],
+                                  "r_stat": inf["r_stat"]}
+            sv.close()
+        out[str(T)] = row
+    return out
+
+
+def oracle_literal(T):
+    """The oracle on the literal-dt cart-pole (seed 0): its status, Newton iterations, the
+    largest co-state and log10 of the norm of the open-loop Jacobian product along its result."""
+    import oracle as O
+    from paper_2409_20027_gb300 import workloads as W
+    p = W.cartpole(dt=0.01)
+    t0 = time.perf_counter()
+    r = O.solve_ip(p, W.cartpole_x0(0), T)
+    ms = (time.perf_counter() - t0) * 1e3
+    M = np.eye(4)
+    lg = 0.0
+    for t in range(T):
+        F, _ = O.jac(p, r["x"][t], r["u"][t])
+        M = F @ M
+        nm = np.linalg.norm(M)
+        lg += np.log10(nm)
+        M /= nm
+    return {"status": r["info"]["status"], "newton_iters": r["info"]["newton_iters"], "ms": ms,
+            "max_abs_lam": float(np.abs(r["lam"]).max()), "log10_norm_prod_F": lg}
+
+
 def run_sequential(args, ptn, W, dev, flush, stream):
     """The paper's comparison axis on this GPU: the same single cart-pole solve (2.56 s
     horizon, T = 1024, FP32 LQR with FP64 solves) by the sequential-in-time baseline (one
@@ -618,6 +737,10 @@ def main():
     ap.add_argument("--no-admm", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-pend", action="store_true")
+    ap.add_argument("--no-synth", action="store_true")
+    ap.add_argument("--no-literal", action="store_true")
+    ap.add_argument("--synth-T", type=int, default=65536)
+    ap.add_argument("--synth-batch", type=int, default=64)
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -747,6 +870,13 @@ def main():
     quad_out = {}
     if not args.no_quad and single:
         quad, quad_out = run_quadrotor(args, ptn, W, dev, flush, stream)
+    literal = None
+    if not args.no_literal and single:
+        literal = run_literal_dt(args, ptn, W, dev, flush, stream, tuned)
+    synth = None
+    synth_out = {}
+    if not args.no_synth and single:
+        synth, synth_out = run_synth(args, ptn, W, dev, flush, stream)
     mpcl = None
     if not args.no_mpc and single:
         mpcl = run_mpc(ptn, W, dev, stream)
@@ -795,6 +925,7 @@ def main():
         # ... and every other result's reference solve, in parallel over the host cores
         jobs = [k for k in gpu_out if k not in refs]
         jobs += [("quad", b, args.quad_T) for b in quad_out]
+        jobs += list(synth_out)
         if batch is not None:
             bc, bref = cpu_batch_baseline()
             batch["cpu_baseline"] = bc
@@ -807,6 +938,7 @@ def main():
         outs = dict(gpu_out)
         outs.update({("quad", b, args.quad_T): v for b, v in quad_out.items()})
         outs.update({("batch", k): v for k, v in batch_out.items()})
+        outs.update(synth_out)
         for key, (x, u, lam, J) in outs.items():
             if key in refs:
                 errs["/".join(str(v) for v in key)] = err_vs_oracle(refs[key], x, u, lam, J)
@@ -827,6 +959,12 @@ def main():
     if quad is not None and errs:
         quad["err_vs_oracle_max"] = max_err([v for k, v in errs.items() if k.startswith("quad/")])
         quad["err_vs_oracle_sample"] = f"instances 0..{QUAD_ORACLE_SAMPLE - 1}"
+    if literal is not None and not args.no_cpu_baseline and world == 1:
+        for T in LITERAL_T[:3]:
+            literal[str(T)]["oracle_mode0"] = oracle_literal(T)
+    if synth is not None and errs:
+        synth["batch"]["err_vs_oracle"] = max_err([v for k, v in errs.items() if k.startswith("synth/")])
+        synth["batch"]["err_vs_oracle_sample"] = "the batch's shortest instance (oracle time grows as n^3 T)"
     line = {"metric": METRIC, "value": ms, "unit": "ms", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic", "config": config(T),
@@ -836,7 +974,8 @@ def main():
             "gpu_launches": args.steps, "clocks": clocks, "kkt_ok": ok, "err_vs_oracle": head_err,
             "newton_iters": last["newton_iters"], "launch": launch or "defaults",
             "phase_share": phase_share(infos), "sweep": sweep, "pendulum": pend,
-            "batch": batch, "quadrotor": quad, "mpc": mpcl, "sequential": seq,
+            "batch": batch, "quadrotor": quad, "synthetic": synth, "literal_dt": literal, "mpc": mpcl,
+            "sequential": seq,
             "multiplier_form": mult, "admm": admm}
     print(json.dumps(line), flush=True)
     if dist is not None:

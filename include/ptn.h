@@ -73,7 +73,7 @@ typedef struct ptn_problem {
 /* Solver settings; ptn_default_options() fills the defaults:
  *   precision FP32_FP64SOLVE, mu 1e-1 -> 1e-6 (x0.1), tol_inner 1e-4, tol_final 1e-6,
  *   block_threads 128, grid_min_T 512, grid_steps_per_thread 2, polish 100, polish_after 50,
- *   cluster_max_blocks 16, sequential 0, costate_mode 0 (the co-state scan),
+ *   cluster_max_blocks 16, sequential 0, costate_mode 0 (the co-state scan), update_mode 0,
  *   max_newton 500 per barrier level, ADMM rho 1, admm_tol 1e-2, max_outer 2000,
  *   alpha0 1e-6 in [1e-10, 1e10], ten step sizes 1, 1/2, ..., Armijo c1 1e-4,
  *   rollout: at most 30 multiple-shooting Newton iterations to relative defect 1e-12. */
@@ -87,7 +87,8 @@ typedef struct ptn_options {
   int block_threads;    /* threads per CTA when one CTA solves one instance */
   int grid_min_T;       /* single solves with T >= grid_min_T use all SMs (0: never) */
   int grid_steps_per_thread;
-  int polish_after;     /* FP32 modes: exact FP64 gradients after this many iterations */
+  int polish_after;     /* FP32 modes: exact FP64 gradients after this many iterations of
+                           a barrier level or ADMM sub-problem */
   int cluster_max_blocks; /* single solves needing 2..cluster_max_blocks CTAs (block_threads
                              threads, grid_steps_per_thread steps each) run on one thread-block
                              cluster (at most 16; 0: never) before the cooperative grid is used */
@@ -104,8 +105,12 @@ typedef struct ptn_options {
                            iteration) restarts the multipliers from the co-states of the
                            scan; more robust than 1 far from the solution (where the
                            pure form can stall), still fewer Newton iterations than 0 on
-                           long horizons.  Modes 1, 2 are not built for nx >= 8
-                           (PTN_ERR_INVALID_ARG). */
+                           long horizons. */
+  int update_mode;      /* 0: a Newton step is taken on the closed-loop nonlinear rollout
+                           (line search over step sizes; the default); 1: the update of
+                           Alg. 4 as printed, x <- x + dx, u <- u + du, taken whenever its
+                           cost is finite (for IP: strictly feasible), which leaves dynamics
+                           defects of second order; for comparisons */
   double mu0, zeta, mu_final, tol_inner, tol_final, rho, admm_tol;
   double alpha0, alpha_min, alpha_max, ls_beta, armijo_c1, armijo_eps, roll_tol;
   double polish;        /* FP32 modes: exact FP64 gradients once max|d| <= polish * tol_final */
@@ -215,11 +220,14 @@ int ptn_solve_batch_async(ptn_solver* s, const double* x0, const double* xref, c
  * envelope theorem on the Lagrangian eq. ocp-lagrangian (gradient in x0 = lam_1); the x*, u*
  * part solves the adjoint LQR (same Hessian as the Newton step, linear terms from
  * gx, gu) with the value and state scans, and its multipliers with the co-state scan.
- * The adjoint runs in FP64 in every precision mode (one CTA per instance, block_threads
- * threads): at a solution the reduced Hessian is ill-conditioned near active bounds.
+ * The adjoint runs in FP64 in every precision mode (one CTA of block_threads threads per
+ * instance; a single instance with T_b >= grid_min_T on the cooperative grid): at a solution
+ * the reduced Hessian is ill-conditioned near active bounds.
  * All array arguments are device pointers; gx, gu may be NULL (J* part only); any output
  * may be NULL.  xref as in ptn_solve_batch.  Returns PTN_ERR_NUMERICAL when the Hessian
- * is not positive definite on the dynamics at some instance's solution. */
+ * is not positive definite on the dynamics at some instance's solution, PTN_ERR_TIMEOUT
+ * when a grid barrier wait expired, PTN_ERR_INVALID_ARG for the synthetic model (no
+ * adjoint is built for it). */
 int ptn_adjoint(ptn_solver* s, int B, const int* T_b, const double* x0, const double* xref,
                 const double* x_star, const double* u_star, double mu, double gJ,
                 const double* gx, const double* gu, double* g_x0, double* g_Qd, double* g_Rd,

@@ -62,7 +62,7 @@ class _Options(C.Structure):
                 ["mu0", "zeta", "mu_final", "tol_inner", "tol_final", "rho", "admm_tol",
                  "alpha0", "alpha_min", "alpha_max", "ls_beta", "armijo_c1", "armijo_eps"]] + \
                [(k, C.c_int) for k in ["max_newton", "max_outer", "ls_count", "admm_fixed_iters",
-                                       "costate_mode"]]
+                                       "costate_mode", "update_mode"]]
 
 
 class _Aug(C.Structure):
@@ -97,6 +97,9 @@ class Options:
     # that updates multipliers of the dynamics by the LQR duals (no recursion through F^T);
     # 2: the multiplier form restarted from the recursion's co-states at every sub-problem
     costate_mode: int = 0
+    # 0: steps accepted on the closed-loop nonlinear rollout (line search); 1: the update
+    # of Alg. 4 as printed, x <- x + dx, u <- u + du (taken when its cost is finite)
+    update_mode: int = 0
 
     def _c(self) -> _Options:
         o = _Options()

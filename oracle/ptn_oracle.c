@@ -62,6 +62,8 @@ typedef struct orc_options {
                          1: multiplier form (dynamics multipliers updated by the LQR duals);
                          2: multiplier form whose multipliers restart from the co-states of
                             the recursion at the start of every Newton sub-problem */
+    int update_mode;  /* 0: step accepted on the closed-loop nonlinear rollout (line search);
+                         1: the update of Alg. 4 as printed, x <- x + dx, u <- u + du */
 } orc_options;
 
 typedef struct orc_aug {
@@ -1204,13 +1206,24 @@ static int newton_solve(const orc_problem *P, const rows_t *R, const orc_aug *G,
         if (q) mult_g1(n, T, q, &W);
         int accepted = 0;
         double s = 1.0, Js = INFINITY;
-        for (int k = 0; k < o->ls_count; k++, s *= o->ls_beta) {
-            if (rollout_closed(P, T, x, u, W.Gam, W.gam, s, xc, uc)) continue;
+        if (o->update_mode == 1) {
+            /* Alg. 4 as printed: the full Newton step on states and controls, no rollout
+             * (the linearised dynamics leave defects x_{t+1} - f(x_t, u_t) of second order).
+             * Reading: the step is taken whenever its cost is finite (for the barrier: the
+             * point is strictly feasible); otherwise it counts as rejected. */
+            for (int i = 0; i < (T + 1) * n; i++) xc[i] = x[i] + W.dx[i];
+            for (int i = 0; i < T * m; i++) uc[i] = u[i] + W.du[i];
             Js = traj_cost(P, R, G, T, xc, uc, NULL);
-            if (!isfinite(Js)) continue;
-            if (Js <= J0 + o->armijo_c1 * s * W.G1 + o->armijo_eps * (1.0 + fabs(J0))) {
-                accepted = 1;
-                break;
+            accepted = isfinite(Js);
+        } else {
+            for (int k = 0; k < o->ls_count; k++, s *= o->ls_beta) {
+                if (rollout_closed(P, T, x, u, W.Gam, W.gam, s, xc, uc)) continue;
+                Js = traj_cost(P, R, G, T, xc, uc, NULL);
+                if (!isfinite(Js)) continue;
+                if (Js <= J0 + o->armijo_c1 * s * W.G1 + o->armijo_eps * (1.0 + fabs(J0))) {
+                    accepted = 1;
+                    break;
+                }
             }
         }
         if (accepted) {

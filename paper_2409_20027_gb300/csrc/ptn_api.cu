@@ -71,6 +71,7 @@ int model_dims(int model, int* nx, int* nu) {
     case PTN_MODEL_PENDULUM: *nx = 2; *nu = 1; return 0;
     case PTN_MODEL_CARTPOLE: *nx = 4; *nu = 1; return 0;
     case PTN_MODEL_QUADROTOR: *nx = 12; *nu = 4; return 0;
+    case PTN_MODEL_SYNTH_TANH: *nx = 32; *nu = 8; return 0;
     default: {
       const UserModel* um = find_user_model(model);
       if (!um) return -1;
@@ -206,6 +207,8 @@ static int check_options(ptn_solver* s, const ptn_options* o) {
   if (o->grid_steps_per_thread < 1) return fail(s, PTN_ERR_INVALID_ARG, "grid_steps_per_thread must be >= 1");
   if (o->cluster_max_blocks < 0 || o->cluster_max_blocks > 16)
     return fail(s, PTN_ERR_INVALID_ARG, "cluster_max_blocks must be in [0, 16]");
+  if (o->update_mode < 0 || o->update_mode > 1)
+    return fail(s, PTN_ERR_INVALID_ARG, "update_mode must be 0 (rollout line search) or 1 (x += dx, u += du)");
   if (o->costate_mode < 0 || o->costate_mode > 2)
     return fail(s, PTN_ERR_INVALID_ARG,
                 "costate_mode must be 0 (co-state scan), 1 (multiplier form) or 2 (multiplier form restarted "
@@ -307,6 +310,27 @@ extern "C" int ptn_solver_create(const ptn_problem* prob, const ptn_options* opt
   CK(cudaGetDevice(&dev));
   CK(cudaGetDeviceProperties(&dp, dev));
   s->num_sms = dp.multiProcessorCount;
+  if (prob->model == PTN_MODEL_SYNTH_TANH) {
+    // the map's matrices A (nx x nx), B (nx x nu), W (nx x nx): FP64 and FP32 copies in
+    // device memory owned by the handle
+    if (!prob->A || !prob->B || !prob->W)
+      return bad(fail(s, PTN_ERR_INVALID_ARG, "the synthetic model needs A, B and W"));
+    const size_t na = (size_t)nx * nx, nb = (size_t)nx * nu, tot = 2 * na + nb;
+    std::vector<double> h(tot);
+    std::vector<float> hf(tot);
+    for (size_t i = 0; i < na; i++) { h[i] = prob->A[i]; h[na + nb + i] = prob->W[i]; }
+    for (size_t i = 0; i < nb; i++) h[na + i] = prob->B[i];
+    for (size_t i = 0; i < tot; i++) {
+      if (!isfinite(h[i])) return bad(fail(s, PTN_ERR_INVALID_ARG, "A, B, W not finite"));
+      hf[i] = (float)h[i];
+    }
+    CK(cudaMalloc(&s->dsynth, tot * (sizeof(double) + sizeof(float))));
+    CK(cudaMemcpy(s->dsynth, h.data(), tot * sizeof(double), cudaMemcpyHostToDevice));
+    float* df = reinterpret_cast<float*>(s->dsynth + tot);
+    CK(cudaMemcpy(df, hf.data(), tot * sizeof(float), cudaMemcpyHostToDevice));
+    P.A = s->dsynth; P.B = s->dsynth + na; P.W = s->dsynth + na + nb;
+    P.A32 = df; P.B32 = df + na; P.W32 = df + na + nb;
+  }
   CK(cudaMalloc(&s->dprob, sizeof(ProbDev)));
   CK(cudaMemcpy(s->dprob, &P, sizeof(ProbDev), cudaMemcpyHostToDevice));
   CK(cudaMalloc(&s->dopt, sizeof(OptDev)));
@@ -389,6 +413,7 @@ static void to_optdev(const ptn_options& o, int method, OptDev* d) {
   d->max_newton = o.max_newton; d->max_outer = o.max_outer; d->ls_count = o.ls_count;
   d->admm_fixed_iters = o.admm_fixed_iters; d->roll_max_iter = o.roll_max_iter; d->method = method;
   d->costate_mode = o.costate_mode;
+  d->update_mode = o.update_mode;
   d->spin_limit = 1ll << 26;
 }
 
@@ -442,10 +467,21 @@ static int plan_launch(ptn_solver* s, int method, int B, const int* T_b, long lo
   // one instance: a thread-block cluster when the horizon needs 2..16 CTAs, else the
   // cooperative grid from grid_min_T on, else one CTA
   int cl_blocks = 0;
-  // models with n >= 8 run the wide tier (one CTA per instance, one warp per chunk)
+  // models with n >= 8 run the wide tier (one warp per chunk): one CTA per instance, or for
+  // one instance from grid_min_T on the whole cooperative grid (tier 6); as many threads per
+  // CTA as block_threads asks and shared memory allows
   const bool wide = s->n >= 8;
-  if (wide && s->opt.costate_mode != 0)
-    return fail(s, PTN_ERR_INVALID_ARG, "the multiplier form (costate_mode 1, 2) is not built for the wide tier (nx >= 8)");
+  int wide_threads = s->opt.block_threads;
+  if (wide) {
+    int fit = 0;
+    q.query = 4;
+    q.max_blocks = &fit;
+    CK(fn(q));
+    if (fit < 32) return fail(s, PTN_ERR_INVALID_ARG, "model %d: one warp's scratch does not fit in shared memory", s->hprob.model);
+    if (wide_threads > fit) wide_threads = fit;
+    q = LaunchReq{};
+    q.precision = s->opt.precision;
+  }
   if (!wide && !s->opt.sequential && B == 1 && s->opt.cluster_max_blocks >= 2) {
     const long long per = (long long)s->opt.block_threads * s->opt.grid_steps_per_thread;
     const long long need = (T_b[0] + per - 1) / per;
@@ -460,13 +496,29 @@ static int plan_launch(ptn_solver* s, int method, int B, const int* T_b, long lo
     }
   }
   const bool grid = !wide && !cl_blocks && B == 1 && s->opt.grid_min_T > 0 && T_b[0] >= s->opt.grid_min_T;
+  const bool wide_grid = wide && B == 1 && s->opt.grid_min_T > 0 && T_b[0] >= s->opt.grid_min_T;
   if (s->opt.sequential && !wide) {
     p->tier = 5;
     p->nthreads = 32;
     p->nblocks = (B + 31) / 32;
+  } else if (wide_grid) {
+    p->tier = 6;
+    p->nthreads = wide_threads;
+    int maxb = 0;
+    q.tier = 6;
+    q.nthreads = wide_threads;
+    q.query = 1;
+    q.max_blocks = &maxb;
+    CK(fn(q));
+    const long long per = (long long)(wide_threads / 32) * s->opt.grid_steps_per_thread;
+    long long want = (T_b[0] + per - 1) / per;
+    int nb = want < maxb ? (int)want : maxb;
+    if (nb > s->grid_cap_blocks) nb = s->grid_cap_blocks;
+    if (nb < 1) return fail(s, PTN_ERR_INVALID_ARG, "no co-resident CTA for the wide grid tier");
+    p->nblocks = nb;
   } else if (wide) {
     p->tier = 4;
-    p->nthreads = s->opt.block_threads;
+    p->nthreads = wide_threads;
     p->nblocks = B;
   } else if (cl_blocks) {
     p->tier = 2;
@@ -527,7 +579,7 @@ static int enqueue(ptn_solver* s, const LaunchPlan& p, const OptDev* dopt, const
   q.args.u_init = u_init;
   q.args.info = dinfo;
   q.args.B = p.B;
-  if (p.tier == 1) {
+  if (p.tier == 1 || p.tier == 6) {
     q.args.gs = s->gs;
     CK(cudaMemsetAsync(s->gs.bar, 0, 2 * sizeof(unsigned), st));
     CK(cudaMemsetAsync(s->gs.err, 0, sizeof(int), st));
@@ -650,6 +702,8 @@ extern "C" int ptn_adjoint(ptn_solver* s, int B, const int* T_b, const double* x
   }
   if (steps > s->cap_steps)
     return fail(s, PTN_ERR_INVALID_ARG, "total horizon %lld exceeds the workspace (%lld)", steps, s->cap_steps);
+  if (s->hprob.model == PTN_MODEL_SYNTH_TANH)
+    return fail(s, PTN_ERR_INVALID_ARG, "the adjoint is not built for the synthetic model");
   // the adjoint LQR runs in FP64 whatever the solver's precision
   launch_fn fn = pick_launcher(s->hprob.model, PTN_FP64);
   if (!fn) return fail(s, PTN_ERR_INVALID_ARG, "FP64 kernels for model %d are not built", s->hprob.model);
@@ -678,12 +732,38 @@ extern "C" int ptn_adjoint(ptn_solver* s, int B, const int* T_b, const double* x
   q.adj = &aa;
   q.nthreads = s->opt.block_threads;
   q.nblocks = B;
+  if (B == 1 && s->n < 8 && s->opt.grid_min_T > 0 && T_b[0] >= s->opt.grid_min_T) {
+    // one long instance: the cooperative grid, 128 threads per CTA, grid_steps_per_thread
+    // steps per thread as far as the co-resident CTAs allow
+    LaunchReq qq{};
+    int maxb = 0;
+    qq.tier = 7;
+    qq.precision = PTN_FP64;
+    qq.nthreads = 128;
+    qq.query = 1;
+    qq.max_blocks = &maxb;
+    CK(fn(qq));
+    const long long per = 128LL * s->opt.grid_steps_per_thread;
+    long long want = (T_b[0] + per - 1) / per;
+    int nb = want < maxb ? (int)want : maxb;
+    if (nb > s->grid_cap_blocks) nb = s->grid_cap_blocks;
+    if (nb < 1) return fail(s, PTN_ERR_INVALID_ARG, "no co-resident CTA for the grid adjoint");
+    q.tier = 7;
+    q.nthreads = 128;
+    q.nblocks = nb;
+    q.args.gs = s->gs;
+    CK(cudaMemsetAsync(s->gs.bar, 0, 2 * sizeof(unsigned), st));
+    CK(cudaMemsetAsync(s->gs.err, 0, sizeof(int), st));
+  }
   CK(fn(q));
   CK(cudaMemcpyAsync(s->hinfo, s->dinfo, sizeof(InfoDev) * B, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
-  for (int i = 0; i < B; i++)
+  for (int i = 0; i < B; i++) {
+    if (s->hinfo[i].status == ST_ETIMEOUT)
+      return fail(s, PTN_ERR_TIMEOUT, "instance %d: a grid barrier wait expired", i);
     if (s->hinfo[i].status != 0)
       return fail(s, PTN_ERR_NUMERICAL, "instance %d: the Hessian is not positive definite on the dynamics", i);
+  }
   return PTN_OK;
 }
 
@@ -772,9 +852,10 @@ extern "C" int ptn_solve_ip_static(const ptn_problem* prob, const ptn_options* o
   int nx, nu;
   if (model_dims(prob->model, &nx, &nu))
     return static_fail(err, err_len, PTN_ERR_INVALID_ARG, "unknown or unsupported model id %d", prob->model);
-  if (nx >= 8 && o.costate_mode != 0)
+  if (prob->model == PTN_MODEL_SYNTH_TANH)
     return static_fail(err, err_len, PTN_ERR_INVALID_ARG,
-                       "the multiplier form (costate_mode 1, 2) is not built for the wide tier (nx >= 8)");
+                       "the synthetic model is not offered without a handle (its matrices live in a handle's "
+                       "device memory)");
   if (o.sequential != 0)
     return static_fail(err, err_len, PTN_ERR_INVALID_ARG,
                        "the sequential-in-time baseline (option sequential) is not offered without a handle");

@@ -50,6 +50,9 @@ struct ProbDev {
   const double* A;  // synthetic model: nx*nx
   const double* B;  // nx*nu
   const double* W;  // nx*nx
+  const float* A32;  // the same in FP32 (the model's FP32 terms)
+  const float* B32;
+  const float* W32;
 };
 
 struct OptDev {
@@ -58,7 +61,8 @@ struct OptDev {
   double roll_tol, polish, armijo_eps32;
   int max_newton, max_outer, ls_count, admm_fixed_iters;
   int roll_max_iter, method, polish_after, init_max_iter;
-  int costate_mode, pad_;  // 0: co-state scan (Alg. 1); 1: multiplier form
+  int costate_mode;        // 0: co-state scan (Alg. 1); 1, 2: multiplier forms
+  int update_mode;         // 0: step on the closed-loop rollout; 1: x += dx, u += du (Alg. 4)
   long long spin_limit;  // bounded waits in grid barriers
 };
 

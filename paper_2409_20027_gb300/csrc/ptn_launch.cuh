@@ -44,7 +44,8 @@ inline Work<L> typed(const WorkRaw& r) {
 struct LaunchReq {
   int tier;       // 0: one CTA per instance, 1: cooperative grid, 2: one cluster on one instance,
                   // 3: adjoint, one CTA per instance, 4: wide (n >= 8, one warp per chunk),
-                  // 5: sequential-in-time baseline (one thread per instance)
+                  // 5: sequential-in-time baseline (one thread per instance), 6: wide on the
+                  // cooperative grid (one instance), 7: adjoint of one instance on the grid
   int precision;  // 0: FP64, 1: FP32 with FP64 solves, 2: FP32
   int nblocks, nthreads;
   int query;      // 1: only report max co-resident grid blocks in *max_blocks;
@@ -78,6 +79,36 @@ cudaError_t launch_typed(LaunchReq& q) {
     if (q.query) return cudaSuccess;
     k_solve_seq<M, L, SV><<<q.nblocks, q.nthreads, 0, q.stream>>>(q.args, typed<L>(q.w));
     return cudaGetLastError();
+  }
+  if (q.tier == 7) {
+    // the adjoint of one instance on the cooperative grid (FP64 units only)
+    if constexpr (std::is_same<L, double>::value) {
+      cudaError_t e = raise_smem_limit<k_adjoint_grid<M, L, SV>>(smem);
+      if (e != cudaSuccess) return e;
+      if (q.query == 1) {
+        int dev = 0, per = 0, sms = 0;
+        e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_adjoint_grid<M, L, SV>, nthreads, smem);
+        if (e != cudaSuccess) return e;
+        *q.max_blocks = per * sms;
+        return cudaSuccess;
+      }
+      if (q.query) return cudaSuccess;
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(q.nblocks);
+      cfg.blockDim = dim3(nthreads);
+      cfg.dynamicSmemBytes = smem;
+      cfg.stream = q.stream;
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeCooperative;
+      at[0].val.cooperative = 1;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      return cudaLaunchKernelEx(&cfg, k_adjoint_grid<M, L, SV>, q.args, typed<L>(q.w), *q.adj);
+    } else {
+      return cudaErrorNotSupported;
+    }
   }
   if (q.tier == 3) {
     // the adjoint is built only in the FP64 units (it runs in FP64 in every mode)

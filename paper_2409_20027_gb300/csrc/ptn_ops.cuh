@@ -85,14 +85,55 @@ PTN_HD void symmetrize(L* X) {
     }
 }
 
-// Value operator (eq. value-fun-param, with b_{t,i} as the last term of b):
-//   A   = A2 K A1,                 K = (I + C1 J2)^{-1}
+// Products of the value operator (eq. value-fun-param, with b_{t,i} as the last term of b)
+// once K = (I + C1 J2)^{-1} is known:
+//   A   = A2 K A1
 //   C   = A2 K C1 A2^T + C2
 //   b   = A2 K (b1 + C1 eta2) + b2
 //   J   = A1^T K^T J2 A1 + J1      K^T = (I + J2 C1)^{-1} since C, J are symmetric
 //   eta = A1^T K^T (eta2 - J2 b1) + eta1
-// C1 J2 is formed in L, and I + C1 J2 inverted in SV (FP64, or FP32 in the all-FP32
-// mode); the products run in L.  Returns false when I + C1 J2 is singular.
+template <int N, class L>
+PTN_HD void value_apply_K(const Val<N, L>& e1, const Val<N, L>& e2, const L* K, Val<N, L>& o) {
+  Val<N, L> r;
+  L t1[N * N], t2[N * N], w[N], tv[N];
+  // A and C
+  mm<N, N, N>(K, e1.A, t1);
+  mm<N, N, N>(e2.A, t1, r.A);
+  mm<N, N, N>(K, e1.C, t1);
+  mm<N, N, N>(e2.A, t1, t2);
+  mmt<N, N, N>(t2, e2.A, r.C);
+#pragma unroll
+  for (int i = 0; i < N * N; i++) r.C[i] += e2.C[i];
+  // b
+  mv<N, N>(e1.C, e2.eta, w);
+#pragma unroll
+  for (int i = 0; i < N; i++) w[i] += e1.b[i];
+  mv<N, N>(K, w, tv);
+  mv<N, N>(e2.A, tv, r.b);
+#pragma unroll
+  for (int i = 0; i < N; i++) r.b[i] += e2.b[i];
+  // J
+  mm<N, N, N>(e2.J, e1.A, t1);
+  mtm<N, N, N>(K, t1, t2);
+  mtm<N, N, N>(e1.A, t2, r.J);
+#pragma unroll
+  for (int i = 0; i < N * N; i++) r.J[i] += e1.J[i];
+  // eta
+  mv<N, N>(e2.J, e1.b, w);
+#pragma unroll
+  for (int i = 0; i < N; i++) w[i] = e2.eta[i] - w[i];
+  mtv<N, N>(K, w, tv);
+  mtv<N, N>(e1.A, tv, r.eta);
+#pragma unroll
+  for (int i = 0; i < N; i++) r.eta[i] += e1.eta[i];
+  symmetrize<N>(r.C);
+  symmetrize<N>(r.J);
+  o = r;
+}
+
+// Value operator (eq. value-fun-param): K = (I + C1 J2)^{-1} with C1 J2 formed in L and
+// I + C1 J2 inverted in SV (FP64, or FP32 in the all-FP32 mode), then value_apply_K in L.
+// Returns false when I + C1 J2 is singular.
 template <class SV = double>
 struct ValueOp {
   template <int N, class L>
@@ -109,41 +150,7 @@ struct ValueOp {
     L K[N * N];
 #pragma unroll
     for (int i = 0; i < N * N; i++) K[i] = L(Md[i]);
-    Val<N, L> r;
-    L t1[N * N], t2[N * N], w[N], tv[N];
-    // A and C
-    mm<N, N, N>(K, e1.A, t1);
-    mm<N, N, N>(e2.A, t1, r.A);
-    mm<N, N, N>(K, e1.C, t1);
-    mm<N, N, N>(e2.A, t1, t2);
-    mmt<N, N, N>(t2, e2.A, r.C);
-#pragma unroll
-    for (int i = 0; i < N * N; i++) r.C[i] += e2.C[i];
-    // b
-    mv<N, N>(e1.C, e2.eta, w);
-#pragma unroll
-    for (int i = 0; i < N; i++) w[i] += e1.b[i];
-    mv<N, N>(K, w, tv);
-    mv<N, N>(e2.A, tv, r.b);
-#pragma unroll
-    for (int i = 0; i < N; i++) r.b[i] += e2.b[i];
-    // J
-    mm<N, N, N>(e2.J, e1.A, t1);
-    mtm<N, N, N>(K, t1, t2);
-    mtm<N, N, N>(e1.A, t2, r.J);
-#pragma unroll
-    for (int i = 0; i < N * N; i++) r.J[i] += e1.J[i];
-    // eta
-    mv<N, N>(e2.J, e1.b, w);
-#pragma unroll
-    for (int i = 0; i < N; i++) w[i] = e2.eta[i] - w[i];
-    mtv<N, N>(K, w, tv);
-    mtv<N, N>(e1.A, tv, r.eta);
-#pragma unroll
-    for (int i = 0; i < N; i++) r.eta[i] += e1.eta[i];
-    symmetrize<N>(r.C);
-    symmetrize<N>(r.J);
-    o = r;
+    value_apply_K<N, L>(e1, e2, K, o);
     return true;
   }
 };
@@ -204,6 +211,92 @@ PTN_HD bool value_init(const L* F, const L* G, const L* Pm, const L* Mm, const L
   }
   symmetrize<N>(e.J);
   symmetrize<N>(e.C);
+  return true;
+}
+
+// Value combination of one step's element nu_t (eq. value-fun-elem-init) with a later
+// element e (eq. value-fun-param, nu_t first), in place: the same element as
+// ValueOp(value_init(F, G, P, M, R, d), e), written through the Woodbury identity.  The
+// step's C_t = G R~^{-1} G^T has rank U, so with Q = R~ + G^T J G (U x U)
+//   (I + C_t J)^{-1} = I - G Q^{-1} G^T J,
+// and the combination becomes one backward Bellman step of (J, eta) -- the recursion of
+// eq. value-fun-feedback with S = J, s = -eta -- plus the propagation of A, b and C:
+//   H = M^T + G^T J F,   Gam = -Q^{-1} H,   gam = Q^{-1} (G^T eta - d)
+//   J   <- P + F^T J F + H^T Gam
+//   eta <- F^T eta - H^T gam
+//   A   <- A (F + G Gam)
+//   b   <- b + (A G) gam
+//   C   <- C + (A G) Q^{-1} (A G)^T
+// (A, b, C, J, eta of e on the right-hand sides).  Q is formed in L and inverted in SV:
+// one U x U solve replaces the N x N inverse of I + C_t J.  Returns false when Q is
+// singular (then I + C_t J is singular as well: det(I + C_t J) = det Q / det R~).
+template <int N, int U, class L, class SV>
+PTN_HD bool value_fold_step(const L* F, const L* G, const L* Pm, const L* Mm, const L* Rm, const double* d,
+                            double alpha, Val<N, L>& e) {
+  L JG[N * U], JF[N * N], GJG[U * U], H[U * N], Ge[U];
+  mm<N, N, U>(e.J, G, JG);
+  mm<N, N, N>(e.J, F, JF);
+  mtm<U, N, U>(G, JG, GJG);
+  mtm<U, N, N>(G, JF, H);
+  mtv<N, U>(G, e.eta, Ge);
+#pragma unroll
+  for (int i = 0; i < U; i++)
+#pragma unroll (N <= 8 ? N : 4)
+    for (int j = 0; j < N; j++) H[i * N + j] += Mm[j * U + i];
+  SV Q[U * U];
+#pragma unroll
+  for (int i = 0; i < U; i++)
+#pragma unroll
+    for (int j = 0; j < U; j++) Q[i * U + j] = SV(Rm[i * U + j]) + SV(GJG[i * U + j]) + (i == j ? SV(alpha) : SV(0));
+  if (!inv_gj<U, SV>(Q)) return false;
+  L Gam[U * N], gam[U], Qi[U * U];
+#pragma unroll
+  for (int i = 0; i < U; i++) {
+#pragma unroll (N <= 8 ? N : 4)
+    for (int j = 0; j < N; j++) {
+      SV s = SV(0);
+#pragma unroll
+      for (int k = 0; k < U; k++) s += Q[i * U + k] * SV(H[k * N + j]);
+      Gam[i * N + j] = L(-s);
+    }
+    SV s = SV(0);
+#pragma unroll
+    for (int k = 0; k < U; k++) s += Q[i * U + k] * (SV(Ge[k]) - SV(d[k]));
+    gam[i] = L(s);
+#pragma unroll
+    for (int j = 0; j < U; j++) Qi[i * U + j] = L(Q[i * U + j]);
+  }
+  // J and eta: the Bellman step
+  L Jn[N * N], HG[N * N], Fe[N], Hg[N];
+  mtm<N, N, N>(F, JF, Jn);
+  mtm<N, U, N>(H, Gam, HG);
+#pragma unroll (N <= 8 ? N * N : 4)
+  for (int i = 0; i < N * N; i++) Jn[i] += Pm[i] + HG[i];
+  symmetrize<N>(Jn);
+  mtv<N, N>(F, e.eta, Fe);
+  mtv<U, N>(H, gam, Hg);
+  // A, b, C: propagated through the closed loop F + G Gam of this step
+  L Fc[N * N], AG[N * U], An[N * N], AGg[N], AQ[N * U], Cn[N * N];
+  mm<N, U, N>(G, Gam, Fc);
+#pragma unroll (N <= 8 ? N * N : 4)
+  for (int i = 0; i < N * N; i++) Fc[i] += F[i];
+  mm<N, N, U>(e.A, G, AG);
+  mm<N, N, N>(e.A, Fc, An);
+  mv<N, U>(AG, gam, AGg);
+  mm<N, U, U>(AG, Qi, AQ);
+  mmt<N, U, N>(AQ, AG, Cn);
+#pragma unroll (N <= 8 ? N * N : 4)
+  for (int i = 0; i < N * N; i++) {
+    e.A[i] = An[i];
+    e.C[i] += Cn[i];
+    e.J[i] = Jn[i];
+  }
+  symmetrize<N>(e.C);
+#pragma unroll
+  for (int i = 0; i < N; i++) {
+    e.eta[i] = Fe[i] - Hg[i];
+    e.b[i] += AGg[i];
+  }
   return true;
 }
 

@@ -44,6 +44,7 @@ struct ProbS {
   int nw, integ, model, pad;
   double dt;
   const double *A, *B, *W;
+  const float *A32, *B32, *W32;
 };
 
 template <int N, int U>
@@ -70,6 +71,7 @@ __device__ void load_prob(ProbS<N, U>& S, const ProbDev& P, const double* xref_o
   if (threadIdx.x == 0) {
     S.nw = P.nw; S.integ = P.integrator; S.model = P.model; S.dt = dt_inst > 0.0 ? dt_inst : P.dt;
     S.A = P.A; S.B = P.B; S.W = P.W;
+    S.A32 = P.A32; S.B32 = P.B32; S.W32 = P.W32;
   }
   __syncthreads();
 }
@@ -95,16 +97,27 @@ struct ValueOpSel {
     else return ValueOp<SV>()(a, b, o);
   }
 };
+// value elements of the narrow tiers combine in row-parallel form across lane groups of
+// G >= N lanes where few combinations are on the critical path (ptn_group.cuh)
+template <class SV, int N, class L>
+struct GroupOp<ValueOpSel<SV>, Val<N, L>> {
+  static constexpr int G = N <= 2 ? 2 : (N <= 4 ? 4 : (N <= 8 ? 8 : 1));
+  __device__ static bool run(const ValueOpSel<SV>& op, const Val<N, L>& a, const Val<N, L>& b, Val<N, L>& o) {
+    if constexpr (G > 1) return value_combine_rows<SV, G, N, L>(a, b, o);
+    else return op(a, b, o);
+  }
+};
+
 template <int N, int U, class L, class SV>
-__device__ __noinline__ bool value_init_ni(const L* F, const L* G, const L* Pm, const L* Mm, const L* Rm,
+__device__ __noinline__ bool value_fold_ni(const L* F, const L* G, const L* Pm, const L* Mm, const L* Rm,
                                            const double* d, double alpha, Val<N, L>& e) {
-  return value_init<N, U, L, SV>(F, G, Pm, Mm, Rm, d, alpha, e);
+  return value_fold_step<N, U, L, SV>(F, G, Pm, Mm, Rm, d, alpha, e);
 }
 template <int N, int U, class L, class SV>
-__device__ __forceinline__ bool value_init_sel(const L* F, const L* G, const L* Pm, const L* Mm, const L* Rm,
+__device__ __forceinline__ bool value_fold_sel(const L* F, const L* G, const L* Pm, const L* Mm, const L* Rm,
                                                const double* d, double alpha, Val<N, L>& e) {
-  if constexpr (Big<N>::value) return value_init_ni<N, U, L, SV>(F, G, Pm, Mm, Rm, d, alpha, e);
-  else return value_init<N, U, L, SV>(F, G, Pm, Mm, Rm, d, alpha, e);
+  if constexpr (Big<N>::value) return value_fold_ni<N, U, L, SV>(F, G, Pm, Mm, Rm, d, alpha, e);
+  else return value_fold_step<N, U, L, SV>(F, G, Pm, Mm, Rm, d, alpha, e);
 }
 template <int N, int U, class L, class SV>
 __device__ __noinline__ bool riccati_step_ni(const L* F, const L* G, const L* Pm, const L* Mm, const L* Rm,
@@ -834,7 +847,7 @@ template <class M, class L, class SV, class Grp>
 __device__ bool value_pass(Grp& g, Inst<M, L>& I, double alpha, const double* qx = nullptr, L* Sv = nullptr,
                            L* sv = nullptr, bool group_ok = true) {
   constexpr int N = M::NX, U = M::NU;
-  bool ok = true, have = false;
+  bool ok = true;
   Val<N, L> agg;
   set_identity(agg);
   if (I.last) {
@@ -843,21 +856,22 @@ __device__ bool value_pass(Grp& g, Inst<M, L>& I, double alpha, const double* qx
 #pragma unroll
       for (int i = 0; i < N; i++) agg.eta[i] = L(-qx[(size_t)I.T * N + i]);
     }
-    have = true;
   }
-  // (a one-member group needs no chunk aggregate: its suffix is the terminal element)
+  // chunk aggregate: the steps' elements combined into it from the right, each in the
+  // Woodbury form of the combination (value_fold_step: one U x U solve per step instead
+  // of the element initialisation and an N x N inverse); the identity element starts a
+  // chunk that does not end the horizon.  A one-member group needs no chunk aggregate:
+  // its suffix is the terminal element.
   for (int t = I.b - 1; t >= I.a && g.size() > 1; t--) {
-    Val<N, L> e;
     L F[N * N];
     load_F<N>(I.E + (size_t)t * N * N, F);
-    ok &= value_init_sel<N, U, L, SV>(F, I.Gm + (size_t)t * N * U, I.Pm + (size_t)t * N * N,
-                                      I.Mm + (size_t)t * N * U, I.Rm + (size_t)t * U * U, I.d + (size_t)t * U, alpha, e);
+    ok &= value_fold_sel<N, U, L, SV>(F, I.Gm + (size_t)t * N * U, I.Pm + (size_t)t * N * N,
+                                      I.Mm + (size_t)t * N * U, I.Rm + (size_t)t * U * U, I.d + (size_t)t * U, alpha,
+                                      agg);
     if (qx) {
 #pragma unroll
-      for (int i = 0; i < N; i++) e.eta[i] -= L(qx[(size_t)t * N + i]);
+      for (int i = 0; i < N; i++) agg.eta[i] -= L(qx[(size_t)t * N + i]);
     }
-    if (!have) { agg = e; have = true; }
-    else ok &= ValueOpSel<SV>()(e, agg, agg);
   }
   Val<N, L> inc = g.scan(agg, ValueOpSel<SV>(), true, ok);
   L S[N * N], s[N];
@@ -1241,11 +1255,40 @@ __device__ double nominal_cost(Grp& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>&
 }
 
 // ---------------------------------------------------------------------------
+// Threads that share one chunk (the wide tier's warps: every lane runs the solver logic for
+// the warp's chunk): a read-modify-write of the chunk's entries visits entry i only from
+// thread first() + k step(), and max() combines those threads' partial maxima, so that each
+// entry is updated once.  One thread per chunk in the narrow tiers.
+template <class Grp>
+struct ChunkLanes {
+  __device__ static int first() { return 0; }
+  __device__ static int step() { return 1; }
+  __device__ static double max(double v) { return v; }
+};
+
 struct NStats {
   int iters, ls_rejects, factor_fails, roll_fails, roll_iters, ls_evals, exact_passes;
   double alpha;
   long long cyc[6];
 };
+
+// The update of Alg. 4 as printed, into the candidate arrays: x_c = x^ + dx, u_c = u^ + du
+// for this thread's (or warp's) chunk; x_0 is fixed (dx_0 = 0).
+template <class M, class L, class Grp>
+__device__ void literal_candidate(Grp& g, Inst<M, L>& I) {
+  constexpr int N = M::NX, U = M::NU;
+  using CL = ChunkLanes<Grp>;
+  for (int t = I.a; t < I.b; t++) {
+    for (int i = CL::first(); i < N; i += CL::step())
+      I.xc[(size_t)t * N + i] = I.xn[(size_t)t * N + i] + double(I.dx[(size_t)t * N + i]);
+    for (int i = CL::first(); i < U; i += CL::step())
+      I.uc[(size_t)t * U + i] = I.un[(size_t)t * U + i] + double(I.du[(size_t)t * U + i]);
+  }
+  if (I.last)
+    for (int i = CL::first(); i < N; i += CL::step())
+      I.xc[(size_t)I.T * N + i] = I.xn[(size_t)I.T * N + i] + double(I.dx[(size_t)I.T * N + i]);
+  g.sync();
+}
 
 // Groups whose passes are always exact (FP64 gradients, rollouts and merits whatever the
 // LQR precision); the Newton loop then skips the FP32-increment phase and its endgame.
@@ -1297,8 +1340,10 @@ __device__ int newton_solve(Grp& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>& P,
     if (g.dead()) return ST_ETIMEOUT;
     long long c0 = clock64();
     r = first_order(exact);
-    if (MIXED && !exact && (stalled || (final_level && (r <= O.polish * tol || it >= O.polish_after)))) {
-      // endgame: below the FP32 noise floor of gradients and merits, switch to FP64.
+    if (MIXED && !exact && (stalled || it >= O.polish_after || (final_level && r <= O.polish * tol))) {
+      // endgame: below the FP32 noise floor of gradients and merits, switch to FP64 (at
+      // the final level near its tolerance; at any level after polish_after iterations,
+      // where the level's tolerance may lie below that floor).
       // First re-project the nominal onto the FP64 dynamics (one exact rollout with
       // s = 0 under the last feedback), so that FP64 merits compare like with like.
       exact = true;
@@ -1360,18 +1405,34 @@ __device__ int newton_solve(Grp& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>& P,
     }
     bool accepted = false;
     double s = 1.0, Js = INFINITY, dJ = INFINITY;
-    for (int k = 0; k < O.ls_count; k++, s *= O.ls_beta) {
-      int ri = 0;
-      double m;
-      const bool okr = rollout(g, I, P, O, A, s, exact, &m, &ri, O.roll_max_iter) == ROLL_OK;
+    if (O.update_mode == 1) {
+      // Alg. 4 as printed: candidate x^ + dx, u^ + du (no rollout), taken whenever its FP64
+      // cost is finite; the linearised dynamics leave defects of second order
+      literal_candidate(g, I);
+      double* t1 = I.xn; I.xn = I.xc; I.xc = t1;
+      double* t2 = I.un; I.un = I.uc; I.uc = t2;
+      bool infl;
+      const double Jl = nominal_cost(g, I, P, A, &infl, nullptr);
+      t1 = I.xn; I.xn = I.xc; I.xc = t1;
+      t2 = I.un; I.un = I.uc; I.uc = t2;
       st.ls_evals++;
-      st.roll_iters += ri;
-      if (!okr) { st.roll_fails++; continue; }
-      const bool diff = MIXED && !exact;  // merits returned as FP32-accumulated differences
-      dJ = diff ? m : m - J0;
-      Js = diff ? J0 + m : m;
-      const double eps = diff ? O.armijo_eps32 : O.armijo_eps;
-      if (dJ <= O.armijo_c1 * s * G1 + eps * (1.0 + fabs(J0))) { accepted = true; break; }
+      accepted = !infl && isfinite(Jl);
+      Js = Jl;
+      dJ = Jl - J0;
+    } else {
+      for (int k = 0; k < O.ls_count; k++, s *= O.ls_beta) {
+        int ri = 0;
+        double m;
+        const bool okr = rollout(g, I, P, O, A, s, exact, &m, &ri, O.roll_max_iter) == ROLL_OK;
+        st.ls_evals++;
+        st.roll_iters += ri;
+        if (!okr) { st.roll_fails++; continue; }
+        const bool diff = MIXED && !exact;  // merits returned as FP32-accumulated differences
+        dJ = diff ? m : m - J0;
+        Js = diff ? J0 + m : m;
+        const double eps = diff ? O.armijo_eps32 : O.armijo_eps;
+        if (dJ <= O.armijo_c1 * s * G1 + eps * (1.0 + fabs(J0))) { accepted = true; break; }
+      }
     }
     st.cyc[4] += clock64() - c4;
     if (accepted) {
@@ -1387,12 +1448,11 @@ __device__ int newton_solve(Grp& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>& P,
         if (MULT) {
           // multipliers := the duals of the LQR's linearised dynamics (full dual step
           // whatever s); the next pass reads the neighbouring chunk's nu, hence the sync
+          using CL = ChunkLanes<Grp>;
           for (int t = I.a; t < I.b; t++)
-#pragma unroll
-            for (int i = 0; i < N; i++) I.lam[(size_t)t * N + i] += I.dnu[(size_t)t * N + i];
+            for (int i = CL::first(); i < N; i += CL::step()) I.lam[(size_t)t * N + i] += I.dnu[(size_t)t * N + i];
           if (I.last)
-#pragma unroll
-            for (int i = 0; i < N; i++) I.lam[(size_t)I.T * N + i] += I.dnu[(size_t)I.T * N + i];
+            for (int i = CL::first(); i < N; i += CL::step()) I.lam[(size_t)I.T * N + i] += I.dnu[(size_t)I.T * N + i];
           g.sync();
         }
       }
@@ -1932,9 +1992,10 @@ __device__ void solve_instance(Grp& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>&
       double r;
       const int s = newton_solve<M, L, SV>(g, I, P, O, A, O.tol_final, true, st, &r, &admm_exact);
       if (s == ST_ENUM || s == ST_ETIMEOUT) { rc = s; k++; break; }
+      using CL = ChunkLanes<Grp>;
       double lrp = 0.0, lrd = 0.0;
       for (int t = I.a; t < I.b; t++)
-        for (int rr = 0; rr < P.nw; rr++) {
+        for (int rr = CL::first(); rr < P.nw; rr += CL::step()) {
           const double zk = P.isx[rr] ? I.xn[(size_t)t * N + P.idx[rr]] : I.un[(size_t)t * U + P.idx[rr]];
           const double w = P.sgn[rr] * (zk - P.bnd[rr]);
           const size_t q = (size_t)t * P.nw + rr;
@@ -1945,7 +2006,7 @@ __device__ void solve_instance(Grp& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>&
           lrd = fmax(lrd, fabs(zn - I.z[q]));
           I.z[q] = zn;
         }
-      double red[2] = {lrp, lrd};
+      double red[2] = {CL::max(lrp), CL::max(lrd)};
       g.template reduce<2>(red, 3u);
       rp = red[0];
       rdl = red[1];
@@ -1991,9 +2052,10 @@ struct KArgs {
 
 template <int N, int U, class L>
 __host__ __device__ constexpr size_t scratch_bytes(int nwarps) {
-  // largest collective element (value element), nwarps + 2 slots, or 8 doubles per warp;
-  // a fused scan + reduction of state elements needs nwarps + 2 slots and 8 + 64 bytes
-  const size_t a = (size_t)(nwarps + 2) * sizeof(Val<N, L>);
+  // the value scan's group form (2 nwarps + 1 + nthreads / G elements and nthreads / G
+  // ints), or 8 doubles per warp; a fused scan + reduction of state elements needs
+  // nwarps + 2 slots and 8 + 64 bytes
+  const size_t a = scan_group_scratch<Val<N, L>, GroupOp<ValueOpSel<double>, Val<N, L>>::G>(32 * nwarps);
   const size_t b = (size_t)nwarps * 8 * 8;
   const size_t c = (size_t)(nwarps + 2) * sizeof(Aff<N, L>) + 72;
   return a > b ? (a > c ? a : c) : (b > c ? b : c);
@@ -2051,6 +2113,25 @@ __global__ void __launch_bounds__(256) k_adjoint_cta(KArgs args, Work<L> w, AdjA
   I.setup(w, id, args.x0 + (size_t)bi * N, threadIdx.x, blockDim.x, P.nw);
   const int rc = adjoint_instance<M, L, SV>(g, I, P, aa, id, bi);
   if (threadIdx.x == 0) args.info[bi].status = rc;
+}
+
+// adjoint of one instance on the cooperative grid (long horizons): the same passes on the
+// grid group; a barrier that expires reports ST_ETIMEOUT
+template <class M, class L, class SV>
+__global__ void __launch_bounds__(128) k_adjoint_grid(KArgs args, Work<L> w, AdjArgs aa) {
+  constexpr int N = M::NX, U = M::NU;
+  extern __shared__ __align__(16) char smem[];
+  ProbS<N, U>& P = *reinterpret_cast<ProbS<N, U>*>(smem);
+  char* scratch = smem + ((sizeof(ProbS<N, U>) + 15) & ~size_t(15));
+  __shared__ int sdead;
+  if (threadIdx.x == 0) sdead = 0;
+  load_prob<N, U>(P, *args.prob, args.xref, args.inst[0].dt);
+  const InstDev id = args.inst[0];
+  GridGroup g{scratch, args.gs, 0, &sdead};
+  Inst<M, L> I;
+  I.setup(w, id, args.x0, g.rank(), g.size(), P.nw);
+  const int rc = adjoint_instance<M, L, SV>(g, I, P, aa, id, 0);
+  if (g.rank() == 0) args.info[0].status = g.dead() ? ST_ETIMEOUT : rc;
 }
 
 // ---------------------------------------------------------------------------

@@ -16,23 +16,40 @@
 namespace ptn {
 
 // ---------------------------------------------------------------------------
-// group: rank = warp, size = number of warps of the CTA
+// group: one warp per time chunk.  One CTA per instance (rank = warp, size = warps of the
+// CTA), or, with grid set, every warp of a cooperative launch on one instance (rank =
+// blockIdx.x * warps per CTA + warp): barriers and reductions then also cross the CTAs
+// (bounded grid barrier, as GridGroup), and a scan ends with a Kogge-Stone over the CTA
+// totals in global memory (scan_grid).
 struct WideGroup {
   char* scr;         // per-warp scratch, warp w at scr + w * scr_bytes
   size_t scr_bytes;
-  char* xs;          // cross-warp scan slots: 2 buffers x nwarps x xs_bytes
+  char* xs;          // cross-warp scan slots: 2 buffers x nwarps x xs_bytes, then the carry slot
   size_t xs_bytes;
-  double* red;       // 8 doubles per warp
+  double* red;       // 8 doubles per warp, then 8 for the grid result
+  int grid;          // nonzero: the cooperative-grid form
+  GridScratch gs;    // grid form: barrier, reduction slots, 2 x nblocks CTA-total slots
+  int* sdead;        // grid form: shared flag, this CTA saw a barrier expire
+  int phase;
 
   __device__ int warp() const { return threadIdx.x >> 5; }
   __device__ int nwarps() const { return blockDim.x >> 5; }
-  __device__ int rank() const { return warp(); }
-  __device__ int size() const { return nwarps(); }
-  __device__ bool dead() const { return false; }
-  __device__ void sync() { __syncthreads(); }
+  __device__ int rank() const { return grid ? (int)blockIdx.x * nwarps() + warp() : warp(); }
+  __device__ int size() const { return grid ? (int)gridDim.x * nwarps() : nwarps(); }
+  __device__ bool dead() const { return grid && *(volatile int*)sdead != 0; }
+  __device__ void sync() {
+    __syncthreads();
+    if (grid) {
+      if (threadIdx.x == 0 && !*sdead) {
+        if (!grid_barrier(gs)) *sdead = 1;
+      }
+      __syncthreads();
+    }
+  }
 
   // every lane of a warp holds the warp's value; lane 0 contributes it.  Fixed order of
-  // combination, so every thread gets the same result.
+  // combination, so every thread gets the same result (in the grid form: warp 0 of each
+  // CTA folds the CTAs' values in the same order).
   template <int K>
   __device__ void reduce(double (&v)[K], unsigned maxmask) {
     static_assert(K <= 8, "at most 8 values per reduction");
@@ -48,16 +65,79 @@ struct WideGroup {
       for (int i = 1; i < nw; i++) a = ((maxmask >> k) & 1u) ? fmax(a, red[i * 8 + k]) : a + red[i * 8 + k];
       v[k] = a;
     }
+    if (!grid) return;
+    double* rs = gs.red + (size_t)phase * gridDim.x * 8;
+    if (threadIdx.x == 0)
+#pragma unroll
+      for (int k = 0; k < K; k++) rs[blockIdx.x * 8 + k] = v[k];
+    sync();
+    double* sres = red + 8 * nw;
+    if (threadIdx.x < 32) {
+      const int lane = threadIdx.x;
+      double a[K];
+#pragma unroll
+      for (int k = 0; k < K; k++) a[k] = ((maxmask >> k) & 1u) ? -INFINITY : 0.0;
+      for (int b = lane; b < (int)gridDim.x; b += 32)
+#pragma unroll
+        for (int k = 0; k < K; k++) {
+          const double o = __ldcg(rs + (size_t)b * 8 + k);
+          a[k] = ((maxmask >> k) & 1u) ? fmax(a[k], o) : a[k] + o;
+        }
+#pragma unroll
+      for (int off = 1; off < 32; off <<= 1)
+#pragma unroll
+        for (int k = 0; k < K; k++) {
+          const double o = __shfl_down_sync(0xffffffffu, a[k], off);
+          if ((lane & (2 * off - 1)) == 0) a[k] = ((maxmask >> k) & 1u) ? fmax(a[k], o) : a[k] + o;
+        }
+      if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < K; k++) sres[k] = a[k];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < K; k++) v[k] = sres[k];
+    __syncthreads();
+    phase ^= 1;
   }
+
+  // AND of a per-warp flag over the group (uniform result)
+  __device__ bool all(bool ok) {
+    double r[1] = {ok ? 0.0 : 1.0};
+    reduce<1>(r, 1u);
+    return r[0] == 0.0;
+  }
+
   template <class T>
   __device__ T* slot(int buf, int w) const {
     return reinterpret_cast<T*>(xs + ((size_t)buf * nwarps() + w) * xs_bytes);
+  }
+  // the carry of the grid form: everything after (suffix) or before (prefix) this CTA
+  template <class T>
+  __device__ T* carry_slot() const {
+    return reinterpret_cast<T*>(xs + (size_t)2 * nwarps() * xs_bytes);
+  }
+  // after a scan whose results are in buffer cur: the combination of all elements after
+  // (suffix) or before (prefix) this warp's chunk -- the neighbouring warp's inclusive
+  // result, or the CTA's carry at the CTA boundary (grid form).  Only for warps that have
+  // such elements (not the group's last chunk for a suffix, not its first for a prefix).
+  template <class T>
+  __device__ const T* neighbor(int cur, bool suffix) const {
+    const int w = warp(), nw = nwarps();
+    if (suffix) return w + 1 < nw ? slot<T>(cur, w + 1) : carry_slot<T>();
+    return w > 0 ? slot<T>(cur, w - 1) : carry_slot<T>();
   }
 };
 
 template <>
 struct multiplier_form_ok<WideGroup> {
-  static constexpr bool value = false;
+  static constexpr bool value = true;
+};
+template <>
+struct ChunkLanes<WideGroup> {
+  __device__ static int first() { return threadIdx.x & 31; }
+  __device__ static int step() { return 32; }
+  __device__ static double max(double v) { return wops::wmax(v); }
 };
 template <>
 struct exact_only<WideGroup> {
@@ -75,9 +155,8 @@ struct WScr {
   double x[N], u[U], xn[N], q[N], r[U], lam[N], v1[N], v2[N];
   double gr[2 * (N + U)];  // per constraint row terms
   double d[U];
-  Aff<N, double> ca;     // co-state aggregate of this warp's chunk
-  Val<N, L> e, agg, out;
-  Aff<N, L> sa, so;      // state aggregate and a combination output
+  double mdl[2 * N];     // model hooks' per-row terms
+  Aff<N, L> sa;          // the rollout's chunk map (scan aggregates live in the warp's scan slot)
   L T1[N * N], T2[N * N], T3[N * N];
   L X[U * C];
   L F[N * N], G[N * U], Pm[N * N], Mm[N * U], Rm[U * U];
@@ -90,6 +169,36 @@ template <class M, class L>
 __device__ __forceinline__ WScr<M, L>* wscr(const WideGroup& g) {
   return reinterpret_cast<WScr<M, L>*>(g.scr + (size_t)g.warp() * g.scr_bytes);
 }
+
+// Model terms of the wide passes, computed by the warp's lanes into shared memory: the
+// Jacobians F, G of the step, the lam-contracted second derivatives (lam^T f)_zz and the
+// FP64 step itself.  Models given by a continuous-time right-hand side use the lane-parallel
+// forward-mode AD of ptn_wops.cuh; a model written as a discrete map specialises this.
+// tmp: 2 N doubles of the warp's shared scratch.
+template <class M>
+struct WModel {
+  static constexpr int N = M::NX, U = M::NU;
+  static constexpr bool has_adjoint = true;
+  template <class S>
+  __device__ static void jac(const ProbS<N, U>& P, const double* x, const double* u, S* F, S* G, double* tmp) {
+    (void)tmp;
+    wops::step_jac<M, S>(P.integ, P.dt, P.prm, x, u, F, G);
+  }
+  template <class L>
+  __device__ static void hess(const ProbS<N, U>& P, const double* x, const double* u, const double* lam, L* Hxx,
+                              L* Hxu, L* Huu, double* tmp) {
+    (void)tmp;
+    wops::step_hess<M, L>(P.integ, P.dt, P.prm, x, u, lam, Hxx, Hxu, Huu);
+  }
+  // xn = f(x, u) in FP64 (x, u, xn in shared memory; xn must not alias x)
+  __device__ static void step(const ProbS<N, U>& P, const double* x, const double* u, double* xn, double* tmp) {
+    (void)tmp;
+    double v[N];
+    ptn::step<M>(P.integ, P.dt, P.prm, x, u, v);
+    for (int i = wops::lane_id(); i < N; i += 32) xn[i] = v[i];
+    __syncwarp();
+  }
+};
 
 namespace wide {
 
@@ -104,15 +213,15 @@ __device__ double stage_cost_w(const ProbS<N, U>& P, const Aug& A, int t, const 
                                bool& infeas, double* lplain) {
   const int l = lane_id();
   double v = 0.0;
-  if (l < N) {
-    double s = 0.0;
-    for (int j = 0; j < N; j++) s += P.Q[l * N + j] * (x[j] - P.xref[j]);
-    v = (x[l] - P.xref[l]) * s;
-  } else if (l < N + U) {
-    const int i = l - N;
-    double s = 0.0;
-    for (int j = 0; j < U; j++) s += P.R[i * U + j] * (u[j] - P.uref[j]);
-    v = (u[i] - P.uref[i]) * s;
+  for (int q = l; q < N + U; q += 32) {  // lane-strided: N + U may exceed 32
+    if (q < N) {
+      const double s = wops::dot4<N, double>([&](int j) { return P.Q[q * N + j] * (x[j] - P.xref[j]); });
+      v += (x[q] - P.xref[q]) * s;
+    } else {
+      const int i = q - N;
+      const double s = wops::dot4<U, double>([&](int j) { return P.R[i * U + j] * (u[j] - P.uref[j]); });
+      v += (u[i] - P.uref[i]) * s;
+    }
   }
   const double lp = wops::wsum(v);
   if (lplain) *lplain = lp;
@@ -138,8 +247,7 @@ __device__ double terminal_cost_w(const ProbS<N, U>& P, const double* x) {
   const int l = lane_id();
   double v = 0.0;
   if (l < N) {
-    double s = 0.0;
-    for (int j = 0; j < N; j++) s += P.Qf[l * N + j] * (x[j] - P.xref[j]);
+    const double s = wops::dot4<N, double>([&](int j) { return P.Qf[l * N + j] * (x[j] - P.xref[j]); });
     v = (x[l] - P.xref[l]) * s;
   }
   return wops::wsum(v);
@@ -158,19 +266,19 @@ __device__ void stage_grad_w(const ProbS<N, U>& P, const Aug& A, int t, const do
                                           P.sgn[r];
   }
   __syncwarp();
-  if (l < N) {
-    double s = 0.0;
-    for (int j = 0; j < N; j++) s += (P.Q[l * N + j] + P.Q[j * N + l]) * (x[j] - P.xref[j]);
-    for (int r = 0; r < P.nw; r++)
-      if (P.isx[r] && P.idx[r] == l) s += gr[r];
-    lx[l] = s;
-  } else if (l < N + U) {
-    const int i = l - N;
-    double s = 0.0;
-    for (int j = 0; j < U; j++) s += (P.R[i * U + j] + P.R[j * U + i]) * (u[j] - P.uref[j]);
-    for (int r = 0; r < P.nw; r++)
-      if (!P.isx[r] && P.idx[r] == i) s += gr[r];
-    lu[i] = s;
+  for (int q = l; q < N + U; q += 32) {
+    if (q < N) {
+      double s = wops::dot4<N, double>([&](int j) { return (P.Q[q * N + j] + P.Q[j * N + q]) * (x[j] - P.xref[j]); });
+      for (int r = 0; r < P.nw; r++)
+        if (P.isx[r] && P.idx[r] == q) s += gr[r];
+      lx[q] = s;
+    } else {
+      const int i = q - N;
+      double s = wops::dot4<U, double>([&](int j) { return (P.R[i * U + j] + P.R[j * U + i]) * (u[j] - P.uref[j]); });
+      for (int r = 0; r < P.nw; r++)
+        if (!P.isx[r] && P.idx[r] == i) s += gr[r];
+      lu[i] = s;
+    }
   }
   __syncwarp();
 }
@@ -178,11 +286,8 @@ __device__ void stage_grad_w(const ProbS<N, U>& P, const Aug& A, int t, const do
 template <int N, int U>
 __device__ void terminal_grad_w(const ProbS<N, U>& P, const double* xT, double* g) {
   const int l = lane_id();
-  if (l < N) {
-    double s = 0.0;
-    for (int j = 0; j < N; j++) s += (P.Qf[l * N + j] + P.Qf[j * N + l]) * (xT[j] - P.xref[j]);
-    g[l] = s;
-  }
+  if (l < N)
+    g[l] = wops::dot4<N, double>([&](int j) { return (P.Qf[l * N + j] + P.Qf[j * N + l]) * (xT[j] - P.xref[j]); });
   __syncwarp();
 }
 
@@ -313,53 +418,6 @@ __device__ bool val_combine(const Val<M::NX, L>* e1, const Val<M::NX, L>* e2, Va
   return true;
 }
 
-// element initialisation (P^-1-free form, as value_init) from the step data in s->F, G,
-// Pm, Mm, Rm, d; into e.  R~ = R + alpha I factorised in SV.
-template <class SV, class M, class L>
-__device__ bool val_init(WScr<M, L>* s, double alpha, Val<M::NX, L>* e) {
-  constexpr int N = M::NX, U = M::NU, C = 2 * N + 1;
-  const int l = lane_id();
-  SV Rt[U * U];
-#pragma unroll
-  for (int i = 0; i < U * U; i++) Rt[i] = SV(s->Rm[i]);
-#pragma unroll
-  for (int i = 0; i < U; i++) Rt[i * U + i] += SV(alpha);
-  if (!ldlt<U, SV>(Rt)) return false;
-  for (int q = l; q < U * C; q += 32) {
-    const int i = q / C, c = q % C;
-    s->X[q] = c < N ? s->Mm[c * U + i] : (c < 2 * N ? s->G[(c - N) * U + i] : L(s->d[i]));
-  }
-  __syncwarp();
-  wops::ldlt_solve_cols<U, C, SV>(Rt, s->X);
-  for (int q = l; q < N * N; q += 32) {
-    const int i = q / N, j = q % N;
-    L gm = L(0), mx = L(0), gg = L(0);
-#pragma unroll
-    for (int k = 0; k < U; k++) {
-      gm += s->G[i * U + k] * s->X[k * C + j];
-      mx += s->Mm[i * U + k] * s->X[k * C + j];
-      gg += s->G[i * U + k] * s->X[k * C + N + j];
-    }
-    e->A[q] = s->F[q] - gm;
-    e->J[q] = s->Pm[q] - mx;
-    e->C[q] = gg;
-  }
-  for (int i = l; i < N; i += 32) {
-    L et = L(0), bb = L(0);
-#pragma unroll
-    for (int k = 0; k < U; k++) {
-      et += s->Mm[i * U + k] * s->X[k * C + 2 * N];
-      bb += s->G[i * U + k] * s->X[k * C + 2 * N];
-    }
-    e->eta[i] = et;
-    e->b[i] = -bb;
-  }
-  __syncwarp();
-  wops::symmetrize<N>(e->J);
-  wops::symmetrize<N>(e->C);
-  return true;
-}
-
 // one feedback step from V_{t+1} = (s->S, s->s) with the step data in s->F, G, Pm, Mm,
 // Rm, d (as riccati_step); writes s->Gam, s->gam and updates S, s in place.
 template <class SV, class M, class L>
@@ -375,10 +433,10 @@ __device__ bool riccati_w(WScr<M, L>* s, double alpha) {
     const int i = q / C, j = q % C;
     L v = L(0);
     if (j < N) {
-      for (int k = 0; k < N; k++) v += s->G[k * U + i] * SF[k * N + j];
+      v += wops::dot4<N, L>([&](int k) { return s->G[k * U + i] * SF[k * N + j]; });
       v += s->Mm[j * U + i];
     } else {
-      for (int k = 0; k < N; k++) v += s->G[k * U + i] * s->s[k];
+      v += wops::dot4<N, L>([&](int k) { return s->G[k * U + i] * s->s[k]; });
       v += L(s->d[i]);
     }
     s->X[q] = v;
@@ -408,16 +466,16 @@ __device__ bool riccati_w(WScr<M, L>* s, double alpha) {
   for (int q = l; q < N * N; q += 32) {
     const int i = q / N, j = q % N;
     L v = s->Pm[q];
-    for (int k = 0; k < N; k++) v += s->F[k * N + i] * SF[k * N + j];
+    v += wops::dot4<N, L>([&](int k) { return s->F[k * N + i] * SF[k * N + j]; });
 #pragma unroll
-    for (int k = 0; k < U; k++) v += Qux[k * N + i] * s->Gam[k * N + j];
+    v += wops::dot4<U, L>([&](int k) { return Qux[k * N + i] * s->Gam[k * N + j]; });
     Sn[q] = v;
   }
   for (int i = l; i < N; i += 32) {
     L v = L(0);
-    for (int k = 0; k < N; k++) v += s->F[k * N + i] * s->s[k];
+    v += wops::dot4<N, L>([&](int k) { return s->F[k * N + i] * s->s[k]; });
 #pragma unroll
-    for (int k = 0; k < U; k++) v += Qux[k * N + i] * s->gam[k];
+    v += wops::dot4<U, L>([&](int k) { return Qux[k * N + i] * s->gam[k]; });
     s->w1[i] = v;
   }
   __syncwarp();
@@ -427,8 +485,139 @@ __device__ bool riccati_w(WScr<M, L>* s, double alpha) {
   return true;
 }
 
-// inclusive scan across warps of the elements in slot(0, w) of g; op(earlier, later,
-// out, scratch).  Returns the buffer holding the results; ok is AND-ed with op's result.
+// step t (data in s->F, G, Pm, Mm, Rm, d) combined into the later element e, in place, in
+// the Woodbury form of the value combination (as value_fold_step): with
+// Q = R~ + G^T J G (U x U, inverted in SV with pivoting), H = M^T + G^T J F,
+// Gam = -Q^{-1} H and gam = Q^{-1} (G^T eta - d),
+//   J <- P + F^T J F + H^T Gam,  eta <- F^T eta - H^T gam,  A <- A (F + G Gam),
+//   b <- b + (A G) gam,  C <- C + (A G) Q^{-1} (A G)^T.
+// Returns false (warp-uniform) when Q is singular.
+template <class SV, class M, class L>
+__device__ bool val_fold_w(WScr<M, L>* s, double alpha, Val<M::NX, L>* e, L* tmpA) {
+  constexpr int N = M::NX, U = M::NU, C = N + 1;
+  static_assert(U * C <= U * (2 * N + 1) && N * U <= N * N, "scratch sizes");
+  const int l = lane_id();
+  L* JF = s->T1;  // N x N
+  L* JG = s->T2;  // N x U
+  wops::mm<N, N, N, false, false>(e->J, s->F, JF);
+  wops::mm<N, N, U, false, false>(e->J, s->G, JG);
+  // X[:, :N] = H = G^T J F + M^T,  X[:, N] = G^T eta - d;  Q = R~ + G^T J G
+  SV* Q = reinterpret_cast<SV*>(s->K);
+  for (int q = l; q < U * C; q += 32) {
+    const int i = q / C, j = q % C;
+    L v = L(0);
+    if (j < N) {
+      v += wops::dot4<N, L>([&](int k) { return s->G[k * U + i] * JF[k * N + j]; });
+      v += s->Mm[j * U + i];
+    } else {
+      v += wops::dot4<N, L>([&](int k) { return s->G[k * U + i] * e->eta[k]; });
+      v -= L(s->d[i]);
+    }
+    s->X[q] = v;
+  }
+  for (int q = l; q < U * U; q += 32) {
+    const int i = q / U, j = q % U;
+    L gjg = L(0);
+    gjg += wops::dot4<N, L>([&](int k) { return s->G[k * U + i] * JG[k * U + j]; });
+    Q[q] = SV(s->Rm[q]) + SV(gjg) + (i == j ? SV(alpha) : SV(0));
+  }
+  __syncwarp();
+  if (!wops::inv<U, SV>(Q, s->piv, reinterpret_cast<SV*>(s->col))) return false;
+  // Gam = -Q^{-1} H, gam = Q^{-1} (G^T eta - d); H kept in T3 for the Bellman step
+  L* H = s->T3;
+  for (int q = l; q < U * C; q += 32) {
+    const int i = q / C, j = q % C;
+    SV v = SV(0);
+#pragma unroll
+    v += wops::dot4<U, SV>([&](int k) { return Q[i * U + k] * SV(s->X[k * C + j]); });
+    if (j < N) {
+      s->Gam[i * N + j] = L(-v);
+      H[i * N + j] = s->X[q];
+    } else {
+      s->gam[i] = L(v);
+    }
+  }
+  __syncwarp();
+  // J' (into T2) and eta' (into w1) from the J, eta of e
+  L* Jn = s->T2;
+  for (int q = l; q < N * N; q += 32) {
+    const int i = q / N, j = q % N;
+    L v = s->Pm[q];
+    v += wops::dot4<N, L>([&](int k) { return s->F[k * N + i] * JF[k * N + j]; });
+#pragma unroll
+    v += wops::dot4<U, L>([&](int k) { return H[k * N + i] * s->Gam[k * N + j]; });
+    Jn[q] = v;
+  }
+  for (int i = l; i < N; i += 32) {
+    L v = L(0);
+    v += wops::dot4<N, L>([&](int k) { return s->F[k * N + i] * e->eta[k]; });
+#pragma unroll
+    for (int k = 0; k < U; k++) v -= H[k * N + i] * s->gam[k];
+    s->w1[i] = v;
+  }
+  __syncwarp();
+  // closed loop F + G Gam (into T1: J F is no longer needed); A G (into X)
+  L* Fc = s->T1;
+  L* AG = s->X;
+  for (int q = l; q < N * N; q += 32) {
+    const int i = q / N, j = q % N;
+    L v = s->F[q];
+#pragma unroll
+    v += wops::dot4<U, L>([&](int k) { return s->G[i * U + k] * s->Gam[k * N + j]; });
+    Fc[q] = v;
+  }
+  wops::mm<N, N, U, false, false>(e->A, s->G, AG);
+  // A' = A (F + G Gam) into tmpA; (A G) Q^{-1} into T3 (H is no longer needed)
+  wops::mm<N, N, N, false, false>(e->A, Fc, tmpA);
+  L* AQ = s->T3;
+  for (int q = l; q < N * U; q += 32) {
+    const int i = q / U, j = q % U;
+    SV v = SV(0);
+#pragma unroll
+    v += wops::dot4<U, SV>([&](int k) { return SV(AG[i * U + k]) * Q[k * U + j]; });
+    AQ[q] = L(v);
+  }
+  __syncwarp();
+  for (int q = l; q < N * N; q += 32) {
+    const int i = q / N, j = q % N;
+    L v = e->C[q];
+#pragma unroll
+    v += wops::dot4<U, L>([&](int k) { return AQ[i * U + k] * AG[j * U + k]; });
+    e->C[q] = v;
+    e->A[q] = tmpA[q];
+    e->J[q] = Jn[q];
+  }
+  for (int i = l; i < N; i += 32) {
+    L v = e->b[i];
+#pragma unroll
+    v += wops::dot4<U, L>([&](int k) { return AG[i * U + k] * s->gam[k]; });
+    e->b[i] = v;
+    e->eta[i] = s->w1[i];
+  }
+  __syncwarp();
+  wops::symmetrize<N>(e->C);
+  wops::symmetrize<N>(e->J);
+  return true;
+}
+
+// copy of one element through L2 (__ldcg: another CTA wrote it before a grid barrier, and
+// L1 is not coherent across SMs), lane-parallel
+template <class E>
+__device__ void copy_cg(const E* src, E* dst) {
+  const unsigned* s4 = reinterpret_cast<const unsigned*>(src);
+  unsigned* d4 = reinterpret_cast<unsigned*>(dst);
+  for (int i = lane_id(); i < (int)(sizeof(E) / 4); i += 32) d4[i] = __ldcg(s4 + i);
+  __syncwarp();
+}
+
+// inclusive scan across warps of the elements in slot(0, w) of g; op(earlier, later, out)
+// on element pointers.  Returns the buffer holding the results (read them through
+// g.neighbor); ok is AND-ed with op's results.  Grid form: the CTA totals (the inclusive
+// result of the CTA's first warp for a suffix, of its last for a prefix) are scanned across
+// the CTAs by a Kogge-Stone in global memory, double-buffered, one combination by warp 0 of
+// each CTA per level behind grid barriers, with its operands staged in shared memory; then
+// every warp combines its result with its CTA's carry (the inclusive result of the next,
+// or the previous, CTA), into the other buffer.
 template <class E, class Op>
 __device__ int scan_warps(WideGroup& g, const Op& op, bool suffix, bool& ok) {
   const int w = g.warp(), nw = g.nwarps();
@@ -448,6 +637,41 @@ __device__ int scan_warps(WideGroup& g, const Op& op, bool suffix, bool& ok) {
     __syncthreads();
     cur ^= 1;
   }
+  if (!g.grid) return cur;
+  const int nb = gridDim.x, b = blockIdx.x;
+  auto gslot = [&](int buf, int i) {
+    return reinterpret_cast<E*>(g.gs.xs + ((size_t)buf * nb + i) * g.gs.elem_bytes);
+  };
+  if (w == 0) wops::copy<sizeof(E) / sizeof(unsigned)>(reinterpret_cast<const unsigned*>(g.slot<E>(cur, suffix ? 0 : nw - 1)),
+                                                        reinterpret_cast<unsigned*>(gslot(0, b)));
+  int gc = 0;
+  g.sync();
+  E* sa = g.slot<E>(cur ^ 1, 0);  // staging (free until the carry is applied)
+  E* sb = g.carry_slot<E>();
+  for (int off = 1; off < nb; off <<= 1) {
+    const int o = suffix ? b + off : b - off;
+    if (w == 0) {
+      if (o >= 0 && o < nb) {
+        copy_cg(gslot(gc, suffix ? b : o), sa);
+        copy_cg(gslot(gc, suffix ? o : b), sb);
+        ok &= op(sa, sb, gslot(gc ^ 1, b));
+      } else {
+        copy_cg(gslot(gc, b), gslot(gc ^ 1, b));
+      }
+    }
+    g.sync();
+    gc ^= 1;
+  }
+  const int cb = suffix ? b + 1 : b - 1;
+  if (cb >= 0 && cb < nb) {
+    if (w == 0) copy_cg(gslot(gc, cb), sb);
+    __syncthreads();
+    E* mine = g.slot<E>(cur, w);
+    E* dst = g.slot<E>(cur ^ 1, w);
+    ok &= suffix ? op(mine, sb, dst) : op(sb, mine, dst);
+    cur ^= 1;
+  }
+  __syncthreads();
   return cur;
 }
 
@@ -467,7 +691,7 @@ __device__ double costate_pass(WideGroup& g, Inst<M, L>& I, const ProbS<M::NX, M
   constexpr int N = M::NX, U = M::NU;
   WScr<M, L>* s = wscr<M, L>(g);
   const int l = wide::lane_id();
-  Aff<N, double>* agg = &s->ca;
+  Aff<N, double>* agg = g.slot<Aff<N, double>>(0, g.warp());  // the chunk aggregate, built in the scan slot
   wide::aff_identity<N>(agg, false);
   if (I.last) {
     wide::terminal_grad_w<N, U>(P, I.xn + (size_t)I.T * N, s->lam);
@@ -478,7 +702,7 @@ __device__ double costate_pass(WideGroup& g, Inst<M, L>& I, const ProbS<M::NX, M
   for (int t = I.b - 1; t >= I.a; t--) {
     const double* x = I.xn + (size_t)t * N;
     const double* u = I.un + (size_t)t * U;
-    wops::step_jac<M, double>(P.integ, P.dt, P.prm, x, u, s->F64, s->G64);
+    WModel<M>::jac(P, x, u, s->F64, s->G64, s->mdl);
     for (int e = l; e < N * N; e += 32) {
       const double E = s->F64[e] - ((e / N == e % N) ? 1.0 : 0.0);
       I.F64[(size_t)t * N * N + e] = E;
@@ -500,7 +724,6 @@ __device__ double costate_pass(WideGroup& g, Inst<M, L>& I, const ProbS<M::NX, M
     }
   }
   // exclusive suffix scan across warps
-  wide::aff_copy<N>(agg, g.slot<Aff<N, double>>(0, g.warp()));
   bool ok = true;
   auto op = [&](const Aff<N, double>* a, const Aff<N, double>* b, Aff<N, double>* o) {
     wide::costate_combine<N>(a, b, o);
@@ -509,7 +732,7 @@ __device__ double costate_pass(WideGroup& g, Inst<M, L>& I, const ProbS<M::NX, M
   const int cur = wide::scan_warps<Aff<N, double>>(g, op, true, ok);
   double* lam = s->lam;
   if (!I.last) {
-    const Aff<N, double>* nx = g.slot<Aff<N, double>>(cur, g.warp() + 1);
+    const Aff<N, double>* nx = g.neighbor<Aff<N, double>>(cur, true);
     for (int i = l; i < N; i += 32) lam[i] = nx->v[i];
   }
   __syncwarp();
@@ -527,7 +750,7 @@ __device__ double costate_pass(WideGroup& g, Inst<M, L>& I, const ProbS<M::NX, M
     double dl = 0.0;
     if (l < U) {
       double v = s->r[l];
-      for (int k = 0; k < N; k++) v += G[k * U + l] * lam[k];
+      v += wops::dot4<N, double>([&](int k) { return G[k * U + l] * lam[k]; });
       I.d[(size_t)t * U + l] = v;
       dl = fabs(v);
       dl = isfinite(dl) ? dl : INFINITY;
@@ -550,6 +773,167 @@ __device__ double costate_pass(WideGroup& g, Inst<M, L>& I, const ProbS<M::NX, M
   return red[0];
 }
 
+// pass 1, multiplier form (costate_mode 1, 2; the variant of multiplier_pass in the narrow
+// tiers): multipliers nu of the dynamics in I.lam, local gradients
+//   d_t = dl/du + G_t^T nu_{t+1},   q_t = dl/dx + F_t^T nu_{t+1} - nu_t   (t >= 1),
+//   q_T = dl_T/dx - nu_T,   nu_0 := dl/dx + F_0^T nu_1 with q_0 = 0,
+// lane-parallel, FP64 Jacobians stored as the co-state pass stores them.  Returns
+// max(max |d|, max |q|) over the group.
+template <class M, class L>
+__device__ double multiplier_pass(WideGroup& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>& P, const Aug& A) {
+  constexpr int N = M::NX, U = M::NU;
+  WScr<M, L>* s = wscr<M, L>(g);
+  const int l = wide::lane_id();
+  double rl = 0.0;
+  for (int t = I.a; t < I.b; t++) {
+    const double* x = I.xn + (size_t)t * N;
+    const double* u = I.un + (size_t)t * U;
+    WModel<M>::jac(P, x, u, s->F64, s->G64, s->mdl);
+    for (int e = l; e < N * N; e += 32) {
+      const double E = s->F64[e] - ((e / N == e % N) ? 1.0 : 0.0);
+      I.F64[(size_t)t * N * N + e] = E;
+      I.E[(size_t)t * N * N + e] = L(E);
+    }
+    for (int e = l; e < N * U; e += 32) {
+      I.G64[(size_t)t * N * U + e] = s->G64[e];
+      I.Gm[(size_t)t * N * U + e] = L(s->G64[e]);
+    }
+    wide::stage_grad_w<N, U>(P, A, t, x, u, s->q, s->r, s->gr);
+    const double* nv = I.lam + (size_t)(t + 1) * N;
+    for (int i = l; i < U; i += 32) {
+      double v = s->r[i];
+      v += wops::dot4<N, double>([&](int k) { return s->G64[k * U + i] * nv[k]; });
+      I.d[(size_t)t * U + i] = v;
+      rl = fmax(rl, isfinite(v) ? fabs(v) : INFINITY);
+    }
+    for (int i = l; i < N; i += 32) {
+      double v = s->q[i];
+      v += wops::dot4<N, double>([&](int k) { return s->F64[k * N + i] * nv[k]; });
+      if (t == 0) {
+        I.lam[i] = v;
+        I.q[i] = 0.0;
+      } else {
+        v -= I.lam[(size_t)t * N + i];
+        I.q[(size_t)t * N + i] = v;
+        rl = fmax(rl, isfinite(v) ? fabs(v) : INFINITY);
+      }
+    }
+    __syncwarp();
+  }
+  if (I.last) {
+    wide::terminal_grad_w<N, U>(P, I.xn + (size_t)I.T * N, s->lam);
+    for (int i = l; i < N; i += 32) {
+      const double v = s->lam[i] - I.lam[(size_t)I.T * N + i];
+      I.q[(size_t)I.T * N + i] = v;
+      rl = fmax(rl, isfinite(v) ? fabs(v) : INFINITY);
+    }
+    __syncwarp();
+  }
+  if (I.a < I.b)
+    for (int i = 0; i < N; i++) I.lamb[i] = I.lam[(size_t)I.b * N + i];
+  double red[1] = {wops::wmax(rl)};
+  g.template reduce<1>(red, 1u);
+  return red[0];
+}
+
+// the FP32-increment multiplier pass of the narrow tiers is not used here (exact_only)
+template <class M>
+__device__ double multiplier_mixed(WideGroup& g, Inst<M, float>& I, const ProbS<M::NX, M::NU>& P, const Aug& A) {
+  return multiplier_pass(g, I, P, A);
+}
+
+// cost of the nominal (as nominal_cost), lane-parallel stage terms
+template <class M, class L>
+__device__ double nominal_cost(WideGroup& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>& P, const Aug& A, bool* infeas,
+                               double* Jplain) {
+  constexpr int N = M::NX, U = M::NU;
+  double c = 0.0, cp = 0.0;
+  bool inf = false;
+  for (int t = I.a; t < I.b; t++) {
+    double lp;
+    c += wide::stage_cost_w<N, U>(P, A, t, I.xn + (size_t)t * N, I.un + (size_t)t * U, inf, &lp);
+    cp += lp;
+  }
+  if (I.last) {
+    const double lt = wide::terminal_cost_w<N, U>(P, I.xn + (size_t)I.T * N);
+    c += lt;
+    cp += lt;
+  }
+  double red[3] = {c, cp, inf ? 1.0 : 0.0};
+  g.template reduce<3>(red, 4u);
+  if (infeas) *infeas = red[2] > 0.0;
+  if (Jplain) *Jplain = red[1];
+  return red[0];
+}
+
+// final residuals (as residuals), the dynamics defects with the lane-parallel step
+template <class M, class L>
+__device__ void residuals(WideGroup& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>& P, const Aug& A, InfoDev& info,
+                          bool mult = false) {
+  constexpr int N = M::NX, U = M::NU;
+  WScr<M, L>* s = wscr<M, L>(g);
+  const int l = wide::lane_id();
+  info.r_stat = mult ? multiplier_pass(g, I, P, A) : costate_pass(g, I, P, A, true);
+  double rd = 0.0, rf = -INFINITY;
+  for (int t = I.a; t < I.b; t++) {
+    for (int i = l; i < N; i += 32) s->x[i] = I.xn[(size_t)t * N + i];
+    for (int i = l; i < U; i += 32) s->u[i] = I.un[(size_t)t * U + i];
+    __syncwarp();
+    WModel<M>::step(P, s->x, s->u, s->xn, s->mdl);
+    for (int i = l; i < N; i += 32) {
+      const double e = fabs(I.xn[(size_t)(t + 1) * N + i] - s->xn[i]);
+      rd = (e <= rd) ? rd : (isfinite(e) ? e : INFINITY);
+    }
+    for (int r = l; r < P.nw; r += 32) {
+      const double zk = P.isx[r] ? s->x[P.idx[r]] : s->u[P.idx[r]];
+      rf = fmax(rf, P.sgn[r] * (zk - P.bnd[r]));
+    }
+    __syncwarp();
+  }
+  double red[2] = {wops::wmax(rd), wops::wmax(rf)};
+  g.template reduce<2>(red, 3u);
+  info.r_dyn = red[0];
+  info.r_feas = fmax(red[1], 0.0);
+  bool inf;
+  double Jp;
+  info.J_c = nominal_cost(g, I, P, A, &inf, &Jp);
+  info.J = Jp;
+}
+
+// initial nominal x = rollout(x0, u_init) (open loop, FP64), integrated by the first warp
+// of the group with the lane-parallel step (the multiple-shooting form of the narrow tiers
+// is not used here)
+template <class M, class L>
+__device__ void initial_rollout(WideGroup& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>& P) {
+  constexpr int N = M::NX, U = M::NU;
+  if (g.rank() == 0) {
+    WScr<M, L>* s = wscr<M, L>(g);
+    const int l = wide::lane_id();
+    for (int i = l; i < N; i += 32) {
+      s->x[i] = I.x0[i];
+      I.xn[i] = I.x0[i];
+    }
+    __syncwarp();
+    for (int t = 0; t < I.T; t++) {
+      for (int i = l; i < U; i += 32) s->u[i] = I.un[(size_t)t * U + i];
+      __syncwarp();
+      WModel<M>::step(P, s->x, s->u, s->xn, s->mdl);
+      for (int i = l; i < N; i += 32) {
+        s->x[i] = s->xn[i];
+        I.xn[(size_t)(t + 1) * N + i] = s->xn[i];
+      }
+      __syncwarp();
+    }
+  }
+  g.sync();
+}
+template <class M, class L>
+__device__ bool initial_rollout_parallel(WideGroup& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>& P, const OptDev& O,
+                                         int* iters) {
+  (void)g; (void)I; (void)P; (void)O; (void)iters;
+  return false;
+}
+
 // pass 2: second-order expansion (Sec. III-C); Hessian contractions in L by lane-parallel
 // hyper-dual numbers, stage Hessians in FP64 added and rounded to L.
 template <class M, class L>
@@ -561,7 +945,7 @@ __device__ void quadratize(WideGroup& g, Inst<M, L>& I, const ProbS<M::NX, M::NU
     const double* x = I.xn + (size_t)t * N;
     const double* u = I.un + (size_t)t * U;
     const double* lam1 = (t + 1 == I.b) ? I.lamb : I.lam + (size_t)(t + 1) * N;
-    wops::step_hess<M, L>(P.integ, P.dt, P.prm, x, u, lam1, s->Pm, s->Mm, s->Rm);
+    WModel<M>::hess(P, x, u, lam1, s->Pm, s->Mm, s->Rm, s->mdl);
     wide::stage_hess_add_w<N, U, L>(P, A, x, u, s->Pm, s->Rm, s->gr);
     for (int e = l; e < N * N; e += 32) I.Pm[(size_t)t * N * N + e] = s->Pm[e];
     for (int e = l; e < N * U; e += 32) I.Mm[(size_t)t * N * U + e] = s->Mm[e];
@@ -592,14 +976,18 @@ __device__ void load_step(Inst<M, L>& I, WScr<M, L>* s, int t) {
   __syncwarp();
 }
 
-// pass 3: value suffix scan (Alg. 2) + feedback sweep
+// pass 3: value suffix scan (Alg. 2) + feedback sweep.  qx: linear state terms of the LQR
+// (adjoint, multiplier form); Sv, sv receive S_t, s_t (multiplier form); group_ok = false
+// returns the warp's flag without the group reduction (as value_pass of the narrow tiers).
 template <class M, class L, class SV>
-__device__ bool value_pass(WideGroup& g, Inst<M, L>& I, double alpha, const double* qx = nullptr) {
+__device__ bool value_pass(WideGroup& g, Inst<M, L>& I, double alpha, const double* qx = nullptr, L* Sv = nullptr,
+                           L* sv = nullptr, bool group_ok = true) {
   constexpr int N = M::NX, U = M::NU;
   WScr<M, L>* s = wscr<M, L>(g);
   const int l = wide::lane_id();
-  bool ok = true, have = false;
-  Val<N, L>* agg = &s->agg;
+  bool ok = true;
+  Val<N, L>* agg = g.slot<Val<N, L>>(0, g.warp());  // the chunk aggregate, built in the scan slot
+  L* tmpA = g.slot<Val<N, L>>(1, g.warp())->A;       // free until the scan
   wide::val_identity<N>(agg);
   if (I.last) {
     for (int e = l; e < N * N; e += 32) {
@@ -612,31 +1000,29 @@ __device__ bool value_pass(WideGroup& g, Inst<M, L>& I, double alpha, const doub
       agg->b[i] = L(0);
     }
     __syncwarp();
-    have = true;
   }
+  // the warp's chunk: each step's element combined into the aggregate from the right in
+  // the Woodbury form (one U x U inverse per step instead of the element initialisation
+  // and an N x N inverse); the identity element starts a chunk that does not end the horizon
   for (int t = I.b - 1; t >= I.a; t--) {
     load_step(I, s, t);
-    ok &= wide::val_init<SV>(s, alpha, &s->e);
+    ok &= wide::val_fold_w<SV>(s, alpha, agg, tmpA);
     if (qx) {
-      for (int i = l; i < N; i += 32) s->e.eta[i] -= L(qx[(size_t)t * N + i]);
+      for (int i = l; i < N; i += 32) agg->eta[i] -= L(qx[(size_t)t * N + i]);
       __syncwarp();
     }
-    if (!have) {
-      wide::val_copy<N>(&s->e, agg);
-      have = true;
-    } else {
-      ok &= wide::val_combine<SV>(&s->e, agg, &s->out, s);
-      wide::val_copy<N>(&s->out, agg);
-    }
   }
-  wide::val_copy<N>(agg, g.slot<Val<N, L>>(0, g.warp()));
   auto op = [&](const Val<N, L>* a, const Val<N, L>* b, Val<N, L>* o) { return wide::val_combine<SV>(a, b, o, s); };
   const int cur = wide::scan_warps<Val<N, L>>(g, op, true, ok);
   if (I.last) {
     for (int e = l; e < N * N; e += 32) s->S[e] = I.Pm[(size_t)I.T * N * N + e];
     for (int i = l; i < N; i += 32) s->s[i] = qx ? L(qx[(size_t)I.T * N + i]) : L(0);
+    if (Sv) {
+      for (int e = l; e < N * N; e += 32) Sv[(size_t)I.T * N * N + e] = s->S[e];
+      for (int i = l; i < N; i += 32) sv[(size_t)I.T * N + i] = s->s[i];
+    }
   } else {
-    const Val<N, L>* nx = g.slot<Val<N, L>>(cur, g.warp() + 1);
+    const Val<N, L>* nx = g.neighbor<Val<N, L>>(cur, true);
     for (int e = l; e < N * N; e += 32) s->S[e] = nx->J[e];
     for (int i = l; i < N; i += 32) s->s[i] = -nx->eta[i];
   }
@@ -647,21 +1033,31 @@ __device__ bool value_pass(WideGroup& g, Inst<M, L>& I, double alpha, const doub
     if (qx) {
       for (int i = l; i < N; i += 32) s->s[i] += L(qx[(size_t)t * N + i]);
     }
+    __syncwarp();
+    if (Sv) {
+      for (int e = l; e < N * N; e += 32) Sv[(size_t)t * N * N + e] = s->S[e];
+      for (int i = l; i < N; i += 32) sv[(size_t)t * N + i] = s->s[i];
+    }
     for (int e = l; e < U * N; e += 32) I.Gam[(size_t)t * U * N + e] = s->Gam[e];
     for (int i = l; i < U; i += 32) I.gam[(size_t)t * U + i] = s->gam[i];
     __syncwarp();
   }
-  return wide::wall(ok);
+  if (!group_ok) return ok;
+  return g.all(ok);
 }
 
-// pass 4: state prefix scan (Alg. 3) and the model terms G1, G2
+// pass 4: state prefix scan (Alg. 3) and the model terms G1, G2.  Multiplier form (qx, Sv,
+// sv, dnu given): G1 also carries sum_t q_t^T dx_t and dnu_t = S_t dx_t + s_t is the dual
+// step (as state_pass of the narrow tiers).  fail: a per-warp flag reduced by maximum with
+// G1, G2; on return the group's flag.
 template <class M, class L>
-__device__ void state_pass(WideGroup& g, Inst<M, L>& I, double& G1, double& G2) {
+__device__ void state_pass(WideGroup& g, Inst<M, L>& I, double& G1, double& G2, const double* qx = nullptr,
+                           const L* Sv = nullptr, const L* sv = nullptr, double* dnu = nullptr, double* fail = nullptr) {
   constexpr int N = M::NX, U = M::NU;
   WScr<M, L>* s = wscr<M, L>(g);
   const int l = wide::lane_id();
   const bool first = (I.a == 0);
-  Aff<N, L>* agg = &s->sa;
+  Aff<N, L>* agg = g.slot<Aff<N, L>>(0, g.warp());  // the chunk aggregate, built in the scan slot
   wide::aff_identity<N>(agg, first);  // the first element has F = 0
   for (int t = I.a; t < I.b; t++) {
     load_step(I, s, t);
@@ -681,7 +1077,6 @@ __device__ void state_pass(WideGroup& g, Inst<M, L>& I, double& G1, double& G2) 
       wops::copy<N * N>(s->T2, agg->M);
     }
   }
-  wide::aff_copy<N>(agg, g.slot<Aff<N, L>>(0, g.warp()));
   bool ok = true;
   auto op = [&](const Aff<N, L>* a, const Aff<N, L>* b, Aff<N, L>* o) {
     wide::state_combine<N>(a, b, o);
@@ -692,7 +1087,7 @@ __device__ void state_pass(WideGroup& g, Inst<M, L>& I, double& G1, double& G2) 
   if (first) {
     for (int i = l; i < N; i += 32) dx[i] = L(0);
   } else {
-    const Aff<N, L>* pv = g.slot<Aff<N, L>>(cur, g.warp() - 1);
+    const Aff<N, L>* pv = g.neighbor<Aff<N, L>>(cur, false);
     for (int i = l; i < N; i += 32) dx[i] = pv->v[i];
   }
   __syncwarp();
@@ -713,16 +1108,27 @@ __device__ void state_pass(WideGroup& g, Inst<M, L>& I, double& G1, double& G2) 
     // model terms
     double a1 = 0.0, a2 = 0.0;
     if (l < U) a1 = s->d[l] * double(s->wu[l]);
-    if (l < N) {
-      L pd = L(0), md = L(0);
-      for (int k = 0; k < N; k++) pd += s->Pm[l * N + k] * dx[k];
-      for (int k = 0; k < U; k++) md += s->Mm[l * U + k] * s->wu[k];
-      a2 += double(dx[l] * (L(0.5) * pd + md));
-    } else if (l < N + U) {
-      const int i = l - N;
-      L rd = L(0);
-      for (int k = 0; k < U; k++) rd += s->Rm[i * U + k] * s->wu[k];
-      a2 += double(L(0.5) * s->wu[i] * rd);
+    for (int q = l; q < N + U; q += 32) {
+      if (q < N) {
+        L pd = L(0), md = L(0);
+        for (int k = 0; k < N; k++) pd += s->Pm[q * N + k] * dx[k];
+        for (int k = 0; k < U; k++) md += s->Mm[q * U + k] * s->wu[k];
+        a2 += double(dx[q] * (L(0.5) * pd + md));
+      } else {
+        const int i = q - N;
+        L rd = L(0);
+        for (int k = 0; k < U; k++) rd += s->Rm[i * U + k] * s->wu[k];
+        a2 += double(L(0.5) * s->wu[i] * rd);
+      }
+    }
+    if (qx) {
+      // multiplier form: q_t^T dx_t in G1 and the dual step S_t dx_t + s_t
+      for (int i = l; i < N; i += 32) {
+        a1 += qx[(size_t)t * N + i] * double(dx[i]);
+        double v = double(sv[(size_t)t * N + i]);
+        v += wops::dot4<N, double>([&](int j) { return double(Sv[(size_t)t * N * N + i * N + j]) * double(dx[j]); });
+        dnu[(size_t)t * N + i] = v;
+      }
     }
     g1 += wops::wsum(a1);
     g2 += wops::wsum(a2);
@@ -732,15 +1138,30 @@ __device__ void state_pass(WideGroup& g, Inst<M, L>& I, double& G1, double& G2) 
     wops::copy<N>(s->w1, dx);
   }
   if (I.last) {
-    double a2 = 0.0;
+    double a1 = 0.0, a2 = 0.0;
     if (l < N) {
       L pd = L(0);
       for (int k = 0; k < N; k++) pd += I.Pm[(size_t)I.T * N * N + l * N + k] * dx[k];
       a2 = double(L(0.5) * dx[l] * pd);
       I.dx[(size_t)I.T * N + l] = dx[l];
+      if (qx) {
+        a1 = qx[(size_t)I.T * N + l] * double(dx[l]);
+        double v = double(sv[(size_t)I.T * N + l]);
+        v += wops::dot4<N, double>([&](int j) { return double(Sv[(size_t)I.T * N * N + l * N + j]) * double(dx[j]); });
+        dnu[(size_t)I.T * N + l] = v;
+      }
     }
+    g1 += wops::wsum(a1);
     g2 += wops::wsum(a2);
     __syncwarp();
+  }
+  if (fail) {
+    double red[3] = {g1, g2, *fail};
+    g.template reduce<3>(red, 4u);
+    G1 = red[0];
+    G2 = red[1];
+    *fail = red[2];
+    return;
   }
   double red[2] = {g1, g2};
   g.template reduce<2>(red, 0u);
@@ -785,7 +1206,7 @@ __device__ int rollout(WideGroup& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>& P
       const double* uh = I.un + (size_t)t * U;
       if (l < U) {
         double v = uh[l] + sstep * double(I.gam[(size_t)t * U + l]);
-        for (int j = 0; j < N; j++) v += double(Gam[l * N + j]) * (xt[j] - xh[j]);
+        v += wops::dot4<N, double>([&](int j) { return double(Gam[l * N + j]) * (xt[j] - xh[j]); });
         ut[l] = v;
         I.uc[(size_t)t * U + l] = v;
       }
@@ -793,10 +1214,9 @@ __device__ int rollout(WideGroup& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>& P
         for (int i = l; i < N; i += 32) I.xc[(size_t)t * N + i] = xt[i];
       __syncwarp();
       cost += wide::stage_cost_w<N, U>(P, A, t, xt, ut, inf, nullptr);
-      // FP64 step (every lane) and the closed-loop Jacobian F + G Gam in L
-      double xnext[N];
-      step<M>(P.integ, P.dt, P.prm, xt, ut, xnext);
-      wops::step_jac<M, L>(P.integ, P.dt, P.prm, xt, ut, s->F, s->G);
+      // FP64 step (into s->xn) and the closed-loop Jacobian F + G Gam in L
+      WModel<M>::step(P, xt, ut, s->xn, s->mdl);
+      WModel<M>::jac(P, xt, ut, s->F, s->G, s->mdl);
       for (int q = l; q < U * N; q += 32) s->Gam[q] = Gam[q];
       __syncwarp();
       wops::mm<N, U, N, false, false>(s->G, s->Gam, s->T1);
@@ -806,7 +1226,7 @@ __device__ int rollout(WideGroup& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>& P
         wops::mm<N, N, N, false, false>(s->T1, el->M, s->T2);
         wops::copy<N * N>(s->T2, el->M);
       }
-      for (int i = l; i < N; i += 32) xt[i] = xnext[i];
+      for (int i = l; i < N; i += 32) xt[i] = s->xn[i];
       __syncwarp();
     }
     double rmax = 0.0, xmax = 0.0;
@@ -861,7 +1281,7 @@ __device__ int rollout(WideGroup& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>& P
       if (first) {
         for (int i = l; i < N; i += 32) dv[i] = L(0);
       } else {
-        const Aff<N, L>* pv = g.slot<Aff<N, L>>(cur, g.warp() - 1);
+        const Aff<N, L>* pv = g.neighbor<Aff<N, L>>(cur, false);
         for (int i = l; i < N; i += 32) dv[i] = pv->v[i];
       }
       __syncwarp();
@@ -879,23 +1299,52 @@ __device__ int rollout(WideGroup& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>& P
 }
 
 // ---------------------------------------------------------------------------
-// one CTA per instance, one warp per chunk
-template <class M, class L, class SV>
-__global__ void __launch_bounds__(512) k_solve_wide(KArgs args, Work<L> w) {
+// shared memory of a wide CTA: problem record, reduction slots (8 doubles per warp and 8
+// for the grid), per-warp scratch, scan slots (2 buffers per warp and the carry slot)
+template <class M, class L>
+__host__ __device__ constexpr size_t wide_slot_bytes() {
+  constexpr int N = M::NX;
+  constexpr size_t xb = sizeof(Val<N, L>) > sizeof(Aff<N, double>) ? sizeof(Val<N, L>) : sizeof(Aff<N, double>);
+  return (xb + 15) & ~size_t(15);
+}
+template <class M, class L>
+__host__ __device__ constexpr size_t wide_smem_bytes(int nwarps) {
   constexpr int N = M::NX, U = M::NU;
-  extern __shared__ __align__(16) char smem[];
-  ProbS<N, U>& P = *reinterpret_cast<ProbS<N, U>*>(smem);
+  return ((sizeof(ProbS<N, U>) + 15) & ~size_t(15)) + (size_t)8 * 8 * (nwarps + 1) +
+         ((sizeof(WScr<M, L>) + 15) & ~size_t(15)) * nwarps + (size_t)(2 * nwarps + 1) * wide_slot_bytes<M, L>();
+}
+
+// largest CTA of the wide kernels of model M (their launch bound); a model whose warp
+// scratch allows few warps per CTA lowers it, which leaves more registers per thread
+template <class M>
+struct WideMaxThreads {
+  static constexpr int value = 256;  // the largest block_threads the options allow
+};
+
+template <class M, class L>
+__device__ void wide_layout(WideGroup& g, char* smem) {
+  constexpr int N = M::NX, U = M::NU;
   size_t off = (sizeof(ProbS<N, U>) + 15) & ~size_t(15);
   const int nw = blockDim.x >> 5;
-  WideGroup g;
   g.red = reinterpret_cast<double*>(smem + off);
-  off += (size_t)8 * 8 * nw;
+  off += (size_t)8 * 8 * (nw + 1);
   g.scr_bytes = (sizeof(WScr<M, L>) + 15) & ~size_t(15);
   g.scr = smem + off;
   off += g.scr_bytes * nw;
-  constexpr size_t xb = sizeof(Val<N, L>) > sizeof(Aff<N, double>) ? sizeof(Val<N, L>) : sizeof(Aff<N, double>);
-  g.xs_bytes = (xb + 15) & ~size_t(15);
+  g.xs_bytes = wide_slot_bytes<M, L>();
   g.xs = smem + off;
+}
+
+// one CTA per instance, one warp per chunk
+template <class M, class L, class SV>
+__global__ void __launch_bounds__(WideMaxThreads<M>::value) k_solve_wide(KArgs args, Work<L> w) {
+  constexpr int N = M::NX, U = M::NU;
+  extern __shared__ __align__(16) char smem[];
+  ProbS<N, U>& P = *reinterpret_cast<ProbS<N, U>*>(smem);
+  const int nw = blockDim.x >> 5;
+  WideGroup g{};
+  wide_layout<M, L>(g, smem);
+  g.grid = 0;
   const int bi = blockIdx.x;
   if (bi >= args.B) return;
   load_prob<N, U>(P, *args.prob, args.xref ? args.xref + (size_t)bi * N : nullptr, args.inst[bi].dt);
@@ -906,12 +1355,26 @@ __global__ void __launch_bounds__(512) k_solve_wide(KArgs args, Work<L> w) {
   solve_instance<M, L, SV>(g, I, P, O, args.u_init ? args.u_init + (size_t)id.uoff * U : nullptr, args.info + bi);
 }
 
-template <class M, class L>
-constexpr size_t wide_smem_bytes(int nwarps) {
+// one instance on every warp of a cooperative grid (long horizons)
+template <class M, class L, class SV>
+__global__ void __launch_bounds__(WideMaxThreads<M>::value) k_solve_wide_grid(KArgs args, Work<L> w) {
   constexpr int N = M::NX, U = M::NU;
-  constexpr size_t xb = sizeof(Val<N, L>) > sizeof(Aff<N, double>) ? sizeof(Val<N, L>) : sizeof(Aff<N, double>);
-  return ((sizeof(ProbS<N, U>) + 15) & ~size_t(15)) + (size_t)8 * 8 * nwarps +
-         ((sizeof(WScr<M, L>) + 15) & ~size_t(15)) * nwarps + 2 * ((xb + 15) & ~size_t(15)) * nwarps;
+  extern __shared__ __align__(16) char smem[];
+  ProbS<N, U>& P = *reinterpret_cast<ProbS<N, U>*>(smem);
+  __shared__ int sdead;
+  if (threadIdx.x == 0) sdead = 0;
+  WideGroup g{};
+  wide_layout<M, L>(g, smem);
+  g.grid = 1;
+  g.gs = args.gs;
+  g.sdead = &sdead;
+  g.phase = 0;
+  load_prob<N, U>(P, *args.prob, args.xref, args.inst[0].dt);
+  const OptDev& O = *args.opt;
+  const InstDev id = args.inst[0];
+  Inst<M, L> I;
+  I.setup(w, id, args.x0, g.rank(), g.size(), P.nw);
+  solve_instance<M, L, SV>(g, I, P, O, args.u_init, args.info);
 }
 
 // ---------------------------------------------------------------------------
@@ -956,6 +1419,7 @@ template <class M>
 __device__ int adjoint_wide(WideGroup& g, Inst<M, double>& I, const ProbS<M::NX, M::NU>& P, const AdjArgs& aa,
                             const InstDev& id, int bi) {
   constexpr int N = M::NX, U = M::NU, NP = M::NP, KO = 3 * N + U + NP;
+  static_assert(N + U <= 32, "the wide adjoint keeps one state or control component per lane");
   using L = double;
   WScr<M, L>* s = wscr<M, L>(g);
   const int l = wide::lane_id();
@@ -1010,17 +1474,17 @@ __device__ int adjoint_wide(WideGroup& g, Inst<M, double>& I, const ProbS<M::NX,
         const double* Pt = I.Pm + (size_t)t * N * N;
         const double* w = I.dx + (size_t)t * N;
         double v = qx[(size_t)t * N + l];
-        for (int j = 0; j < N; j++) v += Pt[l * N + j] * w[j];
+        v += wops::dot4<N, double>([&](int j) { return Pt[l * N + j] * w[j]; });
         if (t < I.T) {
           const double* Mt = I.Mm + (size_t)t * N * U;
           const double* wu = I.du + (size_t)t * U;
-          for (int j = 0; j < U; j++) v += Mt[l * U + j] * wu[j];
+          v += wops::dot4<U, double>([&](int j) { return Mt[l * U + j] * wu[j]; });
         }
         c[l] = v;
       }
       __syncwarp();
     };
-    Aff<N, double>* agg = &s->ca;
+    Aff<N, double>* agg = g.slot<Aff<N, double>>(0, g.warp());  // built in the scan slot
     wide::aff_identity<N>(agg, false);
     if (I.last) {
       cterm(I.T, s->v1);
@@ -1042,7 +1506,6 @@ __device__ int adjoint_wide(WideGroup& g, Inst<M, double>& I, const ProbS<M::NX,
         __syncwarp();
       }
     }
-    wide::aff_copy<N>(agg, g.slot<Aff<N, double>>(0, g.warp()));
     bool ok = true;
     auto op = [&](const Aff<N, double>* a, const Aff<N, double>* b, Aff<N, double>* o) {
       wide::costate_combine<N>(a, b, o);
@@ -1053,7 +1516,7 @@ __device__ int adjoint_wide(WideGroup& g, Inst<M, double>& I, const ProbS<M::NX,
     if (I.last) {
       cterm(I.T, nu);
     } else {
-      const Aff<N, double>* nx = g.slot<Aff<N, double>>(cur, g.warp() + 1);
+      const Aff<N, double>* nx = g.neighbor<Aff<N, double>>(cur, true);
       for (int i = l; i < N; i += 32) nu[i] = nx->v[i];
       __syncwarp();
     }
@@ -1159,18 +1622,10 @@ __global__ void __launch_bounds__(512) k_adjoint_wide(KArgs args, Work<double> w
   constexpr int N = M::NX, U = M::NU;
   extern __shared__ __align__(16) char smem[];
   ProbS<N, U>& P = *reinterpret_cast<ProbS<N, U>*>(smem);
-  size_t off = (sizeof(ProbS<N, U>) + 15) & ~size_t(15);
   const int nw = blockDim.x >> 5;
-  WideGroup g;
-  g.red = reinterpret_cast<double*>(smem + off);
-  off += (size_t)8 * 8 * nw;
-  g.scr_bytes = (sizeof(WScr<M, double>) + 15) & ~size_t(15);
-  g.scr = smem + off;
-  off += g.scr_bytes * nw;
-  constexpr size_t xb =
-      sizeof(Val<N, double>) > sizeof(Aff<N, double>) ? sizeof(Val<N, double>) : sizeof(Aff<N, double>);
-  g.xs_bytes = (xb + 15) & ~size_t(15);
-  g.xs = smem + off;
+  WideGroup g{};
+  wide_layout<M, double>(g, smem);
+  g.grid = 0;
   const int bi = blockIdx.x;
   if (bi >= args.B) return;
   load_prob<N, U>(P, *args.prob, args.xref ? args.xref + (size_t)bi * N : nullptr, args.inst[bi].dt);
@@ -1181,15 +1636,28 @@ __global__ void __launch_bounds__(512) k_adjoint_wide(KArgs args, Work<double> w
   if (threadIdx.x == 0) args.info[bi].status = rc;
 }
 
-// host-side launch of the wide kernel (tier ignored except queries and the adjoint, which
-// this tier does not have)
+// host-side launch of the wide kernels: tier 6 is one instance on the cooperative grid,
+// tier 3 the adjoint (one CTA per instance), every other tier one CTA per instance.
+// Queries: 1, the largest co-resident grid (tier 6) or 0; 2, set the function attributes;
+// 4, the largest number of threads per CTA whose shared memory fits (into *max_blocks).
 template <class M, class L, class SV>
 cudaError_t launch_wide(LaunchReq& q) {
-  constexpr int N = M::NX;
-  if (q.elem_bytes) *q.elem_bytes = sizeof(Val<N, L>) > sizeof(Aff<N, double>) ? sizeof(Val<N, L>) : sizeof(Aff<N, double>);
+  if (q.elem_bytes) *q.elem_bytes = wide_slot_bytes<M, L>();
+  int dev = 0, smax = 0;
+  if (q.query == 4 || q.query == 1) {
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smax, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+  }
+  if (q.query == 4) {
+    int nw = WideMaxThreads<M>::value / 32;
+    while (nw > 1 && wide_smem_bytes<M, L>(nw) > (size_t)smax) nw--;
+    *q.max_blocks = wide_smem_bytes<M, L>(nw) <= (size_t)smax ? 32 * nw : 0;
+    return cudaSuccess;
+  }
   if (q.tier == 3) {
     // the adjoint runs with FP64 LQR data (built only in the FP64 unit)
-    if constexpr (std::is_same<L, double>::value) {
+    if constexpr (std::is_same<L, double>::value && WModel<M>::has_adjoint) {
       if (q.query) return cudaSuccess;
       const int nw = q.nthreads / 32;
       const size_t smem = wide_smem_bytes<M, double>(nw);
@@ -1201,12 +1669,39 @@ cudaError_t launch_wide(LaunchReq& q) {
       return cudaErrorNotSupported;
     }
   }
+  const int nw = q.nthreads / 32;
+  const size_t smem = wide_smem_bytes<M, L>(nw);
+  if (q.tier == 6) {
+    if (!q.attrs_set) {
+      cudaError_t e = raise_smem_limit<k_solve_wide_grid<M, L, SV>>(smem);
+      if (e != cudaSuccess) return e;
+    }
+    if (q.query == 2) return cudaSuccess;
+    if (q.query == 1) {
+      int per = 0, sms = 0;
+      cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_solve_wide_grid<M, L, SV>,
+                                                                              q.nthreads, smem);
+      if (e != cudaSuccess) return e;
+      *q.max_blocks = per * sms;
+      return cudaSuccess;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(q.nblocks);
+    cfg.blockDim = dim3(q.nthreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = q.stream;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_solve_wide_grid<M, L, SV>, q.args, typed<L>(q.w));
+  }
   if (q.query == 1) {
     if (q.max_blocks) *q.max_blocks = 0;
     return cudaSuccess;
   }
-  const int nw = q.nthreads / 32;
-  const size_t smem = wide_smem_bytes<M, L>(nw);
   if (!q.attrs_set) {
     cudaError_t e = raise_smem_limit<k_solve_wide<M, L, SV>>(smem);
     if (e != cudaSuccess) return e;

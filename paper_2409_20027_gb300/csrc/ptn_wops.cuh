@@ -15,20 +15,34 @@ namespace wops {
 
 __device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
 
+// sum over k < K of term(k), in four independent partial sums: with one warp per SM
+// sub-partition nothing else hides the latency of a dependent chain of multiply-adds, so
+// each lane keeps four of them in flight
+template <int K, class S, class Term>
+__device__ __forceinline__ S dot4(const Term& term) {
+  S s0 = S(0), s1 = S(0), s2 = S(0), s3 = S(0);
+#pragma unroll
+  for (int k = 0; k + 3 < K; k += 4) {
+    s0 += term(k);
+    s1 += term(k + 1);
+    s2 += term(k + 2);
+    s3 += term(k + 3);
+  }
+#pragma unroll
+  for (int k = K & ~3; k < K; k++) s0 += term(k);
+  return (s0 + s1) + (s2 + s3);
+}
+
 // C (R x Cc) = op(A) (R x K) * op(B) (K x Cc) [+ C if ACC]; op = transpose when TA / TB.
 // Accumulation in the type of C.
 template <int R, int K, int Cc, bool TA, bool TB, bool ACC = false, class SA, class SB, class SC>
 __device__ void mm(const SA* A, const SB* B, SC* C) {
   for (int e = lane_id(); e < R * Cc; e += 32) {
     const int i = e / Cc, j = e % Cc;
-    SC s = ACC ? C[e] : SC(0);
-#pragma unroll 4
-    for (int k = 0; k < K; k++) {
-      const SC a = SC(TA ? A[k * R + i] : A[i * K + k]);
-      const SC b = SC(TB ? B[j * K + k] : B[k * Cc + j]);
-      s += a * b;
-    }
-    C[e] = s;
+    const SC s = dot4<K, SC>([&](int k) {
+      return SC(TA ? A[k * R + i] : A[i * K + k]) * SC(TB ? B[j * K + k] : B[k * Cc + j]);
+    });
+    C[e] = ACC ? C[e] + s : s;
   }
   __syncwarp();
 }
@@ -37,10 +51,8 @@ __device__ void mm(const SA* A, const SB* B, SC* C) {
 template <int R, int K, bool TA, bool ACC = false, class SA, class SX, class SY>
 __device__ void mv(const SA* A, const SX* x, SY* y) {
   for (int i = lane_id(); i < R; i += 32) {
-    SY s = ACC ? y[i] : SY(0);
-#pragma unroll 4
-    for (int k = 0; k < K; k++) s += SY(TA ? A[k * R + i] : A[i * K + k]) * SY(x[k]);
-    y[i] = s;
+    const SY s = dot4<K, SY>([&](int k) { return SY(TA ? A[k * R + i] : A[i * K + k]) * SY(x[k]); });
+    y[i] = ACC ? y[i] + s : s;
   }
   __syncwarp();
 }

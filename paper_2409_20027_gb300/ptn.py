@@ -40,7 +40,7 @@ class Problem(C.Structure):
 
 _OPT_INTS = ["precision", "max_newton", "max_outer", "ls_count", "admm_fixed_iters", "roll_max_iter",
              "block_threads", "grid_min_T", "grid_steps_per_thread", "polish_after",
-             "cluster_max_blocks", "sequential", "costate_mode"]
+             "cluster_max_blocks", "sequential", "costate_mode", "update_mode"]
 _OPT_DBLS = ["mu0", "zeta", "mu_final", "tol_inner", "tol_final", "rho", "admm_tol", "alpha0",
              "alpha_min", "alpha_max", "ls_beta", "armijo_c1", "armijo_eps", "roll_tol", "polish",
              "armijo_eps32"]

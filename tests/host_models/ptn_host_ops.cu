@@ -7,6 +7,8 @@
 //   S  state combine (Alg. 3):    F1(16) e1(4) F2(16) e2(4)
 //   R  Riccati step with feedback: F(16) G(4) P(16) M(4) R(1) d(1) alpha S(16) s(4)
 //      -> Gam(4) gam(1) S_t(16) s_t(4)
+//   W  step folded into a later element (Woodbury form of the value combination):
+//      F(16) G(4) P(16) M(4) R(1) d(1) alpha e(56: A b C eta J) -> the combined element
 //   K  pivot keys: x -> mag_key(double x) mag_key(float x)
 //   G  FP64 Gauss-Jordan inverse with partial pivoting: A(16) -> A^{-1}(16)
 //   L  LDL^T factorisation and solve: A(16, symmetric) B(4 x 3) -> X = A^{-1} B (12)
@@ -74,6 +76,20 @@ static bool value_init_op(const double* in) {
 }
 
 template <class L>
+static bool value_fold_op(const double* in) {
+  L F[16], G[4], P[16], M[4], R[1];
+  for (int i = 0; i < 16; i++) { F[i] = L(in[i]); P[i] = L(in[20 + i]); }
+  for (int i = 0; i < 4; i++) { G[i] = L(in[16 + i]); M[i] = L(in[36 + i]); }
+  R[0] = L(in[40]);
+  const double d[1] = {in[41]};
+  Val<N, L> e;
+  put_val(in + 43, e);
+  if (!value_fold_step<N, U, L, double>(F, G, P, M, R, d, in[42], e)) return false;
+  print_val(e);
+  return true;
+}
+
+template <class L>
 static bool riccati_op(const double* in) {
   L F[16], G[4], P[16], M[4], R[1], S[16], sv[4], Gam[4], gam[1];
   for (int i = 0; i < 16; i++) { F[i] = L(in[i]); P[i] = L(in[20 + i]); S[i] = L(in[43 + i]); }
@@ -102,6 +118,9 @@ int main() {
     } else if (op[0] == 'I') {
       if (!rd(in, 43)) return 1;
       ok = prec ? value_init_op<float>(in) : value_init_op<double>(in);
+    } else if (op[0] == 'W') {
+      if (!rd(in, 99)) return 1;
+      ok = prec ? value_fold_op<float>(in) : value_fold_op<double>(in);
     } else if (op[0] == 'R') {
       if (!rd(in, 63)) return 1;
       ok = prec ? riccati_op<float>(in) : riccati_op<double>(in);

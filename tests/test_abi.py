@@ -67,7 +67,7 @@ def test_entry_points_refuse_null_handles_and_pointers_without_a_gpu():
     nx, nu = ctypes.c_int(), ctypes.c_int()
     assert lib.ptn_model_dims(1, ctypes.byref(nx), ctypes.byref(nu)) == 0 and (nx.value, nu.value) == (4, 1)
     assert lib.ptn_model_dims(1, None, None) == INVALID
-    assert lib.ptn_model_dims(3, ctypes.byref(nx), ctypes.byref(nu)) == INVALID  # no GPU kernels for it
+    assert lib.ptn_model_dims(3, ctypes.byref(nx), ctypes.byref(nu)) == 0 and (nx.value, nu.value) == (32, 8)
     assert lib.ptn_model_dims(999, ctypes.byref(nx), ctypes.byref(nu)) == INVALID
     tb = (ctypes.c_int * 1)(8)
     assert lib.ptn_batch_prepare(None, 0, 1, tb, None, None) == INVALID

@@ -98,3 +98,31 @@ def test_autograd_wrapper(ptn):
         xo += T + 1
         uo += T
     assert rel(theta.grad.cpu().numpy(), gth) <= 1e-6
+
+
+@pytest.mark.parametrize("with_traj", [False, True], ids=["J_only", "J_and_traj"])
+def test_grid_adjoint_long_horizon_matches_oracle(ptn, with_traj):
+    # one long instance (cart-pole, T = 4096 on the 2.56 s horizon): the adjoint on the
+    # cooperative grid against the one-CTA adjoint at the same solution and against the
+    # oracle's adjoint, in every output, with J* alone and with trajectory gradients too
+    T = 4096
+    p = W.cartpole(T=T, horizon=2.56)
+    s = ptn.Solver(p, max_T=T, precision=0, grid_min_T=512, cluster_max_blocks=0)
+    x0 = dev(W.cartpole_x0(3)).reshape(1, -1)
+    x, u, _, infos = s.solve_batch(x0, [T])
+    assert infos[0]["status"] == 0
+    mu = infos[0]["mu"]
+    rng = np.random.default_rng(13)
+    gx = rng.standard_normal((T + 1, 4)) if with_traj else None
+    gu = rng.standard_normal((T, 1)) if with_traj else None
+    gJ = 0.7
+    args = ([T], x0, x, u, mu, gJ, None if gx is None else dev(gx), None if gu is None else dev(gu))
+    grid = s.adjoint(*args)
+    s.set_options(grid_min_T=0)
+    cta = s.adjoint(*args)
+    ref = O.adjoint(p, mu, x.cpu().numpy(), u.cpu().numpy(), gJ, gx, gu)
+    assert ref["status"] == 0
+    for k in KEYS:
+        g, c = grid[k][0].cpu().numpy(), cta[k][0].cpu().numpy()
+        assert rel(g, ref[k]) <= 1e-6, (k, g, ref[k])
+        assert rel(g, c) <= 1e-9, (k, g, c)

@@ -16,7 +16,7 @@ reduced Hessian: at T = 16384 a solve stopped at max|d| <= 1e-7 pins u only to a
 1e-7 / (2 R dt / 0.01) ~ 3e-4.  The oracle's quadratic endgame lands far below its
 tolerance (its u moves by 6e-8 between tolerances 1e-7 and 1e-9), the FP32 path's linear
 endgame (FP32 LQR directions) stops just below it; the FP32 side of that case is therefore
-solved to 1e-9.
+solved to 1e-8 (u pinned to about 3e-5).
 """
 import os
 
@@ -69,7 +69,7 @@ def test_cartpole_headline_shape_fp32_matches_oracle(ptn):
     T = 16384
     p = W.cartpole(T=T, horizon=2.56)
     x0 = W.cartpole_x0(0)
-    s = ptn.Solver(p, max_T=T, precision=ptn.PTN_FP32_FP64SOLVE, tol_final=1e-9)
+    s = ptn.Solver(p, max_T=T, precision=ptn.PTN_FP32_FP64SOLVE, tol_final=1e-8, max_newton=1000)
     launch = autotune.apply(s, autotune.load(os.path.join(ROOT, "paper_2409_20027_gb300", "tuned_gb300.json")), T)
     # the benchmark's tier and shape: T >= grid_min_T with more CTAs than a cluster holds
     per = s.options.block_threads * s.options.grid_steps_per_thread

@@ -175,16 +175,22 @@ def test_static_entry_point_is_the_handle_solve(ptn):
     assert torch.equal(x, xs) and torch.equal(u, us) and torch.equal(lam, ls)
 
 
-def test_wide_tier_rejects_the_multiplier_form(ptn):
-    # not built for nx >= 8: the handle and the static entry point both refuse it
-    p = W.quadrotor()
-    T = 16
-    s = ptn.Solver(p, max_T=T, precision=ptn.PTN_FP64, costate_mode=1)
-    u0 = dev(np.full((T, 4), W.quadrotor_hover_u()))
-    s.solve_ip(dev(np.zeros(12)), T, u_init=u0)
-    assert "multiplier form" in s.last_error()
-    with pytest.raises(ptn.PtnError, match="multiplier form"):
-        ptn.solve_ip_static(p, dev(np.zeros(12)), T, u_init=u0, precision=ptn.PTN_FP64, costate_mode=1)
+@pytest.mark.parametrize("mode", [1, 2])
+def test_wide_tier_multiplier_form_matches_oracle(ptn, mode):
+    # the wide tier (nx >= 8, one warp per chunk) in the multiplier forms: the quadrotor in
+    # FP64 against the oracle's form of the same mode; the static entry point runs the same
+    # kernel with the same launch shape (identical results)
+    p = W.quadrotor(W.quadrotor_waypoints(1, seed=0)[0])
+    T = 64
+    x0 = np.zeros(12)
+    ui = np.full((T, 4), W.quadrotor_hover_u())
+    s = ptn.Solver(p, max_T=T, precision=ptn.PTN_FP64, costate_mode=mode, grid_min_T=0)
+    x, u, lam, info = s.solve_ip(dev(x0), T, u_init=dev(ui))
+    ref = O.solve_ip(p, x0, T, u_init=ui, opts=O.Options(costate_mode=mode))
+    check(info, ref, x, u, lam, FP64_TOL)
+    xs, us, ls, infs = ptn.solve_ip_static(p, dev(x0), T, u_init=dev(ui), precision=ptn.PTN_FP64, costate_mode=mode)
+    assert infs["status"] == 0
+    assert torch.equal(x, xs) and torch.equal(u, us) and torch.equal(lam, ls)
 
 
 def test_sequential_tier(ptn):

@@ -76,8 +76,12 @@ def test_ragged_horizons_fp64(ptn, T, threads):
 
 
 def test_nonconvergent_instance_reported_like_oracle(ptn):
-    # this instance defeats the method itself: the oracle stops at the iteration cap
-    # without reaching the tolerance, and so must the GPU (no false success)
+    # this instance defeats the oracle's path: it stops at the iteration cap without reaching
+    # the tolerance.  The GPU's iterates follow the oracle's only up to rounding (the scans
+    # associate the same products in another order), and on this instance rounding decides
+    # where they wander.  Whatever the GPU reports must be true (no false success): status -3
+    # with a gradient above the tolerance, or success at a point where the oracle's own
+    # gradient of the barrier problem, the dynamics defects and the constraints pass the test
     p = W.cartpole()
     x0 = W.cartpole_x0(7)
     T = 127
@@ -85,8 +89,15 @@ def test_nonconvergent_instance_reported_like_oracle(ptn):
     assert ref["info"]["status"] == -3
     s = ptn.Solver(p, max_T=T, precision=ptn.PTN_FP64, block_threads=128)
     x, u, lam, info = s.solve_ip(dev(x0), T)
-    assert info["status"] == -3
-    assert info["newton_iters"] == ref["info"]["newton_iters"]
+    if info["status"] == -3:
+        assert info["r_stat"] > 1e-6
+        return
+    assert info["status"] == 0
+    xn, un = x.cpu().numpy(), u.cpu().numpy()
+    nd = O.newton_direction(p, xn, un, 1e-6, "barrier", info["mu"])
+    assert np.abs(nd["d"]).max() <= 1e-6 * (1 + 1e-9)
+    assert max(np.abs(O.step(p, xn[t], un[t]) - xn[t + 1]).max() for t in range(T)) <= 1e-6
+    assert np.all(np.abs(un) < 10.0) and np.all(np.abs(xn[:T, 0]) < 2.0)
 
 
 def test_cartpole_fp64_cta(ptn):
@@ -324,3 +335,24 @@ def test_mixed_mode_recovers_when_fp32_phase_stalls(ptn):
     assert info["status"] == 0 and ref["info"]["status"] == 0
     assert info["r_kkt"] <= 1e-6 * (1 + 1e-9)
     assert abs(info["J"] - ref["info"]["J"]) / max(1.0, abs(ref["info"]["J"])) <= FP32_TOL
+
+
+@pytest.mark.parametrize("case", ["pendulum-cta", "cartpole-grid"])
+def test_printed_update_matches_oracle_at_fixed_iterations(ptn, case):
+    # update_mode 1, the update of Alg. 4 as printed (x += dx, u += du, no rollout): FP64, a
+    # fixed number of Newton iterations on one barrier level (the iterates carry dynamics
+    # defects and need not converge), against the oracle's printed update
+    if case == "pendulum-cta":
+        p, x0, T, opt = W.pendulum(), W.pendulum_x0(2), 64, dict(block_threads=64, grid_min_T=0)
+    else:
+        p, x0, T, opt = W.cartpole(T=1024, horizon=2.56), W.cartpole_x0(2), 1024, dict(grid_min_T=512,
+                                                                                         cluster_max_blocks=0)
+    K = 12
+    lit = dict(update_mode=1, mu0=0.1, mu_final=0.1, max_newton=K, tol_final=1e-14, tol_inner=1e-14)
+    s = ptn.Solver(p, max_T=T, precision=ptn.PTN_FP64, **opt, **lit)
+    x, u, lam, info = s.solve_ip(dev(x0), T)
+    ref = O.solve_ip(p, x0, T, opts=O.Options(**lit))
+    assert info["newton_iters"] == ref["info"]["newton_iters"] == K
+    assert info["ls_rejects"] == ref["info"]["ls_rejects"]
+    assert rel(x.cpu().numpy(), ref["x"]) <= FP64_TOL and rel(u.cpu().numpy(), ref["u"]) <= FP64_TOL
+    assert abs(info["J_c"] - ref["info"]["J_c"]) / max(1.0, abs(ref["info"]["J_c"])) <= FP64_TOL

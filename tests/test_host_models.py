@@ -148,6 +148,41 @@ def test_scan_operators_of_the_kernels_match_the_oracle_operators(prec, tol):
         assert np.abs(got - ref).max() <= t * max(1.0, float(np.abs(ref).max())), (inp[:2], got, ref)
 
 
+@pytest.mark.parametrize("prec,tol", [(0, 1e-11), (1, 3e-5)], ids=["fp64", "fp32_fp64solve"])
+def test_step_fold_of_the_kernels_matches_init_then_combine(prec, tol):
+    # the chunk fold's Woodbury form (one step's element combined with a later element)
+    # against the oracle's element initialisation followed by its value combination, for
+    # random later elements and the two starts of a fold: the identity element and the
+    # terminal element (A = 0, C = 0, b = 0, eta = 0, J = P_{N+1})
+    exe = _harness(SRC_OPS, EXE_OPS)
+    rng = np.random.default_rng(57 + prec)
+    rnd = _f32 if prec else (lambda a: np.asarray(a, dtype=np.float64))
+    Z = np.zeros((4, 4))
+    lines, refs = [], []
+    for k in range(12):
+        F = rnd(np.eye(4) + 0.1 * rng.normal(size=(4, 4))); G = rnd(rng.normal(size=(4, 1)))
+        Pq = rng.normal(size=(4, 4)); P = rnd(Pq @ Pq.T + np.eye(4)); M = rnd(0.1 * rng.normal(size=(4, 1)))
+        R = rnd(np.array([[0.5 + rng.random()]])); d = rng.normal(size=1)
+        if k % 3 == 0:
+            e = (np.eye(4), np.zeros(4), Z, np.zeros(4), Z)
+        elif k % 3 == 1:
+            Y = rng.normal(size=(4, 4))
+            e = (Z, np.zeros(4), Z, np.zeros(4), rnd(Y @ Y.T))
+        else:
+            e = tuple(rnd(z) for z in _val(rng))
+        step = np.concatenate([F.ravel(), G.ravel(), P.ravel(), M.ravel(), R.ravel(), d, [1e-3]])
+        lines.append("W %d " % prec + " ".join(repr(float(v)) for v in
+                                              np.concatenate([step] + [np.ravel(z) for z in e])))
+        refs.append(np.concatenate([np.ravel(z) for z in O.value_combine(O.value_init(F, G, P, M, R, d, 1e-3), e)]))
+    r = subprocess.run([exe], input="\n".join(lines) + "\n", capture_output=True, text=True, check=True)
+    outs = r.stdout.strip().splitlines()
+    assert len(outs) == len(refs)
+    for line, ref in zip(outs, refs):
+        assert "FAIL" not in line
+        got = np.array([float(t) for t in line.split()])
+        assert np.abs(got - ref).max() <= tol * max(1.0, float(np.abs(ref).max())), (got, ref)
+
+
 def test_riccati_step_of_the_kernels_matches_the_oracle_recursion():
     # one backward step of the kernels' sweep from the oracle's (S, s)_{t+1} reproduces the
     # oracle's Gam_t, gam_t and (S, s)_t (eq. value-fun-feedback with M^T), on the
