@@ -960,8 +960,8 @@ def main():
         quad["err_vs_oracle_max"] = max_err([v for k, v in errs.items() if k.startswith("quad/")])
         quad["err_vs_oracle_sample"] = f"instances 0..{QUAD_ORACLE_SAMPLE - 1}"
     if literal is not None and not args.no_cpu_baseline and world == 1:
-        for T in LITERAL_T[:3]:
-            literal[str(T)]["oracle_mode0"] = oracle_literal(T)
+        for Tl in LITERAL_T[:3]:
+            literal[str(Tl)]["oracle_mode0"] = oracle_literal(Tl)
     if synth is not None and errs:
         synth["batch"]["err_vs_oracle"] = max_err([v for k, v in errs.items() if k.startswith("synth/")])
         synth["batch"]["err_vs_oracle_sample"] = "the batch's shortest instance (oracle time grows as n^3 T)"

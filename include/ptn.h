@@ -88,7 +88,8 @@ typedef struct ptn_options {
   int grid_min_T;       /* single solves with T >= grid_min_T use all SMs (0: never) */
   int grid_steps_per_thread;
   int polish_after;     /* FP32 modes: exact FP64 gradients after this many iterations of
-                           a barrier level or ADMM sub-problem */
+                           the final barrier level or an ADMM sub-problem, and of an
+                           intermediate level once max|d| <= polish * its tolerance */
   int cluster_max_blocks; /* single solves needing 2..cluster_max_blocks CTAs (block_threads
                              threads, grid_steps_per_thread steps each) run on one thread-block
                              cluster (at most 16; 0: never) before the cooperative grid is used */

@@ -1340,10 +1340,12 @@ __device__ int newton_solve(Grp& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>& P,
     if (g.dead()) return ST_ETIMEOUT;
     long long c0 = clock64();
     r = first_order(exact);
-    if (MIXED && !exact && (stalled || it >= O.polish_after || (final_level && r <= O.polish * tol))) {
-      // endgame: below the FP32 noise floor of gradients and merits, switch to FP64 (at
-      // the final level near its tolerance; at any level after polish_after iterations,
-      // where the level's tolerance may lie below that floor).
+    const bool near = r <= O.polish * tol;
+    if (MIXED && !exact && (stalled || (it >= O.polish_after && (final_level || near)) || (final_level && near))) {
+      // endgame: below the FP32 noise floor of gradients and merits, switch to FP64: at the
+      // final level near its tolerance or after polish_after iterations; at an intermediate
+      // level after polish_after iterations that end near its tolerance (a level whose
+      // tolerance lies below the floor of a coarsely sampled instance hovers there).
       // First re-project the nominal onto the FP64 dynamics (one exact rollout with
       // s = 0 under the last feedback), so that FP64 merits compare like with like.
       exact = true;
