@@ -428,18 +428,16 @@ __device__ bool riccati_w(WScr<M, L>* s, double alpha) {
   L* SG = s->T2;  // N x U
   wops::mm<N, N, N, false, false>(s->S, s->F, SF);
   wops::mm<N, N, U, false, false>(s->S, s->G, SG);
-  // Qux = G^T S F + M^T (U x N) in X[:, :N]; d + G^T s in X[:, N]
+  // Qux = G^T S F + M^T (U x N) in X[:, :N] (G^T (S F) formed in T3); d + G^T s in X[:, N];
+  // G^T S G (U x U) in T3 behind it
+  static_assert(U * N + U * U <= N * N, "T3 holds G^T S F and G^T S G");
+  L* GSG = s->T3 + U * N;
+  wops::mm<U, N, N, true, false>(s->G, SF, s->T3);
+  wops::mm<U, N, U, true, false>(s->G, SG, GSG);
   for (int q = l; q < U * C; q += 32) {
     const int i = q / C, j = q % C;
-    L v = L(0);
-    if (j < N) {
-      v += wops::dot4<N, L>([&](int k) { return s->G[k * U + i] * SF[k * N + j]; });
-      v += s->Mm[j * U + i];
-    } else {
-      v += wops::dot4<N, L>([&](int k) { return s->G[k * U + i] * s->s[k]; });
-      v += L(s->d[i]);
-    }
-    s->X[q] = v;
+    s->X[q] = (j < N) ? s->T3[i * N + j] + s->Mm[j * U + i]
+                      : wops::dot4<N, L>([&](int k) { return s->G[k * U + i] * s->s[k]; }) + L(s->d[i]);
   }
   // Q = R + G^T S G + alpha I, in every lane
   __syncwarp();
@@ -447,11 +445,7 @@ __device__ bool riccati_w(WScr<M, L>* s, double alpha) {
 #pragma unroll
   for (int i = 0; i < U; i++)
 #pragma unroll
-    for (int j = 0; j < U; j++) {
-      L gsg = L(0);
-      for (int k = 0; k < N; k++) gsg += s->G[k * U + i] * SG[k * U + j];
-      Q[i * U + j] = SV(s->Rm[i * U + j]) + SV(gsg) + (i == j ? SV(alpha) : SV(0));
-    }
+    for (int j = 0; j < U; j++) Q[i * U + j] = SV(s->Rm[i * U + j]) + SV(GSG[i * U + j]) + (i == j ? SV(alpha) : SV(0));
   // keep Qux (U x N) for the S update, before the solve overwrites X
   L* Qux = s->T3;
   for (int q = l; q < U * N; q += 32) Qux[q] = s->X[(q / N) * C + (q % N)];
@@ -461,16 +455,14 @@ __device__ bool riccati_w(WScr<M, L>* s, double alpha) {
   for (int q = l; q < U * N; q += 32) s->Gam[q] = -s->X[(q / N) * C + (q % N)];
   for (int i = l; i < U; i += 32) s->gam[i] = -s->X[i * C + N];
   __syncwarp();
-  // S' = P + F^T S F + Qux^T Gam,  s' = F^T s + Qux^T gam
+  // S' = P + Qux^T Gam + F^T (S F),  s' = F^T s + Qux^T gam  (S G in T2 is used up)
   L* Sn = s->T2;
   for (int q = l; q < N * N; q += 32) {
     const int i = q / N, j = q % N;
-    L v = s->Pm[q];
-    v += wops::dot4<N, L>([&](int k) { return s->F[k * N + i] * SF[k * N + j]; });
-#pragma unroll
-    v += wops::dot4<U, L>([&](int k) { return Qux[k * N + i] * s->Gam[k * N + j]; });
-    Sn[q] = v;
+    Sn[q] = s->Pm[q] + wops::dot4<U, L>([&](int k) { return Qux[k * N + i] * s->Gam[k * N + j]; });
   }
+  __syncwarp();
+  wops::mm<N, N, N, true, false, true>(s->F, SF, Sn);
   for (int i = l; i < N; i += 32) {
     L v = L(0);
     v += wops::dot4<N, L>([&](int k) { return s->F[k * N + i] * s->s[k]; });
@@ -501,19 +493,14 @@ __device__ bool val_fold_w(WScr<M, L>* s, double alpha, Val<M::NX, L>* e, L* tmp
   L* JG = s->T2;  // N x U
   wops::mm<N, N, N, false, false>(e->J, s->F, JF);
   wops::mm<N, N, U, false, false>(e->J, s->G, JG);
-  // X[:, :N] = H = G^T J F + M^T,  X[:, N] = G^T eta - d;  Q = R~ + G^T J G
+  // X[:, :N] = H = G^T J F + M^T (G^T (J F) formed in T3),  X[:, N] = G^T eta - d;
+  // Q = R~ + G^T J G
   SV* Q = reinterpret_cast<SV*>(s->K);
+  wops::mm<U, N, N, true, false>(s->G, JF, s->T3);
   for (int q = l; q < U * C; q += 32) {
     const int i = q / C, j = q % C;
-    L v = L(0);
-    if (j < N) {
-      v += wops::dot4<N, L>([&](int k) { return s->G[k * U + i] * JF[k * N + j]; });
-      v += s->Mm[j * U + i];
-    } else {
-      v += wops::dot4<N, L>([&](int k) { return s->G[k * U + i] * e->eta[k]; });
-      v -= L(s->d[i]);
-    }
-    s->X[q] = v;
+    s->X[q] = (j < N) ? s->T3[i * N + j] + s->Mm[j * U + i]
+                      : wops::dot4<N, L>([&](int k) { return s->G[k * U + i] * e->eta[k]; }) - L(s->d[i]);
   }
   for (int q = l; q < U * U; q += 32) {
     const int i = q / U, j = q % U;
@@ -538,16 +525,15 @@ __device__ bool val_fold_w(WScr<M, L>* s, double alpha, Val<M::NX, L>* e, L* tmp
     }
   }
   __syncwarp();
-  // J' (into T2) and eta' (into w1) from the J, eta of e
+  // J' = P + H^T Gam + F^T (J F) (into T2: J G is used up) and eta' (into w1) from the
+  // J, eta of e
   L* Jn = s->T2;
   for (int q = l; q < N * N; q += 32) {
     const int i = q / N, j = q % N;
-    L v = s->Pm[q];
-    v += wops::dot4<N, L>([&](int k) { return s->F[k * N + i] * JF[k * N + j]; });
-#pragma unroll
-    v += wops::dot4<U, L>([&](int k) { return H[k * N + i] * s->Gam[k * N + j]; });
-    Jn[q] = v;
+    Jn[q] = s->Pm[q] + wops::dot4<U, L>([&](int k) { return H[k * N + i] * s->Gam[k * N + j]; });
   }
+  __syncwarp();
+  wops::mm<N, N, N, true, false, true>(s->F, JF, Jn);
   for (int i = l; i < N; i += 32) {
     L v = L(0);
     v += wops::dot4<N, L>([&](int k) { return s->F[k * N + i] * e->eta[k]; });
@@ -559,13 +545,8 @@ __device__ bool val_fold_w(WScr<M, L>* s, double alpha, Val<M::NX, L>* e, L* tmp
   // closed loop F + G Gam (into T1: J F is no longer needed); A G (into X)
   L* Fc = s->T1;
   L* AG = s->X;
-  for (int q = l; q < N * N; q += 32) {
-    const int i = q / N, j = q % N;
-    L v = s->F[q];
-#pragma unroll
-    v += wops::dot4<U, L>([&](int k) { return s->G[i * U + k] * s->Gam[k * N + j]; });
-    Fc[q] = v;
-  }
+  wops::copy<N * N>(s->F, Fc);
+  wops::mm<N, U, N, false, false, true>(s->G, s->Gam, Fc);
   wops::mm<N, N, U, false, false>(e->A, s->G, AG);
   // A' = A (F + G Gam) into tmpA; (A G) Q^{-1} into T3 (H is no longer needed)
   wops::mm<N, N, N, false, false>(e->A, Fc, tmpA);
@@ -578,12 +559,8 @@ __device__ bool val_fold_w(WScr<M, L>* s, double alpha, Val<M::NX, L>* e, L* tmp
     AQ[q] = L(v);
   }
   __syncwarp();
+  wops::mm<N, U, N, false, true, true>(AQ, AG, e->C);
   for (int q = l; q < N * N; q += 32) {
-    const int i = q / N, j = q % N;
-    L v = e->C[q];
-#pragma unroll
-    v += wops::dot4<U, L>([&](int k) { return AQ[i * U + k] * AG[j * U + k]; });
-    e->C[q] = v;
     e->A[q] = tmpA[q];
     e->J[q] = Jn[q];
   }

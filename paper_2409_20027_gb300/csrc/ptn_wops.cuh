@@ -33,18 +33,110 @@ __device__ __forceinline__ S dot4(const Term& term) {
   return (s0 + s1) + (s2 + s3);
 }
 
+// ---- FP32 products on the tensor cores (mma.sync m16n8k8, TF32 operands) ----
+//
+// A float x is split into hi = tf32(x) and lo = tf32(x - hi) (x - hi is exact in FP32);
+// a product x y is taken as lo_x hi_y + hi_x lo_y + hi_x hi_y with FP32 accumulation in
+// the MMA.  The dropped lo_x lo_y term and the rounding of lo are below 2^-21 of |x y|,
+// so the result carries about FP32 accuracy (three MMAs per tile instead of one).
+__device__ __forceinline__ unsigned tf32_rna(float x) {
+  unsigned r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ void split_tf32(float x, unsigned& hi, unsigned& lo) {
+  hi = tf32_rna(x);
+  lo = tf32_rna(x - __uint_as_float(hi));
+}
+// d += a b for one 16 x 8 tile of d, a 16 x 8 (row-major fragment), b 8 x 8 (column)
+__device__ __forceinline__ void mma_tf32(float (&d)[4], const unsigned (&a)[4], const unsigned (&b)[2]) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// C (R x Cc) = op(A) (R x K) * op(B) (K x Cc) [+ C if ACC], all FP32 in shared memory, on
+// the tensor cores: the output in 16 x 8 tiles held in registers, K in steps of 8, entries
+// outside the matrices read as zero.  Fragment layout (PTX ISA, mma.m16n8k8 .tf32), with
+// g = lane / 4 and c = lane % 4: a = {(g, c), (g + 8, c), (g, c + 4), (g + 8, c + 4)},
+// b = {(c, g), (c + 4, g)}, d = {(g, 2c), (g, 2c + 1), (g + 8, 2c), (g + 8, 2c + 1)}.
+template <int R, int K, int Cc, bool TA, bool TB, bool ACC>
+__device__ void mm_tc(const float* A, const float* B, float* C) {
+  constexpr int MT = (R + 15) / 16, NT = (Cc + 7) / 8, KT = (K + 7) / 8;
+  const int l = lane_id(), g = l >> 2, c = l & 3;
+  auto a_at = [&](int i, int k) -> float {
+    return (i < R && k < K) ? (TA ? A[k * R + i] : A[i * K + k]) : 0.0f;
+  };
+  auto b_at = [&](int k, int j) -> float {
+    return (k < K && j < Cc) ? (TB ? B[j * K + k] : B[k * Cc + j]) : 0.0f;
+  };
+  float acc[MT][NT][4];
+#pragma unroll
+  for (int mt = 0; mt < MT; mt++)
+#pragma unroll
+    for (int nt = 0; nt < NT; nt++)
+#pragma unroll
+      for (int q = 0; q < 4; q++) acc[mt][nt][q] = 0.0f;
+#pragma unroll
+  for (int kt = 0; kt < KT; kt++) {
+    const int k0 = kt * 8 + c;
+    unsigned ah[MT][4], al[MT][4], bh[NT][2], bl[NT][2];
+#pragma unroll
+    for (int mt = 0; mt < MT; mt++) {
+      const int r0 = mt * 16 + g;
+      split_tf32(a_at(r0, k0), ah[mt][0], al[mt][0]);
+      split_tf32(a_at(r0 + 8, k0), ah[mt][1], al[mt][1]);
+      split_tf32(a_at(r0, k0 + 4), ah[mt][2], al[mt][2]);
+      split_tf32(a_at(r0 + 8, k0 + 4), ah[mt][3], al[mt][3]);
+    }
+#pragma unroll
+    for (int nt = 0; nt < NT; nt++) {
+      const int j = nt * 8 + g;
+      split_tf32(b_at(k0, j), bh[nt][0], bl[nt][0]);
+      split_tf32(b_at(k0 + 4, j), bh[nt][1], bl[nt][1]);
+    }
+#pragma unroll
+    for (int mt = 0; mt < MT; mt++)
+#pragma unroll
+      for (int nt = 0; nt < NT; nt++) {
+        mma_tf32(acc[mt][nt], al[mt], bh[nt]);
+        mma_tf32(acc[mt][nt], ah[mt], bl[nt]);
+        mma_tf32(acc[mt][nt], ah[mt], bh[nt]);
+      }
+  }
+  __syncwarp();  // every lane's operand loads precede the first store
+#pragma unroll
+  for (int mt = 0; mt < MT; mt++)
+#pragma unroll
+    for (int nt = 0; nt < NT; nt++)
+#pragma unroll
+      for (int q = 0; q < 4; q++) {
+        const int i = mt * 16 + g + ((q & 2) ? 8 : 0), j = nt * 8 + 2 * c + (q & 1);
+        if (i < R && j < Cc) C[i * Cc + j] = ACC ? C[i * Cc + j] + acc[mt][nt][q] : acc[mt][nt][q];
+      }
+  __syncwarp();
+}
+
 // C (R x Cc) = op(A) (R x K) * op(B) (K x Cc) [+ C if ACC]; op = transpose when TA / TB.
-// Accumulation in the type of C.
+// Accumulation in the type of C.  All-FP32 products of at least 8 x 8 x 8 run on the
+// tensor cores (mm_tc); the others (FP64, mixed, or thin) are lane-parallel dot products.
 template <int R, int K, int Cc, bool TA, bool TB, bool ACC = false, class SA, class SB, class SC>
 __device__ void mm(const SA* A, const SB* B, SC* C) {
-  for (int e = lane_id(); e < R * Cc; e += 32) {
-    const int i = e / Cc, j = e % Cc;
-    const SC s = dot4<K, SC>([&](int k) {
-      return SC(TA ? A[k * R + i] : A[i * K + k]) * SC(TB ? B[j * K + k] : B[k * Cc + j]);
-    });
-    C[e] = ACC ? C[e] + s : s;
+  if constexpr (std::is_same<SA, float>::value && std::is_same<SB, float>::value &&
+                std::is_same<SC, float>::value && R >= 8 && K >= 8 && Cc >= 8) {
+    mm_tc<R, K, Cc, TA, TB, ACC>(A, B, C);
+  } else {
+    for (int e = lane_id(); e < R * Cc; e += 32) {
+      const int i = e / Cc, j = e % Cc;
+      const SC s = dot4<K, SC>([&](int k) {
+        return SC(TA ? A[k * R + i] : A[i * K + k]) * SC(TB ? B[j * K + k] : B[k * Cc + j]);
+      });
+      C[e] = ACC ? C[e] + s : s;
+    }
+    __syncwarp();
   }
-  __syncwarp();
 }
 
 // y (R) = op(A) x [+ y]
