@@ -847,11 +847,13 @@ def main():
             b.record(stream)
             torch.cuda.synchronize()
             sweep[str(Ts)] = {"ms": a.elapsed_time(b), "newton_iters": inf["newton_iters"], "status": inf["status"],
+                              "fp64_finish_iters": inf["finish_iters"],
                               "r_kkt": inf["r_kkt"], "us_per_newton_iter": 1e3 * a.elapsed_time(b) /
                               max(inf["newton_iters"], 1)}
             gpu_out[("cartpole", Ts, 0)] = (xs_.cpu().numpy(), us_.cpu().numpy(), ls_.cpu().numpy(), inf["J"])
             sv.close()
         sweep[str(T)] = {"ms": ms, "newton_iters": infos[-1]["newton_iters"], "status": infos[-1]["status"],
+                         "fp64_finish_iters": [i["finish_iters"] for i in infos],
                          "r_kkt": infos[-1]["r_kkt"], "us_per_newton_iter": 1e3 * ms / max(infos[-1]["newton_iters"], 1),
                          "note": "the headline solves (mean over the timed steps)"}
         sweep["workload"] = ("cart-pole IP on the fixed 2.56 s horizon (dt = 2.56/T, RK4), x0 seed 0, tuned launch "
@@ -971,8 +973,9 @@ def main():
             "roofline": roof, "cpu_baseline": cpu,
             "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": 4 * 8,
                     "d2h_bytes_per_step": ((T + 1) * 4 + T) * 8},
-            "gpu_launches": args.steps, "clocks": clocks, "kkt_ok": ok, "err_vs_oracle": head_err,
-            "newton_iters": last["newton_iters"], "launch": launch or "defaults",
+            "gpu_launches": sum(1 + (i["finish_iters"] > 0) for i in infos), "clocks": clocks, "kkt_ok": ok,
+            "err_vs_oracle": head_err, "newton_iters": [i["newton_iters"] for i in infos],
+            "fp64_finish_iters": [i["finish_iters"] for i in infos], "launch": launch or "defaults",
             "phase_share": phase_share(infos), "sweep": sweep, "pendulum": pend,
             "batch": batch, "quadrotor": quad, "synthetic": synth, "literal_dt": literal, "mpc": mpcl,
             "sequential": seq,

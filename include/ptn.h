@@ -74,7 +74,7 @@ typedef struct ptn_problem {
  *   precision FP32_FP64SOLVE, mu 1e-1 -> 1e-6 (x0.1), tol_inner 1e-4, tol_final 1e-6,
  *   block_threads 128, grid_min_T 512, grid_steps_per_thread 2, polish 100, polish_after 50,
  *   cluster_max_blocks 16, sequential 0, costate_mode 0 (the co-state scan), update_mode 0,
- *   max_newton 500 per barrier level, ADMM rho 1, admm_tol 1e-2, max_outer 2000,
+ *   max_newton 500 per barrier level, ADMM rho 1, admm_tol 1e-2, max_outer 2000, fp64_finish 1,
  *   alpha0 1e-6 in [1e-10, 1e10], ten step sizes 1, 1/2, ..., Armijo c1 1e-4,
  *   rollout: at most 30 multiple-shooting Newton iterations to relative defect 1e-12. */
 typedef struct ptn_options {
@@ -117,16 +117,30 @@ typedef struct ptn_options {
   double polish;        /* FP32 modes: exact FP64 gradients once max|d| <= polish * tol_final */
   double armijo_eps32;  /* FP32 modes: Armijo allowance, relative to |J_c|, for merits
                            accumulated as FP32 differences (their rounding floor) */
+  int fp64_finish;      /* FP32 modes, single IP solves (ptn_solve_ip, ptn_solve_batch with
+                           B = 1): when the solve stops without converging (line search
+                           failure or iteration cap), finish it with FP64 LQR data from its
+                           last iterate: a second launch of the FP64 kernels, warm-started
+                           with the controls reached, starting at the barrier weight where
+                           the first stopped; its Newton iterations are added to
+                           newton_iters and reported in finish_iters.  With the finish on,
+                           the mixed-precision launch also leaves a final barrier level on
+                           which 20 iterations of the exact path have not halved max|d|.
+                           0: off; default 1.  Not done by ptn_solve_batch_async (no host
+                           step) or by ptn_solve_ip_static. */
+  int pad_opt;
 } ptn_options;
 
 /* Per-solve report.  r_kkt = max(r_stat, r_dyn, r_feas, mu) for IP, where r_stat is
  * max_t |d_t|_inf (gradient of the augmented cost), r_dyn the largest dynamics defect and
  * r_feas the largest constraint violation.  cycles[] are SM clock cycles spent by the
  * group's first thread in the co-state pass, second-order expansion, value pass, state
- * pass, line search, initial rollout, and everything else. */
+ * pass, line search, initial rollout, and everything else.  finish_iters: Newton
+ * iterations of the FP64 finish (ptn_options.fp64_finish), 0 when none ran; the cycle
+ * counts and the other counters then add both launches. */
 typedef struct ptn_info {
   int status, newton_iters, outer_iters, ls_rejects, factor_fails, roll_fails;
-  int roll_iters, ls_evals, exact_passes, pad;
+  int roll_iters, ls_evals, exact_passes, finish_iters;
   double mu, alpha, r_stat, r_dyn, r_feas, r_kkt, J, J_c, r_p, r_d;
   long long cycles[7];
 } ptn_info;

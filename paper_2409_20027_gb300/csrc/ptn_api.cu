@@ -186,6 +186,7 @@ extern "C" void ptn_default_options(ptn_options* o) {
   o->armijo_eps32 = 1e-9;
   o->polish_after = 50;
   o->cluster_max_blocks = 16;
+  o->fp64_finish = 1;
 }
 
 extern "C" const char* ptn_version(void) { return "ptn 0.1 (sm_103a)"; }
@@ -420,7 +421,7 @@ static void to_optdev(const ptn_options& o, int method, OptDev* d) {
 static void from_info(const InfoDev& d, ptn_info* o) {
   o->status = d.status; o->newton_iters = d.newton_iters; o->outer_iters = d.outer_iters;
   o->ls_rejects = d.ls_rejects; o->factor_fails = d.factor_fails; o->roll_fails = d.roll_fails;
-  o->roll_iters = d.roll_iters; o->ls_evals = d.ls_evals; o->exact_passes = d.exact_passes; o->pad = 0;
+  o->roll_iters = d.roll_iters; o->ls_evals = d.ls_evals; o->exact_passes = d.exact_passes; o->finish_iters = 0;
   for (int k = 0; k < 7; k++) o->cycles[k] = d.cyc[k];
   o->mu = d.mu; o->alpha = d.alpha; o->r_stat = d.r_stat; o->r_dyn = d.r_dyn; o->r_feas = d.r_feas;
   o->r_kkt = d.r_kkt; o->J = d.J; o->J_c = d.J_c; o->r_p = d.r_p; o->r_d = d.r_d;
@@ -588,6 +589,59 @@ static int enqueue(ptn_solver* s, const LaunchPlan& p, const OptDev* dopt, const
   return PTN_OK;
 }
 
+// whether a solve of this shape gets the FP64 finish when it does not converge
+static bool finish_applies(const ptn_solver* s, int method, int B) {
+  return method == PTN_METHOD_IP && B == 1 && s->opt.fp64_finish && s->opt.precision != PTN_FP64 &&
+         !s->opt.sequential && s->opt.update_mode == 0 && pick_launcher(s->hprob.model, PTN_FP64) != nullptr;
+}
+
+// FP64 finish of a single mixed-precision IP solve that stopped without converging (line
+// search failure or iteration cap): the FP64 kernels relaunched on the same instance,
+// warm-started with the controls reached (u_out serves as u_init: each thread reads its
+// own steps before it writes them), from the barrier weight where the first launch
+// stopped, with the initial nominal built in parallel.  On return s->hinfo[0] holds the
+// finish's report and *first the first launch's; *finished tells whether it ran.
+static int fp64_finish(ptn_solver* s, int method, int B, const int* T_b, long long steps, const double* x0,
+                       const double* xref, double* x_out, double* u_out, double* lam_out, cudaStream_t st,
+                       InfoDev* first, bool* finished) {
+  *finished = false;
+  const int st0 = s->hinfo[0].status;
+  if (!finish_applies(s, method, B) || (st0 != ST_ENOTCONV && st0 != ST_ENUM)) return PTN_OK;
+  *first = s->hinfo[0];
+  const ptn_options keep = s->opt;
+  s->opt.precision = PTN_FP64;
+  s->opt.mu0 = first->mu > keep.mu_final ? first->mu : keep.mu_final;
+  LaunchPlan p;
+  int rc = plan_launch(s, method, B, T_b, steps, &p);
+  if (rc == PTN_OK) {
+    to_optdev(s->opt, method, s->hopt);
+    s->hopt->init_parallel64 = 1;
+    s->opt = keep;
+    CK(cudaMemcpyAsync(s->dopt, s->hopt, sizeof(OptDev), cudaMemcpyHostToDevice, st));
+    rc = enqueue(s, p, s->dopt, s->dinst, x0, xref, u_out, x_out, u_out, lam_out, s->dinfo, st);
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(s->hinfo, s->dinfo, sizeof(InfoDev), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    *finished = true;
+  }
+  s->opt = keep;
+  return rc;
+}
+
+// adds the first launch's counters to the report of the FP64 finish
+static void merge_first(const InfoDev& a, ptn_info* o) {
+  o->finish_iters = o->newton_iters;
+  o->newton_iters += a.newton_iters;
+  o->outer_iters += a.outer_iters;
+  o->ls_rejects += a.ls_rejects;
+  o->factor_fails += a.factor_fails;
+  o->roll_fails += a.roll_fails;
+  o->roll_iters += a.roll_iters;
+  o->ls_evals += a.ls_evals;
+  o->exact_passes += a.exact_passes;
+  for (int k = 0; k < 7; k++) o->cycles[k] += a.cyc[k];
+}
+
 static int solve_common(ptn_solver* s, int method, int B, const int* T_b, const double* x0, const double* xref,
                         const double* u_init, double* x_out, double* u_out, double* lam_out, double* z_out,
                         double* v_out, ptn_info* info, void* stream_, const double* dt_b = nullptr) {
@@ -603,6 +657,8 @@ static int solve_common(ptn_solver* s, int method, int B, const int* T_b, const 
   rc = plan_launch(s, method, B, T_b, steps, &p);
   if (rc) return rc;
   to_optdev(s->opt, method, s->hopt);
+  // a final barrier level that stalls on the mixed path hands over to the FP64 finish
+  s->hopt->stall_exit = finish_applies(s, method, B) ? 20 : 0;
   CK(cudaMemcpyAsync(s->dinst, s->hinst, sizeof(InstDev) * B, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(s->dopt, s->hopt, sizeof(OptDev), cudaMemcpyHostToDevice, st));
   rc = enqueue(s, p, s->dopt, s->dinst, x0, xref, u_init, x_out, u_out, lam_out, s->dinfo, st);
@@ -613,8 +669,15 @@ static int solve_common(ptn_solver* s, int method, int B, const int* T_b, const 
     if (v_out) CK(cudaMemcpyAsync(v_out, s->w.v, sizeof(double) * steps * s->nw, cudaMemcpyDeviceToDevice, st));
   }
   CK(cudaStreamSynchronize(st));
+  InfoDev first{};
+  bool finished = false;
+  rc = fp64_finish(s, method, B, T_b, steps, x0, xref, x_out, u_out, lam_out, st, &first, &finished);
+  if (rc) return rc;
   for (int i = 0; i < B; i++) {
-    if (info) from_info(s->hinfo[i], info + i);
+    if (info) {
+      from_info(s->hinfo[i], info + i);
+      if (finished) merge_first(first, info + i);
+    }
     if (rc == PTN_OK && s->hinfo[i].status != 0) rc = s->hinfo[i].status;
   }
   if (rc != PTN_OK && !s->err[0]) fail(s, rc, "solve finished with status %d", rc);

@@ -63,6 +63,8 @@ struct OptDev {
   int roll_max_iter, method, polish_after, init_max_iter;
   int costate_mode;        // 0: co-state scan (Alg. 1); 1, 2: multiplier forms
   int update_mode;         // 0: step on the closed-loop rollout; 1: x += dx, u += du (Alg. 4)
+  int init_parallel64;     // nonzero: FP64 kernels also build the initial nominal in parallel
+  int stall_exit;          // > 0: mixed modes leave a stalled final level (FP64 finish follows)
   long long spin_limit;  // bounded waits in grid barriers
 };
 

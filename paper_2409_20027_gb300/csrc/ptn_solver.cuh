@@ -1336,6 +1336,10 @@ __device__ int newton_solve(Grp& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>& P,
     costate_pass(g, I, P, A, exact);
   }
   bool stalled = false;  // the FP32-increment phase ran alpha past alpha_max
+  // stall exit (O.stall_exit > 0, set when an FP64 finish follows on the host): on the
+  // exact path of the final level, stop once stall_exit iterations have not halved max|d|
+  double r_ref = INFINITY;
+  int it_ref = 0;
   for (int it = 0; it <= O.max_newton; it++) {
     if (g.dead()) return ST_ETIMEOUT;
     long long c0 = clock64();
@@ -1367,6 +1371,10 @@ __device__ int newton_solve(Grp& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>& P,
     st.cyc[0] += c1 - c0;
     if (r <= tol) { rc = ST_OK; break; }
     if (it == O.max_newton || !isfinite(r) || !isfinite(J0)) break;
+    if (MIXED && exact && final_level && O.stall_exit > 0) {
+      if (r < 0.5 * r_ref) { r_ref = r; it_ref = it; }
+      else if (it - it_ref >= O.stall_exit) break;  // ST_ENOTCONV: the FP64 finish takes over
+    }
     st.iters++;
     quadratize(g, I, P, A);
     long long c2 = clock64();
@@ -1591,7 +1599,8 @@ __device__ void initial_rollout(Grp& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>
   g.sync();
 }
 
-// Initial nominal in parallel (FP32 modes, groups of >= 256 threads, fine time steps):
+// Initial nominal in parallel (FP32 modes, and FP64 when O.init_parallel64 is set: the
+// FP64 finish of a mixed-precision solve; groups of >= 256 threads, fine time steps):
 // the same open-loop trajectory x = rollout(x0, u_init), computed as
 //   1. a coarse pass by the group's first thread with steps K dt (K <= 32, K dt <= 2.5 ms;
 //      controls held), which gives states at t = 0, K, 2K, ...;
@@ -1599,15 +1608,15 @@ __device__ void initial_rollout(Grp& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>
 //      coarse state before it;
 //   3. the multiple-shooting rollout with s = 0 and no feedback, which corrects the
 //      guesses onto the fine trajectory (same dynamics and tolerance as later rollouts).
-// Returns false (group-uniform) when not applicable (FP64, small groups, coarse steps,
-// ADMM) or when the shooting does not converge; the caller then integrates sequentially.
+// Returns false (group-uniform) when not applicable (FP64 unless asked, small groups,
+// coarse steps, ADMM) or when the shooting does not converge; the caller then integrates
+// sequentially.
 template <class M, class L, class Grp>
 __device__ bool initial_rollout_parallel(Grp& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>& P, const OptDev& O,
                                          int* iters) {
-  if constexpr (!std::is_same<L, float>::value) {
-    return false;
-  } else {
+  {
     constexpr int N = M::NX, U = M::NU;
+    if (!std::is_same<L, float>::value && !O.init_parallel64) return false;
     int K = (int)(0.0025 / P.dt);
     K = K > 32 ? 32 : K;
     if (K < 2 || g.size() < 256 || O.method != 0) return false;  // IP only (barrier merit)
@@ -1822,6 +1831,11 @@ __device__ int adjoint_instance(Grp& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>
   Aug A;
   A.kind = AUG_BARRIER; A.mu = aa.mu; A.rho = 1.0; A.z = nullptr; A.v = nullptr;
   costate_exact(g, I, P, A);
+  // lam_0 for the envelope term, read once the co-state pass has ended (its closing group
+  // reduction orders the writes)
+  double lam0[N];
+#pragma unroll
+  for (int i = 0; i < N; i++) lam0[i] = I.lam[i];
   const bool lin = aa.gx || aa.gu;
   // out = [x0 (N), Qd (N), Rd (U), Qfd (N), prm (NP)] accumulated per thread
   constexpr int KO = 3 * N + U + NP;
@@ -1895,11 +1909,11 @@ __device__ int adjoint_instance(Grp& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>
   }
   double out[KO];
 #pragma unroll
-  for (int i = 0; i < KO; i++) out[i] = aa.gJ * env[i] - adj[i];
+  for (int i = 0; i < KO; i++) out[i] = (i < N ? 0.0 : aa.gJ * env[i]) - adj[i];  // x0: lam_0 below
   group_sum<KO>(g, out);  // also orders the co-state writes before lam_1 is read
   if (g.rank() == 0) {
 #pragma unroll
-    for (int i = 0; i < N; i++) out[i] += aa.gJ * I.lam[i];
+    for (int i = 0; i < N; i++) out[i] += aa.gJ * lam0[i];
     if (aa.g_x0)
       for (int i = 0; i < N; i++) aa.g_x0[(size_t)bi * N + i] = out[i];
     if (aa.g_Qd)

@@ -46,14 +46,18 @@ _OPT_DBLS = ["mu0", "zeta", "mu_final", "tol_inner", "tol_final", "rho", "admm_t
              "armijo_eps32"]
 
 
+_OPT_TAIL = ["fp64_finish", "pad_opt"]
+
+
 class Options(C.Structure):
-    _fields_ = [(k, C.c_int) for k in _OPT_INTS] + [(k, C.c_double) for k in _OPT_DBLS]
+    _fields_ = [(k, C.c_int) for k in _OPT_INTS] + [(k, C.c_double) for k in _OPT_DBLS] + \
+               [(k, C.c_int) for k in _OPT_TAIL]
 
 
 class Info(C.Structure):
     _fields_ = [(k, C.c_int) for k in ["status", "newton_iters", "outer_iters", "ls_rejects",
                                        "factor_fails", "roll_fails", "roll_iters", "ls_evals",
-                                       "exact_passes", "pad"]] + \
+                                       "exact_passes", "finish_iters"]] + \
                [(k, C.c_double) for k in ["mu", "alpha", "r_stat", "r_dyn", "r_feas", "r_kkt", "J",
                                           "J_c", "r_p", "r_d"]] + \
                [("cycles", C.c_longlong * 7)]

@@ -78,6 +78,8 @@ def test_entry_points_refuse_null_handles_and_pointers_without_a_gpu():
     opt = ptn.Options()
     lib.ptn_default_options(ctypes.byref(opt))
     assert opt.costate_mode == 0 and opt.precision == ptn.PTN_FP32_FP64SOLVE
+    # the struct mirror matches the C layout up to its last field (defaults read back)
+    assert opt.armijo_eps32 == 1e-9 and opt.polish == 100.0 and opt.fp64_finish == 1
     # the static entry point checks its arguments first as well
     err = ctypes.create_string_buffer(256)
     rc = lib.ptn_solve_ip_static(None, None, None, None, 8, None, None, None, None, err, 256, None)

@@ -126,3 +126,23 @@ def test_batch_slice_with_longest_horizon_matches_oracle(ptn):
         check(infos[b], ref, X[xo:xo + T + 1], U[uo:uo + T], Lm[xo:xo + T + 1], FP32_TOL)
         xo += T + 1
         uo += T
+
+
+def test_cartpole_T65536_with_fp64_finish_matches_oracle(ptn):
+    # the longest horizon of the sweep (T = 65536 on the fixed 2.56 s horizon, tuned grid
+    # shape): the mixed-precision launch stalls near the final tolerance at this seed (its
+    # FP32 LQR directions stop improving max|d|), and the FP64 finish of ptn_solve_ip
+    # completes the solve from where it stopped; both sides to max|d| <= 1e-8 / 1e-7 as
+    # in the T = 16384 case
+    from paper_2409_20027_gb300 import autotune
+    T = 65536
+    p = W.cartpole(T=T, horizon=2.56)
+    x0 = W.cartpole_x0(0)
+    s = ptn.Solver(p, max_T=T, precision=ptn.PTN_FP32_FP64SOLVE, tol_final=1e-8, max_newton=1000)
+    autotune.apply(s, autotune.load(os.path.join(ROOT, "paper_2409_20027_gb300", "tuned_gb300.json")), T)
+    assert s.options.fp64_finish == 1
+    x, u, lam, info = s.solve_ip(dev(x0), T)
+    # finish_iters > 0 when the mixed launch stopped short (it did at this seed on GB300)
+    assert 0 <= info["finish_iters"] < info["newton_iters"], info
+    ref = O.solve_ip(p, x0, T, opts=O.Options(tol_final=1e-7))
+    check(info, ref, x, u, lam, FP32_TOL)
