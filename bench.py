@@ -43,9 +43,10 @@ def algorithmic_flops(n, m, T, info):
     return T * (info["newton_iters"] * per_it + info["roll_iters"] * per_roll)
 
 
-# DRAM bytes (read + write) of one k_solve_grid launch of this workload, from the ncu
-# capture summarised in profiles/k_solve_grid_cartpole_T16384.md
-TRAFFIC_BYTES = (2.443776 + 1.739264) * 1e6
+# DRAM bytes (read + write) of one k_solve_grid launch of this workload (seed 0), from the
+# ncu launch list summarised in profiles/k_solve_grid_cartpole_T16384.md (mean of the
+# three launches after the first)
+TRAFFIC_BYTES = ((3.140864 + 2.888960) + (2.983936 + 2.834432) + (2.950656 + 2.884864)) / 3 * 1e6
 
 
 def flop_split(n, m, T, info):

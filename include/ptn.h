@@ -248,6 +248,23 @@ int ptn_adjoint(ptn_solver* s, int B, const int* T_b, const double* x0, const do
                 const double* gx, const double* gu, double* g_x0, double* g_Qd, double* g_Rd,
                 double* g_Qfd, double* g_prm, void* stream);
 
+/* Checkpointed adjoint of ONE instance whose horizon T may exceed the handle's workspace
+ * (Sec. III-A, eq. ocp-lagrangian: the same gradients as ptn_adjoint).  Only the
+ * trajectory (x_star: (T+1) x nx, u_star: T x nu, device) is kept for the whole horizon;
+ * the horizon is taken in segments of seg_len steps (1 <= seg_len <= max_T * max_batch of
+ * the handle), and every segment's linearisations (Jacobians, Hessians, co-states) are
+ * recomputed from the trajectory in each of three sweeps over the segments: co-states and
+ * the adjoint LQR's value function backward, its states forward, its multipliers and the
+ * gradient contributions backward; the sweeps pass boundary values between segments.
+ * Segments use the CTA tier, or the cooperative grid from grid_min_T on.  Device memory
+ * beyond the handle's workspace: about (T / seg_len) (nx^2 + 4 nx) doubles, allocated and
+ * freed by the call.  gx, gu, outputs and errors as in ptn_adjoint; PTN_ERR_INVALID_ARG
+ * for nx >= 8 (the wide tier has no segmented form). */
+int ptn_adjoint_checkpointed(ptn_solver* s, int T, int seg_len, const double* x0, const double* xref,
+                             const double* x_star, const double* u_star, double mu, double gJ,
+                             const double* gx, const double* gu, double* g_x0, double* g_Qd,
+                             double* g_Rd, double* g_Qfd, double* g_prm, void* stream);
+
 /* Number of constraint rows nw of the handle's problem. */
 int ptn_num_rows(const ptn_solver* s);
 

@@ -743,6 +743,54 @@ extern "C" int ptn_solve_batch_async(ptn_solver* s, const double* x0, const doub
                  (cudaStream_t)stream);
 }
 
+// one adjoint launch (FP64 kernels): the CTA tier, one CTA per instance, or for one long
+// instance the cooperative grid, 128 threads per CTA, grid_steps_per_thread steps per
+// thread as far as the co-resident CTAs allow.  T0: the horizon of the first instance.
+static int launch_adjoint(ptn_solver* s, launch_fn fn, int B, int T0, const InstDev* dinst, const double* x0,
+                          const double* xref, const double* x_star, const double* u_star, const AdjArgs& aa,
+                          InfoDev* dinfo, cudaStream_t st) {
+  LaunchReq q{};
+  q.tier = 3;
+  q.precision = PTN_FP64;
+  q.stream = st;
+  q.w = s->w;
+  q.w.xA = const_cast<double*>(x_star);  // read only: the adjoint writes no trajectory
+  q.w.uA = const_cast<double*>(u_star);
+  q.args.prob = s->dprob;
+  q.args.opt = s->dopt;
+  q.args.inst = dinst;
+  q.args.x0 = x0;
+  q.args.xref = xref;
+  q.args.info = dinfo;
+  q.args.B = B;
+  q.adj = &aa;
+  q.nthreads = s->opt.block_threads;
+  q.nblocks = B;
+  if (B == 1 && s->n < 8 && s->opt.grid_min_T > 0 && T0 >= s->opt.grid_min_T) {
+    LaunchReq qq{};
+    int maxb = 0;
+    qq.tier = 7;
+    qq.precision = PTN_FP64;
+    qq.nthreads = 128;
+    qq.query = 1;
+    qq.max_blocks = &maxb;
+    CK(fn(qq));
+    const long long per = 128LL * s->opt.grid_steps_per_thread;
+    long long want = (T0 + per - 1) / per;
+    int nb = want < maxb ? (int)want : maxb;
+    if (nb > s->grid_cap_blocks) nb = s->grid_cap_blocks;
+    if (nb < 1) return fail(s, PTN_ERR_INVALID_ARG, "no co-resident CTA for the grid adjoint");
+    q.tier = 7;
+    q.nthreads = 128;
+    q.nblocks = nb;
+    q.args.gs = s->gs;
+    CK(cudaMemsetAsync(s->gs.bar, 0, 2 * sizeof(unsigned), st));
+    CK(cudaMemsetAsync(s->gs.err, 0, sizeof(int), st));
+  }
+  CK(fn(q));
+  return PTN_OK;
+}
+
 extern "C" int ptn_adjoint(ptn_solver* s, int B, const int* T_b, const double* x0, const double* xref,
                            const double* x_star, const double* u_star, double mu, double gJ, const double* gx,
                            const double* gu, double* g_x0, double* g_Qd, double* g_Rd, double* g_Qfd,
@@ -778,47 +826,8 @@ extern "C" int ptn_adjoint(ptn_solver* s, int B, const int* T_b, const double* x
   aa.mu = mu;
   aa.gJ = gJ;
   aa.g_x0 = g_x0; aa.g_Qd = g_Qd; aa.g_Rd = g_Rd; aa.g_Qfd = g_Qfd; aa.g_prm = g_prm;
-  LaunchReq q{};
-  q.tier = 3;
-  q.precision = PTN_FP64;
-  q.stream = st;
-  q.w = s->w;
-  q.w.xA = const_cast<double*>(x_star);  // read only: the adjoint writes no trajectory
-  q.w.uA = const_cast<double*>(u_star);
-  q.args.prob = s->dprob;
-  q.args.opt = s->dopt;
-  q.args.inst = s->dinst;
-  q.args.x0 = x0;
-  q.args.xref = xref;
-  q.args.info = s->dinfo;
-  q.args.B = B;
-  q.adj = &aa;
-  q.nthreads = s->opt.block_threads;
-  q.nblocks = B;
-  if (B == 1 && s->n < 8 && s->opt.grid_min_T > 0 && T_b[0] >= s->opt.grid_min_T) {
-    // one long instance: the cooperative grid, 128 threads per CTA, grid_steps_per_thread
-    // steps per thread as far as the co-resident CTAs allow
-    LaunchReq qq{};
-    int maxb = 0;
-    qq.tier = 7;
-    qq.precision = PTN_FP64;
-    qq.nthreads = 128;
-    qq.query = 1;
-    qq.max_blocks = &maxb;
-    CK(fn(qq));
-    const long long per = 128LL * s->opt.grid_steps_per_thread;
-    long long want = (T_b[0] + per - 1) / per;
-    int nb = want < maxb ? (int)want : maxb;
-    if (nb > s->grid_cap_blocks) nb = s->grid_cap_blocks;
-    if (nb < 1) return fail(s, PTN_ERR_INVALID_ARG, "no co-resident CTA for the grid adjoint");
-    q.tier = 7;
-    q.nthreads = 128;
-    q.nblocks = nb;
-    q.args.gs = s->gs;
-    CK(cudaMemsetAsync(s->gs.bar, 0, 2 * sizeof(unsigned), st));
-    CK(cudaMemsetAsync(s->gs.err, 0, sizeof(int), st));
-  }
-  CK(fn(q));
+  int rc = launch_adjoint(s, fn, B, T_b[0], s->dinst, x0, xref, x_star, u_star, aa, s->dinfo, st);
+  if (rc) return rc;
   CK(cudaMemcpyAsync(s->hinfo, s->dinfo, sizeof(InfoDev) * B, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   for (int i = 0; i < B; i++) {
@@ -828,6 +837,126 @@ extern "C" int ptn_adjoint(ptn_solver* s, int B, const int* T_b, const double* x
       return fail(s, PTN_ERR_NUMERICAL, "instance %d: the Hessian is not positive definite on the dynamics", i);
   }
   return PTN_OK;
+}
+
+// Checkpointed adjoint of one long horizon: segments of seg_len steps, each segment's
+// linearisations recomputed from the stored trajectory in each of the three sweeps of the
+// AdjSeg form (co-states and value function backward, LQR states forward, multipliers and
+// gradient shares backward); boundary values pass between segments in device buffers of
+// (segments + 1) entries, the gradient shares are summed on the host.
+extern "C" int ptn_adjoint_checkpointed(ptn_solver* s, int T, int seg_len, const double* x0, const double* xref,
+                                        const double* x_star, const double* u_star, double mu, double gJ,
+                                        const double* gx, const double* gu, double* g_x0, double* g_Qd,
+                                        double* g_Rd, double* g_Qfd, double* g_prm, void* stream_) {
+  if (!s) return PTN_ERR_INVALID_ARG;
+  s->err[0] = 0;
+  cudaStream_t st = (cudaStream_t)stream_;
+  if (T < 1) return fail(s, PTN_ERR_INVALID_ARG, "horizon T=%d must be >= 1", T);
+  if (seg_len < 1 || seg_len > s->cap_steps)
+    return fail(s, PTN_ERR_INVALID_ARG, "segment length %d outside [1, %lld] (the workspace)", seg_len, s->cap_steps);
+  if (!x0 || !x_star || !u_star) return fail(s, PTN_ERR_INVALID_ARG, "NULL argument");
+  if (!(mu > 0) || !isfinite(mu) || !isfinite(gJ)) return fail(s, PTN_ERR_INVALID_ARG, "mu must be positive, gJ finite");
+  if (s->n >= 8) return fail(s, PTN_ERR_INVALID_ARG, "the checkpointed adjoint is built for models with nx < 8");
+  launch_fn fn = pick_launcher(s->hprob.model, PTN_FP64);
+  if (!fn) return fail(s, PTN_ERR_INVALID_ARG, "FP64 kernels for model %d are not built", s->hprob.model);
+  const int n = s->n, m = s->m;
+  const int nseg = (int)(((long long)T + seg_len - 1) / seg_len);
+  const int KO = 3 * n + m + PTN_MAXP;  // x0, Qd, Rd, Qfd, prm shares of one segment
+  // device buffers: boundary values at the nseg + 1 segment ends, per-launch records and
+  // reports, per-segment gradient shares
+  const size_t nb = (size_t)nseg + 1;
+  const size_t o_lam = 0, o_S = o_lam + nb * n, o_s = o_S + nb * n * n, o_dx = o_s + nb * n, o_nu = o_dx + nb * n;
+  const size_t o_out = o_nu + nb * n, nd = o_out + (size_t)nseg * KO;
+  const int nl = 3 * nseg;
+  double* dbuf = nullptr;
+  AdjSeg* dseg = nullptr;
+  InstDev* dinst = nullptr;
+  InfoDev* dinfo = nullptr;
+  int rc = PTN_OK;
+  std::vector<AdjSeg> hseg(nl);
+  std::vector<InstDev> hinst(nseg);
+  std::vector<InfoDev> hinfo(nl);
+  std::vector<double> hout((size_t)nseg * KO), sum(KO, 0.0);
+  auto cleanup = [&]() { cudaFree(dbuf); cudaFree(dseg); cudaFree(dinst); cudaFree(dinfo); };
+  if (cudaMalloc(&dbuf, nd * sizeof(double)) != cudaSuccess || cudaMalloc(&dseg, nl * sizeof(AdjSeg)) != cudaSuccess ||
+      cudaMalloc(&dinst, nseg * sizeof(InstDev)) != cudaSuccess ||
+      cudaMalloc(&dinfo, nl * sizeof(InfoDev)) != cudaSuccess) {
+    cleanup();
+    return fail(s, PTN_ERR_CUDA, "device allocation for the checkpointed adjoint failed");
+  }
+  for (int k = 0; k < nseg; k++) {
+    const long long t0 = (long long)k * seg_len, t1 = t0 + seg_len < T ? t0 + seg_len : T;
+    hinst[k].T = (int)(t1 - t0);
+    hinst[k].xoff = 0;
+    hinst[k].uoff = 0;
+    hinst[k].pad = 0;
+    hinst[k].dt = 0.0;
+    for (int stg = 1; stg <= 3; stg++) {
+      AdjSeg& a = hseg[(size_t)(stg - 1) * nseg + k];
+      a = AdjSeg{};
+      a.stage = stg;
+      a.first = k == 0;
+      a.last = k == nseg - 1;
+      a.lam_end = dbuf + o_lam + (size_t)(k + 1) * n;
+      a.S_end = dbuf + o_S + (size_t)(k + 1) * n * n;
+      a.s_end = dbuf + o_s + (size_t)(k + 1) * n;
+      a.dx_start = dbuf + o_dx + (size_t)k * n;
+      a.nu_end = dbuf + o_nu + (size_t)(k + 1) * n;
+      a.lam_start = dbuf + o_lam + (size_t)k * n;
+      a.S_start = dbuf + o_S + (size_t)k * n * n;
+      a.s_start = dbuf + o_s + (size_t)k * n;
+      a.dx_end = dbuf + o_dx + (size_t)(k + 1) * n;
+      a.nu_start = dbuf + o_nu + (size_t)k * n;
+    }
+  }
+  CK(cudaMemcpyAsync(dseg, hseg.data(), nl * sizeof(AdjSeg), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(dinst, hinst.data(), nseg * sizeof(InstDev), cudaMemcpyHostToDevice, st));
+  CK(cudaMemsetAsync(dbuf, 0, nd * sizeof(double), st));
+  // sweep 1 backward, sweep 2 forward, sweep 3 backward
+  for (int stg = 1; stg <= 3 && rc == PTN_OK; stg++) {
+    for (int j = 0; j < nseg && rc == PTN_OK; j++) {
+      const int k = stg == 2 ? j : nseg - 1 - j;
+      const size_t l = (size_t)(stg - 1) * nseg + k;
+      const size_t xo = (size_t)k * seg_len * n, uo = (size_t)k * seg_len * m;
+      AdjArgs aa{};
+      aa.gx = gx ? gx + xo : nullptr;
+      aa.gu = gu ? gu + uo : nullptr;
+      aa.qx = s->w.xB;
+      aa.mu = mu;
+      aa.gJ = gJ;
+      aa.seg = dseg + l;
+      if (stg == 3) {
+        double* o = dbuf + o_out + (size_t)k * KO;
+        aa.g_x0 = o; aa.g_Qd = o + n; aa.g_Rd = o + 2 * n; aa.g_Qfd = o + 2 * n + m; aa.g_prm = o + 3 * n + m;
+      }
+      rc = launch_adjoint(s, fn, 1, hinst[k].T, dinst + k, x_star + xo, xref, x_star + xo, u_star + uo, aa,
+                          dinfo + l, st);
+    }
+  }
+  if (rc == PTN_OK) {
+    CK(cudaMemcpyAsync(hinfo.data(), dinfo, nl * sizeof(InfoDev), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(hout.data(), dbuf + o_out, (size_t)nseg * KO * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    for (int l = 0; l < nl && rc == PTN_OK; l++) {
+      if (hinfo[l].status == ST_ETIMEOUT) rc = fail(s, PTN_ERR_TIMEOUT, "a grid barrier wait expired");
+      else if (hinfo[l].status != 0)
+        rc = fail(s, PTN_ERR_NUMERICAL, "segment %d: the Hessian is not positive definite on the dynamics", l % nseg);
+    }
+  }
+  if (rc == PTN_OK) {
+    for (int k = 0; k < nseg; k++)
+      for (int i = 0; i < KO; i++) sum[i] += hout[(size_t)k * KO + i];
+    const double* h = sum.data();
+    if (g_x0) CK(cudaMemcpyAsync(g_x0, h, n * sizeof(double), cudaMemcpyHostToDevice, st));
+    if (g_Qd) CK(cudaMemcpyAsync(g_Qd, h + n, n * sizeof(double), cudaMemcpyHostToDevice, st));
+    if (g_Rd) CK(cudaMemcpyAsync(g_Rd, h + 2 * n, m * sizeof(double), cudaMemcpyHostToDevice, st));
+    if (g_Qfd) CK(cudaMemcpyAsync(g_Qfd, h + 2 * n + m, n * sizeof(double), cudaMemcpyHostToDevice, st));
+    if (g_prm) CK(cudaMemcpyAsync(g_prm, h + 3 * n + m, PTN_MAXP * sizeof(double), cudaMemcpyHostToDevice, st));
+    CK(cudaStreamSynchronize(st));
+  }
+  cudaStreamSynchronize(st);
+  cleanup();
+  return rc;
 }
 
 // ---------------------------------------------------------------------------

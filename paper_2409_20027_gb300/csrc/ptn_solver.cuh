@@ -469,15 +469,24 @@ __device__ void terminal_grad(const ProbS<N, U>& P, const double* xT, double* g)
 // pass 1: co-state suffix scan (Alg. 1).  Returns max_t |d_t|_inf (inf if not finite).
 //
 // Exact form (FP64): element (g, F^T) with F = I + E, E from FP64 forward-mode AD.
+//
+// lamT_in (optional): the co-state at t = T, where the horizon continues beyond T (a segment
+// of a longer horizon); otherwise the terminal co-state of eq. co-state-final.
 template <class M, class L, class Grp>
-__device__ double costate_exact(Grp& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>& P, const Aug& A) {
+__device__ double costate_exact(Grp& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>& P, const Aug& A,
+                                const double* lamT_in = nullptr) {
   constexpr int N = M::NX, U = M::NU;
   Aff<N, double> agg;
   set_identity(agg);
   double lamT[N];
   if (I.last) {
     // terminal co-state (eq. co-state-final): a constant map
-    terminal_grad(P, I.xn + (size_t)I.T * N, lamT);
+    if (lamT_in) {
+#pragma unroll
+      for (int i = 0; i < N; i++) lamT[i] = lamT_in[i];
+    } else {
+      terminal_grad(P, I.xn + (size_t)I.T * N, lamT);
+    }
 #pragma unroll
     for (int i = 0; i < N; i++) {
       agg.v[i] = lamT[i];
@@ -944,10 +953,13 @@ __device__ __noinline__ void mult_terms(int t, const L* dx, const double* qx, co
 //
 // fail (optional): a per-thread flag (0 or 1) reduced by maximum with G1, G2; on return
 // the group's flag (the value pass's factorisation result, without a reduction of its own).
+//
+// dx_in (optional): dx at t = 0 where the horizon started before (a segment of a longer
+// horizon); otherwise dx_0 = 0.
 template <class M, class L, class Grp>
 __device__ void state_pass(Grp& g, Inst<M, L>& I, double& G1, double& G2, const double* qx = nullptr,
                            const L* Sv = nullptr, const L* sv = nullptr, double* dnu = nullptr,
-                           double* fail = nullptr) {
+                           double* fail = nullptr, const L* dx_in = nullptr) {
   constexpr int N = M::NX, U = M::NU;
   Aff<N, L> agg;
   set_identity(agg);
@@ -955,6 +967,9 @@ __device__ void state_pass(Grp& g, Inst<M, L>& I, double& G1, double& G2, const 
   if (first) {
 #pragma unroll (N <= 8 ? N * N : 4)
     for (int i = 0; i < N * N; i++) agg.M[i] = L(0);  // the first element has F = 0
+    if (dx_in)
+#pragma unroll
+      for (int i = 0; i < N; i++) agg.v[i] = dx_in[i];  // ... and maps to dx_in
   }
   for (int t = I.a; t < I.b; t++) {
     L Fc[N * N], e[N], GG[N * N];
@@ -981,7 +996,7 @@ __device__ void state_pass(Grp& g, Inst<M, L>& I, double& G1, double& G2, const 
   Aff<N, L> inc = g.scan(agg, StateOp(), false, ok);
   L dx[N];
 #pragma unroll
-  for (int i = 0; i < N; i++) dx[i] = first ? L(0) : inc.v[i];
+  for (int i = 0; i < N; i++) dx[i] = first ? (dx_in ? dx_in[i] : L(0)) : inc.v[i];
   double g1 = 0.0, g2 = 0.0;
   for (int t = I.a; t < I.b; t++) {
     const L* G = I.Gm + (size_t)t * N * U;
@@ -1692,11 +1707,33 @@ __device__ bool initial_rollout_parallel(Grp& g, Inst<M, L>& I, const ProbS<M::N
 //   nu_T = q_T + P_T w_T,  nu_t = q_t + P_t w_t + M_t w_{u,t} + F_t^T nu_{t+1},  q = -gx,
 // come from a co-state-type scan; then dL/dtheta -= w^T d_theta(grad_z L) + nu^T d_theta f.
 // Outputs (per instance): g_x0 (N), g_Qd (N), g_Rd (U), g_Qfd (N), g_prm (PTN_MAXP).
+//
+// Checkpointed form (AdjSeg): a horizon longer than the workspace is taken in segments of
+// at most the workspace's length, and each segment's linearisations are recomputed from
+// the stored trajectory (the checkpoints x*, u*) in three sweeps over the segments:
+//   1 (backward)  co-states and the adjoint LQR's value function at the segment starts,
+//   2 (forward)   the adjoint LQR's state w_x at the segment ends,
+//   3 (backward)  its multipliers nu at the segment starts and the gradient contributions;
+// each sweep hands its boundary values to the next segment it visits.
+struct AdjSeg {
+  int stage;            // 1, 2 or 3
+  int first, last;      // this segment starts / ends the horizon
+  const double* lam_end;                   // co-state at the segment end (not last)
+  const double *S_end, *s_end;             // value function at the segment end (not last)
+  const double* dx_start;                  // w_x at the segment start (stages 2, 3; not first)
+  const double* nu_end;                    // nu at the segment end (stage 3; not last)
+  double* lam_start;                       // out, stage 1
+  double *S_start, *s_start;               // out, stage 1
+  double* dx_end;                          // out, stage 2
+  double* nu_start;                        // out, stage 3
+};
+
 struct AdjArgs {
   const double *gx, *gu;  // (sum T+1) x N, (sum T) x U, or NULL
   double* qx;             // workspace (sum T+1) x N (the linear terms -gx)
   double mu, gJ;
   double *g_x0, *g_Qd, *g_Rd, *g_Qfd, *g_prm;  // may be NULL
+  const AdjSeg* seg;      // checkpointed form: this launch's segment and stage, or NULL
 };
 
 template <int K, class Grp>
@@ -1719,7 +1756,7 @@ __device__ void group_sum(Grp& g, double* v) {
 // enough there even with iterative refinement).
 template <class M, class L, class Grp>
 __device__ void adjoint_nu_pass(Grp& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>& P, const double* qx,
-                                double* envp, double* adjp, double* nu0) {
+                                double* envp, double* adjp, double* nu0, const double* nuT_in = nullptr) {
   static_assert(std::is_same<L, double>::value, "the adjoint runs in FP64");
   constexpr int N = M::NX, U = M::NU, NP = M::NP;
   // c_t = q_t + P_t w_t + M_t w_{u,t}
@@ -1744,7 +1781,12 @@ __device__ void adjoint_nu_pass(Grp& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>
   set_identity(agg);
   double nuT[N];
   if (I.last) {
-    cterm(I.T, nuT);
+    if (nuT_in) {
+#pragma unroll
+      for (int i = 0; i < N; i++) nuT[i] = nuT_in[i];
+    } else {
+      cterm(I.T, nuT);
+    }
 #pragma unroll
     for (int i = 0; i < N; i++) {
       agg.v[i] = nuT[i];
@@ -1823,20 +1865,30 @@ __device__ void adjoint_env_params(Inst<M, L>& I, const ProbS<M::NX, M::NU>& P, 
   }
 }
 
-// returns ST_OK, or ST_ENUM when the Hessian is not positive definite on the dynamics
+// returns ST_OK, or ST_ENUM when the Hessian is not positive definite on the dynamics.
+// Checkpointed form (aa.seg): the passes of the segment's stage, with the boundary values
+// of the neighbouring segments in place of the horizon's ends; stages 1 and 2 only hand
+// on boundary values, stage 3 writes the segment's share of the outputs.
 template <class M, class L, class SV, class Grp>
 __device__ int adjoint_instance(Grp& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>& P, const AdjArgs& aa,
                                 const InstDev& id, int bi) {
   constexpr int N = M::NX, U = M::NU, NP = M::NP;
+  const AdjSeg* sg = aa.seg;
+  const int stage = sg ? sg->stage : 0;  // 0: the whole horizon in one launch
+  const bool seg_first = !sg || sg->first, seg_last = !sg || sg->last;
+  const bool owns0 = I.a == 0 && I.b > 0;  // this thread holds t = 0
   Aug A;
   A.kind = AUG_BARRIER; A.mu = aa.mu; A.rho = 1.0; A.z = nullptr; A.v = nullptr;
-  costate_exact(g, I, P, A);
+  costate_exact(g, I, P, A, seg_last ? nullptr : sg->lam_end);
   // lam_0 for the envelope term, read once the co-state pass has ended (its closing group
   // reduction orders the writes)
   double lam0[N];
 #pragma unroll
   for (int i = 0; i < N; i++) lam0[i] = I.lam[i];
-  const bool lin = aa.gx || aa.gu;
+  if (stage == 1 && owns0)
+#pragma unroll
+    for (int i = 0; i < N; i++) sg->lam_start[i] = lam0[i];
+  const bool lin = sg || aa.gx || aa.gu;
   // out = [x0 (N), Qd (N), Rd (U), Qfd (N), prm (NP)] accumulated per thread
   constexpr int KO = 3 * N + U + NP;
   double env[KO], adj[KO];
@@ -1854,7 +1906,7 @@ __device__ int adjoint_instance(Grp& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>
       env[2 * N + i] += e * e;
     }
   }
-  if (I.last) {
+  if (I.last && seg_last) {
 #pragma unroll
     for (int i = 0; i < N; i++) {
       const double e = I.xn[(size_t)I.T * N + i] - P.xref[i];
@@ -1866,7 +1918,8 @@ __device__ int adjoint_instance(Grp& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>
     adjoint_env_params(I, P, env + 3 * N + U);
   } else {
     quadratize(g, I, P, A);
-    // linear terms of the adjoint LQR: d_t = -gu_t, q_t = -gx_t
+    // linear terms of the adjoint LQR: d_t = -gu_t, q_t = -gx_t; a segment that does not
+    // end the horizon ends with the value function of the segment after it
     double* qx = aa.qx + (size_t)id.xoff * N;
     for (int t = I.a; t < I.b; t++) {
 #pragma unroll
@@ -1875,45 +1928,74 @@ __device__ int adjoint_instance(Grp& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>
       for (int i = 0; i < N; i++) qx[(size_t)t * N + i] = aa.gx ? -aa.gx[((size_t)id.xoff + t) * N + i] : 0.0;
     }
     if (I.last) {
+      if (seg_last) {
 #pragma unroll
-      for (int i = 0; i < N; i++) qx[(size_t)I.T * N + i] = aa.gx ? -aa.gx[((size_t)id.xoff + I.T) * N + i] : 0.0;
+        for (int i = 0; i < N; i++) qx[(size_t)I.T * N + i] = aa.gx ? -aa.gx[((size_t)id.xoff + I.T) * N + i] : 0.0;
+      } else {
+#pragma unroll
+        for (int i = 0; i < N; i++) qx[(size_t)I.T * N + i] = sg->s_end[i];
+#pragma unroll (N <= 8 ? N * N : 4)
+        for (int i = 0; i < N * N; i++) I.Pm[(size_t)I.T * N * N + i] = L(sg->S_end[i]);
+      }
     }
     // the value pass reads q of its own chunk and the terminal one, written by the same
     // thread, and its first group operation orders the rest
-    if (!value_pass<M, L, SV>(g, I, 0.0, qx)) {
+    if (!value_pass<M, L, SV>(g, I, 0.0, qx, stage == 1 ? I.Sv : nullptr, stage == 1 ? I.sv : nullptr)) {
       rc = ST_ENUM;
+    } else if (stage == 1) {
+      // the value function at the segment start, S_0 and s_0 (after the stage at t = 0)
+      if (owns0) {
+#pragma unroll (N <= 8 ? N * N : 4)
+        for (int i = 0; i < N * N; i++) sg->S_start[i] = double(I.Sv[i]);
+#pragma unroll
+        for (int i = 0; i < N; i++) sg->s_start[i] = double(I.sv[i]);
+      }
     } else {
       double G1, G2;
-      state_pass(g, I, G1, G2);  // dx = w_x, du = w_u
-      double nu0[N];
+      const L* dx_in = seg_first ? nullptr : sg->dx_start;
+      state_pass(g, I, G1, G2, (const double*)nullptr, (const L*)nullptr, (const L*)nullptr, (double*)nullptr,
+                 (double*)nullptr, dx_in);  // dx = w_x, du = w_u
+      if (stage == 2) {
+        if (I.last)
 #pragma unroll
-      for (int i = 0; i < N; i++) nu0[i] = 0.0;
-      adjoint_nu_pass(g, I, P, qx, env + 3 * N + U, adj + 3 * N + U, nu0);
+          for (int i = 0; i < N; i++) sg->dx_end[i] = double(I.dx[(size_t)I.T * N + i]);
+      } else {
+        double nu0[N];
 #pragma unroll
-      for (int i = 0; i < N; i++) adj[i] = nu0[i];
-      for (int t = I.a; t < I.b; t++) {
+        for (int i = 0; i < N; i++) nu0[i] = 0.0;
+        adjoint_nu_pass(g, I, P, qx, env + 3 * N + U, adj + 3 * N + U, nu0, seg_last ? nullptr : sg->nu_end);
+        if (stage == 3 && owns0)
 #pragma unroll
-        for (int i = 0; i < N; i++)
-          adj[N + i] += double(I.dx[(size_t)t * N + i]) * 2.0 * (I.xn[(size_t)t * N + i] - P.xref[i]);
+          for (int i = 0; i < N; i++) sg->nu_start[i] = nu0[i];
+        // dJ/dx0 takes nu_0 of the horizon's first step only
 #pragma unroll
-        for (int i = 0; i < U; i++)
-          adj[2 * N + i] += double(I.du[(size_t)t * U + i]) * 2.0 * (I.un[(size_t)t * U + i] - P.uref[i]);
-      }
-      if (I.last) {
+        for (int i = 0; i < N; i++) adj[i] = seg_first ? nu0[i] : 0.0;
+        for (int t = I.a; t < I.b; t++) {
 #pragma unroll
-        for (int i = 0; i < N; i++)
-          adj[2 * N + U + i] =
-              double(I.dx[(size_t)I.T * N + i]) * 2.0 * (I.xn[(size_t)I.T * N + i] - P.xref[i]);
+          for (int i = 0; i < N; i++)
+            adj[N + i] += double(I.dx[(size_t)t * N + i]) * 2.0 * (I.xn[(size_t)t * N + i] - P.xref[i]);
+#pragma unroll
+          for (int i = 0; i < U; i++)
+            adj[2 * N + i] += double(I.du[(size_t)t * U + i]) * 2.0 * (I.un[(size_t)t * U + i] - P.uref[i]);
+        }
+        if (I.last && seg_last) {
+#pragma unroll
+          for (int i = 0; i < N; i++)
+            adj[2 * N + U + i] =
+                double(I.dx[(size_t)I.T * N + i]) * 2.0 * (I.xn[(size_t)I.T * N + i] - P.xref[i]);
+        }
       }
     }
   }
+  if (stage == 1 || stage == 2) return rc;
   double out[KO];
 #pragma unroll
   for (int i = 0; i < KO; i++) out[i] = (i < N ? 0.0 : aa.gJ * env[i]) - adj[i];  // x0: lam_0 below
   group_sum<KO>(g, out);  // also orders the co-state writes before lam_1 is read
   if (g.rank() == 0) {
+    if (seg_first)
 #pragma unroll
-    for (int i = 0; i < N; i++) out[i] += aa.gJ * lam0[i];
+      for (int i = 0; i < N; i++) out[i] += aa.gJ * lam0[i];
     if (aa.g_x0)
       for (int i = 0; i < N; i++) aa.g_x0[(size_t)bi * N + i] = out[i];
     if (aa.g_Qd)

@@ -52,21 +52,22 @@ struct WModel<Synth> {
     __syncwarp();
   }
 
+  // wrk: N x N values of L of the warp's scratch
   template <class L>
   __device__ static void hess(const ProbS<N, U>& P, const double* x, const double* u, const double* lam, L* Hxx,
-                              L* Hxu, L* Huu, double* tmp) {
+                              L* Hxu, L* Huu, double* tmp, L* wrk) {
     (void)u;
     const int l = wops::lane_id();
     const double t = row_tanh(P, x);
     const double wk = (l < N) ? P.prm[0] * lam[l] * (-2.0 * t * (1.0 - t * t)) : 0.0;
     if constexpr (std::is_same<L, float>::value) {
+      // Hxx = W^T (diag(w) W): the scaled rows in wrk, the product on the tensor cores
       float* wf = reinterpret_cast<float*>(tmp);
       if (l < N) wf[l] = float(wk);
       __syncwarp();
-      for (int e = l; e < N * N; e += 32) {
-        const int i = e / N, j = e % N;
-        Hxx[e] = wops::dot4<N, float>([&](int k) { return P.W32[k * N + i] * wf[k] * P.W32[k * N + j]; });
-      }
+      for (int e = l; e < N * N; e += 32) wrk[e] = wf[e / N] * P.W32[e];
+      __syncwarp();
+      wops::mm<N, N, N, true, false>(P.W32, wrk, Hxx);
     } else {
       if (l < N) tmp[l] = wk;
       __syncwarp();

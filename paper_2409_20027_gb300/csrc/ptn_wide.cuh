@@ -184,10 +184,11 @@ struct WModel {
     (void)tmp;
     wops::step_jac<M, S>(P.integ, P.dt, P.prm, x, u, F, G);
   }
+  // wrk: N x N values of L of the warp's scratch (models with closed forms use it)
   template <class L>
   __device__ static void hess(const ProbS<N, U>& P, const double* x, const double* u, const double* lam, L* Hxx,
-                              L* Hxu, L* Huu, double* tmp) {
-    (void)tmp;
+                              L* Hxu, L* Huu, double* tmp, L* wrk) {
+    (void)tmp; (void)wrk;
     wops::step_hess<M, L>(P.integ, P.dt, P.prm, x, u, lam, Hxx, Hxu, Huu);
   }
   // xn = f(x, u) in FP64 (x, u, xn in shared memory; xn must not alias x)
@@ -922,7 +923,7 @@ __device__ void quadratize(WideGroup& g, Inst<M, L>& I, const ProbS<M::NX, M::NU
     const double* x = I.xn + (size_t)t * N;
     const double* u = I.un + (size_t)t * U;
     const double* lam1 = (t + 1 == I.b) ? I.lamb : I.lam + (size_t)(t + 1) * N;
-    WModel<M>::hess(P, x, u, lam1, s->Pm, s->Mm, s->Rm, s->mdl);
+    WModel<M>::hess(P, x, u, lam1, s->Pm, s->Mm, s->Rm, s->mdl, s->T1);
     wide::stage_hess_add_w<N, U, L>(P, A, x, u, s->Pm, s->Rm, s->gr);
     for (int e = l; e < N * N; e += 32) I.Pm[(size_t)t * N * N + e] = s->Pm[e];
     for (int e = l; e < N * U; e += 32) I.Mm[(size_t)t * N * U + e] = s->Mm[e];

@@ -26,7 +26,7 @@ STATUS = {0: "ok", -1: "invalid argument", -2: "infeasible start", -3: "not conv
 EXPORTS = ["ptn_default_options", "ptn_solver_create", "ptn_solver_destroy", "ptn_last_error",
            "ptn_set_options", "ptn_solve_ip", "ptn_solve_admm", "ptn_solve_batch", "ptn_adjoint",
            "ptn_num_rows", "ptn_version", "ptn_solve_ip_static", "ptn_batch_prepare",
-           "ptn_solve_batch_async", "ptn_model_dims"]
+           "ptn_solve_batch_async", "ptn_model_dims", "ptn_adjoint_checkpointed"]
 
 _P = C.POINTER(C.c_double)
 
@@ -95,6 +95,8 @@ def load(path: str = LIB_PATH):
                                          C.POINTER(Info), vp]
         lib.ptn_adjoint.argtypes = [vp, C.c_int, ip, vp, vp, vp, vp, C.c_double, C.c_double, vp, vp, vp, vp,
                                     vp, vp, vp, vp]
+        lib.ptn_adjoint_checkpointed.argtypes = [vp, C.c_int, C.c_int, vp, vp, vp, vp, C.c_double, C.c_double, vp,
+                                                 vp, vp, vp, vp, vp, vp, vp]
         lib.ptn_num_rows.argtypes = [vp]
         lib.ptn_solve_ip_static.argtypes = [C.POINTER(Problem), C.POINTER(Options), vp, vp, C.c_int, vp, vp, vp,
                                             C.POINTER(Info), C.c_char_p, C.c_int, vp]
@@ -314,6 +316,25 @@ class Solver:
                                 _dptr(out["prm"]), _stream(stream))
         if rc != 0:
             raise PtnError(f"ptn_adjoint failed ({rc}): {self.last_error()}")
+        return out
+
+    def adjoint_checkpointed(self, T: int, seg_len: int, x0, x_star, u_star, mu: float, gJ: float = 1.0, gx=None,
+                             gu=None, xref=None, stream=None):
+        """adjoint() of one instance whose horizon T may exceed the workspace: segments of
+        seg_len steps, linearisations recomputed from the trajectory in each sweep."""
+        import torch
+        dev = x_star.device
+        out = {k: torch.zeros((1, c), dtype=torch.float64, device=dev)
+               for k, c in [("x0", self.nx), ("Qd", self.nx), ("Rd", self.nu), ("Qfd", self.nx), ("prm", 8)]}
+        for a, rows, cols in [(x_star, T + 1, self.nx), (u_star, T, self.nu), (gx, T + 1, self.nx), (gu, T, self.nu)]:
+            if a is not None and (a.numel() != rows * cols or not a.is_contiguous() or a.device != dev):
+                raise ValueError("x_star, u_star, gx, gu: contiguous (T+1) x nx / T x nu on the solver's device")
+        rc = load().ptn_adjoint_checkpointed(self._h, int(T), int(seg_len), _dptr(x0), _dptr(xref), _dptr(x_star),
+                                             _dptr(u_star), float(mu), float(gJ), _dptr(gx), _dptr(gu),
+                                             _dptr(out["x0"]), _dptr(out["Qd"]), _dptr(out["Rd"]),
+                                             _dptr(out["Qfd"]), _dptr(out["prm"]), _stream(stream))
+        if rc != 0:
+            raise PtnError(f"ptn_adjoint_checkpointed failed ({rc}): {self.last_error()}")
         return out
 
 

@@ -126,3 +126,43 @@ def test_grid_adjoint_long_horizon_matches_oracle(ptn, with_traj):
         g, c = grid[k][0].cpu().numpy(), cta[k][0].cpu().numpy()
         assert rel(g, ref[k]) <= 1e-6, (k, g, ref[k])
         assert rel(g, c) <= 1e-9, (k, g, c)
+
+
+@pytest.mark.parametrize("T,seg,grid_min_T,with_traj", [(300, 64, 0, True), (300, 64, 0, False),
+                                                         (4096, 1000, 512, True)],
+                         ids=["cta-traj", "cta-J_only", "grid-traj"])
+def test_checkpointed_adjoint_matches_oracle(ptn, T, seg, grid_min_T, with_traj):
+    # a horizon that does not fit the handle's workspace (seg_len steps): segments of
+    # seg_len steps with a shorter last one, linearisations recomputed from the trajectory
+    # in each sweep; against the oracle's adjoint and the whole-horizon GPU adjoint
+    p = W.cartpole(T=T, horizon=2.56)
+    x0 = W.cartpole_x0(4)
+    whole = ptn.Solver(p, max_T=T, precision=0, cluster_max_blocks=0)
+    x, u, _, infos = whole.solve_batch(dev(x0).reshape(1, -1), [T])
+    assert infos[0]["status"] == 0
+    mu = infos[0]["mu"]
+    rng = np.random.default_rng(5)
+    gx = rng.standard_normal((T + 1, 4)) if with_traj else None
+    gu = rng.standard_normal((T, 1)) if with_traj else None
+    gJ = 0.7
+    s = ptn.Solver(p, max_T=seg, precision=0, grid_min_T=grid_min_T, cluster_max_blocks=0)
+    got = s.adjoint_checkpointed(T, seg, dev(x0), x, u, mu, gJ, None if gx is None else dev(gx),
+                                 None if gu is None else dev(gu))
+    one = whole.adjoint([T], dev(x0).reshape(1, -1), x, u, mu, gJ, None if gx is None else dev(gx),
+                        None if gu is None else dev(gu))
+    ref = O.adjoint(p, mu, x.cpu().numpy(), u.cpu().numpy(), gJ, gx, gu)
+    assert ref["status"] == 0
+    for k in KEYS:
+        g, w = got[k][0].cpu().numpy(), one[k][0].cpu().numpy()
+        assert rel(g, ref[k]) <= 1e-6, (k, g, ref[k])
+        assert rel(g, w) <= 1e-9, (k, g, w)
+
+
+def test_checkpointed_adjoint_refuses_bad_segments(ptn):
+    p = W.cartpole(T=64, horizon=2.56)
+    s = ptn.Solver(p, max_T=32, precision=0)
+    x = torch.zeros((65, 4), dtype=torch.float64, device="cuda:0")
+    u = torch.zeros((64, 1), dtype=torch.float64, device="cuda:0")
+    for seg in [0, 33]:
+        with pytest.raises(ptn.PtnError):
+            s.adjoint_checkpointed(64, seg, x[0], x, u, 1e-3)
