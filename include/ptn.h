@@ -85,7 +85,11 @@ typedef struct ptn_options {
   int admm_fixed_iters; /* > 0: run exactly this many ADMM iterations */
   int roll_max_iter;    /* multiple-shooting Newton iterations per rollout */
   int block_threads;    /* threads per CTA when one CTA solves one instance */
-  int grid_min_T;       /* single solves with T >= grid_min_T use all SMs (0: never) */
+  int grid_min_T;       /* single solves with T >= grid_min_T use all SMs (0: never); with
+                           grid_min_T > 0, batches of a model with nx >= 8 also use every
+                           co-resident CTA of one cooperative launch, a contiguous CTA range
+                           per instance sized by its horizon (when one CTA per instance
+                           fits), else one CTA per instance */
   int grid_steps_per_thread;
   int polish_after;     /* FP32 modes: exact FP64 gradients after this many iterations of
                            the final barrier level or an ADMM sub-problem, and of an

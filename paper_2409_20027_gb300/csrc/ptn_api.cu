@@ -380,7 +380,7 @@ extern "C" int ptn_solver_create(const ptn_problem* prob, const ptn_options* opt
   s->w.q = (double*)(b + o_q); s->w.dnu = (double*)(b + o_dnu); s->w.Sv = b + o_Sv; s->w.sv = b + o_sv;
   // grid-tier scratch, sized for 4 co-resident blocks per SM
   s->grid_cap_blocks = 4 * s->num_sms;
-  CK(cudaMalloc(&s->gs.bar, 2 * sizeof(unsigned)));
+  CK(cudaMalloc(&s->gs.bar, 2 * sizeof(unsigned) * max_batch));  // a counter pair per instance (wide batches)
   CK(cudaMalloc(&s->gs.err, sizeof(int)));
   CK(cudaMalloc(&s->gs.red, sizeof(double) * 2 * 8 * s->grid_cap_blocks));
   size_t eb = 0;
@@ -454,6 +454,45 @@ static int fill_instances(ptn_solver* s, int B, const int* T_b, const double* dt
 // Choose the execution tier and launch shape of a solve of B instances (host-side
 // occupancy queries only, no stream work) and set the kernel's function attributes for
 // it, so that the launch itself needs no other runtime call.
+// Wide batch on every co-resident CTA (tier 8): instance i gets a contiguous range of n_i
+// CTAs, first CTA in hinst[i].pad, n_i >= 1 and grown one at a time for the instance with
+// the most steps per warp (n_i warps no more than its steps).  Returns false (tier 4 is
+// used) when the batch does not fit one CTA per instance in one cooperative launch.
+static bool wide_batch_ranges(ptn_solver* s, launch_fn fn, int B, const int* T_b, int threads, LaunchPlan* p) {
+  LaunchReq q{};
+  int maxb = 0;
+  q.tier = 8;
+  q.precision = s->opt.precision;
+  q.nthreads = threads;
+  q.query = 1;
+  q.max_blocks = &maxb;
+  if (fn(q) != cudaSuccess) return false;
+  if (maxb > s->grid_cap_blocks) maxb = s->grid_cap_blocks;
+  if (B > maxb) return false;
+  const int nw = threads / 32;
+  std::vector<int> n(B, 1);
+  for (int extra = maxb - B; extra > 0; extra--) {
+    int best = -1;
+    double key = 0.0;
+    for (int i = 0; i < B; i++) {
+      if ((long long)(n[i] + 1) * nw > T_b[i]) continue;  // every warp keeps a step
+      const double k = (double)T_b[i] / n[i];
+      if (k > key) { key = k; best = i; }
+    }
+    if (best < 0) break;
+    n[best]++;
+  }
+  int c = 0;
+  for (int i = 0; i < B; i++) {
+    s->hinst[i].pad = c;
+    c += n[i];
+  }
+  p->tier = 8;
+  p->nthreads = threads;
+  p->nblocks = c;
+  return true;
+}
+
 static int plan_launch(ptn_solver* s, int method, int B, const int* T_b, long long steps, LaunchPlan* p) {
   launch_fn fn = pick_launcher(s->hprob.model, s->opt.precision);
   if (!fn) return fail(s, PTN_ERR_INVALID_ARG, "kernels for model %d, precision %d are not built", s->hprob.model, s->opt.precision);
@@ -517,6 +556,8 @@ static int plan_launch(ptn_solver* s, int method, int B, const int* T_b, long lo
     if (nb > s->grid_cap_blocks) nb = s->grid_cap_blocks;
     if (nb < 1) return fail(s, PTN_ERR_INVALID_ARG, "no co-resident CTA for the wide grid tier");
     p->nblocks = nb;
+  } else if (wide && B > 1 && s->opt.grid_min_T > 0 && wide_batch_ranges(s, fn, B, T_b, wide_threads, p)) {
+    // tier 8 planned: CTA ranges per instance in hinst[].pad
   } else if (wide) {
     p->tier = 4;
     p->nthreads = wide_threads;
@@ -580,9 +621,9 @@ static int enqueue(ptn_solver* s, const LaunchPlan& p, const OptDev* dopt, const
   q.args.u_init = u_init;
   q.args.info = dinfo;
   q.args.B = p.B;
-  if (p.tier == 1 || p.tier == 6) {
+  if (p.tier == 1 || p.tier == 6 || p.tier == 8) {
     q.args.gs = s->gs;
-    CK(cudaMemsetAsync(s->gs.bar, 0, 2 * sizeof(unsigned), st));
+    CK(cudaMemsetAsync(s->gs.bar, 0, 2 * sizeof(unsigned) * (p.tier == 8 ? p.B : 1), st));
     CK(cudaMemsetAsync(s->gs.err, 0, sizeof(int), st));
   }
   CK(p.fn(q));

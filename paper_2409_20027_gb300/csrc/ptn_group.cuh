@@ -404,12 +404,14 @@ struct GridScratch {
   int pad;
 };
 
-__device__ __forceinline__ bool grid_barrier(const GridScratch& gs) {
+// count: the CTAs that take part (all of the launch, or the CTA range of one instance
+// with its own counters)
+__device__ __forceinline__ bool grid_barrier(const GridScratch& gs, unsigned count) {
   volatile unsigned* gen = gs.bar + 1;
   const unsigned g0 = *gen;
   __threadfence();
   const unsigned arrived = atomicAdd(gs.bar, 1u);
-  if (arrived == gridDim.x - 1) {
+  if (arrived == count - 1) {
     atomicExch(gs.bar, 0u);
     __threadfence();
     atomicAdd(gs.bar + 1, 1u);
@@ -440,7 +442,7 @@ struct GridGroup {
   __device__ void sync() {
     __syncthreads();
     if (threadIdx.x == 0 && !*sdead) {
-      if (!grid_barrier(gs)) *sdead = 1;
+      if (!grid_barrier(gs, gridDim.x)) *sdead = 1;
     }
     __syncthreads();
   }

@@ -45,7 +45,8 @@ struct LaunchReq {
   int tier;       // 0: one CTA per instance, 1: cooperative grid, 2: one cluster on one instance,
                   // 3: adjoint, one CTA per instance, 4: wide (n >= 8, one warp per chunk),
                   // 5: sequential-in-time baseline (one thread per instance), 6: wide on the
-                  // cooperative grid (one instance), 7: adjoint of one instance on the grid
+                  // cooperative grid (one instance), 7: adjoint of one instance on the grid,
+                  // 8: wide batch on a cooperative grid, a CTA range per instance
   int precision;  // 0: FP64, 1: FP32 with FP64 solves, 2: FP32
   int nblocks, nthreads;
   int query;      // 1: only report max co-resident grid blocks in *max_blocks;

@@ -17,10 +17,11 @@ namespace ptn {
 
 // ---------------------------------------------------------------------------
 // group: one warp per time chunk.  One CTA per instance (rank = warp, size = warps of the
-// CTA), or, with grid set, every warp of a cooperative launch on one instance (rank =
-// blockIdx.x * warps per CTA + warp): barriers and reductions then also cross the CTAs
-// (bounded grid barrier, as GridGroup), and a scan ends with a Kogge-Stone over the CTA
-// totals in global memory (scan_grid).
+// CTA), or, with grid set, the warps of the CTA range [b0, b0 + nb) of a cooperative launch
+// on one instance (rank = (blockIdx.x - b0) * warps per CTA + warp; the whole launch for a
+// single instance, one range per instance for a batch): barriers and reductions then also
+// cross the range's CTAs (bounded barrier on the instance's own counters), and a scan ends
+// with a Kogge-Stone over the CTA totals in global memory (scan_warps).
 struct WideGroup {
   char* scr;         // per-warp scratch, warp w at scr + w * scr_bytes
   size_t scr_bytes;
@@ -28,20 +29,22 @@ struct WideGroup {
   size_t xs_bytes;
   double* red;       // 8 doubles per warp, then 8 for the grid result
   int grid;          // nonzero: the cooperative-grid form
-  GridScratch gs;    // grid form: barrier, reduction slots, 2 x nblocks CTA-total slots
+  int b0, nb;        // grid form: the group's CTAs blockIdx.x in [b0, b0 + nb)
+  GridScratch gs;    // grid form: barrier, reduction slots, 2 x nb CTA-total slots (the group's own)
   int* sdead;        // grid form: shared flag, this CTA saw a barrier expire
   int phase;
 
   __device__ int warp() const { return threadIdx.x >> 5; }
   __device__ int nwarps() const { return blockDim.x >> 5; }
-  __device__ int rank() const { return grid ? (int)blockIdx.x * nwarps() + warp() : warp(); }
-  __device__ int size() const { return grid ? (int)gridDim.x * nwarps() : nwarps(); }
+  __device__ int blk() const { return (int)blockIdx.x - b0; }
+  __device__ int rank() const { return grid ? blk() * nwarps() + warp() : warp(); }
+  __device__ int size() const { return grid ? nb * nwarps() : nwarps(); }
   __device__ bool dead() const { return grid && *(volatile int*)sdead != 0; }
   __device__ void sync() {
     __syncthreads();
     if (grid) {
       if (threadIdx.x == 0 && !*sdead) {
-        if (!grid_barrier(gs)) *sdead = 1;
+        if (!grid_barrier(gs, (unsigned)nb)) *sdead = 1;
       }
       __syncthreads();
     }
@@ -66,10 +69,10 @@ struct WideGroup {
       v[k] = a;
     }
     if (!grid) return;
-    double* rs = gs.red + (size_t)phase * gridDim.x * 8;
+    double* rs = gs.red + (size_t)phase * nb * 8;
     if (threadIdx.x == 0)
 #pragma unroll
-      for (int k = 0; k < K; k++) rs[blockIdx.x * 8 + k] = v[k];
+      for (int k = 0; k < K; k++) rs[blk() * 8 + k] = v[k];
     sync();
     double* sres = red + 8 * nw;
     if (threadIdx.x < 32) {
@@ -77,7 +80,7 @@ struct WideGroup {
       double a[K];
 #pragma unroll
       for (int k = 0; k < K; k++) a[k] = ((maxmask >> k) & 1u) ? -INFINITY : 0.0;
-      for (int b = lane; b < (int)gridDim.x; b += 32)
+      for (int b = lane; b < nb; b += 32)
 #pragma unroll
         for (int k = 0; k < K; k++) {
           const double o = __ldcg(rs + (size_t)b * 8 + k);
@@ -616,7 +619,7 @@ __device__ int scan_warps(WideGroup& g, const Op& op, bool suffix, bool& ok) {
     cur ^= 1;
   }
   if (!g.grid) return cur;
-  const int nb = gridDim.x, b = blockIdx.x;
+  const int nb = g.nb, b = g.blk();
   auto gslot = [&](int buf, int i) {
     return reinterpret_cast<E*>(g.gs.xs + ((size_t)buf * nb + i) * g.gs.elem_bytes);
   };
@@ -1344,6 +1347,8 @@ __global__ void __launch_bounds__(WideMaxThreads<M>::value) k_solve_wide_grid(KA
   WideGroup g{};
   wide_layout<M, L>(g, smem);
   g.grid = 1;
+  g.b0 = 0;
+  g.nb = (int)gridDim.x;
   g.gs = args.gs;
   g.sdead = &sdead;
   g.phase = 0;
@@ -1353,6 +1358,45 @@ __global__ void __launch_bounds__(WideMaxThreads<M>::value) k_solve_wide_grid(KA
   Inst<M, L> I;
   I.setup(w, id, args.x0, g.rank(), g.size(), P.nw);
   solve_instance<M, L, SV>(g, I, P, O, args.u_init, args.info);
+}
+
+// a batch on every co-resident CTA of a cooperative launch: instance i on the CTA range
+// [inst[i].pad, inst[i + 1].pad) (the host sizes the ranges in proportion to the horizons),
+// with its own barrier counters and scan and reduction slots: a segment of args.gs at
+// offsets 2 i (counters), 2 x 8 x first CTA (reduction slots) and 2 x first CTA (element
+// slots)
+template <class M, class L, class SV>
+__global__ void __launch_bounds__(WideMaxThreads<M>::value) k_solve_wide_bgrid(KArgs args, Work<L> w) {
+  constexpr int N = M::NX, U = M::NU;
+  extern __shared__ __align__(16) char smem[];
+  ProbS<N, U>& P = *reinterpret_cast<ProbS<N, U>*>(smem);
+  __shared__ int sdead;
+  if (threadIdx.x == 0) sdead = 0;
+  // the instance whose range holds this CTA: the last i with inst[i].pad <= blockIdx.x
+  int lo = 0, hi = args.B - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (args.inst[mid].pad <= (int)blockIdx.x) lo = mid;
+    else hi = mid - 1;
+  }
+  const int bi = lo;
+  const InstDev id = args.inst[bi];
+  WideGroup g{};
+  wide_layout<M, L>(g, smem);
+  g.grid = 1;
+  g.b0 = id.pad;
+  g.nb = (bi + 1 < args.B ? args.inst[bi + 1].pad : (int)gridDim.x) - id.pad;
+  g.gs = args.gs;
+  g.gs.bar = args.gs.bar + 2 * bi;
+  g.gs.red = args.gs.red + (size_t)2 * 8 * id.pad;
+  g.gs.xs = args.gs.xs + (size_t)2 * id.pad * args.gs.elem_bytes;
+  g.sdead = &sdead;
+  g.phase = 0;
+  load_prob<N, U>(P, *args.prob, args.xref ? args.xref + (size_t)bi * N : nullptr, id.dt);
+  const OptDev& O = *args.opt;
+  Inst<M, L> I;
+  I.setup(w, id, args.x0 + (size_t)bi * N, g.rank(), g.size(), P.nw);
+  solve_instance<M, L, SV>(g, I, P, O, args.u_init ? args.u_init + (size_t)id.uoff * U : nullptr, args.info + bi);
 }
 
 // ---------------------------------------------------------------------------
@@ -1675,6 +1719,33 @@ cudaError_t launch_wide(LaunchReq& q) {
     cfg.attrs = at;
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, k_solve_wide_grid<M, L, SV>, q.args, typed<L>(q.w));
+  }
+  if (q.tier == 8) {
+    if (!q.attrs_set) {
+      cudaError_t e = raise_smem_limit<k_solve_wide_bgrid<M, L, SV>>(smem);
+      if (e != cudaSuccess) return e;
+    }
+    if (q.query == 2) return cudaSuccess;
+    if (q.query == 1) {
+      int per = 0, sms = 0;
+      cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_solve_wide_bgrid<M, L, SV>,
+                                                                              q.nthreads, smem);
+      if (e != cudaSuccess) return e;
+      *q.max_blocks = per * sms;
+      return cudaSuccess;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(q.nblocks);
+    cfg.blockDim = dim3(q.nthreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = q.stream;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_solve_wide_bgrid<M, L, SV>, q.args, typed<L>(q.w));
   }
   if (q.query == 1) {
     if (q.max_blocks) *q.max_blocks = 0;

@@ -99,11 +99,13 @@ def test_synth_T1024_multiplier_form_matches_oracle(ptn, refs, tier):
     check(info, refs(("s1024", T, 0, 1)), x, u, lam, FP32_TOL)
 
 
-def test_synth_batch_matches_oracle(ptn, refs):
+@pytest.mark.parametrize("grid_min_T", [0, 512], ids=["cta_per_instance", "cta_ranges"])
+def test_synth_batch_matches_oracle(ptn, refs, grid_min_T):
+    # one CTA per instance, or the cooperative launch with a CTA range per instance
     Tb = np.array([256, 200], dtype=np.int32)
     ks = [0, 4]
     s = ptn.Solver(W.synth(0), max_T=256, max_batch=2, precision=ptn.PTN_FP32_FP64SOLVE, costate_mode=1,
-                   tol_final=TOL)
+                   tol_final=TOL, grid_min_T=grid_min_T)
     X, U, Lm, infos = s.solve_batch(dev(np.stack([W.synth_x0(k) for k in ks])), Tb)
     xo = uo = 0
     for b, (T, k) in enumerate(zip(Tb.tolist(), ks)):

@@ -43,15 +43,16 @@ def check(info, ref, x, u, tol=TOL):
     assert info["r_stat"] <= 1e-6 and info["r_dyn"] <= 1e-6 and info["r_feas"] == 0.0
 
 
-@pytest.mark.parametrize("threads", [128, 256])
-def test_quadrotor_batch_matches_oracle(ptn, threads):
-    # ragged horizons, including ones shorter than the number of warps (empty chunks)
+@pytest.mark.parametrize("threads,grid_min_T", [(128, 512), (256, 512), (128, 0)])
+def test_quadrotor_batch_matches_oracle(ptn, threads, grid_min_T):
+    # ragged horizons, including ones shorter than the number of warps (empty chunks);
+    # a CTA range per instance of one cooperative launch (grid_min_T > 0), or one CTA each
     Tb = np.array([32, 3, 64, 17], dtype=np.int32)
     B = len(Tb)
     wps = W.quadrotor_waypoints(B, 1)
     base = W.quadrotor()
     xrefs = np.stack([W.quadrotor(wps[b]).xref for b in range(B)])
-    s = ptn.Solver(base, max_T=int(Tb.max()), max_batch=B, block_threads=threads)
+    s = ptn.Solver(base, max_T=int(Tb.max()), max_batch=B, block_threads=threads, grid_min_T=grid_min_T)
     u0 = np.concatenate([hover(int(T)) for T in Tb])
     X, U, Lm, infos = s.solve_batch(dev(np.zeros((B, 12))), Tb, xref=dev(xrefs), u_init=dev(u0))
     X, U = X.cpu().numpy(), U.cpu().numpy()
