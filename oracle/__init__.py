@@ -54,7 +54,8 @@ class _Problem(C.Structure):
     _fields_ = [("model", C.c_int), ("nx", C.c_int), ("nu", C.c_int), ("integrator", C.c_int),
                 ("dt", C.c_double), ("prm", C.c_double * MAXP),
                 ("A", _P), ("B", _P), ("W", _P), ("Q", _P), ("R", _P), ("Qf", _P),
-                ("xref", _P), ("uref", _P), ("xlo", _P), ("xhi", _P), ("ulo", _P), ("uhi", _P)]
+                ("xref", _P), ("uref", _P), ("xref_traj", _P), ("uref_traj", _P), ("T_traj", C.c_int),
+                ("xlo", _P), ("xhi", _P), ("ulo", _P), ("uhi", _P)]
 
 
 class _Options(C.Structure):
@@ -132,9 +133,11 @@ def _ptr(a):
 
 
 class _Bound:
-    """Keeps the numpy arrays referenced by a C problem struct alive."""
+    """Keeps the numpy arrays referenced by a C problem struct alive.  T: the horizon of
+    a call that evaluates costs (time-varying targets, (T+1) x nx and T x nu, are bound
+    and checked against it); without T they are not bound (model-only calls)."""
 
-    def __init__(self, prob):
+    def __init__(self, prob, T=None):
         self.keep = []
         c = _Problem()
         c.model, c.nx, c.nu = int(prob.model), int(prob.nx), int(prob.nu)
@@ -150,6 +153,19 @@ class _Bound:
                 setattr(c, name, None)
             else:
                 a = _arr(v).ravel().copy()
+                self.keep.append(a)
+                setattr(c, name, _ptr(a))
+        xt, ut = getattr(prob, "xref_traj", None), getattr(prob, "uref_traj", None)
+        c.xref_traj = c.uref_traj = None
+        c.T_traj = 0
+        if (xt is not None or ut is not None) and T is not None:
+            c.T_traj = int(T)
+            for name, v, rows, cols in [("xref_traj", xt, T + 1, c.nx), ("uref_traj", ut, T, c.nu)]:
+                if v is None:
+                    continue
+                a = _arr(v).reshape(-1).copy()
+                if a.size != rows * cols:
+                    raise ValueError(f"{name} must have {rows} x {cols} entries")
                 self.keep.append(a)
                 setattr(c, name, _ptr(a))
         self.c = c
@@ -238,7 +254,7 @@ def constraints(prob, x, u):
 
 def cost(prob, x, u, aug="none", mu=0.0, rho=1.0, z=None, v=None):
     """(J_c, J): augmented cost of Sec. III-A and the plain cost of eq. ocp."""
-    b = _Bound(prob); x = _arr(x); u = _arr(u); T = u.shape[0]
+    x = _arr(x); u = _arr(u); T = u.shape[0]; b = _Bound(prob, T)
     a, keep = _aug(aug, mu, rho, z, v, num_rows(prob))
     Jp = C.c_double(0.0)
     lib().orc_cost.restype = C.c_double
@@ -249,7 +265,7 @@ def cost(prob, x, u, aug="none", mu=0.0, rho=1.0, z=None, v=None):
 def newton_direction(prob, x, u, alpha, aug="barrier", mu=0.1, rho=1.0, z=None, v=None):
     """One Newton step at the nominal (x, u) (Sec. III): dict with lam, d, S, s, Gam, gam,
     dx, du, P, M, R, F, G, G1, G2 and status (1 = R~ or Q not positive definite)."""
-    b = _Bound(prob); x = _arr(x); u = _arr(u); T = u.shape[0]; n, m = b.n, b.m
+    x = _arr(x); u = _arr(u); T = u.shape[0]; b = _Bound(prob, T); n, m = b.n, b.m
     a, keep = _aug(aug, mu, rho, z, v, num_rows(prob))
     out = dict(lam=np.zeros((T + 1, n)), d=np.zeros((T, m)), S=np.zeros((T + 1, n, n)),
                s=np.zeros((T + 1, n)), Gam=np.zeros((T, m, n)), gam=np.zeros((T, m)),
@@ -268,7 +284,7 @@ def newton_direction_mult(prob, x, u, nu, alpha, aug="barrier", mu=0.1, rho=1.0,
     """One Newton step of the multiplier form (a variant, not in the paper: multipliers nu
     of the dynamics instead of the co-state recursion of Sec. III-B) at (x, u, nu): dict
     with q, d, dx, du, dnu (dual step S_t dx_t + s_t), G1, G2 and status."""
-    b = _Bound(prob); x = _arr(x); u = _arr(u); T = u.shape[0]; n, m = b.n, b.m
+    x = _arr(x); u = _arr(u); T = u.shape[0]; b = _Bound(prob, T); n, m = b.n, b.m
     nu = _arr(nu, (T + 1, n))
     a, keep = _aug(aug, mu, rho, z, v, num_rows(prob))
     out = dict(q=np.zeros((T + 1, n)), d=np.zeros((T, m)), dx=np.zeros((T + 1, n)),
@@ -331,7 +347,7 @@ def _info(a):
 def solve_ip(prob, x0, T, u_init=None, opts: Options | None = None):
     """Primal log-barrier IP (eq. lb-min, lb-step-2) with Newton sub-solves (Alg. 4)."""
     opts = opts or Options()
-    b = _Bound(prob); n, m = b.n, b.m; x0 = _arr(x0)
+    b = _Bound(prob, T); n, m = b.n, b.m; x0 = _arr(x0)
     ui = None if u_init is None else _arr(u_init, (T, m))
     x = np.zeros((T + 1, n)); u = np.zeros((T, m)); lam = np.zeros((T + 1, n)); info = np.zeros(16)
     o = opts._c()
@@ -343,7 +359,7 @@ def solve_ip(prob, x0, T, u_init=None, opts: Options | None = None):
 def solve_fixed_mu(prob, x0, T, mu, tol, u_init, opts: Options | None = None):
     """Newton on the barrier problem at a single mu, warm-started from u_init."""
     opts = opts or Options()
-    b = _Bound(prob); n, m = b.n, b.m; x0 = _arr(x0); ui = _arr(u_init, (T, m))
+    b = _Bound(prob, T); n, m = b.n, b.m; x0 = _arr(x0); ui = _arr(u_init, (T, m))
     x = np.zeros((T + 1, n)); u = np.zeros((T, m)); lam = np.zeros((T + 1, n)); info = np.zeros(16)
     o = opts._c()
     lib().orc_solve_fixed_mu(b.ref(), C.byref(o), C.c_double(mu), C.c_double(tol), _ptr(x0),
@@ -354,7 +370,7 @@ def solve_fixed_mu(prob, x0, T, mu, tol, u_init, opts: Options | None = None):
 def solve_admm(prob, x0, T, u_init=None, opts: Options | None = None):
     """ADMM (eq. admm-min ... admm-step-5) with Newton sub-solves (Alg. 4)."""
     opts = opts or Options()
-    b = _Bound(prob); n, m = b.n, b.m; x0 = _arr(x0); nw = num_rows(prob)
+    b = _Bound(prob, T); n, m = b.n, b.m; x0 = _arr(x0); nw = num_rows(prob)
     ui = None if u_init is None else _arr(u_init, (T, m))
     x = np.zeros((T + 1, n)); u = np.zeros((T, m)); lam = np.zeros((T + 1, n)); info = np.zeros(16)
     z = np.zeros((T, nw)); v = np.zeros((T, nw))
@@ -366,7 +382,7 @@ def solve_admm(prob, x0, T, u_init=None, opts: Options | None = None):
 
 def adjoint(prob, mu, x, u, gJ=1.0, gx=None, gu=None):
     """Gradients of gJ*J* + <gx, x*> + <gu, u*> w.r.t. x0, diag Q, diag R, diag Qf, prm."""
-    b = _Bound(prob); n, m = b.n, b.m; x = _arr(x); u = _arr(u); T = u.shape[0]
+    x = _arr(x); u = _arr(u); T = u.shape[0]; b = _Bound(prob, T); n, m = b.n, b.m
     gx = None if gx is None else _arr(gx, (T + 1, n))
     gu = None if gu is None else _arr(gu, (T, m))
     out = dict(x0=np.zeros(n), Qd=np.zeros(n), Rd=np.zeros(m), Qfd=np.zeros(n), prm=np.zeros(MAXP))

@@ -51,6 +51,9 @@ typedef struct orc_problem {
     const double *A, *B, *W;         /* synthetic model matrices, row-major */
     const double *Q, *R, *Qf;        /* cost weights, row-major */
     const double *xref, *uref;       /* tracking targets */
+    const double *xref_traj;         /* time-varying targets (T+1) x nx, or NULL: xref at every t */
+    const double *uref_traj;         /* T x nu, or NULL: uref at every t */
+    int T_traj;                      /* horizon of the target trajectories (the terminal index) */
     const double *xlo, *xhi, *ulo, *uhi; /* box bounds; |b| >= 1e300 or non-finite = none */
 } orc_problem;
 
@@ -455,6 +458,16 @@ void orc_constraints(const orc_problem *P, const double *x, const double *u, dou
     for (int r = 0; r < R.nw; r++) w[r] = row_value(&R, r, x, u);
 }
 
+/* tracking targets at step t (the stage cost l_t of Sec. II-A may vary with t) */
+static const double *xref_at(const orc_problem *P, int t)
+{
+    return P->xref_traj ? P->xref_traj + (size_t)t * P->nx : P->xref;
+}
+static const double *uref_at(const orc_problem *P, int t)
+{
+    return P->uref_traj ? P->uref_traj + (size_t)t * P->nu : P->uref;
+}
+
 /* Stage cost l_t + c_t at step t (Sec. III-A).  *infeas is set when a barrier row is
  * not strictly negative. */
 static double stage_cost(const orc_problem *P, const rows_t *R, const orc_aug *G, int t,
@@ -462,8 +475,9 @@ static double stage_cost(const orc_problem *P, const rows_t *R, const orc_aug *G
 {
     int n = P->nx, m = P->nu;
     double ex[ORC_MAXN], eu[ORC_MAXM], l = 0.0;
-    for (int i = 0; i < n; i++) ex[i] = x[i] - P->xref[i];
-    for (int i = 0; i < m; i++) eu[i] = u[i] - P->uref[i];
+    const double *xr = xref_at(P, t), *ur = uref_at(P, t);
+    for (int i = 0; i < n; i++) ex[i] = x[i] - xr[i];
+    for (int i = 0; i < m; i++) eu[i] = u[i] - ur[i];
     for (int i = 0; i < n; i++)
         for (int j = 0; j < n; j++) l += ex[i] * P->Q[i * n + j] * ex[j];
     for (int i = 0; i < m; i++)
@@ -489,16 +503,17 @@ static void stage_derivs(const orc_problem *P, const rows_t *R, const orc_aug *G
                          double *lxu, double *luu)
 {
     int n = P->nx, m = P->nu;
+    const double *xr = xref_at(P, t), *ur = uref_at(P, t);
     for (int i = 0; i < n; i++) {
         double s = 0.0;
-        for (int j = 0; j < n; j++) s += (P->Q[i * n + j] + P->Q[j * n + i]) * (x[j] - P->xref[j]);
+        for (int j = 0; j < n; j++) s += (P->Q[i * n + j] + P->Q[j * n + i]) * (x[j] - xr[j]);
         lx[i] = s;
         for (int j = 0; j < n; j++) lxx[i * n + j] = P->Q[i * n + j] + P->Q[j * n + i];
         for (int j = 0; j < m; j++) lxu[i * m + j] = 0.0;
     }
     for (int i = 0; i < m; i++) {
         double s = 0.0;
-        for (int j = 0; j < m; j++) s += (P->R[i * m + j] + P->R[j * m + i]) * (u[j] - P->uref[j]);
+        for (int j = 0; j < m; j++) s += (P->R[i * m + j] + P->R[j * m + i]) * (u[j] - ur[j]);
         lu[i] = s;
         for (int j = 0; j < m; j++) luu[i * m + j] = P->R[i * m + j] + P->R[j * m + i];
     }
@@ -522,17 +537,19 @@ static void stage_derivs(const orc_problem *P, const rows_t *R, const orc_aug *G
 static double terminal_cost(const orc_problem *P, const double *x)
 {
     int n = P->nx;
+    const double *xr = xref_at(P, P->T_traj);
     double l = 0.0;
     for (int i = 0; i < n; i++)
-        for (int j = 0; j < n; j++) l += (x[i] - P->xref[i]) * P->Qf[i * n + j] * (x[j] - P->xref[j]);
+        for (int j = 0; j < n; j++) l += (x[i] - xr[i]) * P->Qf[i * n + j] * (x[j] - xr[j]);
     return l;
 }
 static void terminal_grad(const orc_problem *P, const double *x, double *g, double *H)
 {
     int n = P->nx;
+    const double *xr = xref_at(P, P->T_traj);
     for (int i = 0; i < n; i++) {
         double s = 0.0;
-        for (int j = 0; j < n; j++) s += (P->Qf[i * n + j] + P->Qf[j * n + i]) * (x[j] - P->xref[j]);
+        for (int j = 0; j < n; j++) s += (P->Qf[i * n + j] + P->Qf[j * n + i]) * (x[j] - xr[j]);
         g[i] = s;
         if (H) for (int j = 0; j < n; j++) H[i * n + j] = P->Qf[i * n + j] + P->Qf[j * n + i];
     }
@@ -1473,14 +1490,14 @@ int orc_adjoint(const orc_problem *P, double mu, int T, const double *x, const d
     for (int i = 0; i < n; i++) {
         g_x0[i] = gJ * W.lam[i];
         double sq = 0.0;
-        for (int t = 0; t < T; t++) { double e = x[t * n + i] - P->xref[i]; sq += e * e; }
+        for (int t = 0; t < T; t++) { double e = x[t * n + i] - xref_at(P, t)[i]; sq += e * e; }
         g_Qd[i] = gJ * sq;
-        double e = x[T * n + i] - P->xref[i];
+        double e = x[T * n + i] - xref_at(P, T)[i];
         g_Qfd[i] = gJ * e * e;
     }
     for (int i = 0; i < m; i++) {
         double sq = 0.0;
-        for (int t = 0; t < T; t++) { double e = u[t * m + i] - P->uref[i]; sq += e * e; }
+        for (int t = 0; t < T; t++) { double e = u[t * m + i] - uref_at(P, t)[i]; sq += e * e; }
         g_Rd[i] = gJ * sq;
     }
     for (int k = 0; k < ORC_MAXP; k++) g_prm[k] = 0.0;
@@ -1520,13 +1537,13 @@ int orc_adjoint(const orc_problem *P, double mu, int T, const double *x, const d
         for (int i = 0; i < n; i++) {
             g_x0[i] -= nu[i];
             double a = 0.0;
-            for (int t = 0; t < T; t++) a += W.dx[t * n + i] * 2.0 * (x[t * n + i] - P->xref[i]);
+            for (int t = 0; t < T; t++) a += W.dx[t * n + i] * 2.0 * (x[t * n + i] - xref_at(P, t)[i]);
             g_Qd[i] -= a;
-            g_Qfd[i] -= W.dx[T * n + i] * 2.0 * (x[T * n + i] - P->xref[i]);
+            g_Qfd[i] -= W.dx[T * n + i] * 2.0 * (x[T * n + i] - xref_at(P, T)[i]);
         }
         for (int i = 0; i < m; i++) {
             double a = 0.0;
-            for (int t = 0; t < T; t++) a += W.du[t * m + i] * 2.0 * (u[t * m + i] - P->uref[i]);
+            for (int t = 0; t < T; t++) a += W.du[t * m + i] * 2.0 * (u[t * m + i] - uref_at(P, t)[i]);
             g_Rd[i] -= a;
         }
         for (int t = 0; t < T; t++) {

@@ -43,6 +43,8 @@ class Problem:
     B: np.ndarray | None = None
     W: np.ndarray | None = None
     name: str = ""
+    xref_traj: np.ndarray | None = None  # time-varying targets, (T+1) x nx (replaces xref)
+    uref_traj: np.ndarray | None = None  # T x nu (replaces uref)
 
     def replace(self, **kw) -> "Problem":
         d = dict(self.__dict__)
