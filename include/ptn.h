@@ -175,6 +175,19 @@ const char* ptn_last_error(const ptn_solver* s);
 /* Replace the options of an existing handle (e.g. precision, tolerances). */
 int ptn_set_options(ptn_solver* s, const ptn_options* opt);
 
+/* Time-varying tracking targets for the solves and adjoints that follow (the stage cost
+ * l_t of Sec. II-A, eq. ocp, with targets that change with t):
+ *   l_t = (x_t - xr_t)^T Q (x_t - xr_t) + (u_t - ur_t)^T R (u_t - ur_t),
+ *   terminal (x_T - xr_T)^T Qf (x_T - xr_T).
+ * xref_traj: device, the instances' target states concatenated like the state outputs
+ * (instance b: T_b + 1 rows of nx); uref_traj: device, like the control outputs (T_b rows
+ * of nu).  Either may be NULL (the constant targets of the problem, or of xref per
+ * instance, apply).  The handle keeps the pointers, not the data: the arrays must stay
+ * valid and match the horizons of every solve until the next call (NULL, NULL restores
+ * constant targets).  Not used by ptn_solve_ip_static.  Returns PTN_OK, or
+ * PTN_ERR_INVALID_ARG for a NULL handle. */
+int ptn_set_reference(ptn_solver* s, const double* xref_traj, const double* uref_traj);
+
 /* Primal log-barrier IP solve of one instance (Sec. II-B with Alg. 4 sub-solves).
  *   x0      device, nx            initial state x_1
  *   u_init  device, T x nu        strictly feasible initial controls, or NULL (zeros)

@@ -110,6 +110,8 @@ struct LaunchPlan {
 
 struct ptn_solver {
   ptn_options opt;
+  const double* xtraj = nullptr;  // time-varying targets of the solves (ptn_set_reference), device
+  const double* utraj = nullptr;
   ProbDev hprob;
   ProbDev* dprob = nullptr;
   OptDev* dopt = nullptr;
@@ -222,6 +224,14 @@ extern "C" int ptn_set_options(ptn_solver* s, const ptn_options* opt) {
   int rc = check_options(s, opt);
   if (rc) return rc;
   s->opt = *opt;
+  return PTN_OK;
+}
+
+extern "C" int ptn_set_reference(ptn_solver* s, const double* xref_traj, const double* uref_traj) {
+  if (!s) return PTN_ERR_INVALID_ARG;
+  s->err[0] = 0;
+  s->xtraj = xref_traj;
+  s->utraj = uref_traj;
   return PTN_OK;
 }
 
@@ -619,6 +629,8 @@ static int enqueue(ptn_solver* s, const LaunchPlan& p, const OptDev* dopt, const
   q.args.x0 = x0;
   q.args.xref = xref;
   q.args.u_init = u_init;
+  q.args.xtraj = s->xtraj;
+  q.args.utraj = s->utraj;
   q.args.info = dinfo;
   q.args.B = p.B;
   if (p.tier == 1 || p.tier == 6 || p.tier == 8) {
@@ -789,7 +801,7 @@ extern "C" int ptn_solve_batch_async(ptn_solver* s, const double* x0, const doub
 // thread as far as the co-resident CTAs allow.  T0: the horizon of the first instance.
 static int launch_adjoint(ptn_solver* s, launch_fn fn, int B, int T0, const InstDev* dinst, const double* x0,
                           const double* xref, const double* x_star, const double* u_star, const AdjArgs& aa,
-                          InfoDev* dinfo, cudaStream_t st) {
+                          InfoDev* dinfo, cudaStream_t st, const double* xtr, const double* utr) {
   LaunchReq q{};
   q.tier = 3;
   q.precision = PTN_FP64;
@@ -802,6 +814,8 @@ static int launch_adjoint(ptn_solver* s, launch_fn fn, int B, int T0, const Inst
   q.args.inst = dinst;
   q.args.x0 = x0;
   q.args.xref = xref;
+  q.args.xtraj = xtr;
+  q.args.utraj = utr;
   q.args.info = dinfo;
   q.args.B = B;
   q.adj = &aa;
@@ -867,7 +881,8 @@ extern "C" int ptn_adjoint(ptn_solver* s, int B, const int* T_b, const double* x
   aa.mu = mu;
   aa.gJ = gJ;
   aa.g_x0 = g_x0; aa.g_Qd = g_Qd; aa.g_Rd = g_Rd; aa.g_Qfd = g_Qfd; aa.g_prm = g_prm;
-  int rc = launch_adjoint(s, fn, B, T_b[0], s->dinst, x0, xref, x_star, u_star, aa, s->dinfo, st);
+  int rc = launch_adjoint(s, fn, B, T_b[0], s->dinst, x0, xref, x_star, u_star, aa, s->dinfo, st, s->xtraj,
+                          s->utraj);
   if (rc) return rc;
   CK(cudaMemcpyAsync(s->hinfo, s->dinfo, sizeof(InfoDev) * B, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
@@ -971,7 +986,7 @@ extern "C" int ptn_adjoint_checkpointed(ptn_solver* s, int T, int seg_len, const
         aa.g_x0 = o; aa.g_Qd = o + n; aa.g_Rd = o + 2 * n; aa.g_Qfd = o + 2 * n + m; aa.g_prm = o + 3 * n + m;
       }
       rc = launch_adjoint(s, fn, 1, hinst[k].T, dinst + k, x_star + xo, xref, x_star + xo, u_star + uo, aa,
-                          dinfo + l, st);
+                          dinfo + l, st, s->xtraj ? s->xtraj + xo : nullptr, s->utraj ? s->utraj + uo : nullptr);
     }
   }
   if (rc == PTN_OK) {

@@ -41,16 +41,30 @@ struct ProbS {
   double prm[PTN_MAXP];
   double sgn[NW], bnd[NW];
   int isx[NW], idx[NW];
-  int nw, integ, model, pad;
+  int nw, integ, model, Tr;  // Tr: the instance's horizon (index of the terminal target)
   double dt;
   const double *A, *B, *W;
   const float *A32, *B32, *W32;
+  const double *xtr, *utr;  // time-varying targets of the instance ((Tr+1) x N, Tr x U) or null
 };
+
+// the tracking targets of step t: the instance's target trajectories when given, else the
+// constant targets (the stage cost l_t of Sec. II-A may vary with t)
+template <int N, int U>
+__device__ __forceinline__ const double* xref_at(const ProbS<N, U>& P, int t) {
+  return P.xtr ? P.xtr + (size_t)t * N : P.xref;
+}
+template <int N, int U>
+__device__ __forceinline__ const double* uref_at(const ProbS<N, U>& P, int t) {
+  return P.utr ? P.utr + (size_t)t * U : P.uref;
+}
 
 template <int N, int U>
 // dt_inst > 0: the instance's own time step; the stage weights Q, R are scaled by
 // dt_inst / P.dt (the same continuous-time cost at another sampling rate), Qf is not.
-__device__ void load_prob(ProbS<N, U>& S, const ProbDev& P, const double* xref_override, double dt_inst = 0.0) {
+// xtr, utr (optional): the instance's target trajectories; T: its horizon.
+__device__ void load_prob(ProbS<N, U>& S, const ProbDev& P, const double* xref_override, double dt_inst = 0.0,
+                          const double* xtr = nullptr, const double* utr = nullptr, int T = 0) {
   const double sc = dt_inst > 0.0 ? dt_inst / P.dt : 1.0;
   for (int i = threadIdx.x; i < N * N; i += blockDim.x) {
     S.Q[i] = sc * P.Q[i];
@@ -72,6 +86,7 @@ __device__ void load_prob(ProbS<N, U>& S, const ProbDev& P, const double* xref_o
     S.nw = P.nw; S.integ = P.integrator; S.model = P.model; S.dt = dt_inst > 0.0 ? dt_inst : P.dt;
     S.A = P.A; S.B = P.B; S.W = P.W;
     S.A32 = P.A32; S.B32 = P.B32; S.W32 = P.W32;
+    S.xtr = xtr; S.utr = utr; S.Tr = T;
   }
   __syncthreads();
 }
@@ -207,9 +222,10 @@ struct AugF {
 template <int N, int U>
 __device__ double stage_cost(const ProbS<N, U>& P, const Aug& A, int t, const double* x, const double* u,
                              bool& infeas, double* lplain = nullptr) {
+  const double *xr = xref_at(P, t), *ur = uref_at(P, t);
   double l = 0.0, e[N];
 #pragma unroll
-  for (int i = 0; i < N; i++) e[i] = x[i] - P.xref[i];
+  for (int i = 0; i < N; i++) e[i] = x[i] - xr[i];
 #pragma unroll
   for (int i = 0; i < N; i++) {
     double s = 0.0;
@@ -219,7 +235,7 @@ __device__ double stage_cost(const ProbS<N, U>& P, const Aug& A, int t, const do
   }
   double eu[U];
 #pragma unroll
-  for (int i = 0; i < U; i++) eu[i] = u[i] - P.uref[i];
+  for (int i = 0; i < U; i++) eu[i] = u[i] - ur[i];
 #pragma unroll
   for (int i = 0; i < U; i++) {
     double s = 0.0;
@@ -245,18 +261,19 @@ __device__ double stage_cost(const ProbS<N, U>& P, const Aug& A, int t, const do
 template <int N, int U>
 __device__ void stage_grad(const ProbS<N, U>& P, const Aug& A, int t, const double* x, const double* u,
                            double* lx, double* lu) {
+  const double *xr = xref_at(P, t), *ur = uref_at(P, t);
 #pragma unroll
   for (int i = 0; i < N; i++) {
     double s = 0.0;
 #pragma unroll
-    for (int j = 0; j < N; j++) s += (P.Q[i * N + j] + P.Q[j * N + i]) * (x[j] - P.xref[j]);
+    for (int j = 0; j < N; j++) s += (P.Q[i * N + j] + P.Q[j * N + i]) * (x[j] - xr[j]);
     lx[i] = s;
   }
 #pragma unroll
   for (int i = 0; i < U; i++) {
     double s = 0.0;
 #pragma unroll
-    for (int j = 0; j < U; j++) s += (P.R[i * U + j] + P.R[j * U + i]) * (u[j] - P.uref[j]);
+    for (int j = 0; j < U; j++) s += (P.R[i * U + j] + P.R[j * U + i]) * (u[j] - ur[j]);
     lu[i] = s;
   }
   for (int r = 0; r < P.nw; r++) {
@@ -295,13 +312,14 @@ __device__ void stage_hess_add(const ProbS<N, U>& P, const Aug& A, const double*
 
 template <int N, int U>
 __device__ double terminal_cost(const ProbS<N, U>& P, const double* x) {
+  const double* xr = xref_at(P, P.Tr);
   double l = 0.0;
 #pragma unroll
   for (int i = 0; i < N; i++) {
     double s = 0.0;
 #pragma unroll
-    for (int j = 0; j < N; j++) s += P.Qf[i * N + j] * (x[j] - P.xref[j]);
-    l += (x[i] - P.xref[i]) * s;
+    for (int j = 0; j < N; j++) s += P.Qf[i * N + j] * (x[j] - xr[j]);
+    l += (x[i] - xr[i]) * s;
   }
   return l;
 }
@@ -311,11 +329,12 @@ __device__ double terminal_cost(const ProbS<N, U>& P, const double* x) {
 template <int N, int U>
 __device__ void stage_grad32(const ProbS<N, U>& P, const Aug& A, int t, const double* x, const double* u,
                              float* lx, float* lu) {
+  const double *xr = xref_at(P, t), *ur = uref_at(P, t);
   float e[N], eu[U];
 #pragma unroll
-  for (int i = 0; i < N; i++) e[i] = float(x[i] - P.xref[i]);
+  for (int i = 0; i < N; i++) e[i] = float(x[i] - xr[i]);
 #pragma unroll
-  for (int i = 0; i < U; i++) eu[i] = float(u[i] - P.uref[i]);
+  for (int i = 0; i < U; i++) eu[i] = float(u[i] - ur[i]);
   mv<N, N>(P.Qs, e, lx);
   mv<U, U>(P.Rs, eu, lu);
   const AugF F(A);
@@ -340,11 +359,12 @@ __device__ void stage_grad32(const ProbS<N, U>& P, const Aug& A, int t, const do
 template <int N, int U>
 __device__ float stage_delta(const ProbS<N, U>& P, const Aug& A, int t, const double* x0, const double* u0,
                              const float* dx, const float* du, bool& infeas) {
+  const double *xr = xref_at(P, t), *ur = uref_at(P, t);
   float e[N], eu[U], qe[N], qd[N], re[U], rd[U];
 #pragma unroll
-  for (int i = 0; i < N; i++) e[i] = float(x0[i] - P.xref[i]);
+  for (int i = 0; i < N; i++) e[i] = float(x0[i] - xr[i]);
 #pragma unroll
-  for (int i = 0; i < U; i++) eu[i] = float(u0[i] - P.uref[i]);
+  for (int i = 0; i < U; i++) eu[i] = float(u0[i] - ur[i]);
   mv<N, N>(P.Qs, e, qe);   // (Q + Q^T) e
   mv<N, N>(P.Qs, dx, qd);  // (Q + Q^T) dx
   mv<U, U>(P.Rs, eu, re);
@@ -376,9 +396,10 @@ __device__ float stage_delta(const ProbS<N, U>& P, const Aug& A, int t, const do
 
 template <int N, int U>
 __device__ float terminal_delta(const ProbS<N, U>& P, const double* x0, const float* dx) {
+  const double* xr = xref_at(P, P.Tr);
   float e[N], qe[N], qd[N];
 #pragma unroll
-  for (int i = 0; i < N; i++) e[i] = float(x0[i] - P.xref[i]);
+  for (int i = 0; i < N; i++) e[i] = float(x0[i] - xr[i]);
   mv<N, N>(P.Qfs, e, qe);
   mv<N, N>(P.Qfs, dx, qd);
   float l = 0.0f;
@@ -460,7 +481,7 @@ __device__ void terminal_grad(const ProbS<N, U>& P, const double* xT, double* g)
   for (int i = 0; i < N; i++) {
     double s = 0.0;
 #pragma unroll
-    for (int j = 0; j < N; j++) s += (P.Qf[i * N + j] + P.Qf[j * N + i]) * (xT[j] - P.xref[j]);
+    for (int j = 0; j < N; j++) s += (P.Qf[i * N + j] + P.Qf[j * N + i]) * (xT[j] - xref_at(P, P.Tr)[j]);
     g[i] = s;
   }
 }
@@ -1897,19 +1918,19 @@ __device__ int adjoint_instance(Grp& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>
   for (int t = I.a; t < I.b; t++) {
 #pragma unroll
     for (int i = 0; i < N; i++) {
-      const double e = I.xn[(size_t)t * N + i] - P.xref[i];
+      const double e = I.xn[(size_t)t * N + i] - xref_at(P, t)[i];
       env[N + i] += e * e;
     }
 #pragma unroll
     for (int i = 0; i < U; i++) {
-      const double e = I.un[(size_t)t * U + i] - P.uref[i];
+      const double e = I.un[(size_t)t * U + i] - uref_at(P, t)[i];
       env[2 * N + i] += e * e;
     }
   }
   if (I.last && seg_last) {
 #pragma unroll
     for (int i = 0; i < N; i++) {
-      const double e = I.xn[(size_t)I.T * N + i] - P.xref[i];
+      const double e = I.xn[(size_t)I.T * N + i] - xref_at(P, I.T)[i];
       env[2 * N + U + i] = e * e;
     }
   }
@@ -1973,16 +1994,16 @@ __device__ int adjoint_instance(Grp& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>
         for (int t = I.a; t < I.b; t++) {
 #pragma unroll
           for (int i = 0; i < N; i++)
-            adj[N + i] += double(I.dx[(size_t)t * N + i]) * 2.0 * (I.xn[(size_t)t * N + i] - P.xref[i]);
+            adj[N + i] += double(I.dx[(size_t)t * N + i]) * 2.0 * (I.xn[(size_t)t * N + i] - xref_at(P, t)[i]);
 #pragma unroll
           for (int i = 0; i < U; i++)
-            adj[2 * N + i] += double(I.du[(size_t)t * U + i]) * 2.0 * (I.un[(size_t)t * U + i] - P.uref[i]);
+            adj[2 * N + i] += double(I.du[(size_t)t * U + i]) * 2.0 * (I.un[(size_t)t * U + i] - uref_at(P, t)[i]);
         }
         if (I.last && seg_last) {
 #pragma unroll
           for (int i = 0; i < N; i++)
             adj[2 * N + U + i] =
-                double(I.dx[(size_t)I.T * N + i]) * 2.0 * (I.xn[(size_t)I.T * N + i] - P.xref[i]);
+                double(I.dx[(size_t)I.T * N + i]) * 2.0 * (I.xn[(size_t)I.T * N + i] - xref_at(P, I.T)[i]);
         }
       }
     }
@@ -2143,10 +2164,22 @@ struct KArgs {
   const double* x0;      // B x N
   const double* xref;    // B x N or null
   const double* u_init;  // concatenated controls or null
+  const double* xtraj;   // time-varying targets: concatenated like the states, or null
+  const double* utraj;   // ... like the controls, or null
   InfoDev* info;         // B
   GridScratch gs;
   int B, pad;
 };
+
+// the time-varying targets of instance id (null when the solve has none)
+template <int N>
+__device__ __forceinline__ const double* inst_xtraj(const KArgs& a, const InstDev& id) {
+  return a.xtraj ? a.xtraj + (size_t)id.xoff * N : nullptr;
+}
+template <int U>
+__device__ __forceinline__ const double* inst_utraj(const KArgs& a, const InstDev& id) {
+  return a.utraj ? a.utraj + (size_t)id.uoff * U : nullptr;
+}
 
 template <int N, int U, class L>
 __host__ __device__ constexpr size_t scratch_bytes(int nwarps) {
@@ -2168,7 +2201,8 @@ __global__ void __launch_bounds__(256) k_solve_cta(KArgs args, Work<L> w) {
   char* scratch = smem + ((sizeof(ProbS<N, U>) + 15) & ~size_t(15));
   const int bi = blockIdx.x;
   if (bi >= args.B) return;
-  load_prob<N, U>(P, *args.prob, args.xref ? args.xref + (size_t)bi * N : nullptr, args.inst[bi].dt);
+  load_prob<N, U>(P, *args.prob, args.xref ? args.xref + (size_t)bi * N : nullptr, args.inst[bi].dt,
+                  inst_xtraj<N>(args, args.inst[bi]), inst_utraj<U>(args, args.inst[bi]), args.inst[bi].T);
   const OptDev& O = *args.opt;  // read where used (a local copy would hold ~50 registers)
   const InstDev id = args.inst[bi];
   CtaGroup g{scratch};
@@ -2186,7 +2220,8 @@ __global__ void __launch_bounds__(128) k_solve_grid(KArgs args, Work<L> w) {
   char* scratch = smem + ((sizeof(ProbS<N, U>) + 15) & ~size_t(15));
   __shared__ int sdead;
   if (threadIdx.x == 0) sdead = 0;
-  load_prob<N, U>(P, *args.prob, args.xref, args.inst[0].dt);
+  load_prob<N, U>(P, *args.prob, args.xref, args.inst[0].dt,
+                  inst_xtraj<N>(args, args.inst[0]), inst_utraj<U>(args, args.inst[0]), args.inst[0].T);
   const OptDev& O = *args.opt;  // read where used (a local copy would hold ~50 registers)
   const InstDev id = args.inst[0];
   GridGroup g{scratch, args.gs, 0, &sdead};
@@ -2204,7 +2239,8 @@ __global__ void __launch_bounds__(256) k_adjoint_cta(KArgs args, Work<L> w, AdjA
   char* scratch = smem + ((sizeof(ProbS<N, U>) + 15) & ~size_t(15));
   const int bi = blockIdx.x;
   if (bi >= args.B) return;
-  load_prob<N, U>(P, *args.prob, args.xref ? args.xref + (size_t)bi * N : nullptr, args.inst[bi].dt);
+  load_prob<N, U>(P, *args.prob, args.xref ? args.xref + (size_t)bi * N : nullptr, args.inst[bi].dt,
+                  inst_xtraj<N>(args, args.inst[bi]), inst_utraj<U>(args, args.inst[bi]), args.inst[bi].T);
   const InstDev id = args.inst[bi];
   CtaGroup g{scratch};
   Inst<M, L> I;
@@ -2223,7 +2259,8 @@ __global__ void __launch_bounds__(128) k_adjoint_grid(KArgs args, Work<L> w, Adj
   char* scratch = smem + ((sizeof(ProbS<N, U>) + 15) & ~size_t(15));
   __shared__ int sdead;
   if (threadIdx.x == 0) sdead = 0;
-  load_prob<N, U>(P, *args.prob, args.xref, args.inst[0].dt);
+  load_prob<N, U>(P, *args.prob, args.xref, args.inst[0].dt,
+                  inst_xtraj<N>(args, args.inst[0]), inst_utraj<U>(args, args.inst[0]), args.inst[0].T);
   const InstDev id = args.inst[0];
   GridGroup g{scratch, args.gs, 0, &sdead};
   Inst<M, L> I;
@@ -2257,7 +2294,8 @@ struct SeqGroup {
 
 // problem record for one thread (as load_prob, without the CTA-wide copy)
 template <int N, int U>
-__device__ void load_prob_thread(ProbS<N, U>& S, const ProbDev& P, const double* xref_override, double dt_inst) {
+__device__ void load_prob_thread(ProbS<N, U>& S, const ProbDev& P, const double* xref_override, double dt_inst,
+                                 const double* xtr, const double* utr, int T) {
   const double sc = dt_inst > 0.0 ? dt_inst / P.dt : 1.0;
   for (int i = 0; i < N * N; i++) {
     S.Q[i] = sc * P.Q[i];
@@ -2277,6 +2315,7 @@ __device__ void load_prob_thread(ProbS<N, U>& S, const ProbDev& P, const double*
   }
   S.nw = P.nw; S.integ = P.integrator; S.model = P.model; S.dt = dt_inst > 0.0 ? dt_inst : P.dt;
   S.A = P.A; S.B = P.B; S.W = P.W;
+  S.xtr = xtr; S.utr = utr; S.Tr = T;
 }
 
 template <class M, class L, class SV>
@@ -2285,7 +2324,8 @@ __global__ void __launch_bounds__(64) k_solve_seq(KArgs args, Work<L> w) {
   const int bi = blockIdx.x * blockDim.x + threadIdx.x;
   if (bi >= args.B) return;  // no group barriers below: threads are independent
   ProbS<N, U> P;
-  load_prob_thread<N, U>(P, *args.prob, args.xref ? args.xref + (size_t)bi * N : nullptr, args.inst[bi].dt);
+  load_prob_thread<N, U>(P, *args.prob, args.xref ? args.xref + (size_t)bi * N : nullptr, args.inst[bi].dt,
+                         inst_xtraj<N>(args, args.inst[bi]), inst_utraj<U>(args, args.inst[bi]), args.inst[bi].T);
   const OptDev& O = *args.opt;  // read where used (a local copy would hold ~50 registers)
   const InstDev id = args.inst[bi];
   SeqGroup g;
@@ -2305,7 +2345,8 @@ __global__ void __launch_bounds__(256) k_solve_cluster(KArgs args, Work<L> w) {
   const size_t sbytes = scratch_bytes<N, U, L>(nwarps);
   constexpr int XB = (int)((sizeof(Val<N, double>) > 64 ? sizeof(Val<N, double>) : 64) + 15) / 16 * 16;
   char* xch = scratch + ((sbytes + 15) & ~size_t(15));
-  load_prob<N, U>(P, *args.prob, args.xref, args.inst[0].dt);
+  load_prob<N, U>(P, *args.prob, args.xref, args.inst[0].dt,
+                  inst_xtraj<N>(args, args.inst[0]), inst_utraj<U>(args, args.inst[0]), args.inst[0].T);
   const OptDev& O = *args.opt;  // read where used (a local copy would hold ~50 registers)
   const InstDev id = args.inst[0];
   ClusterGroup g{scratch, xch, XB, 0};

@@ -216,15 +216,16 @@ template <int N, int U>
 __device__ double stage_cost_w(const ProbS<N, U>& P, const Aug& A, int t, const double* x, const double* u,
                                bool& infeas, double* lplain) {
   const int l = lane_id();
+  const double *xr = xref_at(P, t), *ur = uref_at(P, t);
   double v = 0.0;
   for (int q = l; q < N + U; q += 32) {  // lane-strided: N + U may exceed 32
     if (q < N) {
-      const double s = wops::dot4<N, double>([&](int j) { return P.Q[q * N + j] * (x[j] - P.xref[j]); });
-      v += (x[q] - P.xref[q]) * s;
+      const double s = wops::dot4<N, double>([&](int j) { return P.Q[q * N + j] * (x[j] - xr[j]); });
+      v += (x[q] - xr[q]) * s;
     } else {
       const int i = q - N;
-      const double s = wops::dot4<U, double>([&](int j) { return P.R[i * U + j] * (u[j] - P.uref[j]); });
-      v += (u[i] - P.uref[i]) * s;
+      const double s = wops::dot4<U, double>([&](int j) { return P.R[i * U + j] * (u[j] - ur[j]); });
+      v += (u[i] - ur[i]) * s;
     }
   }
   const double lp = wops::wsum(v);
@@ -249,10 +250,11 @@ __device__ double stage_cost_w(const ProbS<N, U>& P, const Aug& A, int t, const 
 template <int N, int U>
 __device__ double terminal_cost_w(const ProbS<N, U>& P, const double* x) {
   const int l = lane_id();
+  const double* xr = xref_at(P, P.Tr);
   double v = 0.0;
   if (l < N) {
-    const double s = wops::dot4<N, double>([&](int j) { return P.Qf[l * N + j] * (x[j] - P.xref[j]); });
-    v = (x[l] - P.xref[l]) * s;
+    const double s = wops::dot4<N, double>([&](int j) { return P.Qf[l * N + j] * (x[j] - xr[j]); });
+    v = (x[l] - xr[l]) * s;
   }
   return wops::wsum(v);
 }
@@ -262,6 +264,7 @@ template <int N, int U>
 __device__ void stage_grad_w(const ProbS<N, U>& P, const Aug& A, int t, const double* x, const double* u,
                              double* lx, double* lu, double* gr) {
   const int l = lane_id();
+  const double *xr = xref_at(P, t), *ur = uref_at(P, t);
   for (int r = l; r < P.nw; r += 32) {
     const double zk = P.isx[r] ? x[P.idx[r]] : u[P.idx[r]];
     const double w = P.sgn[r] * (zk - P.bnd[r]);
@@ -272,13 +275,13 @@ __device__ void stage_grad_w(const ProbS<N, U>& P, const Aug& A, int t, const do
   __syncwarp();
   for (int q = l; q < N + U; q += 32) {
     if (q < N) {
-      double s = wops::dot4<N, double>([&](int j) { return (P.Q[q * N + j] + P.Q[j * N + q]) * (x[j] - P.xref[j]); });
+      double s = wops::dot4<N, double>([&](int j) { return (P.Q[q * N + j] + P.Q[j * N + q]) * (x[j] - xr[j]); });
       for (int r = 0; r < P.nw; r++)
         if (P.isx[r] && P.idx[r] == q) s += gr[r];
       lx[q] = s;
     } else {
       const int i = q - N;
-      double s = wops::dot4<U, double>([&](int j) { return (P.R[i * U + j] + P.R[j * U + i]) * (u[j] - P.uref[j]); });
+      double s = wops::dot4<U, double>([&](int j) { return (P.R[i * U + j] + P.R[j * U + i]) * (u[j] - ur[j]); });
       for (int r = 0; r < P.nw; r++)
         if (!P.isx[r] && P.idx[r] == i) s += gr[r];
       lu[i] = s;
@@ -290,8 +293,9 @@ __device__ void stage_grad_w(const ProbS<N, U>& P, const Aug& A, int t, const do
 template <int N, int U>
 __device__ void terminal_grad_w(const ProbS<N, U>& P, const double* xT, double* g) {
   const int l = lane_id();
+  const double* xr = xref_at(P, P.Tr);
   if (l < N)
-    g[l] = wops::dot4<N, double>([&](int j) { return (P.Qf[l * N + j] + P.Qf[j * N + l]) * (xT[j] - P.xref[j]); });
+    g[l] = wops::dot4<N, double>([&](int j) { return (P.Qf[l * N + j] + P.Qf[j * N + l]) * (xT[j] - xr[j]); });
   __syncwarp();
 }
 
@@ -1328,7 +1332,8 @@ __global__ void __launch_bounds__(WideMaxThreads<M>::value) k_solve_wide(KArgs a
   g.grid = 0;
   const int bi = blockIdx.x;
   if (bi >= args.B) return;
-  load_prob<N, U>(P, *args.prob, args.xref ? args.xref + (size_t)bi * N : nullptr, args.inst[bi].dt);
+  load_prob<N, U>(P, *args.prob, args.xref ? args.xref + (size_t)bi * N : nullptr, args.inst[bi].dt,
+                  inst_xtraj<N>(args, args.inst[bi]), inst_utraj<U>(args, args.inst[bi]), args.inst[bi].T);
   const OptDev& O = *args.opt;  // read where used (a local copy would hold ~50 registers)
   const InstDev id = args.inst[bi];
   Inst<M, L> I;
@@ -1352,7 +1357,8 @@ __global__ void __launch_bounds__(WideMaxThreads<M>::value) k_solve_wide_grid(KA
   g.gs = args.gs;
   g.sdead = &sdead;
   g.phase = 0;
-  load_prob<N, U>(P, *args.prob, args.xref, args.inst[0].dt);
+  load_prob<N, U>(P, *args.prob, args.xref, args.inst[0].dt,
+                  inst_xtraj<N>(args, args.inst[0]), inst_utraj<U>(args, args.inst[0]), args.inst[0].T);
   const OptDev& O = *args.opt;
   const InstDev id = args.inst[0];
   Inst<M, L> I;
@@ -1392,7 +1398,8 @@ __global__ void __launch_bounds__(WideMaxThreads<M>::value) k_solve_wide_bgrid(K
   g.gs.xs = args.gs.xs + (size_t)2 * id.pad * args.gs.elem_bytes;
   g.sdead = &sdead;
   g.phase = 0;
-  load_prob<N, U>(P, *args.prob, args.xref ? args.xref + (size_t)bi * N : nullptr, id.dt);
+  load_prob<N, U>(P, *args.prob, args.xref ? args.xref + (size_t)bi * N : nullptr, id.dt,
+                  inst_xtraj<N>(args, id), inst_utraj<U>(args, id), id.T);
   const OptDev& O = *args.opt;
   Inst<M, L> I;
   I.setup(w, id, args.x0 + (size_t)bi * N, g.rank(), g.size(), P.nw);
@@ -1475,15 +1482,15 @@ __device__ int adjoint_wide(WideGroup& g, Inst<M, double>& I, const ProbS<M::NX,
   // quadratic-weight envelope terms
   for (int t = I.a; t < I.b; t++) {
     if (l < N) {
-      const double e = I.xn[(size_t)t * N + l] - P.xref[l];
+      const double e = I.xn[(size_t)t * N + l] - xref_at(P, t)[l];
       env[N + l] += e * e;
     } else if (l < N + U) {
-      const double e = I.un[(size_t)t * U + (l - N)] - P.uref[l - N];
+      const double e = I.un[(size_t)t * U + (l - N)] - uref_at(P, t)[l - N];
       env[2 * N + (l - N)] += e * e;
     }
   }
   if (I.last && l < N) {
-    const double e = I.xn[(size_t)I.T * N + l] - P.xref[l];
+    const double e = I.xn[(size_t)I.T * N + l] - xref_at(P, I.T)[l];
     env[2 * N + U + l] = e * e;
   }
   __syncwarp();
@@ -1585,12 +1592,13 @@ __device__ int adjoint_wide(WideGroup& g, Inst<M, double>& I, const ProbS<M::NX,
       for (int i = l; i < N; i += 32) adj[i] = nu[i];
     // quadratic-weight adjoint terms
     for (int t = I.a; t < I.b; t++) {
-      if (l < N) adj[N + l] += I.dx[(size_t)t * N + l] * 2.0 * (I.xn[(size_t)t * N + l] - P.xref[l]);
+      if (l < N) adj[N + l] += I.dx[(size_t)t * N + l] * 2.0 * (I.xn[(size_t)t * N + l] - xref_at(P, t)[l]);
       else if (l < N + U)
-        adj[2 * N + (l - N)] += I.du[(size_t)t * U + (l - N)] * 2.0 * (I.un[(size_t)t * U + (l - N)] - P.uref[l - N]);
+        adj[2 * N + (l - N)] +=
+            I.du[(size_t)t * U + (l - N)] * 2.0 * (I.un[(size_t)t * U + (l - N)] - uref_at(P, t)[l - N]);
     }
     if (I.last && l < N)
-      adj[2 * N + U + l] = I.dx[(size_t)I.T * N + l] * 2.0 * (I.xn[(size_t)I.T * N + l] - P.xref[l]);
+      adj[2 * N + U + l] = I.dx[(size_t)I.T * N + l] * 2.0 * (I.xn[(size_t)I.T * N + l] - xref_at(P, I.T)[l]);
     __syncwarp();
   } else {
     for (int t = I.a; t < I.b; t++) {
@@ -1650,7 +1658,8 @@ __global__ void __launch_bounds__(512) k_adjoint_wide(KArgs args, Work<double> w
   g.grid = 0;
   const int bi = blockIdx.x;
   if (bi >= args.B) return;
-  load_prob<N, U>(P, *args.prob, args.xref ? args.xref + (size_t)bi * N : nullptr, args.inst[bi].dt);
+  load_prob<N, U>(P, *args.prob, args.xref ? args.xref + (size_t)bi * N : nullptr, args.inst[bi].dt,
+                  inst_xtraj<N>(args, args.inst[bi]), inst_utraj<U>(args, args.inst[bi]), args.inst[bi].T);
   const InstDev id = args.inst[bi];
   Inst<M, double> I;
   I.setup(w, id, args.x0 + (size_t)bi * N, g.warp(), nw, P.nw);

@@ -26,7 +26,7 @@ STATUS = {0: "ok", -1: "invalid argument", -2: "infeasible start", -3: "not conv
 EXPORTS = ["ptn_default_options", "ptn_solver_create", "ptn_solver_destroy", "ptn_last_error",
            "ptn_set_options", "ptn_solve_ip", "ptn_solve_admm", "ptn_solve_batch", "ptn_adjoint",
            "ptn_num_rows", "ptn_version", "ptn_solve_ip_static", "ptn_batch_prepare",
-           "ptn_solve_batch_async", "ptn_model_dims", "ptn_adjoint_checkpointed"]
+           "ptn_solve_batch_async", "ptn_model_dims", "ptn_adjoint_checkpointed", "ptn_set_reference"]
 
 _P = C.POINTER(C.c_double)
 
@@ -97,6 +97,7 @@ def load(path: str = LIB_PATH):
                                     vp, vp, vp, vp]
         lib.ptn_adjoint_checkpointed.argtypes = [vp, C.c_int, C.c_int, vp, vp, vp, vp, C.c_double, C.c_double, vp,
                                                  vp, vp, vp, vp, vp, vp, vp]
+        lib.ptn_set_reference.argtypes = [vp, vp, vp]
         lib.ptn_num_rows.argtypes = [vp]
         lib.ptn_solve_ip_static.argtypes = [C.POINTER(Problem), C.POINTER(Options), vp, vp, C.c_int, vp, vp, vp,
                                             C.POINTER(Info), C.c_char_p, C.c_int, vp]
@@ -202,6 +203,18 @@ class Solver:
         for k, v in kw.items():
             setattr(self.options, k, v)
         rc = load().ptn_set_options(self._h, C.byref(self.options))
+        if rc != 0:
+            raise PtnError(self.last_error())
+
+    def set_reference(self, xref_traj=None, uref_traj=None):
+        """Time-varying targets for the following solves (ptn_set_reference): contiguous
+        float64 CUDA tensors laid out like the state / control outputs of those solves, or
+        None.  The solver keeps references to the tensors."""
+        for a in (xref_traj, uref_traj):
+            if a is not None and (not a.is_cuda or a.dtype.itemsize != 8 or not a.is_contiguous()):
+                raise ValueError("targets must be contiguous float64 CUDA tensors")
+        self._refs = (xref_traj, uref_traj)
+        rc = load().ptn_set_reference(self._h, _dptr(xref_traj), _dptr(uref_traj))
         if rc != 0:
             raise PtnError(self.last_error())
 

@@ -74,6 +74,7 @@ def test_entry_points_refuse_null_handles_and_pointers_without_a_gpu():
     assert lib.ptn_solve_batch_async(None, None, None, None, None, None, None, None, None) == INVALID
     assert lib.ptn_solve_ip(None, None, None, 8, None, None, None, None, None) == INVALID
     assert lib.ptn_set_options(None, None) == INVALID
+    assert lib.ptn_set_reference(None, None, None) == INVALID
     assert lib.ptn_adjoint_checkpointed(None, 8, 4, None, None, None, None, 1.0, 1.0, None, None, None, None, None,
                                         None, None, None) == INVALID
     assert lib.ptn_last_error(None) is not None
