@@ -174,6 +174,15 @@ def _oracle_ref(job):
         _, b, T = job
         args = (W.quadrotor(W.quadrotor_waypoints(b + 1, seed=0)[b]), np.zeros(12), T)
         kw = {"u_init": np.full((T, 4), W.quadrotor_hover_u())}
+    elif kind == "admm_pend":
+        # ADMM on the paper's pendulum with the bench's settings (rho, the 1e-2 rule)
+        T = job[1]
+        t0 = time.perf_counter()
+        r = O.solve_admm(W.pendulum_paper(dt=3.2 / T), W.pendulum_x0(0), T,
+                         opts=O.Options(rho=W.PAPER_ADMM["pendulum_rho"], admm_tol=W.PAPER_ADMM["tol"],
+                                        max_outer=2000))
+        r["ms"] = (time.perf_counter() - t0) * 1e3
+        return r
     else:
         raise ValueError(job)
     t0 = time.perf_counter()
@@ -383,6 +392,7 @@ def run_multiplier(args, ptn, W, dev, flush, stream, tuned, x0):
     import torch
     from paper_2409_20027_gb300 import autotune
     out = {"single": {}}
+    sols = {}
     for Ts in [1024, 4096, args.T]:
         ps = cartpole_instance(Ts)
         row = {}
@@ -394,11 +404,13 @@ def run_multiplier(args, ptn, W, dev, flush, stream, tuned, x0):
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             flush.zero_()
             a.record(stream)
-            _, _, _, inf = sv.solve_ip(x0, Ts)
+            xs_, us_, ls_, inf = sv.solve_ip(x0, Ts)
             b.record(stream)
             torch.cuda.synchronize()
             row[f"mode{mode}"] = {"ms": a.elapsed_time(b), "newton_iters": inf["newton_iters"],
                                   "status": inf["status"], "r_kkt": inf["r_kkt"]}
+            if mode > 0:
+                sols[("mult", Ts, mode)] = (xs_.cpu().numpy(), us_.cpu().numpy(), ls_.cpu().numpy(), inf["J"])
             sv.close()
         out["single"][str(Ts)] = row
     B = args.batch
@@ -426,7 +438,7 @@ def run_multiplier(args, ptn, W, dev, flush, stream, tuned, x0):
     out["workload"] = ("cart-pole IP as the sweep (2.56 s horizon, tuned launch, x0 seed 0) in co-state forms "
                        "0 (scan), 1 (multiplier), 2 (multiplier restarted per barrier level); the batch "
                        "workload in forms 1 and 2 (form 0: the batch section)")
-    return out
+    return out, sols
 
 
 def _admm_solve(ptn, prob, T, x0, stream, flush, tuned, **opt):
@@ -439,12 +451,13 @@ def _admm_solve(ptn, prob, T, x0, stream, flush, tuned, **opt):
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     flush.zero_()
     a.record(stream)
-    _, _, _, inf = sv.solve_admm(x0, T)
+    xs, us, ls, inf = sv.solve_admm(x0, T)
     b.record(stream)
     torch.cuda.synchronize()
     sv.close()
-    return {"ms": a.elapsed_time(b), "status": inf["status"], "outer_iters": inf["outer_iters"],
-            "newton_iters": inf["newton_iters"], "r_p": inf["r_p"], "r_d": inf["r_d"], "r_stat": inf["r_stat"]}
+    row = {"ms": a.elapsed_time(b), "status": inf["status"], "outer_iters": inf["outer_iters"],
+           "newton_iters": inf["newton_iters"], "r_p": inf["r_p"], "r_d": inf["r_d"], "r_stat": inf["r_stat"]}
+    return row, (xs.cpu().numpy(), us.cpu().numpy(), None, inf["J"])
 
 
 def run_admm(args, ptn, W, dev, flush, stream, tuned, x0):
@@ -458,17 +471,20 @@ def run_admm(args, ptn, W, dev, flush, stream, tuned, x0):
     import torch
     out = {"pendulum_paper": {}, "cartpole": {}}
     xp = torch.tensor(W.pendulum_x0(0), dtype=torch.float64, device=dev)
+    sols = {}
     for Ts in [256, 1024, 4096, 16384]:
-        out["pendulum_paper"][str(Ts)] = _admm_solve(ptn, W.pendulum_paper(dt=3.2 / Ts), Ts, xp, stream, flush, tuned,
-                                                     rho=W.PAPER_ADMM["pendulum_rho"], admm_tol=W.PAPER_ADMM["tol"],
-                                                     max_outer=2000)
+        row, sol = _admm_solve(ptn, W.pendulum_paper(dt=3.2 / Ts), Ts, xp, stream, flush, tuned,
+                               rho=W.PAPER_ADMM["pendulum_rho"], admm_tol=W.PAPER_ADMM["tol"], max_outer=2000)
+        out["pendulum_paper"][str(Ts)] = row
+        if Ts == 256:
+            sols[("admm_pend", Ts)] = sol
     for Ts in [256, 1024]:
-        out["cartpole"][str(Ts)] = _admm_solve(ptn, cartpole_instance(Ts), Ts, x0, stream, flush, tuned, rho=1.0,
-                                               admm_tol=1e-2, max_outer=2000)
+        out["cartpole"][str(Ts)], _ = _admm_solve(ptn, cartpole_instance(Ts), Ts, x0, stream, flush, tuned, rho=1.0,
+                                                  admm_tol=1e-2, max_outer=2000)
     out["workload"] = ("ADMM, stop at max|w-z|, max|z-z_prev| <= 1e-2 or 2000 outer iterations; the paper's pendulum "
                        "(rho 1) on 3.2 s at dt = 3.2/T, x0 seed 0; the cart-pole of the sweep (rho 1, 2.56 s, x0 seed "
                        "0); Newton sub-problems to 1e-6, FP32 LQR with FP64 solves")
-    return out
+    return out, sols
 
 
 PHASES = ["costate", "second_order", "value", "state", "line_search", "initial_rollout", "other"]
@@ -663,7 +679,7 @@ def run_literal_dt(args, ptn, W, dev, flush, stream, tuned):
             b.record(stream)
             torch.cuda.synchronize()
             row[f"mode{mode}"] = {"ms": a.elapsed_time(b), "status": inf["status"], "newton_iters": inf["newton_iters"],
-                                  "r_stat": inf["r_stat"]}
+                                  "r_stat": inf["r_stat"], "J": inf["J"]}
             sv.close()
         out[str(T)] = row
     return out
@@ -686,7 +702,7 @@ def oracle_literal(T):
         nm = np.linalg.norm(M)
         lg += np.log10(nm)
         M /= nm
-    return {"status": r["info"]["status"], "newton_iters": r["info"]["newton_iters"], "ms": ms,
+    return {"status": r["info"]["status"], "newton_iters": r["info"]["newton_iters"], "ms": ms, "J": r["info"]["J"],
             "max_abs_lam": float(np.abs(r["lam"]).max()), "log10_norm_prod_F": lg}
 
 
@@ -696,7 +712,7 @@ def run_sequential(args, ptn, W, dev, flush, stream):
     thread running the serial recursions) next to the parallel-in-time solve of the sweep.
     (Bounded to one solve: the FP64 sequential baseline runs for minutes on this GPU.)"""
     import torch
-    out = {}
+    out, sols = {}, {}
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     for T in [1024]:
         p = cartpole_instance(T)
@@ -704,12 +720,13 @@ def run_sequential(args, ptn, W, dev, flush, stream):
         xs = torch.tensor(W.cartpole_x0(0), dtype=torch.float64, device=dev)
         flush.zero_()
         a.record(stream)
-        _, _, _, inf = sv.solve_ip(xs, T)
+        xq, uq, lq, inf = sv.solve_ip(xs, T)
         b.record(stream)
         torch.cuda.synchronize()
         out[str(T)] = {"ms": a.elapsed_time(b), "newton_iters": inf["newton_iters"], "status": inf["status"]}
+        sols[("seq", T)] = (xq.cpu().numpy(), uq.cpu().numpy(), lq.cpu().numpy(), inf["J"])
         sv.close()
-    return out
+    return out, sols
 
 
 def config(T):
@@ -883,15 +900,21 @@ def main():
     mpcl = None
     if not args.no_mpc and single:
         mpcl = run_mpc(ptn, W, dev, stream)
+    # solutions compared with an oracle solve of another section's workload: key ->
+    # (the oracle job, the GPU solution)
+    cross_out = {}
     seq = None
     if not args.no_seq and single:
-        seq = run_sequential(args, ptn, W, dev, flush, stream)
+        seq, so = run_sequential(args, ptn, W, dev, flush, stream)
+        cross_out.update({k: (("cartpole", k[1], 0), v) for k, v in so.items()})
     admm = None
+    admm_out = {}
     if not args.no_admm and single:
-        admm = run_admm(args, ptn, W, dev, flush, stream, tuned, x0s[0])
+        admm, admm_out = run_admm(args, ptn, W, dev, flush, stream, tuned, x0s[0])
     mult = None
     if not args.no_mult and single:
-        mult = run_multiplier(args, ptn, W, dev, flush, stream, tuned, x0s[0])
+        mult, mo = run_multiplier(args, ptn, W, dev, flush, stream, tuned, x0s[0])
+        cross_out.update({k: (("cartpole", k[1], 0), v) for k, v in mo.items()})
     peaks = measured_fma_peaks() if rank == 0 else None
 
     if rank != 0:
@@ -929,6 +952,8 @@ def main():
         jobs = [k for k in gpu_out if k not in refs]
         jobs += [("quad", b, args.quad_T) for b in quad_out]
         jobs += list(synth_out)
+        jobs += list(admm_out)
+        jobs += [j for j, _ in cross_out.values() if j not in refs and j not in jobs]
         if batch is not None:
             bc, bref = cpu_batch_baseline()
             batch["cpu_baseline"] = bc
@@ -942,9 +967,13 @@ def main():
         outs.update({("quad", b, args.quad_T): v for b, v in quad_out.items()})
         outs.update({("batch", k): v for k, v in batch_out.items()})
         outs.update(synth_out)
+        outs.update(admm_out)
         for key, (x, u, lam, J) in outs.items():
             if key in refs:
                 errs["/".join(str(v) for v in key)] = err_vs_oracle(refs[key], x, u, lam, J)
+        for key, (job, (x, u, lam, J)) in cross_out.items():
+            if job in refs:
+                errs["/".join(str(v) for v in key)] = err_vs_oracle(refs[job], x, u, lam, J)
         if pend is not None:
             pend["oracle_ms_median"] = float(np.median([refs[("pendulum", sd)]["ms"] for sd in range(10)
                                                         if ("pendulum", sd) in refs] or [np.nan]))
@@ -968,6 +997,35 @@ def main():
     if synth is not None and errs:
         synth["batch"]["err_vs_oracle"] = max_err([v for k, v in errs.items() if k.startswith("synth/")])
         synth["batch"]["err_vs_oracle_sample"] = "the batch's shortest instance (oracle time grows as n^3 T)"
+    if synth is not None:
+        # the oracle's own solve of the single T = 65536 instance (stored: it takes minutes)
+        gold = os.path.join(ROOT, "tests", "golden", "synth_T65536.json")
+        if os.path.exists(gold) and synth["single"]["T"] == 65536:
+            with open(gold) as f:
+                g = json.load(f)["info"]
+            synth["single"]["oracle"] = {"status": g["status"], "newton_iters": g["newton_iters"], "J": g["J"],
+                                         "note": "stored oracle solve (tests/golden/synth_reference.py): the FP64 "
+                                                 "oracle does not converge on this instance, so no error is stated"}
+    if errs:
+        if seq is not None:
+            for Tq in seq:
+                seq[Tq]["err_vs_oracle"] = errs.get(f"seq/{Tq}")
+        if mult is not None:
+            for Tm, row in mult["single"].items():
+                for mode in [1, 2]:
+                    e = errs.get(f"mult/{Tm}/{mode}")
+                    if e is not None:
+                        row[f"mode{mode}"]["err_vs_oracle"] = e
+            mult["err_vs_oracle_reference"] = "the oracle's co-state form (mode 0) at the same instance"
+        if admm is not None and "admm_pend/256" in errs:
+            admm["pendulum_paper"]["256"]["err_vs_oracle"] = errs["admm_pend/256"]
+    if literal is not None:
+        for Tl, row in literal.items():
+            o = row.get("oracle_mode0") if isinstance(row, dict) else None
+            if o and o["status"] == 0:
+                for mode in ["mode0", "mode1"]:
+                    if row[mode]["status"] == 0:
+                        row[mode]["J_err_vs_oracle"] = abs(row[mode]["J"] - o["J"]) / max(1.0, abs(o["J"]))
     line = {"metric": METRIC, "value": ms, "unit": "ms", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic", "config": config(T),
