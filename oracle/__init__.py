@@ -50,11 +50,19 @@ def build(force: bool = False) -> str:
 _P = C.POINTER(C.c_double)
 
 
+# callbacks of user-written terms (orc_ustage_fn, orc_uterm_fn, orc_ucons_fn)
+_USTAGE = C.CFUNCTYPE(C.c_double, C.c_void_p, C.c_int, _P, _P, _P, _P)
+_UTERM = C.CFUNCTYPE(C.c_double, C.c_void_p, _P, _P, _P)
+_UCONS = C.CFUNCTYPE(None, C.c_void_p, C.c_int, _P, _P, _P, _P, _P)
+
+
 class _Problem(C.Structure):
     _fields_ = [("model", C.c_int), ("nx", C.c_int), ("nu", C.c_int), ("integrator", C.c_int),
                 ("dt", C.c_double), ("prm", C.c_double * MAXP),
                 ("A", _P), ("B", _P), ("W", _P), ("Q", _P), ("R", _P), ("Qf", _P),
                 ("xref", _P), ("uref", _P), ("xref_traj", _P), ("uref_traj", _P), ("T_traj", C.c_int),
+                ("ustage", _USTAGE), ("uterm", _UTERM), ("ucons", _UCONS), ("nc", C.c_int),
+                ("uctx", C.c_void_p),
                 ("xlo", _P), ("xhi", _P), ("ulo", _P), ("uhi", _P)]
 
 
@@ -168,8 +176,52 @@ class _Bound:
                     raise ValueError(f"{name} must have {rows} x {cols} entries")
                 self.keep.append(a)
                 setattr(c, name, _ptr(a))
+        self._bind_user_terms(prob, c)
         self.c = c
         self.n, self.m = c.nx, c.nu
+
+    def _bind_user_terms(self, prob, c):
+        # user-written stage cost, terminal cost and inequality rows (Problem.user_terms: an
+        # object with stage(t, x, u) -> (l, grad_z, hess_z), terminal(x) -> (l, grad, hess),
+        # constraints(t, x, u) -> (g, jac_z, hess_z) and nc; any of them may be None)
+        ut = getattr(prob, "user_terms", None)
+        c.nc = 0
+        if ut is None:
+            return
+        n, m = int(prob.nx), int(prob.nu)
+        K = n + m
+
+        def put(ptr, a):
+            if ptr:
+                a = np.asarray(a, dtype=np.float64).ravel()
+                for i, v in enumerate(a):
+                    ptr[i] = v
+
+        if getattr(ut, "stage", None) is not None:
+            def stage(ctx, t, x, u, gz, Hz):
+                xa = np.ctypeslib.as_array(x, shape=(n,)).copy()
+                ua = np.ctypeslib.as_array(u, shape=(m,)).copy()
+                l, g, H = ut.stage(int(t), xa, ua)
+                put(gz, g); put(Hz, np.asarray(H).reshape(K, K))
+                return float(l)
+            cb = _USTAGE(stage); self.keep.append(cb); c.ustage = cb
+        if getattr(ut, "terminal", None) is not None:
+            def term(ctx, x, gx, Hx):
+                xa = np.ctypeslib.as_array(x, shape=(n,)).copy()
+                l, g, H = ut.terminal(xa)
+                put(gx, g); put(Hx, np.asarray(H).reshape(n, n))
+                return float(l)
+            cb = _UTERM(term); self.keep.append(cb); c.uterm = cb
+        if getattr(ut, "constraints", None) is not None and int(ut.nc) > 0:
+            nc = int(ut.nc)
+
+            def cons(ctx, t, x, u, g, Jz, Hz):
+                xa = np.ctypeslib.as_array(x, shape=(n,)).copy()
+                ua = np.ctypeslib.as_array(u, shape=(m,)).copy()
+                gv, J, H = ut.constraints(int(t), xa, ua)
+                put(g, gv); put(Jz, np.asarray(J).reshape(nc, K)); put(Hz, np.asarray(H).reshape(nc, K, K))
+            cb = _UCONS(cons); self.keep.append(cb); c.ucons = cb
+            c.nc = nc
 
     def ref(self):
         return C.byref(self.c)

@@ -44,6 +44,23 @@ enum { ORC_EULER = 0, ORC_RK4 = 1 };
 enum { ORC_OK = 0, ORC_EINVAL = -1, ORC_EINFEAS = -2, ORC_ENOTCONV = -3, ORC_ENUM = -4 };
 enum { AUG_NONE = 0, AUG_BARRIER = 1, AUG_ADMM = 2 };
 
+/* Optional user-written terms of the problem statement (Sec. II-A, eq. ocp: a general stage
+ * cost l_t, terminal cost l_T and inequality rows g_t(x, u) <= 0), given as callbacks with
+ * their derivatives over z = (x, u):
+ *   ustage: l_t(x, u); gz (n + m) its gradient and Hz ((n+m) x (n+m), row-major) its
+ *           Hessian when the pointers are non-NULL;
+ *   uterm:  l_T(x); gx (n), Hx (n x n) likewise;
+ *   ucons:  the nc rows g_i(t, x, u) into g (nc); Jz (nc x (n+m)) and Hz (nc x (n+m) x (n+m))
+ *           when non-NULL.
+ * A user stage / terminal cost replaces the quadratic tracking term; user rows join the
+ * box rows in the log barrier (interior point only). */
+typedef double (*orc_ustage_fn)(void *ctx, int t, const double *x, const double *u, double *gz, double *Hz);
+typedef double (*orc_uterm_fn)(void *ctx, const double *x, double *gx, double *Hx);
+typedef void (*orc_ucons_fn)(void *ctx, int t, const double *x, const double *u, double *g, double *Jz,
+                             double *Hz);
+
+#define ORC_MAXC 8
+
 typedef struct orc_problem {
     int model, nx, nu, integrator;
     double dt;
@@ -54,6 +71,11 @@ typedef struct orc_problem {
     const double *xref_traj;         /* time-varying targets (T+1) x nx, or NULL: xref at every t */
     const double *uref_traj;         /* T x nu, or NULL: uref at every t */
     int T_traj;                      /* horizon of the target trajectories (the terminal index) */
+    orc_ustage_fn ustage;            /* user stage cost, or NULL (quadratic tracking) */
+    orc_uterm_fn uterm;              /* user terminal cost, or NULL */
+    orc_ucons_fn ucons;              /* user inequality rows, or NULL */
+    int nc;                          /* number of user rows (<= ORC_MAXC) */
+    void *uctx;                      /* passed to the callbacks */
     const double *xlo, *xhi, *ulo, *uhi; /* box bounds; |b| >= 1e300 or non-finite = none */
 } orc_problem;
 
@@ -475,14 +497,26 @@ static double stage_cost(const orc_problem *P, const rows_t *R, const orc_aug *G
 {
     int n = P->nx, m = P->nu;
     double ex[ORC_MAXN], eu[ORC_MAXM], l = 0.0;
-    const double *xr = xref_at(P, t), *ur = uref_at(P, t);
-    for (int i = 0; i < n; i++) ex[i] = x[i] - xr[i];
-    for (int i = 0; i < m; i++) eu[i] = u[i] - ur[i];
-    for (int i = 0; i < n; i++)
-        for (int j = 0; j < n; j++) l += ex[i] * P->Q[i * n + j] * ex[j];
-    for (int i = 0; i < m; i++)
-        for (int j = 0; j < m; j++) l += eu[i] * P->R[i * m + j] * eu[j];
+    if (P->ustage) {
+        l = P->ustage(P->uctx, t, x, u, NULL, NULL);
+    } else {
+        const double *xr = xref_at(P, t), *ur = uref_at(P, t);
+        for (int i = 0; i < n; i++) ex[i] = x[i] - xr[i];
+        for (int i = 0; i < m; i++) eu[i] = u[i] - ur[i];
+        for (int i = 0; i < n; i++)
+            for (int j = 0; j < n; j++) l += ex[i] * P->Q[i * n + j] * ex[j];
+        for (int i = 0; i < m; i++)
+            for (int j = 0; j < m; j++) l += eu[i] * P->R[i * m + j] * eu[j];
+    }
     if (lonly) *lonly = l;
+    if (P->ucons && P->nc > 0 && G->kind == AUG_BARRIER) {  /* user rows: the IP method */
+        double g[ORC_MAXC];
+        P->ucons(P->uctx, t, x, u, g, NULL, NULL);
+        for (int i = 0; i < P->nc; i++) {
+            if (!(g[i] < 0.0)) { *infeas = 1; return INFINITY; }
+            l -= G->mu * log(-g[i]);
+        }
+    }
     double c = 0.0;
     for (int r = 0; r < R->nw; r++) {
         double w = row_value(R, r, x, u);
@@ -502,20 +536,53 @@ static void stage_derivs(const orc_problem *P, const rows_t *R, const orc_aug *G
                          const double *x, const double *u, double *lx, double *lu, double *lxx,
                          double *lxu, double *luu)
 {
-    int n = P->nx, m = P->nu;
-    const double *xr = xref_at(P, t), *ur = uref_at(P, t);
-    for (int i = 0; i < n; i++) {
-        double s = 0.0;
-        for (int j = 0; j < n; j++) s += (P->Q[i * n + j] + P->Q[j * n + i]) * (x[j] - xr[j]);
-        lx[i] = s;
-        for (int j = 0; j < n; j++) lxx[i * n + j] = P->Q[i * n + j] + P->Q[j * n + i];
-        for (int j = 0; j < m; j++) lxu[i * m + j] = 0.0;
+    int n = P->nx, m = P->nu, K = n + m;
+    if (P->ustage) {
+        double gz[ORC_MAXN + ORC_MAXM], Hz[(ORC_MAXN + ORC_MAXM) * (ORC_MAXN + ORC_MAXM)];
+        P->ustage(P->uctx, t, x, u, gz, Hz);
+        for (int i = 0; i < n; i++) {
+            lx[i] = gz[i];
+            for (int j = 0; j < n; j++) lxx[i * n + j] = Hz[i * K + j];
+            for (int j = 0; j < m; j++) lxu[i * m + j] = Hz[i * K + n + j];
+        }
+        for (int i = 0; i < m; i++) {
+            lu[i] = gz[n + i];
+            for (int j = 0; j < m; j++) luu[i * m + j] = Hz[(n + i) * K + n + j];
+        }
+    } else {
+        const double *xr = xref_at(P, t), *ur = uref_at(P, t);
+        for (int i = 0; i < n; i++) {
+            double s = 0.0;
+            for (int j = 0; j < n; j++) s += (P->Q[i * n + j] + P->Q[j * n + i]) * (x[j] - xr[j]);
+            lx[i] = s;
+            for (int j = 0; j < n; j++) lxx[i * n + j] = P->Q[i * n + j] + P->Q[j * n + i];
+            for (int j = 0; j < m; j++) lxu[i * m + j] = 0.0;
+        }
+        for (int i = 0; i < m; i++) {
+            double s = 0.0;
+            for (int j = 0; j < m; j++) s += (P->R[i * m + j] + P->R[j * m + i]) * (u[j] - ur[j]);
+            lu[i] = s;
+            for (int j = 0; j < m; j++) luu[i * m + j] = P->R[i * m + j] + P->R[j * m + i];
+        }
     }
-    for (int i = 0; i < m; i++) {
-        double s = 0.0;
-        for (int j = 0; j < m; j++) s += (P->R[i * m + j] + P->R[j * m + i]) * (u[j] - ur[j]);
-        lu[i] = s;
-        for (int j = 0; j < m; j++) luu[i * m + j] = P->R[i * m + j] + P->R[j * m + i];
+    if (P->ucons && P->nc > 0 && G->kind == AUG_BARRIER) {
+        /* -mu log(-g): gradient mu grad(g) / (-g), Hessian mu (grad g grad g^T / g^2 + Hess(g) / (-g)) */
+        double g[ORC_MAXC], Jz[ORC_MAXC * (ORC_MAXN + ORC_MAXM)],
+            Hz[ORC_MAXC * (ORC_MAXN + ORC_MAXM) * (ORC_MAXN + ORC_MAXM)];
+        P->ucons(P->uctx, t, x, u, g, Jz, Hz);
+        for (int c = 0; c < P->nc; c++) {
+            const double a = G->mu / (-g[c]), b = G->mu / (g[c] * g[c]);
+            const double *J = Jz + c * K, *H = Hz + (size_t)c * K * K;
+            for (int i = 0; i < K; i++) {
+                if (i < n) lx[i] += a * J[i]; else lu[i - n] += a * J[i];
+                for (int j = 0; j < K; j++) {
+                    const double h = b * J[i] * J[j] + a * H[i * K + j];
+                    if (i < n && j < n) lxx[i * n + j] += h;
+                    else if (i < n) lxu[i * m + (j - n)] += h;
+                    else if (j >= n) luu[(i - n) * m + (j - n)] += h;
+                }
+            }
+        }
     }
     for (int r = 0; r < R->nw; r++) {
         double w = row_value(R, r, x, u), sg = R->sgn[r], g1, g2;
@@ -537,6 +604,7 @@ static void stage_derivs(const orc_problem *P, const rows_t *R, const orc_aug *G
 static double terminal_cost(const orc_problem *P, const double *x)
 {
     int n = P->nx;
+    if (P->uterm) return P->uterm(P->uctx, x, NULL, NULL);
     const double *xr = xref_at(P, P->T_traj);
     double l = 0.0;
     for (int i = 0; i < n; i++)
@@ -546,6 +614,12 @@ static double terminal_cost(const orc_problem *P, const double *x)
 static void terminal_grad(const orc_problem *P, const double *x, double *g, double *H)
 {
     int n = P->nx;
+    if (P->uterm) {
+        double Hx[ORC_MAXN * ORC_MAXN];
+        P->uterm(P->uctx, x, g, Hx);
+        if (H) memcpy(H, Hx, sizeof(double) * n * n);
+        return;
+    }
     const double *xr = xref_at(P, P->T_traj);
     for (int i = 0; i < n; i++) {
         double s = 0.0;
@@ -1294,6 +1368,11 @@ static void residuals(const orc_problem *P, const rows_t *R, const orc_aug *G, i
         orc_step(P, x + t * n, u + t * m, xn);
         for (int i = 0; i < n; i++) rd = fmax(rd, fabs(x[(t + 1) * n + i] - xn[i]));
         for (int r = 0; r < R->nw; r++) rf = fmax(rf, row_value(R, r, x + t * n, u + t * m));
+        if (P->ucons && P->nc > 0) {
+            double g[ORC_MAXC];
+            P->ucons(P->uctx, t, x + t * n, u + t * m, g, NULL, NULL);
+            for (int c = 0; c < P->nc; c++) rf = fmax(rf, g[c]);
+        }
     }
     double Jp;
     double Jc = traj_cost(P, R, G, T, x, u, &Jp);
@@ -1314,9 +1393,16 @@ static int check_feasible(const orc_problem *P, const rows_t *R, int T, const do
                           const double *u)
 {
     int n = P->nx, m = P->nu;
-    for (int t = 0; t < T; t++)
+    for (int t = 0; t < T; t++) {
         for (int r = 0; r < R->nw; r++)
             if (!(row_value(R, r, x + t * n, u + t * m) < 0.0)) return 0;
+        if (P->ucons && P->nc > 0) {
+            double g[ORC_MAXC];
+            P->ucons(P->uctx, t, x + t * n, u + t * m, g, NULL, NULL);
+            for (int c = 0; c < P->nc; c++)
+                if (!(g[c] < 0.0)) return 0;
+        }
+    }
     return 1;
 }
 
@@ -1403,6 +1489,7 @@ int orc_solve_admm(const orc_problem *P, const orc_options *o, const double *x0,
     int n = P->nx, m = P->nu;
     memset(info, 0, sizeof(double) * 16);
     if (T < 1 || n < 1 || n > ORC_MAXN || m < 1 || m > ORC_MAXM) { info[0] = ORC_EINVAL; return ORC_EINVAL; }
+    if (P->ucons && P->nc > 0) { info[0] = ORC_EINVAL; return ORC_EINVAL; }  /* user rows: IP only */
     rows_t R;
     build_rows(P, &R);
     int nw = R.nw;
@@ -1491,14 +1578,14 @@ int orc_adjoint(const orc_problem *P, double mu, int T, const double *x, const d
         g_x0[i] = gJ * W.lam[i];
         double sq = 0.0;
         for (int t = 0; t < T; t++) { double e = x[t * n + i] - xref_at(P, t)[i]; sq += e * e; }
-        g_Qd[i] = gJ * sq;
+        g_Qd[i] = P->ustage ? 0.0 : gJ * sq;  /* a user stage cost does not depend on Q, R */
         double e = x[T * n + i] - xref_at(P, T)[i];
-        g_Qfd[i] = gJ * e * e;
+        g_Qfd[i] = P->uterm ? 0.0 : gJ * e * e;
     }
     for (int i = 0; i < m; i++) {
         double sq = 0.0;
         for (int t = 0; t < T; t++) { double e = u[t * m + i] - uref_at(P, t)[i]; sq += e * e; }
-        g_Rd[i] = gJ * sq;
+        g_Rd[i] = P->ustage ? 0.0 : gJ * sq;
     }
     for (int k = 0; k < ORC_MAXP; k++) g_prm[k] = 0.0;
     for (int t = 0; t < T; t++) {
@@ -1538,13 +1625,13 @@ int orc_adjoint(const orc_problem *P, double mu, int T, const double *x, const d
             g_x0[i] -= nu[i];
             double a = 0.0;
             for (int t = 0; t < T; t++) a += W.dx[t * n + i] * 2.0 * (x[t * n + i] - xref_at(P, t)[i]);
-            g_Qd[i] -= a;
-            g_Qfd[i] -= W.dx[T * n + i] * 2.0 * (x[T * n + i] - xref_at(P, T)[i]);
+            if (!P->ustage) g_Qd[i] -= a;
+            if (!P->uterm) g_Qfd[i] -= W.dx[T * n + i] * 2.0 * (x[T * n + i] - xref_at(P, T)[i]);
         }
         for (int i = 0; i < m; i++) {
             double a = 0.0;
             for (int t = 0; t < T; t++) a += W.du[t * m + i] * 2.0 * (u[t * m + i] - uref_at(P, t)[i]);
-            g_Rd[i] -= a;
+            if (!P->ustage) g_Rd[i] -= a;
         }
         for (int t = 0; t < T; t++) {
             orc_param_jac(P, x + t * n, u + t * m, dfdp);

@@ -45,6 +45,7 @@ class Problem:
     name: str = ""
     xref_traj: np.ndarray | None = None  # time-varying targets, (T+1) x nx (replaces xref)
     uref_traj: np.ndarray | None = None  # T x nu (replaces uref)
+    user_terms: object | None = None     # user-written stage / terminal costs and rows (oracle side)
 
     def replace(self, **kw) -> "Problem":
         d = dict(self.__dict__)
