@@ -39,7 +39,7 @@ typedef cudaError_t (*launch_fn)(LaunchReq&);
 // models registered from outside the library (ptn_user_model.cuh); filled by static
 // initialisers of the user units while the library loads, read-only afterwards
 struct UserModel {
-  int id, nx, nu;
+  int id, nx, nu, nrows;  // nrows: the model's own inequality rows (interior point only)
   launch_fn f64, f32d, f32;
 };
 constexpr int kMaxUserModels = 32;
@@ -87,10 +87,11 @@ bool has_bound(const double* b, int i) { return b && isfinite(b[i]) && fabs(b[i]
 }  // namespace
 
 namespace ptn {
-int register_model(int id, int nx, int nu, user_launch_fn f64, user_launch_fn f32d, user_launch_fn f32) {
+int register_model(int id, int nx, int nu, user_launch_fn f64, user_launch_fn f32d, user_launch_fn f32,
+                   int nrows) {
   if (id < PTN_USER_MODEL_MIN || nx < 1 || nx > PTN_MAXN || nu < 1 || nu > PTN_MAXM) return -1;
   if (find_user_model(id) || g_num_user_models >= kMaxUserModels) return -1;
-  g_user_models[g_num_user_models++] = UserModel{id, nx, nu, f64, f32d, f32};
+  g_user_models[g_num_user_models++] = UserModel{id, nx, nu, nrows, f64, f32d, f32};
   return 0;
 }
 }  // namespace ptn
@@ -504,6 +505,11 @@ static bool wide_batch_ranges(ptn_solver* s, launch_fn fn, int B, const int* T_b
 }
 
 static int plan_launch(ptn_solver* s, int method, int B, const int* T_b, long long steps, LaunchPlan* p) {
+  if (method == PTN_METHOD_ADMM) {
+    const UserModel* um = find_user_model(s->hprob.model);
+    if (um && um->nrows > 0)
+      return fail(s, PTN_ERR_INVALID_ARG, "model %d has its own constraint rows: interior point only", um->id);
+  }
   launch_fn fn = pick_launcher(s->hprob.model, s->opt.precision);
   if (!fn) return fail(s, PTN_ERR_INVALID_ARG, "kernels for model %d, precision %d are not built", s->hprob.model, s->opt.precision);
   *p = LaunchPlan{};

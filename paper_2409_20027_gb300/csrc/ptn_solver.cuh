@@ -219,9 +219,9 @@ struct AugF {
   __device__ AugF(const Aug& A) : mu(float(A.mu)), rho(float(A.rho)), irho(float(1.0 / A.rho)) {}
 };
 
+// quadratic tracking term of l_t
 template <int N, int U>
-__device__ double stage_cost(const ProbS<N, U>& P, const Aug& A, int t, const double* x, const double* u,
-                             bool& infeas, double* lplain = nullptr) {
+__device__ double track_cost(const ProbS<N, U>& P, int t, const double* x, const double* u) {
   const double *xr = xref_at(P, t), *ur = uref_at(P, t);
   double l = 0.0, e[N];
 #pragma unroll
@@ -243,7 +243,15 @@ __device__ double stage_cost(const ProbS<N, U>& P, const Aug& A, int t, const do
     for (int j = 0; j < U; j++) s += P.R[i * U + j] * eu[j];
     l += eu[i] * s;
   }
-  if (lplain) *lplain = l;
+  return l;
+}
+
+// barrier / penalty terms c_t of the box rows; infeas set when a barrier row is not
+// strictly inside
+template <int N, int U>
+__device__ double rows_cost(const ProbS<N, U>& P, const Aug& A, int t, const double* x, const double* u,
+                            bool& infeas) {
+  double l = 0.0;
   for (int r = 0; r < P.nw; r++) {
     const double zk = P.isx[r] ? x[P.idx[r]] : u[P.idx[r]];
     const double w = P.sgn[r] * (zk - P.bnd[r]);
@@ -259,22 +267,31 @@ __device__ double stage_cost(const ProbS<N, U>& P, const Aug& A, int t, const do
 }
 
 template <int N, int U>
+__device__ double stage_cost(const ProbS<N, U>& P, const Aug& A, int t, const double* x, const double* u,
+                             bool& infeas, double* lplain = nullptr) {
+  const double l = track_cost(P, t, x, u);
+  if (lplain) *lplain = l;
+  return l + rows_cost(P, A, t, x, u, infeas);
+}
+
+// gradient of l_t + c_t into lx, lu; with_track = false: of c_t alone (box rows)
+template <int N, int U>
 __device__ void stage_grad(const ProbS<N, U>& P, const Aug& A, int t, const double* x, const double* u,
-                           double* lx, double* lu) {
+                           double* lx, double* lu, bool with_track = true) {
   const double *xr = xref_at(P, t), *ur = uref_at(P, t);
 #pragma unroll
   for (int i = 0; i < N; i++) {
     double s = 0.0;
 #pragma unroll
     for (int j = 0; j < N; j++) s += (P.Q[i * N + j] + P.Q[j * N + i]) * (x[j] - xr[j]);
-    lx[i] = s;
+    lx[i] = with_track ? s : 0.0;
   }
 #pragma unroll
   for (int i = 0; i < U; i++) {
     double s = 0.0;
 #pragma unroll
     for (int j = 0; j < U; j++) s += (P.R[i * U + j] + P.R[j * U + i]) * (u[j] - ur[j]);
-    lu[i] = s;
+    lu[i] = with_track ? s : 0.0;
   }
   for (int r = 0; r < P.nw; r++) {
     const int k = P.idx[r];
@@ -288,18 +305,21 @@ __device__ void stage_grad(const ProbS<N, U>& P, const Aug& A, int t, const doub
   }
 }
 
-// adds the Hessians of l_t + c_t to P (N x N), R (U x U); l_xu = c_xu = 0 for box rows
+// adds the Hessians of l_t + c_t to P (N x N), R (U x U); l_xu = c_xu = 0 for box rows;
+// with_track = false: of c_t alone
 template <int N, int U, class L>
 __device__ void stage_hess_add(const ProbS<N, U>& P, const Aug& A, const double* x, const double* u, L* Pm,
-                               L* Rm) {
+                               L* Rm, bool with_track = true) {
+  if (with_track) {
 #pragma unroll
-  for (int i = 0; i < N; i++)
+    for (int i = 0; i < N; i++)
 #pragma unroll
-    for (int j = 0; j < N; j++) Pm[i * N + j] += L(P.Q[i * N + j] + P.Q[j * N + i]);
+      for (int j = 0; j < N; j++) Pm[i * N + j] += L(P.Q[i * N + j] + P.Q[j * N + i]);
 #pragma unroll
-  for (int i = 0; i < U; i++)
+    for (int i = 0; i < U; i++)
 #pragma unroll
-    for (int j = 0; j < U; j++) Rm[i * U + j] += L(P.R[i * U + j] + P.R[j * U + i]);
+      for (int j = 0; j < U; j++) Rm[i * U + j] += L(P.R[i * U + j] + P.R[j * U + i]);
+  }
   for (int r = 0; r < P.nw; r++) {
     const int k = P.idx[r];
     const double zk = P.isx[r] ? x[k] : u[k];
@@ -409,6 +429,292 @@ __device__ float terminal_delta(const ProbS<N, U>& P, const double* x0, const fl
 }
 
 // ---------------------------------------------------------------------------
+// User-written terms (the general l_t, l_T and rows g_t(x, u) <= 0 of Sec. II-A, eq. ocp).
+// A model may declare, as templates over the scalar type S (plain values, Dual and nested
+// Dual numbers: derivatives come from forward-mode AD, as for its dynamics):
+//   static constexpr bool USER_COST = true;
+//   template <class S> static S stage_l(int t, const double* p, const S* x, const S* u);
+//   template <class S> static S terminal_l(const double* p, const S* x);
+// replacing the quadratic tracking terms, and
+//   static constexpr int NC = ...;   // <= PTN_MAXC
+//   template <class S> static void constraints(int t, const double* p, const S* x, const S* u, S* g);
+// rows g_c <= 0 that join the box rows in the log barrier (interior point only).  The
+// functions below give the costs and their derivatives for any model (the built-in terms
+// when the model declares none).
+template <class M, class = void>
+struct user_cost {
+  static constexpr bool value = false;
+};
+template <class M>
+struct user_cost<M, std::void_t<decltype(M::USER_COST)>> {
+  static constexpr bool value = M::USER_COST;
+};
+template <class M, class = void>
+struct user_rows {
+  static constexpr int value = 0;
+};
+template <class M>
+struct user_rows<M, std::void_t<decltype(M::NC)>> {
+  static constexpr int value = M::NC;
+};
+template <class M>
+struct has_user_terms {
+  static constexpr bool value = user_cost<M>::value || user_rows<M>::value > 0;
+};
+
+// value and gradient over z = (x, u) of the user stage cost (Dual numbers)
+template <class M, int N, int U>
+__device__ double user_l_grad(const ProbS<N, U>& P, int t, const double* x, const double* u, double* gz) {
+  constexpr int K = N + U;
+  using D = Dual<double, K>;
+  D xd[N], ud[U];
+#pragma unroll
+  for (int i = 0; i < N; i++) { xd[i] = D(x[i]); xd[i].d[i] = 1.0; }
+#pragma unroll
+  for (int i = 0; i < U; i++) { ud[i] = D(u[i]); ud[i].d[N + i] = 1.0; }
+  const D l = M::template stage_l<D>(t, P.prm, xd, ud);
+#pragma unroll
+  for (int k = 0; k < K; k++) gz[k] = l.d[k];
+  return l.v;
+}
+// user rows and their Jacobian over z (Dual numbers): g (NC), J (NC x K)
+template <class M, int N, int U>
+__device__ void user_rows_jac(const ProbS<N, U>& P, int t, const double* x, const double* u, double* g, double* J) {
+  constexpr int K = N + U, NC = user_rows<M>::value;
+  using D = Dual<double, K>;
+  D xd[N], ud[U], gd[NC];
+#pragma unroll
+  for (int i = 0; i < N; i++) { xd[i] = D(x[i]); xd[i].d[i] = 1.0; }
+#pragma unroll
+  for (int i = 0; i < U; i++) { ud[i] = D(u[i]); ud[i].d[N + i] = 1.0; }
+  M::template constraints<D>(t, P.prm, xd, ud, gd);
+#pragma unroll
+  for (int c = 0; c < NC; c++) {
+    g[c] = gd[c].v;
+#pragma unroll
+    for (int k = 0; k < K; k++) J[c * K + k] = gd[c].d[k];
+  }
+}
+// second derivatives over z of the user stage cost (Hl, K x K) and rows (Hg, NC x K x K):
+// one nested Dual evaluation per pair a <= b
+template <class M, int N, int U>
+__device__ void user_hess(const ProbS<N, U>& P, int t, const double* x, const double* u, double* Hl, double* Hg) {
+  constexpr int K = N + U, NC = user_rows<M>::value;
+  using D1 = Dual<double, 1>;
+  using D2 = Dual<D1, 1>;
+  for (int a = 0; a < K; a++)
+    for (int b = a; b < K; b++) {
+      D2 xd[N], ud[U];
+#pragma unroll
+      for (int i = 0; i < N; i++) {
+        xd[i] = D2(D1(x[i]));
+        xd[i].v.d[0] = (i == a) ? 1.0 : 0.0;
+        xd[i].d[0] = D1((i == b) ? 1.0 : 0.0);
+      }
+#pragma unroll
+      for (int i = 0; i < U; i++) {
+        ud[i] = D2(D1(u[i]));
+        ud[i].v.d[0] = (N + i == a) ? 1.0 : 0.0;
+        ud[i].d[0] = D1((N + i == b) ? 1.0 : 0.0);
+      }
+      if constexpr (user_cost<M>::value) {
+        const D2 l = M::template stage_l<D2>(t, P.prm, xd, ud);
+        Hl[a * K + b] = Hl[b * K + a] = l.d[0].d[0];
+      }
+      if constexpr (NC > 0) {
+        D2 gd[NC];
+        M::template constraints<D2>(t, P.prm, xd, ud, gd);
+#pragma unroll
+        for (int c = 0; c < NC; c++) Hg[(c * K + a) * K + b] = Hg[(c * K + b) * K + a] = gd[c].d[0].d[0];
+      }
+    }
+}
+
+// l_t + c_t (+ the user rows' barrier)
+template <class M, int N, int U>
+__device__ double mstage_cost(const ProbS<N, U>& P, const Aug& A, int t, const double* x, const double* u,
+                              bool& infeas, double* lplain = nullptr) {
+  if constexpr (!has_user_terms<M>::value) {
+    return stage_cost(P, A, t, x, u, infeas, lplain);
+  } else {
+    double l;
+    if constexpr (user_cost<M>::value) l = M::template stage_l<double>(t, P.prm, x, u);
+    else l = track_cost(P, t, x, u);
+    if (lplain) *lplain = l;
+    l += rows_cost(P, A, t, x, u, infeas);
+    if constexpr (user_rows<M>::value > 0) {
+      if (A.kind == AUG_BARRIER) {
+        double g[user_rows<M>::value];
+        M::template constraints<double>(t, P.prm, x, u, g);
+#pragma unroll
+        for (int c = 0; c < user_rows<M>::value; c++) {
+          if (!(g[c] < 0.0)) infeas = true;
+          else l -= A.mu * log(-g[c]);
+        }
+      }
+    }
+    return l;
+  }
+}
+
+template <class M, int N, int U>
+__device__ void mstage_grad(const ProbS<N, U>& P, const Aug& A, int t, const double* x, const double* u,
+                            double* lx, double* lu) {
+  if constexpr (!has_user_terms<M>::value) {
+    stage_grad(P, A, t, x, u, lx, lu);
+  } else {
+    constexpr int K = N + U, NC = user_rows<M>::value;
+    stage_grad(P, A, t, x, u, lx, lu, !user_cost<M>::value);
+    if constexpr (user_cost<M>::value) {
+      double gz[K];
+      user_l_grad<M>(P, t, x, u, gz);
+#pragma unroll
+      for (int i = 0; i < N; i++) lx[i] += gz[i];
+#pragma unroll
+      for (int i = 0; i < U; i++) lu[i] += gz[N + i];
+    }
+    if constexpr (NC > 0) {
+      if (A.kind == AUG_BARRIER) {
+        double g[NC], J[NC * K];
+        user_rows_jac<M>(P, t, x, u, g, J);
+#pragma unroll
+        for (int c = 0; c < NC; c++) {
+          const double a = A.mu / (-g[c]);
+#pragma unroll
+          for (int i = 0; i < N; i++) lx[i] += a * J[c * K + i];
+#pragma unroll
+          for (int i = 0; i < U; i++) lu[i] += a * J[c * K + N + i];
+        }
+      }
+    }
+  }
+}
+
+// adds the Hessians of l_t + c_t (and the user terms, with the x-u block into Mm)
+template <class M, int N, int U, class L>
+__device__ void mstage_hess_add(const ProbS<N, U>& P, const Aug& A, int t, const double* x, const double* u,
+                                L* Pm, L* Mm, L* Rm) {
+  if constexpr (!has_user_terms<M>::value) {
+    (void)t; (void)Mm;
+    stage_hess_add(P, A, x, u, Pm, Rm);
+  } else {
+    constexpr int K = N + U, NC = user_rows<M>::value;
+    stage_hess_add(P, A, x, u, Pm, Rm, !user_cost<M>::value);
+    double H[K * K], Hg[NC > 0 ? NC * K * K : 1];
+#pragma unroll
+    for (int i = 0; i < K * K; i++) H[i] = 0.0;
+    user_hess<M>(P, t, x, u, H, Hg);
+    if constexpr (NC > 0) {
+      if (A.kind == AUG_BARRIER) {
+        double g[NC], J[NC * K];
+        user_rows_jac<M>(P, t, x, u, g, J);
+        // -mu log(-g): mu (grad g grad g^T / g^2 + Hess(g) / (-g))
+#pragma unroll
+        for (int c = 0; c < NC; c++) {
+          const double a = A.mu / (-g[c]), b = A.mu / (g[c] * g[c]);
+          for (int i = 0; i < K; i++)
+            for (int j = 0; j < K; j++) H[i * K + j] += b * J[c * K + i] * J[c * K + j] + a * Hg[(c * K + i) * K + j];
+        }
+      }
+    }
+    for (int i = 0; i < N; i++) {
+      for (int j = 0; j < N; j++) Pm[i * N + j] += L(H[i * K + j]);
+      for (int j = 0; j < U; j++) Mm[i * U + j] += L(H[i * K + N + j]);
+    }
+    for (int i = 0; i < U; i++)
+      for (int j = 0; j < U; j++) Rm[i * U + j] += L(H[(N + i) * K + N + j]);
+  }
+}
+
+template <class M, int N, int U>
+__device__ double mterminal_cost(const ProbS<N, U>& P, const double* x) {
+  if constexpr (user_cost<M>::value) return M::template terminal_l<double>(P.prm, x);
+  else return terminal_cost(P, x);
+}
+template <class M, int N, int U>
+__device__ void mterminal_grad(const ProbS<N, U>& P, const double* xT, double* g) {
+  if constexpr (user_cost<M>::value) {
+    using D = Dual<double, N>;
+    D xd[N];
+#pragma unroll
+    for (int i = 0; i < N; i++) { xd[i] = D(xT[i]); xd[i].d[i] = 1.0; }
+    const D l = M::template terminal_l<D>(P.prm, xd);
+#pragma unroll
+    for (int i = 0; i < N; i++) g[i] = l.d[i];
+  } else {
+    terminal_grad(P, xT, g);
+  }
+}
+// terminal Hessian (N x N) in L
+template <class M, int N, int U, class L>
+__device__ void mterminal_hess(const ProbS<N, U>& P, const double* xT, L* H) {
+  if constexpr (user_cost<M>::value) {
+    using D1 = Dual<double, 1>;
+    using D2 = Dual<D1, 1>;
+    for (int a = 0; a < N; a++)
+      for (int b = a; b < N; b++) {
+        D2 xd[N];
+#pragma unroll
+        for (int i = 0; i < N; i++) {
+          xd[i] = D2(D1(xT[i]));
+          xd[i].v.d[0] = (i == a) ? 1.0 : 0.0;
+          xd[i].d[0] = D1((i == b) ? 1.0 : 0.0);
+        }
+        const D2 l = M::template terminal_l<D2>(P.prm, xd);
+        H[a * N + b] = H[b * N + a] = L(l.d[0].d[0]);
+      }
+  } else {
+#pragma unroll (N <= 8 ? N * N : 4)
+    for (int i = 0; i < N * N; i++) H[i] = L(P.Qf[i] + P.Qf[(i % N) * N + i / N]);
+  }
+}
+
+// FP32 forms of the mixed modes: the built-in terms in FP32, the user terms in FP64 and
+// rounded (gradient; merit change from the nominal (x0, u0) by (dx, du))
+template <class M, int N, int U>
+__device__ void mstage_grad32(const ProbS<N, U>& P, const Aug& A, int t, const double* x, const double* u,
+                              float* lx, float* lu) {
+  if constexpr (!has_user_terms<M>::value) {
+    stage_grad32(P, A, t, x, u, lx, lu);
+  } else {
+    double gx[N], gu[U];
+    mstage_grad<M>(P, A, t, x, u, gx, gu);
+#pragma unroll
+    for (int i = 0; i < N; i++) lx[i] = float(gx[i]);
+#pragma unroll
+    for (int i = 0; i < U; i++) lu[i] = float(gu[i]);
+  }
+}
+template <class M, int N, int U>
+__device__ float mstage_delta(const ProbS<N, U>& P, const Aug& A, int t, const double* x0, const double* u0,
+                              const float* dx, const float* du, bool& infeas) {
+  if constexpr (!has_user_terms<M>::value) {
+    return stage_delta(P, A, t, x0, u0, dx, du, infeas);
+  } else {
+    double x1[N], u1[U];
+#pragma unroll
+    for (int i = 0; i < N; i++) x1[i] = x0[i] + double(dx[i]);
+#pragma unroll
+    for (int i = 0; i < U; i++) u1[i] = u0[i] + double(du[i]);
+    bool inf0 = false;
+    const double l1 = mstage_cost<M>(P, A, t, x1, u1, infeas);
+    const double l0 = mstage_cost<M>(P, A, t, x0, u0, inf0);
+    return float(l1 - l0);
+  }
+}
+template <class M, int N, int U>
+__device__ float mterminal_delta(const ProbS<N, U>& P, const double* x0, const float* dx) {
+  if constexpr (!user_cost<M>::value) {
+    return terminal_delta(P, x0, dx);
+  } else {
+    double x1[N];
+#pragma unroll
+    for (int i = 0; i < N; i++) x1[i] = x0[i] + double(dx[i]);
+    return float(mterminal_cost<M>(P, x1) - mterminal_cost<M>(P, x0));
+  }
+}
+
+// ---------------------------------------------------------------------------
 // device workspace: base pointers of the concatenated per-instance arrays
 template <class L>
 struct Work {
@@ -506,7 +812,7 @@ __device__ double costate_exact(Grp& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>
 #pragma unroll
       for (int i = 0; i < N; i++) lamT[i] = lamT_in[i];
     } else {
-      terminal_grad(P, I.xn + (size_t)I.T * N, lamT);
+      mterminal_grad<M>(P, I.xn + (size_t)I.T * N, lamT);
     }
 #pragma unroll
     for (int i = 0; i < N; i++) {
@@ -524,7 +830,7 @@ __device__ double costate_exact(Grp& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>
     for (int i = 0; i < N * N; i++) { I.F64[(size_t)t * N * N + i] = E[i]; I.E[(size_t)t * N * N + i] = L(E[i]); }
 #pragma unroll
     for (int i = 0; i < N * U; i++) { I.G64[(size_t)t * N * U + i] = G[i]; I.Gm[(size_t)t * N * U + i] = L(G[i]); }
-    stage_grad(P, A, t, x, u, q, r);
+    mstage_grad<M>(P, A, t, x, u, q, r);
     double vn[N];
     mtv<N, N>(E, agg.v, vn);  // (I + E)^T v = v + E^T v
 #pragma unroll
@@ -552,7 +858,7 @@ __device__ double costate_exact(Grp& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>
     const double* E = I.F64 + (size_t)t * N * N;
     const double* G = I.G64 + (size_t)t * N * U;
     double q[N], r[U], ln[N], dd[U];
-    stage_grad(P, A, t, x, u, q, r);
+    mstage_grad<M>(P, A, t, x, u, q, r);
     mtv<N, N>(E, lam, ln);
     mtv<N, U>(G, lam, dd);
 #pragma unroll
@@ -614,7 +920,7 @@ __device__ double costate_mixed(Grp& g, Inst<M, float>& I, const ProbS<M::NX, M:
   set_identity(agg);
   double lamT[N];
   if (I.last) {
-    terminal_grad(P, I.xn + (size_t)I.T * N, lamT);
+    mterminal_grad<M>(P, I.xn + (size_t)I.T * N, lamT);
 #pragma unroll
     for (int i = 0; i < N; i++) {
       agg.g[i] = lamT[i];
@@ -631,7 +937,7 @@ __device__ double costate_mixed(Grp& g, Inst<M, float>& I, const ProbS<M::NX, M:
     for (int i = 0; i < N * N; i++) I.E[(size_t)t * N * N + i] = E[i];
 #pragma unroll
     for (int i = 0; i < N * U; i++) I.Gm[(size_t)t * N * U + i] = G[i];
-    stage_grad32(P, A, t, x, u, q, r);
+    mstage_grad32<M>(P, A, t, x, u, q, r);
 #pragma unroll
     for (int i = 0; i < N; i++) gf[i] = float(agg.g[i]);
     mtv<N, N>(E, gf, Eg);
@@ -662,7 +968,7 @@ __device__ double costate_mixed(Grp& g, Inst<M, float>& I, const ProbS<M::NX, M:
     const float* E = I.E + (size_t)t * N * N;
     const float* G = I.Gm + (size_t)t * N * U;
     float q[N], r[U], lf[N], ln[N], dd[U];
-    stage_grad32(P, A, t, x, u, q, r);
+    mstage_grad32<M>(P, A, t, x, u, q, r);
 #pragma unroll
     for (int i = 0; i < N; i++) lf[i] = float(lam[i]);
     mtv<N, N>(E, lf, ln);
@@ -714,7 +1020,7 @@ __device__ __noinline__ double multiplier_pass(Grp& g, Inst<M, L>& I, const Prob
     for (int i = 0; i < N * N; i++) { I.F64[(size_t)t * N * N + i] = E[i]; I.E[(size_t)t * N * N + i] = L(E[i]); }
 #pragma unroll
     for (int i = 0; i < N * U; i++) { I.G64[(size_t)t * N * U + i] = G[i]; I.Gm[(size_t)t * N * U + i] = L(G[i]); }
-    stage_grad(P, A, t, x, u, lx, lu);
+    mstage_grad<M>(P, A, t, x, u, lx, lu);
 #pragma unroll
     for (int i = 0; i < N; i++) nv[i] = I.lam[(size_t)(t + 1) * N + i];
     mtv<N, N>(E, nv, Et);  // F^T nu = nu + E^T nu
@@ -742,7 +1048,7 @@ __device__ __noinline__ double multiplier_pass(Grp& g, Inst<M, L>& I, const Prob
   }
   if (I.last) {
     double gT[N];
-    terminal_grad(P, I.xn + (size_t)I.T * N, gT);
+    mterminal_grad<M>(P, I.xn + (size_t)I.T * N, gT);
 #pragma unroll
     for (int i = 0; i < N; i++) {
       const double v = gT[i] - I.lam[(size_t)I.T * N + i];
@@ -781,7 +1087,7 @@ __device__ __noinline__ double multiplier_mixed(Grp& g, Inst<M, float>& I, const
     for (int i = 0; i < N * N; i++) I.E[(size_t)t * N * N + i] = E[i];
 #pragma unroll
     for (int i = 0; i < N * U; i++) I.Gm[(size_t)t * N * U + i] = G[i];
-    stage_grad32(P, A, t, x, u, lx, lu);
+    mstage_grad32<M>(P, A, t, x, u, lx, lu);
 #pragma unroll
     for (int i = 0; i < N; i++) {
       nv[i] = I.lam[(size_t)(t + 1) * N + i];
@@ -812,7 +1118,7 @@ __device__ __noinline__ double multiplier_mixed(Grp& g, Inst<M, float>& I, const
   }
   if (I.last) {
     double gT[N];
-    terminal_grad(P, I.xn + (size_t)I.T * N, gT);
+    mterminal_grad<M>(P, I.xn + (size_t)I.T * N, gT);
 #pragma unroll
     for (int i = 0; i < N; i++) {
       const double v = gT[i] - I.lam[(size_t)I.T * N + i];
@@ -847,7 +1153,7 @@ __device__ void quadratize(Grp& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>& P, 
     const double* u = I.un + (size_t)t * U;
     L Pm[N * N], Mm[N * U], Rm[U * U];
     MOps<M>::hess(P, x, u, (t + 1 == I.b) ? I.lamb : I.lam + (size_t)(t + 1) * N, Pm, Mm, Rm);
-    stage_hess_add(P, A, x, u, Pm, Rm);
+    mstage_hess_add<M>(P, A, t, x, u, Pm, Mm, Rm);
 #pragma unroll (N <= 8 ? N * N : 4)
     for (int i = 0; i < N * N; i++) I.Pm[(size_t)t * N * N + i] = Pm[i];
 #pragma unroll
@@ -855,10 +1161,7 @@ __device__ void quadratize(Grp& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>& P, 
 #pragma unroll
     for (int i = 0; i < U * U; i++) I.Rm[(size_t)t * U * U + i] = Rm[i];
   }
-  if (I.last) {
-#pragma unroll (N <= 8 ? N * N : 4)
-    for (int i = 0; i < N * N; i++) I.Pm[(size_t)I.T * N * N + i] = L(P.Qf[i] + P.Qf[(i % N) * N + i / N]);
-  }
+  if (I.last) mterminal_hess<M>(P, I.xn + (size_t)I.T * N, I.Pm + (size_t)I.T * N * N);
 }
 
 // pass 3: value suffix scan (Alg. 2) + feedback sweep.  Returns true on success; false
@@ -1148,7 +1451,7 @@ __device__ int rollout(Grp& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>& P, cons
 #pragma unroll
           for (int i = 0; i < N; i++) I.xc[(size_t)t * N + i] = xt[i];
         }
-        cost += double(stage_delta(P, A, t, xh, uh, dxh, duf, inf));
+        cost += double(mstage_delta<M>(P, A, t, xh, uh, dxh, duf, inf));
         // increment at the FP32-rounded point plus the first-order correction for the
         // rounding residuals, so the step map stays smooth far below FP32 resolution
         MOps<M>::ijac(P, xt, ut, Ex, Gx, dv);
@@ -1179,7 +1482,7 @@ __device__ int rollout(Grp& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>& P, cons
 #pragma unroll
           for (int i = 0; i < N; i++) I.xc[(size_t)t * N + i] = xt[i];
         }
-        cost += stage_cost(P, A, t, xt, ut, inf);
+        cost += mstage_cost<M>(P, A, t, xt, ut, inf);
         double xnext[N], Fd[N * N], Gd[U * N];
 #pragma unroll
         for (int i = 0; i < U * N; i++) Gd[i] = double(Gam[i]);
@@ -1215,9 +1518,9 @@ __device__ int rollout(Grp& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>& P, cons
         float dT[N];
 #pragma unroll
         for (int i = 0; i < N; i++) dT[i] = float(xt[i] - I.xn[(size_t)I.T * N + i]);
-        cost += double(terminal_delta(P, I.xn + (size_t)I.T * N, dT));
+        cost += double(mterminal_delta<M>(P, I.xn + (size_t)I.T * N, dT));
       } else {
-        cost += terminal_cost(P, xt);
+        cost += mterminal_cost<M>(P, xt);
       }
 #pragma unroll
       for (int i = 0; i < N; i++) el.v[i] = L(0);
@@ -1275,11 +1578,11 @@ __device__ double nominal_cost(Grp& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>&
   bool inf = false;
   for (int t = I.a; t < I.b; t++) {
     double lp;
-    c += stage_cost(P, A, t, I.xn + (size_t)t * N, I.un + (size_t)t * U, inf, &lp);
+    c += mstage_cost<M>(P, A, t, I.xn + (size_t)t * N, I.un + (size_t)t * U, inf, &lp);
     cp += lp;
   }
   if (I.last) {
-    const double lt = terminal_cost(P, I.xn + (size_t)I.T * N);
+    const double lt = mterminal_cost<M>(P, I.xn + (size_t)I.T * N);
     c += lt;
     cp += lt;
   }
@@ -1545,6 +1848,12 @@ __device__ void residuals(Grp& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>& P, c
     for (int r = 0; r < P.nw; r++) {
       const double zk = P.isx[r] ? I.xn[(size_t)t * N + P.idx[r]] : I.un[(size_t)t * U + P.idx[r]];
       rf = fmax(rf, P.sgn[r] * (zk - P.bnd[r]));
+    }
+    if constexpr (user_rows<M>::value > 0) {
+      double gr[user_rows<M>::value];
+      M::template constraints<double>(t, P.prm, I.xn + (size_t)t * N, I.un + (size_t)t * U, gr);
+#pragma unroll
+      for (int c = 0; c < user_rows<M>::value; c++) rf = fmax(rf, gr[c]);
     }
   }
   double red[2] = {rd, rf};
@@ -2012,6 +2321,11 @@ __device__ int adjoint_instance(Grp& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>
   double out[KO];
 #pragma unroll
   for (int i = 0; i < KO; i++) out[i] = (i < N ? 0.0 : aa.gJ * env[i]) - adj[i];  // x0: lam_0 below
+  if constexpr (user_cost<M>::value) {
+    // a user-written cost does not depend on the weights Q, R, Qf
+#pragma unroll
+    for (int i = N; i < 3 * N + U; i++) out[i] = 0.0;
+  }
   group_sum<KO>(g, out);  // also orders the co-state writes before lam_1 is read
   if (g.rank() == 0) {
     if (seg_first)
