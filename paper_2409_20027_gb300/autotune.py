@@ -75,7 +75,10 @@ def sweep(prob, x0, Ts, precision: int, candidates=None, reps: int = 2, u_init=N
         for c in cands:
             s.set_options(**c)
             ui = None if u_init is None else u_init(T)
-            s.solve_ip(x0, T, u_init=ui)  # warm-up
+            try:
+                s.solve_ip(x0, T, u_init=ui)  # warm-up
+            except ptn.PtnError:
+                continue  # a shape this device or horizon cannot take
             torch.cuda.synchronize()
             times = []
             ok = True

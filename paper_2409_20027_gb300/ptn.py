@@ -232,9 +232,15 @@ class Solver:
         lam_out = self._out(T + 1, self.nx, x0) if lam_out is None else lam_out
         _check_solve_bufs(T, self.nx, self.nu, x0, u_init, x_out, u_out, lam_out)
         info = Info()
-        load().ptn_solve_ip(self._h, _dptr(x0), _dptr(u_init), int(T), _dptr(x_out), _dptr(u_out),
-                            _dptr(lam_out), C.byref(info), _stream(stream))
+        rc = load().ptn_solve_ip(self._h, _dptr(x0), _dptr(u_init), int(T), _dptr(x_out), _dptr(u_out),
+                                 _dptr(lam_out), C.byref(info), _stream(stream))
+        self._raise_unsolved(rc, "ptn_solve_ip")
         return x_out, u_out, lam_out, info.as_dict()
+
+    def _raise_unsolved(self, rc, name):
+        # refused before any solve ran (argument checks, CUDA errors): no report was written
+        if rc in (PTN_ERR_INVALID_ARG, PTN_ERR_CUDA):
+            raise PtnError(f"{name}: {self.last_error()} ({rc})")
 
     def solve_admm(self, x0, T: int, u_init=None, stream=None, with_zv=False):
         """ADMM solve (Sec. II-C).  Returns (x, u, lam, info) or with z, v."""
@@ -244,8 +250,9 @@ class Solver:
         z = self._out(T, max(self.nw, 1), x0) if with_zv else None
         v = self._out(T, max(self.nw, 1), x0) if with_zv else None
         info = Info()
-        load().ptn_solve_admm(self._h, _dptr(x0), _dptr(u_init), int(T), _dptr(x), _dptr(u), _dptr(lam),
-                              _dptr(z), _dptr(v), C.byref(info), _stream(stream))
+        rc = load().ptn_solve_admm(self._h, _dptr(x0), _dptr(u_init), int(T), _dptr(x), _dptr(u), _dptr(lam),
+                                   _dptr(z), _dptr(v), C.byref(info), _stream(stream))
+        self._raise_unsolved(rc, "ptn_solve_admm")
         if with_zv:
             return x, u, lam, z, v, info.as_dict()
         return x, u, lam, info.as_dict()
@@ -265,10 +272,11 @@ class Solver:
         u_out = self._out(S, self.nu, x0) if u_out is None else u_out
         lam_out = self._out(S + B, self.nx, x0) if lam_out is None else lam_out
         infos = (Info * B)()
-        load().ptn_solve_batch(self._h, int(method), B, Tb.ctypes.data_as(C.POINTER(C.c_int)),
-                               None if dtb is None else dtb.ctypes.data_as(C.POINTER(C.c_double)), _dptr(x0),
-                               _dptr(xref), _dptr(u_init), _dptr(x_out), _dptr(u_out), _dptr(lam_out), infos,
-                               _stream(stream))
+        rc = load().ptn_solve_batch(self._h, int(method), B, Tb.ctypes.data_as(C.POINTER(C.c_int)),
+                                    None if dtb is None else dtb.ctypes.data_as(C.POINTER(C.c_double)), _dptr(x0),
+                                    _dptr(xref), _dptr(u_init), _dptr(x_out), _dptr(u_out), _dptr(lam_out), infos,
+                                    _stream(stream))
+        self._raise_unsolved(rc, "ptn_solve_batch")
         return x_out, u_out, lam_out, [i.as_dict() for i in infos]
 
     def prepare_batch(self, T_b, method: int = METHOD_IP, dt_b=None, stream=None):
