@@ -327,6 +327,19 @@ int ptn_solve_ip_static(const ptn_problem* prob, const ptn_options* opt, const d
 /* Library version string. */
 const char* ptn_version(void);
 
+/* Self-check of the arithmetic routines the kernels' FP64 solves use in place of a
+ * division and of the FP32 <-> FP64 conversion instructions (no counterpart in the paper;
+ * for tests).  For i < n: rcp_out[i] = the pivot reciprocal of p[i] (0 where p[i] counts
+ * as a singular pivot: zero, not finite, or a binary exponent outside [-1000, 1000]),
+ * f2d_out[i] = f[i] widened to FP64, d2f_out[i] = d[i] rounded to FP32 (nearest even),
+ * each by the device routine the solver uses.  All pointers are device pointers to n
+ * elements owned by the caller; an input and its output may both be NULL to skip that
+ * routine.  Enqueued on `stream` (NULL: the legacy default stream); returns PTN_OK,
+ * PTN_ERR_INVALID_ARG for n < 0 or an output without its input, or PTN_ERR_CUDA when the
+ * launch fails. */
+int ptn_arith_check(int n, const double* p, double* rcp_out, const float* f, double* f2d_out,
+                    const double* d, float* d2f_out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -194,6 +194,25 @@ extern "C" void ptn_default_options(ptn_options* o) {
 
 extern "C" const char* ptn_version(void) { return "ptn 0.1 (sm_103a)"; }
 
+// the solves' pivot reciprocal and conversions, element by element (ptn_arith_check)
+__global__ void k_arith_check(int n, const double* p, double* rcp_out, const float* f, double* f2d_out,
+                              const double* d, float* d2f_out) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    if (p) rcp_out[i] = ptn::pivot_ok(p[i]) ? ptn::pivot_rcp(p[i]) : 0.0;
+    if (f) f2d_out[i] = ptn::f32_to_f64(f[i]);
+    if (d) d2f_out[i] = ptn::f64_to_f32(d[i]);
+  }
+}
+
+extern "C" int ptn_arith_check(int n, const double* p, double* rcp_out, const float* f, double* f2d_out,
+                               const double* d, float* d2f_out, void* stream) {
+  if (n < 0 || (p && !rcp_out) || (f && !f2d_out) || (d && !d2f_out)) return PTN_ERR_INVALID_ARG;
+  if (n == 0) return PTN_OK;
+  const int blocks = (n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024;
+  k_arith_check<<<blocks, 256, 0, (cudaStream_t)stream>>>(n, p, rcp_out, f, f2d_out, d, d2f_out);
+  return cudaGetLastError() == cudaSuccess ? PTN_OK : PTN_ERR_CUDA;
+}
+
 extern "C" const char* ptn_last_error(const ptn_solver* s) { return s ? s->err : ""; }
 
 extern "C" int ptn_num_rows(const ptn_solver* s) { return s ? s->nw : 0; }

@@ -211,6 +211,86 @@ PTN_HD void mtv(const T1* A, const S* x, S* y) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// FP64 helpers for the solves of the mixed modes.  On this GPU every FP64 warp instruction
+// (DFMA, conversions to and from FP32 included) occupies the SM sub-partition's FP64 pipe
+// for about 64 cycles, whatever the number of active lanes, and a correctly rounded FP64
+// division takes about nine of them.  The solves of I + C1 J2 and of the U x U blocks are
+// on the scans' critical paths, so their pivots and conversions avoid that pipe where
+// plain arithmetic allows.
+
+// Pivot test and reciprocal.  Device FP64: pivots with a binary exponent outside
+// [-1000, 1000] count as singular (as zero or non-finite pivots do everywhere), and the
+// reciprocal is the hardware's approximation (rcp.approx.ftz.f64) refined by two steps of
+// Newton's iteration for f(r) = 1/r - p, r <- r + r (1 - p r), each of which squares the
+// relative error; the result is within one unit in the last place of 1/p.  Elsewhere
+// (FP32, host code): the division.
+template <class S>
+PTN_HD bool pivot_ok(S p) {
+#ifdef __CUDA_ARCH__
+  if constexpr (std::is_same<S, double>::value) {
+    const unsigned e = (unsigned)((unsigned long long)__double_as_longlong(p) >> 52) & 0x7ffu;
+    return e >= 1023u - 1000u && e <= 1023u + 1000u;
+  }
+#endif
+  return (p != S(0)) && isfinite(p);
+}
+template <class S>
+PTN_HD S pivot_rcp(S p) {
+#ifdef __CUDA_ARCH__
+  if constexpr (std::is_same<S, double>::value) {
+    double r;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(p));
+    double e = fma(-p, r, 1.0);
+    r = fma(r, e, r);
+    e = fma(-p, r, 1.0);
+    return fma(r, e, r);
+  }
+#endif
+  return S(1) / p;
+}
+
+// FP32 <-> FP64 conversions by integer operations on the IEEE-754 fields (device code,
+// off the FP64 pipe).  Exact for zeros, normal numbers and infinities; NaNs stay NaNs.
+// Round to nearest even from FP64, as the conversion instruction; FP32 subnormals (below
+// 2^-126 in magnitude) become signed zeros in both directions.  Host code converts
+// natively.
+PTN_HD double f32_to_f64(float f) {
+#ifdef __CUDA_ARCH__
+  const unsigned u = __float_as_uint(f);
+  const unsigned sg = u & 0x80000000u, e = (u >> 23) & 0xffu, m = u & 0x7fffffu;
+  unsigned hi = sg | ((e + 896u) << 20) | (m >> 3), lo = m << 29;
+  if (e == 0u) { hi = sg; lo = 0u; }
+  if (e == 255u) hi = sg | 0x7ff00000u | (m >> 3) | (m != 0u ? 0x80000u : 0u);
+  return __hiloint2double((int)hi, (int)lo);
+#else
+  return double(f);
+#endif
+}
+PTN_HD float f64_to_f32(double d) {
+#ifdef __CUDA_ARCH__
+  const unsigned hi = (unsigned)__double2hiint(d), lo = (unsigned)__double2loint(d);
+  const unsigned sg = hi & 0x80000000u, ef = (hi >> 20) & 0x7ffu;
+  const unsigned mant = ((hi & 0xfffffu) << 3) | (lo >> 29), rest = lo & 0x1fffffffu;
+  const unsigned up = (rest > 0x10000000u || (rest == 0x10000000u && (mant & 1u))) ? 1u : 0u;
+  const int e = (int)ef - 896;
+  unsigned r = ((unsigned)e << 23) + mant + up;  // a carry out of the mantissa bumps e
+  if (e <= 0) r = 0u;
+  else if (e >= 255 || r >= 0x7f800000u) r = 0x7f800000u;
+  if (ef == 0x7ffu) r = (mant | (hi & 0xfffffu) | lo) != 0u ? 0x7fc00000u : 0x7f800000u;
+  return __uint_as_float(sg | r);
+#else
+  return float(d);
+#endif
+}
+// L <-> SV conversions of the solves: the integer forms for FP32 <-> FP64
+template <class To, class From>
+PTN_HD To cvt_solve(From x) {
+  if constexpr (std::is_same<From, float>::value && std::is_same<To, double>::value) return f32_to_f64(x);
+  else if constexpr (std::is_same<From, double>::value && std::is_same<To, float>::value) return f64_to_f32(x);
+  else return To(x);
+}
+
 // In-place Cholesky A = L L^T (lower triangle written, upper untouched).
 // Returns false when A is not positive definite.
 template <int N, class S = double>
@@ -267,8 +347,8 @@ PTN_HD bool ldlt(S* A) {
     S dj = A[j * N + j];
 #pragma unroll
     for (int k = 0; k < j; k++) dj -= A[j * N + k] * A[j * N + k] * D[k];
-    if (!(dj > S(0)) || !isfinite(dj)) return false;
-    const S id = S(1) / dj;
+    if (!(dj > S(0)) || !pivot_ok(dj)) return false;
+    const S id = pivot_rcp(dj);
     D[j] = dj;
     A[j * N + j] = id;
 #pragma unroll
@@ -356,8 +436,8 @@ PTN_HD bool inv_gj(S* A) {
       }
     }
     const S pv = A[k * N + k];
-    if (!(pv != S(0)) || !isfinite(pv)) return false;
-    S ip = S(1) / pv;
+    if (!pivot_ok(pv)) return false;
+    const S ip = pivot_rcp(pv);
     A[k * N + k] = S(1);
 #pragma unroll (N <= 8 ? N : 4)
     for (int j = 0; j < N; j++) A[k * N + j] *= ip;
@@ -370,12 +450,28 @@ PTN_HD bool inv_gj(S* A) {
       for (int j = 0; j < N; j++) A[i * N + j] -= f * A[k * N + j];
     }
   }
-  // undo the row permutation as a column permutation of the inverse
-  S tmp[N];
-#pragma unroll (N <= 8 ? N : 1)
-  for (int i = 0; i < N; i++) {
-    for (int j = 0; j < N; j++) tmp[piv[j]] = A[i * N + j];
-    for (int j = 0; j < N; j++) A[i * N + j] = tmp[j];
+  // undo the row permutation as a column permutation of the inverse (column piv[j] of
+  // the result is column j; selects with static indices keep A in registers)
+  if constexpr (N <= 8) {
+    S tmp[N * N];
+#pragma unroll
+    for (int i = 0; i < N; i++)
+#pragma unroll
+      for (int c = 0; c < N; c++) {
+        S v = S(0);
+#pragma unroll
+        for (int j = 0; j < N; j++)
+          if (piv[j] == c) v = A[i * N + j];
+        tmp[i * N + c] = v;
+      }
+#pragma unroll
+    for (int i = 0; i < N * N; i++) A[i] = tmp[i];
+  } else {
+    S tmp[N];
+    for (int i = 0; i < N; i++) {
+      for (int j = 0; j < N; j++) tmp[piv[j]] = A[i * N + j];
+      for (int j = 0; j < N; j++) A[i * N + j] = tmp[j];
+    }
   }
   return true;
 }

@@ -94,9 +94,9 @@ __device__ bool inv_gj_rows(S (&row)[N]) {
 #pragma unroll
     for (int j = 0; j < N; j++) pk[j] = __shfl_sync(PTN_FULL, row[j], base + k);
     const S pv = pk[k];
-    const bool good = (pv != S(0)) && isfinite(pv);
+    const bool good = pivot_ok(pv);
     ok &= good;
-    const S ip = good ? S(1) / pv : S(0);
+    const S ip = good ? pivot_rcp(pv) : S(0);
     pk[k] = S(1);
 #pragma unroll
     for (int j = 0; j < N; j++) pk[j] *= ip;
@@ -140,12 +140,12 @@ __device__ bool value_combine_rows(const Val<N, L>& e1, const Val<N, L>& e2, Val
 #pragma unroll
     for (int i = 0; i < N; i++)
       if (i == r) v = Ml[i * N + j];
-    row[j] = SV(v) + (r == j ? SV(1) : SV(0));
+    row[j] = cvt_solve<SV>(v) + (r == j ? SV(1) : SV(0));
   }
   const bool ok = inv_gj_rows<N, G, SV>(row);
   L rl[N], K[N * N];
 #pragma unroll
-  for (int j = 0; j < N; j++) rl[j] = L(row[j]);
+  for (int j = 0; j < N; j++) rl[j] = cvt_solve<L>(row[j]);
 #pragma unroll
   for (int i = 0; i < N; i++)
 #pragma unroll
@@ -203,11 +203,13 @@ __device__ void block_fold_groups(const Op& op, bool& ok, int lo, int hi, const 
   const int cnt = hi - lo;
   const int used = cnt < ngr ? cnt : ngr;
   const int per = (cnt + ngr - 1) / ngr;
+  // the group's first element starts its fold; the rest are combined into it
   E acc;
-  set_identity(acc);
-  bool have = false;
+  bool have = lo + gi * per < hi && gi < used;
+  if (have) load(lo + gi * per, acc);
+  else set_identity(acc);
 #pragma unroll 1
-  for (int k = 0; k < per; k++) {  // the same trip count in every lane
+  for (int k = 1; k < per; k++) {  // the same trip count in every lane
     const int b = lo + gi * per + k;
     const bool valid = b < hi && gi < used;
     E t;
@@ -215,11 +217,7 @@ __device__ void block_fold_groups(const Op& op, bool& ok, int lo, int hi, const 
     else set_identity(t);
     E res;
     const bool okc = GO::run(op, acc, t, res);
-    if (valid) {
-      if (have) { acc = res; ok &= okc; }
-      else acc = t;
-      have = true;
-    }
+    if (valid) { acc = res; ok &= okc; }
   }
   if (lead && gi < ngr) {
     tree[gi] = acc;

@@ -143,13 +143,13 @@ struct ValueOp {
     mm<N, N, N>(e1.C, e2.J, Ml);
     SV Md[N * N];
 #pragma unroll
-    for (int i = 0; i < N * N; i++) Md[i] = SV(Ml[i]);
+    for (int i = 0; i < N * N; i++) Md[i] = cvt_solve<SV>(Ml[i]);
 #pragma unroll
     for (int i = 0; i < N; i++) Md[i * N + i] += SV(1);
     if (!inv_gj<N, SV>(Md)) return false;
     L K[N * N];
 #pragma unroll
-    for (int i = 0; i < N * N; i++) K[i] = L(Md[i]);
+    for (int i = 0; i < N * N; i++) K[i] = cvt_solve<L>(Md[i]);
     value_apply_K<N, L>(e1, e2, K, o);
     return true;
   }

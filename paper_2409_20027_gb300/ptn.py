@@ -26,7 +26,8 @@ STATUS = {0: "ok", -1: "invalid argument", -2: "infeasible start", -3: "not conv
 EXPORTS = ["ptn_default_options", "ptn_solver_create", "ptn_solver_destroy", "ptn_last_error",
            "ptn_set_options", "ptn_solve_ip", "ptn_solve_admm", "ptn_solve_batch", "ptn_adjoint",
            "ptn_num_rows", "ptn_version", "ptn_solve_ip_static", "ptn_batch_prepare",
-           "ptn_solve_batch_async", "ptn_model_dims", "ptn_adjoint_checkpointed", "ptn_set_reference"]
+           "ptn_solve_batch_async", "ptn_model_dims", "ptn_adjoint_checkpointed", "ptn_set_reference",
+           "ptn_arith_check"]
 
 _P = C.POINTER(C.c_double)
 
@@ -104,6 +105,7 @@ def load(path: str = LIB_PATH):
         lib.ptn_batch_prepare.argtypes = [vp, C.c_int, C.c_int, ip, C.POINTER(C.c_double), vp]
         lib.ptn_solve_batch_async.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp]
         lib.ptn_model_dims.argtypes = [C.c_int, ip, ip]
+        lib.ptn_arith_check.argtypes = [C.c_int, vp, vp, vp, vp, vp, vp, vp]
         lib.ptn_version.restype = C.c_char_p
         _lib = lib
     return _lib
@@ -365,6 +367,28 @@ def model_dims(model: int):
     nx, nu = C.c_int(), C.c_int()
     rc = load().ptn_model_dims(int(model), C.byref(nx), C.byref(nu))
     return (nx.value, nu.value) if rc == 0 else None
+
+
+def arith_check(p=None, f=None, d=None, stream=None):
+    """ptn_arith_check: the kernels' pivot reciprocal of p (FP64), FP32 -> FP64 widening of
+    f and FP64 -> FP32 rounding of d, each a 1-D contiguous CUDA tensor (or None).  Returns
+    (rcp, f2d, d2f), None where the input was None; synchronises the stream."""
+    import torch
+    ns = {len(t) for t in (p, f, d) if t is not None}
+    if len(ns) != 1:
+        raise ValueError("give at least one input; all inputs have the same length")
+    n = ns.pop()
+    for t, dt, name in ((p, torch.float64, "p"), (f, torch.float32, "f"), (d, torch.float64, "d")):
+        if t is not None and (not t.is_cuda or t.dtype != dt or not t.is_contiguous() or t.dim() != 1):
+            raise ValueError(f"{name}: a 1-D contiguous CUDA {dt} tensor")
+    out = lambda t, dt: None if t is None else torch.empty(n, dtype=dt, device=t.device)
+    rcp, f2d, d2f = out(p, torch.float64), out(f, torch.float64), out(d, torch.float32)
+    ptr = lambda t: None if t is None else C.c_void_p(t.data_ptr())
+    rc = load().ptn_arith_check(n, ptr(p), ptr(rcp), ptr(f), ptr(f2d), ptr(d), ptr(d2f), _stream(stream))
+    if rc != 0:
+        raise PtnError(f"ptn_arith_check failed ({rc})")
+    torch.cuda.current_stream().synchronize() if stream is None else stream.synchronize()
+    return rcp, f2d, d2f
 
 
 def infos_from_device(info_dev, B: int):
