@@ -1483,14 +1483,28 @@ __device__ int rollout(Grp& g, Inst<M, L>& I, const ProbS<M::NX, M::NU>& P, cons
           for (int i = 0; i < N; i++) I.xc[(size_t)t * N + i] = xt[i];
         }
         cost += mstage_cost<M>(P, A, t, xt, ut, inf);
-        double xnext[N], Fd[N * N], Gd[U * N];
-#pragma unroll
-        for (int i = 0; i < U * N; i++) Gd[i] = double(Gam[i]);
-        // FP64 Jacobian: quadratic convergence of the shooting Newton, so the rollout
-        // reaches the FP64 dynamics to rounding and FP64 merits stay noise-free
+        double xnext[N];
+        // FP64 states and merits: the rollout reaches the FP64 dynamics to rounding and
+        // FP64 merits stay noise-free.  The chunk Jacobian only steers the shooting Newton
+        // and is stored in L: with L = FP32 it comes from FP32 forward-mode AD at the FP64
+        // point (I + E + G Gam, E and G as the FP32-increment passes form them), which has
+        // the same absolute accuracy as the FP64 AD Jacobian rounded to FP32 at a fraction
+        // of the FP64 instructions; with L = FP64 from FP64 AD.
         if (first) {
           MOps<M>::f(P, xt, ut, xnext);  // the first chunk's map is constant: no Jacobian
+        } else if constexpr (std::is_same<L, float>::value) {
+          float Ex[N * N], Gx[N * U];
+          MOps<M>::ijac(P, xt, ut, Ex, Gx);
+          mm<N, U, N>(Gx, Gam, Fc);
+#pragma unroll (N <= 8 ? N * N : 4)
+          for (int i = 0; i < N * N; i++) Fc[i] += Ex[i];
+#pragma unroll
+          for (int i = 0; i < N; i++) Fc[i * N + i] += 1.0f;
+          MOps<M>::f(P, xt, ut, xnext);
         } else {
+          double Fd[N * N], Gd[U * N];
+#pragma unroll
+          for (int i = 0; i < U * N; i++) Gd[i] = double(Gam[i]);
           MOps<M>::cl(P, xt, ut, Gd, xnext, Fd);
 #pragma unroll (N <= 8 ? N * N : 4)
           for (int i = 0; i < N * N; i++) Fc[i] = L(Fd[i]);
