@@ -46,7 +46,7 @@ def algorithmic_flops(n, m, T, info):
 # DRAM bytes (read + write) of one k_solve_grid launch of this workload (seed 0), from the
 # ncu launch list summarised in profiles/k_solve_grid_cartpole_T16384.md (mean of the
 # three launches after the first)
-TRAFFIC_BYTES = ((3.140864 + 2.888960) + (2.983936 + 2.834432) + (2.950656 + 2.884864)) / 3 * 1e6
+TRAFFIC_BYTES = ((3.645440 + 2.659584) + (3.320576 + 2.477824) + (3.235584 + 2.478336)) / 3 * 1e6
 
 
 def flop_split(n, m, T, info):
