@@ -251,25 +251,20 @@ PTN_HD S pivot_rcp(S p) {
 }
 
 // FP32 <-> FP64 conversions by integer operations on the IEEE-754 fields (device code,
-// off the FP64 pipe).  Exact for zeros, normal numbers and infinities; NaNs stay NaNs.
-// Round to nearest even from FP64, as the conversion instruction; FP32 subnormals (below
-// 2^-126 in magnitude) become signed zeros in both directions.  Host code converts
-// natively.
-PTN_HD double f32_to_f64(float f) {
-#ifdef __CUDA_ARCH__
-  const unsigned u = __float_as_uint(f);
+// off the FP64 pipe).  Exact for zeros, normal numbers and infinities; a NaN stays a NaN
+// (FP32 -> FP64: payload kept and quieted; FP64 -> FP32: the canonical quiet NaN).  Round
+// to nearest even from FP64, as the conversion instruction; FP32 subnormals (below 2^-126
+// in magnitude) become signed zeros in both directions.  The bit-field functions are the
+// same on host and device (checked over every FP32 bit pattern on the host); host code
+// converts natively.
+PTN_HD void f32_bits_to_f64_bits(unsigned u, unsigned& hi, unsigned& lo) {
   const unsigned sg = u & 0x80000000u, e = (u >> 23) & 0xffu, m = u & 0x7fffffu;
-  unsigned hi = sg | ((e + 896u) << 20) | (m >> 3), lo = m << 29;
+  hi = sg | ((e + 896u) << 20) | (m >> 3);
+  lo = m << 29;
   if (e == 0u) { hi = sg; lo = 0u; }
   if (e == 255u) hi = sg | 0x7ff00000u | (m >> 3) | (m != 0u ? 0x80000u : 0u);
-  return __hiloint2double((int)hi, (int)lo);
-#else
-  return double(f);
-#endif
 }
-PTN_HD float f64_to_f32(double d) {
-#ifdef __CUDA_ARCH__
-  const unsigned hi = (unsigned)__double2hiint(d), lo = (unsigned)__double2loint(d);
+PTN_HD unsigned f64_bits_to_f32_bits(unsigned hi, unsigned lo) {
   const unsigned sg = hi & 0x80000000u, ef = (hi >> 20) & 0x7ffu;
   const unsigned mant = ((hi & 0xfffffu) << 3) | (lo >> 29), rest = lo & 0x1fffffffu;
   const unsigned up = (rest > 0x10000000u || (rest == 0x10000000u && (mant & 1u))) ? 1u : 0u;
@@ -277,8 +272,21 @@ PTN_HD float f64_to_f32(double d) {
   unsigned r = ((unsigned)e << 23) + mant + up;  // a carry out of the mantissa bumps e
   if (e <= 0) r = 0u;
   else if (e >= 255 || r >= 0x7f800000u) r = 0x7f800000u;
-  if (ef == 0x7ffu) r = (mant | (hi & 0xfffffu) | lo) != 0u ? 0x7fc00000u : 0x7f800000u;
-  return __uint_as_float(sg | r);
+  if (ef == 0x7ffu) r = ((hi & 0xfffffu) | lo) != 0u ? 0x7fc00000u : 0x7f800000u;
+  return sg | r;
+}
+PTN_HD double f32_to_f64(float f) {
+#ifdef __CUDA_ARCH__
+  unsigned hi, lo;
+  f32_bits_to_f64_bits(__float_as_uint(f), hi, lo);
+  return __hiloint2double((int)hi, (int)lo);
+#else
+  return double(f);
+#endif
+}
+PTN_HD float f64_to_f32(double d) {
+#ifdef __CUDA_ARCH__
+  return __uint_as_float(f64_bits_to_f32_bits((unsigned)__double2hiint(d), (unsigned)__double2loint(d)));
 #else
   return float(d);
 #endif

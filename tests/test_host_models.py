@@ -26,6 +26,8 @@ CSRC = os.path.join(ROOT, "paper_2409_20027_gb300", "csrc")
 EXE = os.path.join(ROOT, "paper_2409_20027_gb300", "_build", "host_models")
 EXE_OPS = os.path.join(ROOT, "paper_2409_20027_gb300", "_build", "host_ops")
 EXE_SYN = os.path.join(ROOT, "paper_2409_20027_gb300", "_build", "host_synth")
+SRC_ARITH = os.path.join(ROOT, "tests", "host_models", "ptn_host_arith.cu")
+EXE_ARITH = os.path.join(ROOT, "paper_2409_20027_gb300", "_build", "host_arith")
 
 
 def _harness(src=SRC, exe=EXE):
@@ -338,3 +340,17 @@ def test_mixed_costate_operator_matches_the_oracle_combine():
         v = np.array([float(t) for t in o.split()])
         assert np.abs(v[:4] - g).max() <= 1e-6 * max(1.0, float(np.abs(g).max()))
         assert np.abs(v[4:] - D.ravel()).max() <= 1e-6 * max(1e-3, float(np.abs(D).max()))
+
+
+def test_solve_conversions_match_ieee_on_every_fp32_pattern():
+    """The integer FP32 -> FP64 widening of the FP64 solves equals the host's conversion on
+    all 2^32 bit patterns (FP32 subnormals become signed zeros; NaNs keep their payload,
+    quieted), and the FP64 -> FP32 rounding equals the host's round-to-nearest-even on
+    random doubles, exact ties and their neighbours and the overflow threshold."""
+    exe = _harness(SRC_ARITH, EXE_ARITH)
+    r = subprocess.run([exe, "F"], capture_output=True, text=True, check=True, timeout=600)
+    bad, n = (int(t) for t in r.stdout.split())
+    assert n == 2 ** 32 and bad == 0, r.stderr
+    r = subprocess.run([exe, "D", "4000000", "7"], capture_output=True, text=True, check=True, timeout=600)
+    bad, n = (int(t) for t in r.stdout.split())
+    assert n > 4000000 and bad == 0, r.stderr
