@@ -67,7 +67,8 @@ def test_f64_to_f32_round_to_nearest_even():
     half = np.spacing(np.abs(fl)).astype(np.float64) / 2.0
     ties = fl.astype(np.float64) + half
     fmax = float(np.finfo(np.float32).max)
-    special = np.array([0.0, -0.0, np.inf, -np.inf, np.nan, 1e39, -1e39, fmax, fmax + np.spacing(np.float32(fmax)) / 2,
+    # fmax + 2^103 is the tie between FLT_MAX and 2^128: it rounds to inf
+    special = np.array([0.0, -0.0, np.inf, -np.inf, np.nan, 1e39, -1e39, fmax, fmax + 2.0 ** 103,
                         fmax * (1 + 2 ** -30), 1e-40, -1e-42, 2.0 ** -126, 2.0 ** -126 * (1 - 2 ** -30), 1e300, 1e-300])
     d = np.concatenate([d, ties, np.nextafter(ties, np.inf), np.nextafter(ties, -np.inf), special])
     _, _, d2f = ptn.arith_check(d=torch.tensor(d, device="cuda:0"))
